@@ -1,0 +1,163 @@
+/*
+ * btrt.h -- C ABI of the GB300 (sm_103a) block triple-relaxation-time (B-TriRT)
+ * lattice Boltzmann solver for nonlinear anisotropic convection-diffusion
+ * equations on the D2Q9 lattice.
+ *
+ * The equation solved is
+ *     d_t phi + div B(phi) = div( A(phi) grad C(phi) ) + S(x, t)            (Eq. 1, Eq. 29)
+ * with B(phi) = u phi + b2 (phi^2/2)(1,1), C(phi) = phi + c3 phi^3 (the paper's
+ * D = C I), A(phi) = (1 + a2 phi^2) A0, and S = 0, a constant, or a separable
+ * trigonometric field exp(lam t) sum_pq alpha_pq X_p(k x) Y_q(k y).
+ *
+ * One time step is one fused sweep (stream + collide, Eq. 38 with Eq. 6):
+ * pull the nine populations, take phi, evaluate B, C, A, build the first-order
+ * relaxation block K1 = (A / (cs^2 dt) + I/2)^{-1} from Eq. 30, take k2 from
+ * Eq. 62, relax the three blocks (Eqs. 94-95, 99), add the convective correction
+ * (Eq. 11) and the source (Eq. 8, scheme 2 of Remark III), write back, and apply
+ * half-way bounce-back Dirichlet walls (Eqs. 54-56).
+ *
+ * Conventions
+ *  - All inputs are physical; the library converts to lattice units internally.
+ *  - Nodes are cell centred: x_i = x0 + (i + 1/2) dx, y_j = y0 + (j + 1/2) dx.
+ *  - Arrays of nodes are row major [ny][nx] (x fastest).
+ *  - Velocity order: c0 = (0,0), c1 = (1,0), c2 = (0,1), c3 = (-1,0), c4 = (0,-1),
+ *    c5 = (1,1), c6 = (-1,1), c7 = (-1,-1), c8 = (1,-1) (rows of Eq. 85).
+ *  - Every function returns a btrt_status; on failure btrt_last_error() returns a
+ *    thread-local message.  No function aborts, throws or traps; device-side
+ *    problems are reported through flags that the host reads.
+ *  - Device memory is owned by the caller: btrt_create borrows a workspace of
+ *    btrt_workspace_bytes() bytes and never frees it.  The library itself never
+ *    allocates device memory.
+ *  - All work is enqueued on the CUDA stream given at creation (0 = legacy
+ *    default stream); functions that return host values synchronise that stream.
+ */
+#ifndef BTRT_H
+#define BTRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    BTRT_OK = 0,
+    BTRT_EINVAL = -1,     /* invalid argument or unstable parameter set */
+    BTRT_ENOMEM = -2,     /* workspace or host buffer too small           */
+    BTRT_ECUDA = -3,      /* a CUDA runtime call failed                   */
+    BTRT_EUNSTABLE = -4,  /* non-finite phi detected on the device        */
+    BTRT_ETIMEOUT = -5,   /* a bounded device wait gave up                */
+    BTRT_ESTATE = -6      /* call out of order (e.g. step before init)    */
+} btrt_status;
+
+enum { BTRT_BC_PERIODIC = 0, BTRT_BC_HBB = 1 };                 /* boundary kinds     */
+enum { BTRT_F64 = 0, BTRT_F32 = 1, BTRT_F16 = 2, BTRT_BF16 = 3 };/* number formats     */
+enum { BTRT_K2_HBB = 0, BTRT_K2_CONST = 1 };                    /* second-order block */
+enum { BTRT_SRC_NONE = 0, BTRT_SRC_CONST = 1, BTRT_SRC_TRIG = 2 };
+enum { BTRT_SIDE_XMIN = 0, BTRT_SIDE_XMAX = 1, BTRT_SIDE_YMIN = 2, BTRT_SIDE_YMAX = 3 };
+
+typedef struct btrt_lattice_s *btrt_lattice;
+
+/* Grid, number formats and the shift of reduced-precision storage. */
+typedef struct {
+    int32_t nx, ny;        /* nodes; 3 <= nx, ny <= 65536                               */
+    int32_t bc[4];         /* BTRT_BC_* for sides x-, x+, y-, y+; opposite sides match  */
+    int32_t compute;       /* BTRT_F64 or BTRT_F32: arithmetic of the sweep             */
+    int32_t storage;       /* population storage: F64 (compute F64 only), F32, F16, BF16*/
+    double dx, dt;         /* physical spacing and time step (c = dx/dt, cs^2 = c^2/3)  */
+    double x0, y0;         /* physical position of the lower-left domain corner         */
+    double phi_ref;        /* populations are stored as f_i - w_i phi_ref                */
+} btrt_grid_desc;
+
+/* Coefficients of Eq. 1 and the relaxation parameters (physical units). */
+typedef struct {
+    double u[2];           /* B(phi) = u phi + b2 (phi^2/2)(1,1)                 */
+    double b2;
+    double c3;             /* C(phi) = phi + c3 phi^3                             */
+    double A0[3];          /* A(phi) = (1 + a2 phi^2) A0; A0 = {xx, xy, yy}, SPD  */
+    double a2;
+    double k0;             /* relaxation of the remaining moments, in (0, 2)      */
+    int32_t k2_mode;       /* BTRT_K2_HBB: Eq. 62 at k1_eff = 2/tr(K1^-1); CONST   */
+    int32_t src_kind;      /* BTRT_SRC_*                                          */
+    double k2;             /* used when k2_mode == BTRT_K2_CONST, in (0, 2)       */
+    double src_const;      /* BTRT_SRC_CONST: S = src_const                       */
+    double src_lam, src_k; /* BTRT_SRC_TRIG: S = exp(lam t) sum alpha_pq X_p Y_q  */
+    double src_alpha[4];   /*   {ss, sc, cs, cc}: X_s = sin(k x), X_c = cos(k x)  */
+    double wall_lam;       /* wall values carry the factor exp(wall_lam t)        */
+} btrt_coeffs;
+
+/* Bytes of device workspace a lattice with this description needs.  Returns 0
+ * for an invalid description (see btrt_last_error). */
+size_t btrt_workspace_bytes(const btrt_grid_desc *g);
+
+/* Create a lattice in the caller's workspace (device pointer, >= 256-byte
+ * aligned, btrt_workspace_bytes(g) bytes).  cuda_stream is a cudaStream_t (may
+ * be NULL for the default stream).  The workspace stays owned by the caller and
+ * must outlive the lattice. */
+btrt_status btrt_create(const btrt_grid_desc *g, void *dev_workspace, size_t workspace_bytes,
+                        void *cuda_stream, btrt_lattice *out);
+
+/* Set the coefficients (Eq. 1), k0 and the k2 rule.  Checks that A0 is SPD, k0
+ * and k2 are in (0, 2) and that the first-order block is stable at phi = 0;
+ * otherwise BTRT_EINVAL.  May be called again between steps. */
+btrt_status btrt_set_coeffs(btrt_lattice L, const btrt_coeffs *c);
+
+/* Dirichlet value phi_w of a bounce-back side (Eqs. 54-56).  n == 1: one value
+ * for the whole side; n == side length (nx for y sides, ny for x sides): one
+ * value per boundary node, read from host memory and copied.  The value used at
+ * a step is phi_w * exp(wall_lam * t_{n+1}). */
+btrt_status btrt_set_boundary(btrt_lattice L, int32_t side, const double *phi_w_host, int32_t n);
+
+/* Initial state f_i = f_i^eq(phi0) at time t0 (Sec. 4).  phi0: nx*ny values of
+ * dtype BTRT_F64 or BTRT_F32, in host memory (on_device = 0) or device memory
+ * (on_device = 1), row major without padding.  The first collision (at t0) is
+ * performed here; afterwards the lattice is at step 0. */
+btrt_status btrt_init_phi(btrt_lattice L, const void *phi0, int32_t dtype, int32_t on_device,
+                          double t0);
+
+/* Advance nsteps time steps (asynchronous on the lattice's stream). */
+btrt_status btrt_step(btrt_lattice L, int64_t nsteps);
+
+/* Copy phi (nx*ny values, dtype F64 or F32) to host (on_device = 0, synchronises)
+ * or device memory (on_device = 1, asynchronous). */
+btrt_status btrt_read_phi(btrt_lattice L, void *dst, int32_t dtype, int32_t on_device);
+
+/* Copy the current post-collision populations of a window [x0, x0+w) x [y0, y0+h)
+ * to host memory as FP64, layout [9][h][w] (undone storage shift).  Synchronises. */
+btrt_status btrt_read_f(btrt_lattice L, double *dst_host, int32_t x0, int32_t y0, int32_t w,
+                        int32_t h);
+
+/* Sum of phi over all nodes, in FP64 with a fixed reduction order (deterministic).
+ * Synchronises. */
+btrt_status btrt_mass(btrt_lattice L, double *out);
+
+/* Non-finite flag raised by the sweep since the last btrt_init_phi: *flags = 1
+ * if any node produced a NaN/Inf phi.  Synchronises; returns BTRT_EUNSTABLE
+ * when the flag is set. */
+btrt_status btrt_check(btrt_lattice L, int32_t *flags);
+
+/* Number of completed steps and the current time t0 + n dt. */
+btrt_status btrt_get_time(btrt_lattice L, int64_t *step, double *t);
+
+/* Checkpoint: bytes needed, save the full state (populations, phi, step) to
+ * host memory, load it back.  A resumed run is bitwise equal to an
+ * uninterrupted one.  Synchronises. */
+size_t btrt_state_bytes(btrt_lattice L);
+btrt_status btrt_save(btrt_lattice L, void *host_buf, size_t n);
+btrt_status btrt_load(btrt_lattice L, const void *host_buf, size_t n);
+
+/* Release the host-side handle (the workspace stays with the caller). */
+btrt_status btrt_destroy(btrt_lattice L);
+
+/* Thread-local description of the last error ("" if none). */
+const char *btrt_last_error(void);
+
+/* Library build identification (architecture, version). */
+const char *btrt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BTRT_H */

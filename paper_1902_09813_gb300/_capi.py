@@ -1,0 +1,92 @@
+"""ctypes declarations of the C ABI in include/btrt.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+from pathlib import Path
+
+LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libbtrt.so"
+
+OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
+BC_PERIODIC, BC_HBB = 0, 1
+F64, F32, F16, BF16 = 0, 1, 2, 3
+K2_HBB, K2_CONST = 0, 1
+SRC_NONE, SRC_CONST, SRC_TRIG = 0, 1, 2
+
+FORMATS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+
+
+class GridDesc(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("bc", ctypes.c_int32 * 4),
+        ("compute", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+        ("x0", ctypes.c_double), ("y0", ctypes.c_double),
+        ("phi_ref", ctypes.c_double),
+    ]
+
+
+class Coeffs(ctypes.Structure):
+    _fields_ = [
+        ("u", ctypes.c_double * 2), ("b2", ctypes.c_double), ("c3", ctypes.c_double),
+        ("A0", ctypes.c_double * 3), ("a2", ctypes.c_double), ("k0", ctypes.c_double),
+        ("k2_mode", ctypes.c_int32), ("src_kind", ctypes.c_int32),
+        ("k2", ctypes.c_double), ("src_const", ctypes.c_double),
+        ("src_lam", ctypes.c_double), ("src_k", ctypes.c_double),
+        ("src_alpha", ctypes.c_double * 4), ("wall_lam", ctypes.c_double),
+    ]
+
+
+class BtrtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"btrt error {code}: {msg}")
+        self.code = code
+
+
+# (name, restype, argtypes) of every exported entry point
+_vp, _dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+_i32, _i64, _sz = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+SIGNATURES = [
+    ("btrt_workspace_bytes", _sz, [ctypes.POINTER(GridDesc)]),
+    ("btrt_create", ctypes.c_int, [ctypes.POINTER(GridDesc), _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    ("btrt_set_coeffs", ctypes.c_int, [_vp, ctypes.POINTER(Coeffs)]),
+    ("btrt_set_boundary", ctypes.c_int, [_vp, _i32, _dp, _i32]),
+    ("btrt_init_phi", ctypes.c_int, [_vp, _vp, _i32, _i32, ctypes.c_double]),
+    ("btrt_step", ctypes.c_int, [_vp, _i64]),
+    ("btrt_read_phi", ctypes.c_int, [_vp, _vp, _i32, _i32]),
+    ("btrt_read_f", ctypes.c_int, [_vp, _dp, _i32, _i32, _i32, _i32]),
+    ("btrt_mass", ctypes.c_int, [_vp, _dp]),
+    ("btrt_check", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    ("btrt_get_time", ctypes.c_int, [_vp, ctypes.POINTER(_i64), _dp]),
+    ("btrt_state_bytes", _sz, [_vp]),
+    ("btrt_save", ctypes.c_int, [_vp, _vp, _sz]),
+    ("btrt_load", ctypes.c_int, [_vp, _vp, _sz]),
+    ("btrt_destroy", ctypes.c_int, [_vp]),
+    ("btrt_last_error", ctypes.c_char_p, []),
+    ("btrt_version", ctypes.c_char_p, []),
+]
+
+_lib = None
+
+
+def load():
+    """Load libbtrt.so.  Raises if the library has not been built: there is no
+    fallback implementation."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -c 'import __graft_entry__ as g; g.build()'`")
+        lib = ctypes.CDLL(str(LIB_PATH))
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def check(code: int):
+    if code != OK:
+        raise BtrtError(code, load().btrt_last_error().decode())
+    return code

@@ -1,0 +1,650 @@
+// btrt_api.cu -- host runtime and C ABI of the B-TriRT D2Q9 solver (see include/btrt.h).
+//
+// A lattice lives entirely in a caller-owned device workspace:
+//   [F buffer 0: 9 planes][F buffer 1: 9 planes][phi plane][trig tables][wall arrays][reduction scratch]
+// Planes are row major with a row pitch of nx rounded up to 64 elements; every
+// region starts on a 256-byte boundary.  Populations are double buffered: a
+// sweep reads buffer `cur` and writes buffer 1 - cur.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/btrt.h"
+#include "btrt_internal.h"
+
+using namespace btrt;
+
+namespace {
+
+thread_local std::string g_err;
+
+btrt_status fail(btrt_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(expr)                                                                    \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return fail(BTRT_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),    \
+                        __FILE__, __LINE__);                                              \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+constexpr int kRedBlocks = 1024;     // fixed grid of the FP64 reductions (deterministic order)
+constexpr int kRedThreads = 256;
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+size_t elem_size(int fmt) {
+    switch (fmt) {
+    case BTRT_F64: return 8;
+    case BTRT_F32: return 4;
+    case BTRT_F16: return 2;
+    case BTRT_BF16: return 2;
+    default: return 0;
+    }
+}
+
+struct Layout {
+    long long pitch = 0;     // elements per row (f planes and phi plane)
+    long long plane = 0;     // elements per plane
+    size_t fbuf_bytes = 0;   // one buffer of 9 planes
+    size_t off_f[2] = {0, 0};
+    size_t off_phi = 0, off_tab = 0, off_wall = 0, off_red = 0, total = 0;
+    int maxside = 0;
+};
+
+btrt_status check_desc(const btrt_grid_desc *g) {
+    if (!g) return fail(BTRT_EINVAL, "null grid description");
+    if (g->nx < 3 || g->ny < 3 || g->nx > 65536 || g->ny > 65536)
+        return fail(BTRT_EINVAL, "grid %d x %d outside [3, 65536]", g->nx, g->ny);
+    for (int k = 0; k < 4; ++k)
+        if (g->bc[k] != BTRT_BC_PERIODIC && g->bc[k] != BTRT_BC_HBB)
+            return fail(BTRT_EINVAL, "bc[%d] = %d is not a boundary kind", k, g->bc[k]);
+    if (g->bc[0] != g->bc[1] || g->bc[2] != g->bc[3])
+        return fail(BTRT_EINVAL, "opposite sides must share the boundary kind");
+    if (g->compute == BTRT_F64) {
+        if (g->storage != BTRT_F64)
+            return fail(BTRT_EINVAL, "FP64 compute requires FP64 storage");
+    } else if (g->compute == BTRT_F32) {
+        if (g->storage != BTRT_F32 && g->storage != BTRT_F16 && g->storage != BTRT_BF16)
+            return fail(BTRT_EINVAL, "FP32 compute takes F32, F16 or BF16 storage");
+    } else {
+        return fail(BTRT_EINVAL, "compute must be BTRT_F64 or BTRT_F32");
+    }
+    if (!(g->dx > 0.0) || !(g->dt > 0.0) || !std::isfinite(g->dx) || !std::isfinite(g->dt))
+        return fail(BTRT_EINVAL, "dx and dt must be positive and finite");
+    if (!std::isfinite(g->phi_ref) || !std::isfinite(g->x0) || !std::isfinite(g->y0))
+        return fail(BTRT_EINVAL, "phi_ref, x0, y0 must be finite");
+    return BTRT_OK;
+}
+
+Layout make_layout(const btrt_grid_desc *g) {
+    Layout L;
+    const size_t sf = elem_size(g->storage);
+    const size_t sr = elem_size(g->compute);
+    L.pitch = (long long)align_up((size_t)g->nx, 64);
+    L.plane = L.pitch * (long long)g->ny;
+    L.maxside = g->nx > g->ny ? g->nx : g->ny;
+    L.fbuf_bytes = align_up(9 * (size_t)L.plane * sf, kAlign);
+    size_t off = 0;
+    L.off_f[0] = off;
+    off += L.fbuf_bytes;
+    L.off_f[1] = off;
+    off += L.fbuf_bytes;
+    L.off_phi = off;
+    off += align_up((size_t)L.plane * sr, kAlign);
+    L.off_tab = off;
+    off += align_up(2 * ((size_t)g->nx + (size_t)g->ny) * sr, kAlign);
+    L.off_wall = off;
+    off += align_up(4 * (size_t)L.maxside * sr, kAlign);
+    L.off_red = off;
+    off += align_up((kRedBlocks + 2) * sizeof(double) + 16, kAlign);
+    L.total = off;
+    return L;
+}
+
+// ---------------------------------------------------------------- small kernels
+template <typename Real, typename In>
+__global__ void dense_to_plane(const In *__restrict__ src, Real *__restrict__ dst, int nx, int ny,
+                               long long pitch) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x < nx && y < ny) dst[(long long)y * pitch + x] = (Real)src[(long long)y * nx + x];
+}
+
+template <typename Real, typename Out>
+__global__ void plane_to_dense(const Real *__restrict__ src, Out *__restrict__ dst, int nx, int ny,
+                               long long pitch) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x < nx && y < ny) dst[(long long)y * nx + x] = (Out)src[(long long)y * pitch + x];
+}
+
+// FP64 sum of a plane: every block owns the rows y = b, b + gridDim.x, ...;
+// threads stride over x; fixed tree inside the block.  Deterministic for a
+// fixed grid size.
+template <typename Real>
+__global__ void __launch_bounds__(kRedThreads)
+plane_sum_partials(const Real *__restrict__ a, int nx, int ny, long long pitch, double *partials) {
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    for (int y = blockIdx.x; y < ny; y += gridDim.x)
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) acc += (double)a[(long long)y * pitch + x];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kRedThreads) sum_partials(const double *partials, int n, double *out) {
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- the lattice object
+struct btrt_lattice_s {
+    btrt_grid_desc g;
+    btrt_coeffs c;
+    Layout lay;
+    unsigned char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    int cur = 0;              // buffer holding the current post-collision populations
+    int64_t step = 0;
+    double t0 = 0.0;
+    bool have_coeffs = false, ready = false;
+    // lattice-unit constants derived from the coefficients
+    double ux = 0, uy = 0, b2 = 0, A0[3] = {0, 0, 0}, K1[3] = {0, 0, 0}, k2 = 1;
+    bool nonlin_A = false;
+    double wall_const[4] = {0, 0, 0, 0};
+    bool wall_is_arr[4] = {false, false, false, false};
+
+    template <typename Real> Real *phi() { return reinterpret_cast<Real *>(ws + lay.off_phi); }
+    void *fbuf(int k) { return ws + lay.off_f[k]; }
+    template <typename Real> Real *tab() { return reinterpret_cast<Real *>(ws + lay.off_tab); }
+    template <typename Real> Real *wall(int side) {
+        return reinterpret_cast<Real *>(ws + lay.off_wall) + (size_t)side * lay.maxside;
+    }
+    double *partials() { return reinterpret_cast<double *>(ws + lay.off_red); }
+    double *red_out() { return partials() + kRedBlocks; }
+    int *flags() { return reinterpret_cast<int *>(partials() + kRedBlocks + 2); }
+};
+
+namespace {
+
+template <typename Real>
+void fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool first) {
+    const btrt_grid_desc &g = L->g;
+    const btrt_coeffs &c = L->c;
+    std::memset(&p, 0, sizeof p);
+    p.fin = L->fbuf(L->cur);
+    p.fout = L->fbuf(first ? L->cur : 1 - L->cur);
+    p.phi = L->phi<Real>();
+    p.nx = g.nx;
+    p.ny = g.ny;
+    p.pitch = L->lay.pitch;
+    p.plane = L->lay.plane;
+    p.hbb_x = g.bc[0] == BTRT_BC_HBB;
+    p.hbb_y = g.bc[2] == BTRT_BC_HBB;
+    const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    for (int i = 0; i < 9; ++i) p.wref[i] = (Real)(w[i] * g.phi_ref);
+    const double tn = L->t0 + (double)n * g.dt;
+    for (int s = 0; s < 4; ++s) {
+        p.wall_const[s] = (Real)L->wall_const[s];
+        p.wall_arr[s] = L->wall_is_arr[s] ? L->wall<Real>(s) : nullptr;
+    }
+    // bounce-back values of the streaming that ends at t_n
+    p.wall_fac = (Real)std::exp(c.wall_lam * tn);
+    p.ux = (Real)L->ux;
+    p.uy = (Real)L->uy;
+    p.b2 = (Real)L->b2;
+    p.c3 = (Real)c.c3;
+    p.A0xx = (Real)L->A0[0];
+    p.A0xy = (Real)L->A0[1];
+    p.A0yy = (Real)L->A0[2];
+    p.a2 = (Real)c.a2;
+    p.k0 = (Real)c.k0;
+    p.nonlin_A = L->nonlin_A ? 1 : 0;
+    p.k2_hbb = c.k2_mode == BTRT_K2_HBB;
+    p.k2c = (Real)c.k2;
+    p.K1xx = (Real)L->K1[0];
+    p.K1xy = (Real)L->K1[1];
+    p.K1yy = (Real)L->K1[2];
+    p.k2 = (Real)L->k2;
+    p.cond_limit = (Real)1.0e4;
+    p.src_kind = c.src_kind;
+    if (c.src_kind == BTRT_SRC_CONST) {
+        p.src_val = (Real)(c.src_const * g.dt);
+    } else if (c.src_kind == BTRT_SRC_TRIG) {
+        // dt S_i + dt^2/2 (S_i^n - S_i^{n-1})/dt = w_i dt (3 S^n - S^{n-1}) / 2 (scheme 2)
+        const double Tn = std::exp(c.src_lam * tn);
+        const double Tp = first ? Tn : std::exp(c.src_lam * (tn - g.dt));
+        p.src_val = (Real)(g.dt * 0.5 * (3.0 * Tn - Tp));
+        Real *tb = L->tab<Real>();
+        p.Xs = tb;
+        p.Xc = tb + g.nx;
+        p.Ys = tb + 2 * g.nx;
+        p.Yc = tb + 2 * g.nx + g.ny;
+    }
+    p.first = first ? 1 : 0;
+    p.flags = L->flags();
+}
+
+btrt_status launch(btrt_lattice L, int64_t n, bool first) {
+    if (L->g.compute == BTRT_F64) {
+        SweepParams<double> p;
+        fill_params(L, p, n, first);
+        CUDA_TRY(launch_sweep_f64(p, L->stream));
+    } else {
+        SweepParams<float> p;
+        fill_params(L, p, n, first);
+        CUDA_TRY(launch_sweep_f32(p, L->g.storage, L->stream));
+    }
+    return BTRT_OK;
+}
+
+template <typename Real>
+btrt_status upload_tables(btrt_lattice L) {
+    const btrt_grid_desc &g = L->g;
+    const btrt_coeffs &c = L->c;
+    std::vector<Real> h(2 * ((size_t)g.nx + g.ny));
+    for (int i = 0; i < g.nx; ++i) {
+        const double x = g.x0 + (i + 0.5) * g.dx;
+        h[i] = (Real)std::sin(c.src_k * x);
+        h[g.nx + i] = (Real)std::cos(c.src_k * x);
+    }
+    for (int j = 0; j < g.ny; ++j) {
+        const double y = g.y0 + (j + 0.5) * g.dx;
+        const double sy = std::sin(c.src_k * y), cy = std::cos(c.src_k * y);
+        // alpha folded in: S_spatial = Xs (a_ss sy + a_sc cy) + Xc (a_cs sy + a_cc cy)
+        h[2 * g.nx + j] = (Real)(c.src_alpha[0] * sy + c.src_alpha[1] * cy);
+        h[2 * g.nx + g.ny + j] = (Real)(c.src_alpha[2] * sy + c.src_alpha[3] * cy);
+    }
+    CUDA_TRY(cudaMemcpyAsync(L->tab<Real>(), h.data(), h.size() * sizeof(Real),
+                             cudaMemcpyHostToDevice, L->stream));
+    CUDA_TRY(cudaStreamSynchronize(L->stream));
+    return BTRT_OK;
+}
+
+template <typename Real>
+btrt_status upload_wall(btrt_lattice L, int side, const double *v, int n) {
+    std::vector<Real> h(n);
+    for (int k = 0; k < n; ++k) h[k] = (Real)v[k];
+    CUDA_TRY(cudaMemcpyAsync(L->wall<Real>(side), h.data(), n * sizeof(Real),
+                             cudaMemcpyHostToDevice, L->stream));
+    CUDA_TRY(cudaStreamSynchronize(L->stream));
+    return BTRT_OK;
+}
+
+template <typename Real>
+btrt_status stage_phi0(btrt_lattice L, const void *phi0, int dtype, int on_device) {
+    const btrt_grid_desc &g = L->g;
+    const size_t n = (size_t)g.nx * g.ny;
+    const size_t bytes = n * elem_size(dtype);
+    const void *dev_src = phi0;
+    if (!on_device) {
+        // stage the dense host array in population buffer 1 (overwritten below)
+        if (bytes > L->lay.fbuf_bytes) return fail(BTRT_ENOMEM, "staging area too small");
+        CUDA_TRY(cudaMemcpyAsync(L->fbuf(1), phi0, bytes, cudaMemcpyHostToDevice, L->stream));
+        dev_src = L->fbuf(1);
+    }
+    const dim3 blk(256), grd((unsigned)((g.nx + 255) / 256), (unsigned)g.ny);
+    if (dtype == BTRT_F64)
+        dense_to_plane<Real, double><<<grd, blk, 0, L->stream>>>((const double *)dev_src, L->phi<Real>(),
+                                                                 g.nx, g.ny, L->lay.pitch);
+    else
+        dense_to_plane<Real, float><<<grd, blk, 0, L->stream>>>((const float *)dev_src, L->phi<Real>(),
+                                                                g.nx, g.ny, L->lay.pitch);
+    CUDA_TRY(cudaGetLastError());
+    if (!on_device) CUDA_TRY(cudaStreamSynchronize(L->stream));  // host buffer may be reused
+    return BTRT_OK;
+}
+
+template <typename Real>
+btrt_status copy_phi_out(btrt_lattice L, void *dst, int dtype, int on_device) {
+    const btrt_grid_desc &g = L->g;
+    const size_t n = (size_t)g.nx * g.ny;
+    if (on_device) {
+        const dim3 blk(256), grd((unsigned)((g.nx + 255) / 256), (unsigned)g.ny);
+        if (dtype == BTRT_F64)
+            plane_to_dense<Real, double><<<grd, blk, 0, L->stream>>>(L->phi<Real>(), (double *)dst,
+                                                                     g.nx, g.ny, L->lay.pitch);
+        else
+            plane_to_dense<Real, float><<<grd, blk, 0, L->stream>>>(L->phi<Real>(), (float *)dst,
+                                                                    g.nx, g.ny, L->lay.pitch);
+        CUDA_TRY(cudaGetLastError());
+        return BTRT_OK;
+    }
+    if (dtype == (sizeof(Real) == 8 ? BTRT_F64 : BTRT_F32)) {
+        CUDA_TRY(cudaMemcpy2DAsync(dst, g.nx * sizeof(Real), L->phi<Real>(), L->lay.pitch * sizeof(Real),
+                                   g.nx * sizeof(Real), g.ny, cudaMemcpyDeviceToHost, L->stream));
+        CUDA_TRY(cudaStreamSynchronize(L->stream));
+        return BTRT_OK;
+    }
+    std::vector<Real> h(n);
+    CUDA_TRY(cudaMemcpy2DAsync(h.data(), g.nx * sizeof(Real), L->phi<Real>(), L->lay.pitch * sizeof(Real),
+                               g.nx * sizeof(Real), g.ny, cudaMemcpyDeviceToHost, L->stream));
+    CUDA_TRY(cudaStreamSynchronize(L->stream));
+    if (dtype == BTRT_F64)
+        for (size_t k = 0; k < n; ++k) ((double *)dst)[k] = (double)h[k];
+    else
+        for (size_t k = 0; k < n; ++k) ((float *)dst)[k] = (float)h[k];
+    return BTRT_OK;
+}
+
+template <typename Real>
+btrt_status reduce_phi(btrt_lattice L, double *out) {
+    const btrt_grid_desc &g = L->g;
+    plane_sum_partials<Real><<<kRedBlocks, kRedThreads, 0, L->stream>>>(L->phi<Real>(), g.nx, g.ny,
+                                                                          L->lay.pitch, L->partials());
+    CUDA_TRY(cudaGetLastError());
+    sum_partials<<<1, kRedThreads, 0, L->stream>>>(L->partials(), kRedBlocks, L->red_out());
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(out, L->red_out(), sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    CUDA_TRY(cudaStreamSynchronize(L->stream));
+    return BTRT_OK;
+}
+
+double host_half_to_double(int fmt, const unsigned char *p) {
+    uint16_t b;
+    std::memcpy(&b, p, 2);
+    if (fmt == BTRT_BF16) {
+        uint32_t u = (uint32_t)b << 16;
+        float f;
+        std::memcpy(&f, &u, 4);
+        return f;
+    }
+    // IEEE binary16 -> double, by its definition
+    const int sign = (b >> 15) & 1, e = (b >> 10) & 31, m = b & 1023;
+    double v;
+    if (e == 0) v = std::ldexp((double)m, -24);
+    else if (e == 31) v = m ? NAN : INFINITY;
+    else v = std::ldexp((double)(m | 1024), e - 25);
+    return sign ? -v : v;
+}
+
+struct StateHeader {
+    char magic[8];
+    int32_t nx, ny, compute, storage;
+    int64_t step;
+    double t0;
+    int32_t cur, pad;
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- C ABI
+extern "C" {
+
+size_t btrt_workspace_bytes(const btrt_grid_desc *g) {
+    if (check_desc(g) != BTRT_OK) return 0;
+    return make_layout(g).total;
+}
+
+btrt_status btrt_create(const btrt_grid_desc *g, void *dev_workspace, size_t workspace_bytes,
+                        void *cuda_stream, btrt_lattice *out) {
+    if (!out) return fail(BTRT_EINVAL, "null output handle");
+    *out = nullptr;
+    btrt_status st = check_desc(g);
+    if (st != BTRT_OK) return st;
+    if (!dev_workspace) return fail(BTRT_EINVAL, "null workspace");
+    if (((uintptr_t)dev_workspace) % kAlign) return fail(BTRT_EINVAL, "workspace not 256-byte aligned");
+    Layout lay = make_layout(g);
+    if (workspace_bytes < lay.total)
+        return fail(BTRT_ENOMEM, "workspace of %zu bytes < required %zu", workspace_bytes, lay.total);
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, dev_workspace) != cudaSuccess || attr.type != cudaMemoryTypeDevice) {
+        cudaGetLastError();
+        return fail(BTRT_EINVAL, "workspace is not device memory");
+    }
+    btrt_lattice L = new (std::nothrow) btrt_lattice_s();
+    if (!L) return fail(BTRT_ENOMEM, "host allocation failed");
+    L->g = *g;
+    L->lay = lay;
+    L->ws = static_cast<unsigned char *>(dev_workspace);
+    L->stream = static_cast<cudaStream_t>(cuda_stream);
+    std::memset(&L->c, 0, sizeof L->c);
+    L->c.k0 = 1.0;
+    cudaError_t e = cudaMemsetAsync(L->flags(), 0, 16, L->stream);
+    if (e != cudaSuccess) {
+        delete L;
+        return fail(BTRT_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    *out = L;
+    return BTRT_OK;
+}
+
+btrt_status btrt_set_coeffs(btrt_lattice L, const btrt_coeffs *c) {
+    if (!L || !c) return fail(BTRT_EINVAL, "null argument");
+    const btrt_grid_desc &g = L->g;
+    const double cl = g.dx / g.dt;                 // lattice speed c
+    const double axx = c->A0[0], axy = c->A0[1], ayy = c->A0[2];
+    if (!(axx > 0.0) || !(ayy > 0.0) || !(axx * ayy - axy * axy > 0.0))
+        return fail(BTRT_EINVAL, "A0 must be symmetric positive definite");
+    if (!(c->k0 > 0.0 && c->k0 < 2.0)) return fail(BTRT_EINVAL, "k0 = %g outside (0, 2)", c->k0);
+    if (c->k2_mode != BTRT_K2_HBB && c->k2_mode != BTRT_K2_CONST)
+        return fail(BTRT_EINVAL, "unknown k2 mode %d", c->k2_mode);
+    if (c->k2_mode == BTRT_K2_CONST && !(c->k2 > 0.0 && c->k2 < 2.0))
+        return fail(BTRT_EINVAL, "k2 = %g outside (0, 2)", c->k2);
+    if (c->src_kind < BTRT_SRC_NONE || c->src_kind > BTRT_SRC_TRIG)
+        return fail(BTRT_EINVAL, "unknown source kind %d", c->src_kind);
+    if (!std::isfinite(c->a2) || c->a2 < 0.0) return fail(BTRT_EINVAL, "a2 must be >= 0");
+    L->c = *c;
+    // lattice units: B^ = B dt/dx, A^ = A dt/dx^2
+    L->ux = c->u[0] / cl;
+    L->uy = c->u[1] / cl;
+    L->b2 = c->b2 / cl;
+    const double sA = g.dt / (g.dx * g.dx);
+    L->A0[0] = axx * sA;
+    L->A0[1] = axy * sA;
+    L->A0[2] = ayy * sA;
+    // K1 = (3 A^ + I/2)^{-1} at A = A0 (Eq. 30), k2 from Eq. 62 or constant
+    const double mxx = 3 * L->A0[0] + 0.5, mxy = 3 * L->A0[1], myy = 3 * L->A0[2] + 0.5;
+    const double det = mxx * myy - mxy * mxy;
+    L->K1[0] = myy / det;
+    L->K1[1] = -mxy / det;
+    L->K1[2] = mxx / det;
+    const double k1eff = 2.0 / (mxx + myy);
+    L->k2 = c->k2_mode == BTRT_K2_HBB ? 8.0 * (k1eff - 2.0) / (3.0 * (k1eff - 4.0)) : c->k2;
+    L->nonlin_A = c->a2 != 0.0;
+    L->have_coeffs = true;
+    if (c->src_kind == BTRT_SRC_TRIG) {
+        btrt_status st = g.compute == BTRT_F64 ? upload_tables<double>(L) : upload_tables<float>(L);
+        if (st != BTRT_OK) return st;
+    }
+    return BTRT_OK;
+}
+
+btrt_status btrt_set_boundary(btrt_lattice L, int32_t side, const double *phi_w_host, int32_t n) {
+    if (!L || !phi_w_host) return fail(BTRT_EINVAL, "null argument");
+    if (side < 0 || side > 3) return fail(BTRT_EINVAL, "side %d outside 0..3", side);
+    const int len = side < 2 ? L->g.ny : L->g.nx;
+    if (n == 1) {
+        if (!std::isfinite(phi_w_host[0])) return fail(BTRT_EINVAL, "non-finite wall value");
+        L->wall_const[side] = phi_w_host[0];
+        L->wall_is_arr[side] = false;
+        return BTRT_OK;
+    }
+    if (n != len) return fail(BTRT_EINVAL, "side %d takes 1 or %d values, got %d", side, len, n);
+    for (int k = 0; k < n; ++k)
+        if (!std::isfinite(phi_w_host[k])) return fail(BTRT_EINVAL, "non-finite wall value at %d", k);
+    btrt_status st = L->g.compute == BTRT_F64 ? upload_wall<double>(L, side, phi_w_host, n)
+                                              : upload_wall<float>(L, side, phi_w_host, n);
+    if (st != BTRT_OK) return st;
+    L->wall_is_arr[side] = true;
+    return BTRT_OK;
+}
+
+btrt_status btrt_init_phi(btrt_lattice L, const void *phi0, int32_t dtype, int32_t on_device, double t0) {
+    if (!L || !phi0) return fail(BTRT_EINVAL, "null argument");
+    if (!L->have_coeffs) return fail(BTRT_ESTATE, "btrt_set_coeffs must come before btrt_init_phi");
+    if (dtype != BTRT_F64 && dtype != BTRT_F32) return fail(BTRT_EINVAL, "phi0 dtype must be F64 or F32");
+    if (!std::isfinite(t0)) return fail(BTRT_EINVAL, "t0 must be finite");
+    btrt_status st = L->g.compute == BTRT_F64 ? stage_phi0<double>(L, phi0, dtype, on_device)
+                                              : stage_phi0<float>(L, phi0, dtype, on_device);
+    if (st != BTRT_OK) return st;
+    L->t0 = t0;
+    L->step = 0;
+    L->cur = 0;
+    CUDA_TRY(cudaMemsetAsync(L->flags(), 0, 16, L->stream));
+    st = launch(L, 0, true);
+    if (st != BTRT_OK) return st;
+    L->ready = true;
+    return BTRT_OK;
+}
+
+btrt_status btrt_step(btrt_lattice L, int64_t nsteps) {
+    if (!L) return fail(BTRT_EINVAL, "null lattice");
+    if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
+    if (nsteps < 0) return fail(BTRT_EINVAL, "negative step count");
+    for (int64_t k = 0; k < nsteps; ++k) {
+        btrt_status st = launch(L, L->step + 1, false);
+        if (st != BTRT_OK) return st;
+        L->cur = 1 - L->cur;
+        L->step += 1;
+    }
+    return BTRT_OK;
+}
+
+btrt_status btrt_read_phi(btrt_lattice L, void *dst, int32_t dtype, int32_t on_device) {
+    if (!L || !dst) return fail(BTRT_EINVAL, "null argument");
+    if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
+    if (dtype != BTRT_F64 && dtype != BTRT_F32) return fail(BTRT_EINVAL, "dtype must be F64 or F32");
+    return L->g.compute == BTRT_F64 ? copy_phi_out<double>(L, dst, dtype, on_device)
+                                    : copy_phi_out<float>(L, dst, dtype, on_device);
+}
+
+btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int32_t w, int32_t h) {
+    if (!L || !dst) return fail(BTRT_EINVAL, "null argument");
+    if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
+    const btrt_grid_desc &g = L->g;
+    if (w <= 0 || h <= 0 || x0 < 0 || y0 < 0 || x0 + w > g.nx || y0 + h > g.ny)
+        return fail(BTRT_EINVAL, "window outside the grid");
+    const size_t sf = elem_size(g.storage);
+    std::vector<unsigned char> raw((size_t)w * h * sf);
+    const double wts[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    for (int i = 0; i < 9; ++i) {
+        const unsigned char *src = static_cast<unsigned char *>(L->fbuf(L->cur)) +
+                                   ((size_t)i * L->lay.plane + (size_t)y0 * L->lay.pitch + x0) * sf;
+        CUDA_TRY(cudaMemcpy2DAsync(raw.data(), w * sf, src, L->lay.pitch * sf, w * sf, h,
+                                   cudaMemcpyDeviceToHost, L->stream));
+        CUDA_TRY(cudaStreamSynchronize(L->stream));
+        // the stored values are rounded from Real = f - w_i phi_ref in the compute precision
+        const double shift = g.compute == BTRT_F64 ? wts[i] * g.phi_ref
+                                                   : (double)(float)(wts[i] * g.phi_ref);
+        for (size_t k = 0; k < (size_t)w * h; ++k) {
+            double v;
+            if (g.storage == BTRT_F64) std::memcpy(&v, &raw[k * 8], 8);
+            else if (g.storage == BTRT_F32) { float fv; std::memcpy(&fv, &raw[k * 4], 4); v = fv; }
+            else v = host_half_to_double(g.storage, &raw[k * 2]);
+            dst[(size_t)i * w * h + k] = v + shift;
+        }
+    }
+    return BTRT_OK;
+}
+
+btrt_status btrt_mass(btrt_lattice L, double *out) {
+    if (!L || !out) return fail(BTRT_EINVAL, "null argument");
+    if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
+    return L->g.compute == BTRT_F64 ? reduce_phi<double>(L, out) : reduce_phi<float>(L, out);
+}
+
+btrt_status btrt_check(btrt_lattice L, int32_t *flags) {
+    if (!L || !flags) return fail(BTRT_EINVAL, "null argument");
+    CUDA_TRY(cudaMemcpyAsync(flags, L->flags(), sizeof(int32_t), cudaMemcpyDeviceToHost, L->stream));
+    CUDA_TRY(cudaStreamSynchronize(L->stream));
+    if (*flags & 1) return fail(BTRT_EUNSTABLE, "non-finite phi detected (unstable parameters?)");
+    return BTRT_OK;
+}
+
+btrt_status btrt_get_time(btrt_lattice L, int64_t *step, double *t) {
+    if (!L) return fail(BTRT_EINVAL, "null lattice");
+    if (step) *step = L->step;
+    if (t) *t = L->t0 + (double)L->step * L->g.dt;
+    return BTRT_OK;
+}
+
+size_t btrt_state_bytes(btrt_lattice L) {
+    if (!L) return 0;
+    return sizeof(StateHeader) + L->lay.fbuf_bytes + (size_t)L->lay.plane * elem_size(L->g.compute);
+}
+
+btrt_status btrt_save(btrt_lattice L, void *host_buf, size_t n) {
+    if (!L || !host_buf) return fail(BTRT_EINVAL, "null argument");
+    if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
+    if (n < btrt_state_bytes(L)) return fail(BTRT_ENOMEM, "buffer of %zu bytes too small", n);
+    StateHeader h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "BTRTST1", 8);
+    h.nx = L->g.nx;
+    h.ny = L->g.ny;
+    h.compute = L->g.compute;
+    h.storage = L->g.storage;
+    h.step = L->step;
+    h.t0 = L->t0;
+    std::memcpy(host_buf, &h, sizeof h);
+    unsigned char *p = static_cast<unsigned char *>(host_buf) + sizeof h;
+    CUDA_TRY(cudaMemcpyAsync(p, L->fbuf(L->cur), L->lay.fbuf_bytes, cudaMemcpyDeviceToHost, L->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + L->lay.fbuf_bytes, L->ws + L->lay.off_phi,
+                             (size_t)L->lay.plane * elem_size(L->g.compute), cudaMemcpyDeviceToHost, L->stream));
+    CUDA_TRY(cudaStreamSynchronize(L->stream));
+    return BTRT_OK;
+}
+
+btrt_status btrt_load(btrt_lattice L, const void *host_buf, size_t n) {
+    if (!L || !host_buf) return fail(BTRT_EINVAL, "null argument");
+    if (!L->have_coeffs) return fail(BTRT_ESTATE, "btrt_set_coeffs must come before btrt_load");
+    if (n < btrt_state_bytes(L)) return fail(BTRT_ENOMEM, "buffer of %zu bytes too small", n);
+    StateHeader h;
+    std::memcpy(&h, host_buf, sizeof h);
+    if (std::memcmp(h.magic, "BTRTST1", 8) != 0 || h.nx != L->g.nx || h.ny != L->g.ny ||
+        h.compute != L->g.compute || h.storage != L->g.storage)
+        return fail(BTRT_EINVAL, "state does not match this lattice");
+    const unsigned char *p = static_cast<const unsigned char *>(host_buf) + sizeof h;
+    L->cur = 0;
+    CUDA_TRY(cudaMemcpyAsync(L->fbuf(0), p, L->lay.fbuf_bytes, cudaMemcpyHostToDevice, L->stream));
+    CUDA_TRY(cudaMemcpyAsync(L->ws + L->lay.off_phi, p + L->lay.fbuf_bytes,
+                             (size_t)L->lay.plane * elem_size(L->g.compute), cudaMemcpyHostToDevice, L->stream));
+    CUDA_TRY(cudaMemsetAsync(L->flags(), 0, 16, L->stream));
+    CUDA_TRY(cudaStreamSynchronize(L->stream));
+    L->step = h.step;
+    L->t0 = h.t0;
+    L->ready = true;
+    return BTRT_OK;
+}
+
+btrt_status btrt_destroy(btrt_lattice L) {
+    delete L;
+    return BTRT_OK;
+}
+
+const char *btrt_last_error(void) { return g_err.c_str(); }
+
+const char *btrt_version(void) { return "btrt 0.1 (D2Q9 B-TriRT, sm_103a)"; }
+
+}  // extern "C"

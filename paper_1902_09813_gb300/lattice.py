@@ -1,0 +1,210 @@
+"""Python binding of one lattice: argument marshalling around the C ABI.
+
+PyTorch provides the device workspace and the CUDA stream; every step of the
+sweep runs in libbtrt's kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _capi as C
+
+_K2 = {"hbb": C.K2_HBB, "const": C.K2_CONST}
+_SRC = {"none": C.SRC_NONE, "const": C.SRC_CONST, "trig": C.SRC_TRIG}
+
+
+def grid_desc(nx, ny, dx, dt, bc=(0, 0, 0, 0), compute="f64", storage="f64",
+              x0=0.0, y0=0.0, phi_ref=0.0) -> C.GridDesc:
+    g = C.GridDesc()
+    g.nx, g.ny = int(nx), int(ny)
+    for k in range(4):
+        g.bc[k] = int(bc[k])
+    g.compute, g.storage = C.FORMATS[compute], C.FORMATS[storage]
+    g.dx, g.dt, g.x0, g.y0, g.phi_ref = float(dx), float(dt), float(x0), float(y0), float(phi_ref)
+    return g
+
+
+def coeffs(u=(0.0, 0.0), b2=0.0, c3=0.0, A0=(0.0, 0.0, 0.0), a2=0.0, k0=1.0, k2_mode="hbb",
+           k2=1.0, source=None, wall_lam=0.0) -> C.Coeffs:
+    c = C.Coeffs()
+    c.u[0], c.u[1] = float(u[0]), float(u[1])
+    c.b2, c.c3, c.a2, c.k0 = float(b2), float(c3), float(a2), float(k0)
+    for k in range(3):
+        c.A0[k] = float(A0[k])
+    c.k2_mode = _K2[k2_mode]
+    c.k2 = float(k2)
+    if source is not None:
+        c.src_kind = _SRC[source.kind]
+        c.src_const, c.src_lam, c.src_k = float(source.const), float(source.lam), float(source.k)
+        for k in range(4):
+            c.src_alpha[k] = float(source.alpha[k])
+    c.wall_lam = float(wall_lam)
+    return c
+
+
+def workspace_bytes(desc: C.GridDesc) -> int:
+    n = C.load().btrt_workspace_bytes(ctypes.byref(desc))
+    if n == 0:
+        raise C.BtrtError(C.EINVAL, C.load().btrt_last_error().decode())
+    return int(n)
+
+
+class Lattice:
+    """One B-TriRT D2Q9 lattice resident on the GPU.
+
+    Build it with :meth:`from_problem` (any object with the attributes of
+    ``workloads.Problem``) or from a :class:`GridDesc` and :class:`Coeffs`.
+    """
+
+    def __init__(self, desc: C.GridDesc, coef: C.Coeffs, device=None, stream=None,
+                 workspace: Optional[torch.Tensor] = None):
+        self.lib = C.load()
+        self.desc = desc
+        self.coef = coef
+        self.device = torch.device(device if device is not None else "cuda")
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = workspace_bytes(desc)
+        if workspace is None:
+            workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        elif workspace.numel() * workspace.element_size() < nbytes:
+            raise ValueError("workspace too small")
+        self.workspace = workspace
+        h = ctypes.c_void_p()
+        C.check(self.lib.btrt_create(ctypes.byref(desc), ctypes.c_void_p(workspace.data_ptr()),
+                                     nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
+        self.handle = h
+        C.check(self.lib.btrt_set_coeffs(self.handle, ctypes.byref(coef)))
+
+    # ------------------------------------------------------------ construction
+    @classmethod
+    def from_problem(cls, p, compute="f64", storage=None, device=None, stream=None,
+                     phi_ref=None) -> "Lattice":
+        storage = storage or compute
+        desc = grid_desc(p.nx, p.ny, p.dx, p.dt, p.bc, compute, storage, p.x0, p.y0,
+                         p.phi_ref if phi_ref is None else phi_ref)
+        coef = coeffs(p.u, p.b2, p.c3, p.A0, p.a2, p.k0, p.k2_mode, p.k2, p.source,
+                      getattr(p, "wall_lam", 0.0))
+        lat = cls(desc, coef, device=device, stream=stream)
+        for side in range(4):
+            arrs = getattr(p, "wall_arrays", None)
+            if arrs is not None and arrs[side] is not None:
+                lat.set_boundary(side, arrs[side])
+            else:
+                lat.set_boundary(side, [p.wall[side]])
+        return lat
+
+    @property
+    def nx(self):
+        return self.desc.nx
+
+    @property
+    def ny(self):
+        return self.desc.ny
+
+    @property
+    def real_dtype(self):
+        return torch.float64 if self.desc.compute == C.F64 else torch.float32
+
+    def set_boundary(self, side: int, values):
+        v = np.ascontiguousarray(np.atleast_1d(np.asarray(values, dtype=np.float64)))
+        C.check(self.lib.btrt_set_boundary(self.handle, side,
+                                           v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), v.size))
+
+    def set_coeffs(self, coef: C.Coeffs):
+        self.coef = coef
+        C.check(self.lib.btrt_set_coeffs(self.handle, ctypes.byref(coef)))
+
+    # ------------------------------------------------------------ state
+    def init(self, phi0, t0: float = 0.0):
+        """f = f_eq(phi0).  phi0: numpy array (host) or torch tensor (host or device),
+        float64 or float32, shape (ny, nx)."""
+        if isinstance(phi0, np.ndarray):
+            a = np.ascontiguousarray(phi0)
+            if a.dtype not in (np.float64, np.float32):
+                a = a.astype(np.float64)
+            assert a.shape == (self.ny, self.nx)
+            dt = C.F64 if a.dtype == np.float64 else C.F32
+            C.check(self.lib.btrt_init_phi(self.handle, ctypes.c_void_p(a.ctypes.data), dt, 0, float(t0)))
+            return self
+        t = phi0.contiguous()
+        if t.dtype not in (torch.float64, torch.float32):
+            t = t.double()
+        assert tuple(t.shape) == (self.ny, self.nx)
+        dt = C.F64 if t.dtype == torch.float64 else C.F32
+        C.check(self.lib.btrt_init_phi(self.handle, ctypes.c_void_p(t.data_ptr()), dt,
+                                       1 if t.is_cuda else 0, float(t0)))
+        if t.is_cuda:
+            self._keep = t   # the copy is asynchronous on the stream
+        return self
+
+    def step(self, nsteps: int = 1):
+        C.check(self.lib.btrt_step(self.handle, int(nsteps)))
+        return self
+
+    def phi(self, out: Optional[torch.Tensor] = None, dtype=None) -> torch.Tensor:
+        """phi as a device tensor (asynchronous on the lattice stream)."""
+        dtype = dtype or self.real_dtype
+        if out is None:
+            out = torch.empty((self.ny, self.nx), dtype=dtype, device=self.device)
+        code = C.F64 if out.dtype == torch.float64 else C.F32
+        C.check(self.lib.btrt_read_phi(self.handle, ctypes.c_void_p(out.data_ptr()), code,
+                                       1 if out.is_cuda else 0))
+        return out
+
+    def phi_host(self, dtype=np.float64) -> np.ndarray:
+        out = np.empty((self.ny, self.nx), dtype=dtype)
+        code = C.F64 if out.dtype == np.float64 else C.F32
+        C.check(self.lib.btrt_read_phi(self.handle, ctypes.c_void_p(out.ctypes.data), code, 0))
+        return out
+
+    def read_f(self, x0=0, y0=0, w=None, h=None) -> np.ndarray:
+        """Post-collision populations of a window, FP64, shape (9, h, w)."""
+        w = self.nx - x0 if w is None else w
+        h = self.ny - y0 if h is None else h
+        out = np.empty((9, h, w), dtype=np.float64)
+        C.check(self.lib.btrt_read_f(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                     x0, y0, w, h))
+        return out
+
+    def mass(self) -> float:
+        v = ctypes.c_double()
+        C.check(self.lib.btrt_mass(self.handle, ctypes.byref(v)))
+        return v.value
+
+    def check(self) -> int:
+        """Raises BtrtError(EUNSTABLE) if the sweep has produced a non-finite phi."""
+        flags = ctypes.c_int32()
+        C.check(self.lib.btrt_check(self.handle, ctypes.byref(flags)))
+        return flags.value
+
+    def time(self):
+        s = ctypes.c_int64()
+        t = ctypes.c_double()
+        C.check(self.lib.btrt_get_time(self.handle, ctypes.byref(s), ctypes.byref(t)))
+        return s.value, t.value
+
+    def save(self) -> bytes:
+        n = self.lib.btrt_state_bytes(self.handle)
+        buf = ctypes.create_string_buffer(n)
+        C.check(self.lib.btrt_save(self.handle, buf, n))
+        return buf.raw
+
+    def load(self, state: bytes):
+        buf = ctypes.create_string_buffer(state, len(state))
+        C.check(self.lib.btrt_load(self.handle, buf, len(state)))
+        return self
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.btrt_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

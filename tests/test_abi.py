@@ -1,0 +1,89 @@
+"""Host-side checks of the C ABI that need no GPU: the library loads, exports every
+entry point declared in include/*.h, and rejects invalid descriptions before
+touching the device."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"\b(btrt_[a-z0-9_]+)\s*\(", text):
+            names.add(m.group(1))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1902_09813_gb300 as pkg
+    pkg.build()
+    from paper_1902_09813_gb300 import _capi
+    return _capi.load()
+
+
+def test_header_declares_entry_points():
+    names = _declared_symbols()
+    for expect in ("btrt_create", "btrt_step", "btrt_set_coeffs", "btrt_set_boundary",
+                   "btrt_init_phi", "btrt_read_phi", "btrt_mass", "btrt_workspace_bytes"):
+        assert expect in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_symbols() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_python_binding_covers_every_symbol():
+    from paper_1902_09813_gb300 import _capi
+    bound = {name for name, _, _ in _capi.SIGNATURES}
+    assert set(_declared_symbols()) <= bound
+
+
+def _desc(**kw):
+    from paper_1902_09813_gb300.lattice import grid_desc
+    base = dict(nx=64, ny=48, dx=1.0, dt=1.0, bc=(0, 0, 1, 1), compute="f64", storage="f64")
+    base.update(kw)
+    return grid_desc(**base)
+
+
+def test_workspace_layout(lib):
+    from paper_1902_09813_gb300 import _capi as C
+    d = _desc()
+    n = lib.btrt_workspace_bytes(ctypes.byref(d))
+    pitch = 64
+    fbuf = 9 * pitch * 48 * 8
+    assert n >= 2 * fbuf + pitch * 48 * 8
+    assert n % 256 == 0
+    d16 = _desc(compute="f32", storage="f16")
+    n16 = lib.btrt_workspace_bytes(ctypes.byref(d16))
+    assert n16 < n
+    assert C.OK == 0
+
+
+@pytest.mark.parametrize("kw", [dict(nx=2), dict(ny=70000), dict(bc=(0, 1, 0, 0)),
+                                dict(compute="f64", storage="f16"), dict(compute="f32", storage="f64"),
+                                dict(dx=0.0), dict(dt=-1.0)])
+def test_invalid_descriptions_rejected(lib, kw):
+    d = _desc(**kw)
+    assert lib.btrt_workspace_bytes(ctypes.byref(d)) == 0
+    assert len(lib.btrt_last_error()) > 0
+
+
+def test_create_rejects_null_workspace(lib):
+    from paper_1902_09813_gb300 import _capi as C
+    d = _desc()
+    h = ctypes.c_void_p()
+    assert lib.btrt_create(ctypes.byref(d), None, 1 << 30, None, ctypes.byref(h)) == C.EINVAL
+    assert not h.value
+
+
+def test_version(lib):
+    assert b"sm_103a" in lib.btrt_version()

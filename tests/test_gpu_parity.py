@@ -1,0 +1,211 @@
+"""GPU parity: the CUDA sweep (through the C ABI) against the FP64 oracle on the
+same seeded inputs.  Tolerances: relative L2 <= 1e-11 for FP64 compute and
+<= 2e-5 for FP32 compute with FP32 storage."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+from conftest import cpu_threads
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+TOL32 = 2e-5
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def _lattice(p, compute="f64", storage=None, **kw):
+    from paper_1902_09813_gb300 import Lattice
+    return Lattice.from_problem(p, compute=compute, storage=storage, **kw)
+
+
+def _gpu_run(p, nsteps, compute="f64", storage=None):
+    lat = _lattice(p, compute, storage)
+    lat.init(p.phi0(), t0=p.t0).step(nsteps)
+    return lat
+
+
+def _oracle_run(p, nsteps):
+    """Oracle after nsteps + 1 collisions: phi at t_n and the post-collision
+    populations at t_n (the state the GPU keeps)."""
+    lat = oracle.OracleLattice(p, nthreads=cpu_threads()).init()
+    lat.step(nsteps)
+    phi = lat.phi()
+    lat.step(1)
+    return phi, lat.fpost.copy()
+
+
+CASES = [
+    # (nx, ny, bc, nonlinear, source, steps)
+    (37, 29, (0, 0, 0, 0), True, "trig", 12),
+    (37, 29, (1, 1, 1, 1), True, "trig", 12),
+    (70, 65, (0, 0, 1, 1), True, "const", 10),
+    (70, 65, (1, 1, 0, 0), False, "none", 10),
+    (96, 40, (1, 1, 1, 1), False, "trig", 9),
+    (3, 3, (0, 0, 0, 0), True, "trig", 7),
+    (3, 3, (1, 1, 1, 1), True, "const", 7),
+    (5, 97, (1, 1, 0, 0), True, "trig", 6),
+    (130, 3, (0, 0, 1, 1), True, "none", 6),
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}-bc{''.join(map(str, c[2]))}-{c[4]}")
+def test_fp64_random_states(case):
+    nx, ny, bc, nonlin, src, steps = case
+    p = w.random_state_problem(nx, ny, seed=nx * 131 + ny, bc=bc, nonlinear=nonlin, source=src)
+    lat = _gpu_run(p, steps)
+    phi_ref, fpost_ref = _oracle_run(p, steps)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL64
+    f = lat.read_f()
+    assert _rel(f, fpost_ref) <= TOL64
+    assert np.max(np.abs(f - fpost_ref)) <= 1e-12 * np.max(np.abs(fpost_ref)) * 10
+
+
+def test_fp64_wall_arrays_and_time_factor():
+    """Per-node wall values carrying exp(lam t) (Table 3 setup, smaller grid)."""
+    p = w.linear_cde(n=40, alpha=0.01, u=(0.3, 0.3), c=5.0, t_end=0.1, walls=True)
+    lat = _gpu_run(p, p.nsteps)
+    phi_ref, _ = _oracle_run(p, p.nsteps)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL64
+
+
+def test_fp64_gaussian_hill_64():
+    """64 x 64 periodic Gaussian hill, dx = dt = 1, 500 steps."""
+    p = w.gaussian_hill()
+    lat = _gpu_run(p, p.nsteps)
+    phi_ref, _ = _oracle_run(p, p.nsteps)
+    got = lat.phi_host()
+    assert _rel(got, phi_ref) <= TOL64
+    # mass conservation to rounding on the periodic grid
+    m0 = p.phi0().sum()
+    assert abs(lat.mass() - m0) <= 1e-12 * abs(m0)
+    # same discretisation error against the closed form as the oracle
+    ex = w.gaussian_hill_exact(p, p.nsteps * p.dt)
+    assert w.gre(got, ex) == pytest.approx(w.gre(phi_ref, ex), rel=1e-9)
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_fp64_manufactured_solution(n):
+    """Full-tensor manufactured solution with HBB walls, diffusive scaling."""
+    p = w.mms_sinsin(n=n)
+    lat = _gpu_run(p, p.nsteps)
+    phi_ref, _ = _oracle_run(p, p.nsteps)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL64
+
+
+def test_fp64_nonlinear_modes_small():
+    """Nonlinear anisotropic modes workload at 96 x 96, 60 steps."""
+    p = w.nonlinear_modes(n=96, nsteps=60)
+    lat = _gpu_run(p, p.nsteps)
+    phi_ref, _ = _oracle_run(p, p.nsteps)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL64
+
+
+def test_fp64_steady_diffusion_exact():
+    """Half-way bounce-back steady state with Eq. 62 is exact on the GPU too."""
+    p = w.steady_diffusion(n=10, nsteps=30000)
+    lat = _gpu_run(p, p.nsteps)
+    assert w.gre(lat.phi_host(), w.steady_diffusion_exact(p)) < 1e-12
+
+
+@pytest.mark.parametrize("p_fn", [lambda: w.random_state_problem(70, 65, seed=9, bc=(1, 1, 0, 0)),
+                                  lambda: w.nonlinear_modes(n=96, nsteps=60),
+                                  lambda: w.mms_sinsin(n=64)],
+                         ids=["random", "nonlinear", "mms"])
+def test_fp32_compute_fp32_storage(p_fn):
+    p = p_fn()
+    steps = min(p.nsteps, 60)
+    lat = _gpu_run(p, steps, compute="f32", storage="f32")
+    phi_ref, _ = _oracle_run(p, steps)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL32
+
+
+def test_checkpoint_resume_bitwise():
+    p = w.random_state_problem(45, 33, seed=4, bc=(1, 1, 1, 1))
+    a = _gpu_run(p, 5)
+    state = a.save()
+    a.step(7)
+    b = _lattice(p)
+    b.load(state).step(7)
+    assert np.array_equal(a.phi_host(), b.phi_host())
+    assert np.array_equal(a.read_f(), b.read_f())
+    assert a.time() == b.time()
+
+
+def test_nonfinite_flag_reported():
+    """A NaN in host-provided initial data is reported as EUNSTABLE (no device fault)."""
+    from paper_1902_09813_gb300 import _capi as C
+    p = w.random_state_problem(20, 20, seed=1)
+    phi0 = p.phi0()
+    phi0[3, 4] = float("nan")
+    lat = _lattice(p)
+    lat.init(phi0).step(3)
+    with pytest.raises(C.BtrtError) as ei:
+        lat.check()
+    assert ei.value.code == C.EUNSTABLE
+    ok = _gpu_run(p, 3)
+    assert ok.check() == 0
+
+
+def _window(lat, ix, iy):
+    """3 x 3 x 9 window of post-collision populations around (ix, iy), periodically
+    wrapped (entries beyond a wall are never used by the oracle)."""
+    win = np.zeros((3, 3, 9))
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            x, y = (ix + dx) % lat.nx, (iy + dy) % lat.ny
+            win[dy + 1, dx + 1] = lat.read_f(x, y, 1, 1)[:, 0, 0]
+    return win
+
+
+@pytest.mark.parametrize("which", ["mms_8192", "nonlinear_8192"])
+def test_full_size_sampled_nodes(which):
+    """At the benchmark's full size and launch configuration: one more step of the
+    GPU sweep at sampled nodes (corners, edges, interior) equals the oracle's
+    single-node step from the GPU's own neighbourhood."""
+    import torch
+    if which == "mms_8192":
+        p = w.mms_sinsin(n=8192, nsteps=3)
+        compute = "f64"
+        tol = 1e-13
+    else:
+        p = w.nonlinear_modes(n=8192, nsteps=3)
+        compute = "f64"
+        tol = 1e-13
+    lat = _gpu_run(p, 3, compute=compute)
+    n = p.nx
+    pts = [(0, 0), (n - 1, 0), (0, n - 1), (n - 1, n - 1), (1, 0), (0, 5), (n - 1, 77),
+           (4095, 0), (4096, n - 1), (31, 32), (32, 31), (5000, 6000), (n - 2, n - 2)]
+    rng = np.random.default_rng(0)
+    pts += [tuple(int(v) for v in rng.integers(0, n, size=2)) for _ in range(6)]
+    wins = {pt: _window(lat, *pt) for pt in pts}
+    phi_dev = lat.phi()
+    phi_prev = {pt: float(phi_dev[pt[1], pt[0]].item()) for pt in pts}
+    _, t_now = lat.time()
+    lat.step(1)
+    phi_dev = lat.phi()
+    torch.cuda.synchronize()
+    for pt in pts:
+        fp, phi = oracle.node_step(p, wins[pt], pt[0], pt[1], phi_prev[pt], t_now + p.dt)
+        got = lat.read_f(pt[0], pt[1], 1, 1)[:, 0, 0]
+        assert np.allclose(got, fp, rtol=tol, atol=tol * np.abs(fp).max()), pt
+        assert float(phi_dev[pt[1], pt[0]].item()) == pytest.approx(phi, rel=tol, abs=tol)
+
+
+def test_full_size_mass_conservation_fp64():
+    """8192^2 periodic nonlinear workload: FP64 mass is conserved to rounding."""
+    p = w.nonlinear_modes(n=8192, nsteps=20)
+    lat = _lattice(p)
+    lat.init(p.phi0())
+    m0 = lat.mass()
+    lat.step(20)
+    m1 = lat.mass()
+    # both sums carry at most ~N eps |phi| ~ 1e-8 of rounding; a lost or duplicated
+    # population would move the mass by O(1e-3) or more
+    assert abs(m1 - m0) <= 1e-8
