@@ -150,6 +150,27 @@ btrt_status btrt_load(btrt_lattice L, const void *host_buf, size_t n);
 /* Release the host-side handle (the workspace stays with the caller). */
 btrt_status btrt_destroy(btrt_lattice L);
 
+/* FP64 sum of a phi plane that allocates no device memory -- for callers that
+ * cannot call cudaMalloc or lend a workspace: a serving process that reserves
+ * its whole device-memory budget at start-up and forbids later allocations, or a
+ * plug-in inside a host framework that owns the device allocator.  The paper has
+ * no counterpart; it is the btrt_mass reduction (same fixed order, same result)
+ * applied to any device plane.
+ *   phi_dev: device array of dtype BTRT_F64 or BTRT_F32, ny rows of `pitch`
+ *   elements, the first nx of each row summed; 1 <= nx, ny <= 65536, pitch >= nx;
+ *   larger planes are rejected with BTRT_EINVAL.  out_host: host double.
+ * The partial sums live in a fixed 8200-byte array of the library's own device
+ * memory (held by every GPU that loads the library until the process exits), not
+ * in caller memory; no cudaMalloc/cudaFree or allocating library call is made.
+ * The first call on a device looks up that array's device address for the
+ * current device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls on a device share the array: calls that overlap on the GPU
+ * (different streams, or host threads without ordering) race and may return
+ * wrong sums.  Enqueued on cuda_stream (NULL = default stream); synchronises it. */
+#define BTRT_PHI_SUM_STATIC_MAX_SIDE 65536
+btrt_status btrt_phi_sum_static(const void *phi_dev, int32_t dtype, int32_t nx, int32_t ny,
+                                int64_t pitch, void *cuda_stream, double *out_host);
+
 /* Thread-local description of the last error ("" if none). */
 const char *btrt_last_error(void);
 

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("btrt_save", ctypes.c_int, [_vp, _vp, _sz]),
     ("btrt_load", ctypes.c_int, [_vp, _vp, _sz]),
     ("btrt_destroy", ctypes.c_int, [_vp]),
+    ("btrt_phi_sum_static", ctypes.c_int, [_vp, _i32, _i32, _i32, _i64, _vp, _dp]),
     ("btrt_last_error", ctypes.c_char_p, []),
     ("btrt_version", ctypes.c_char_p, []),
 ]

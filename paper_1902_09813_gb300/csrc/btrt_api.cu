@@ -167,6 +167,15 @@ __global__ void __launch_bounds__(kRedThreads) sum_partials(const double *partia
 
 }  // namespace
 
+void btrt::set_last_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
 // ---------------------------------------------------------------- the lattice object
 struct btrt_lattice_s {
     btrt_grid_desc g;

@@ -14,4 +14,7 @@ namespace btrt {
 cudaError_t launch_sweep_f64(const SweepParams<double> &p, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepParams<float> &p, int storage, cudaStream_t s);
 
+// Record the thread-local message returned by btrt_last_error (printf format).
+void set_last_error(const char *fmt, ...);
+
 }  // namespace btrt
