@@ -67,7 +67,7 @@ typedef struct {
     int32_t storage;       /* population storage: F64 (compute F64 only), F32, F16, BF16*/
     double dx, dt;         /* physical spacing and time step (c = dx/dt, cs^2 = c^2/3)  */
     double x0, y0;         /* physical position of the lower-left domain corner         */
-    double phi_ref;        /* populations are stored as f_i - w_i phi_ref                */
+    double phi_ref;        /* F32/F16/BF16 storage holds f_i - w_i phi_ref (F64: unshifted) */
 } btrt_grid_desc;
 
 /* Coefficients of Eq. 1 and the relaxation parameters (physical units). */

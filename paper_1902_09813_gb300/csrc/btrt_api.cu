@@ -88,6 +88,9 @@ btrt_status check_desc(const btrt_grid_desc *g) {
         return fail(BTRT_EINVAL, "dx and dt must be positive and finite");
     if (!std::isfinite(g->phi_ref) || !std::isfinite(g->x0) || !std::isfinite(g->y0))
         return fail(BTRT_EINVAL, "phi_ref, x0, y0 must be finite");
+    const long long pitch = (long long)((g->nx + 63) / 64) * 64;
+    if (pitch * (long long)g->ny >= (1LL << 31))
+        return fail(BTRT_EINVAL, "grid %d x %d: a plane must hold fewer than 2^31 nodes", g->nx, g->ny);
     return BTRT_OK;
 }
 
@@ -211,13 +214,17 @@ void fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool first) {
     const btrt_grid_desc &g = L->g;
     const btrt_coeffs &c = L->c;
     std::memset(&p, 0, sizeof p);
-    p.fin = L->fbuf(L->cur);
-    p.fout = L->fbuf(first ? L->cur : 1 - L->cur);
+    const size_t sf = elem_size(g.storage);
+    unsigned char *bin = static_cast<unsigned char *>(L->fbuf(L->cur));
+    unsigned char *bout = static_cast<unsigned char *>(L->fbuf(first ? L->cur : 1 - L->cur));
+    for (int i = 0; i < 9; ++i) {
+        p.fin[i] = bin + (size_t)i * L->lay.plane * sf;
+        p.fout[i] = bout + (size_t)i * L->lay.plane * sf;
+    }
     p.phi = L->phi<Real>();
     p.nx = g.nx;
     p.ny = g.ny;
-    p.pitch = L->lay.pitch;
-    p.plane = L->lay.plane;
+    p.pitch = (int)L->lay.pitch;
     p.hbb_x = g.bc[0] == BTRT_BC_HBB;
     p.hbb_y = g.bc[2] == BTRT_BC_HBB;
     const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
@@ -262,17 +269,48 @@ void fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool first) {
     }
     p.first = first ? 1 : 0;
     p.flags = L->flags();
+    // constants of the linear fast path (B = u phi, C = phi, constant A)
+    {
+        const double k0 = c.k0, K1xx = L->K1[0], K1xy = L->K1[1], K1yy = L->K1[2];
+        const double kap = 4.5 * (L->k2 - k0);
+        const double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w5 = 1.0 / 36.0;
+        LinearConsts<Real> &q = p.lin;
+        q.ux = (Real)L->ux;
+        q.uy = (Real)L->uy;
+        q.ux3 = (Real)(3.0 * k0 * L->ux);
+        q.uy3 = (Real)(3.0 * k0 * L->uy);
+        q.Qxx = (Real)(3.0 * (K1xx - k0));
+        q.Qxy = (Real)(3.0 * K1xy);
+        q.Qyy = (Real)(3.0 * (K1yy - k0));
+        q.gx = (Real)(3.0 * ((1.0 - 0.5 * K1xx) * L->ux - 0.5 * K1xy * L->uy));
+        q.gy = (Real)(3.0 * (-0.5 * K1xy * L->ux + (1.0 - 0.5 * K1yy) * L->uy));
+        q.k0 = (Real)k0;
+        q.c0 = (Real)(w0 * kap / 3.0);
+        q.k6 = (Real)(-w1 * kap / 6.0);
+        q.k6x3 = (Real)(-w1 * kap / 2.0);
+        q.kd = (Real)(-2.0 * w5 * kap / 3.0);
+        q.kdx3 = (Real)(-2.0 * w5 * kap);
+    }
+}
+
+// Which compiled variant of the sweep serves these coefficients.
+int sweep_mode(btrt_lattice L) {
+    const btrt_coeffs &c = L->c;
+    const bool linear = c.b2 == 0.0 && c.c3 == 0.0 && c.a2 == 0.0;
+    if (!linear) return kGeneral;
+    if (L->g.compute == BTRT_F64 && c.k0 == 1.0) return kLinearK0One;
+    return kLinear;
 }
 
 btrt_status launch(btrt_lattice L, int64_t n, bool first) {
     if (L->g.compute == BTRT_F64) {
         SweepParams<double> p;
         fill_params(L, p, n, first);
-        CUDA_TRY(launch_sweep_f64(p, L->stream));
+        CUDA_TRY(launch_sweep_f64(p, sweep_mode(L), L->stream));
     } else {
         SweepParams<float> p;
         fill_params(L, p, n, first);
-        CUDA_TRY(launch_sweep_f32(p, L->g.storage, L->stream));
+        CUDA_TRY(launch_sweep_f32(p, L->g.storage, sweep_mode(L), L->stream));
     }
     return BTRT_OK;
 }
@@ -564,8 +602,8 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
                                    cudaMemcpyDeviceToHost, L->stream));
         CUDA_TRY(cudaStreamSynchronize(L->stream));
         // the stored values are rounded from Real = f - w_i phi_ref in the compute precision
-        const double shift = g.compute == BTRT_F64 ? wts[i] * g.phi_ref
-                                                   : (double)(float)(wts[i] * g.phi_ref);
+        // FP64 storage is never shifted; FP32 compute shifts by (float)(w_i phi_ref)
+        const double shift = g.storage == BTRT_F64 ? 0.0 : (double)(float)(wts[i] * g.phi_ref);
         for (size_t k = 0; k < (size_t)w * h; ++k) {
             double v;
             if (g.storage == BTRT_F64) std::memcpy(&v, &raw[k * 8], 8);

@@ -34,15 +34,27 @@ template <> struct Storage<__nv_bfloat16> {
 };
 
 // ---------------------------------------------------------------- parameters
+// Per-lattice constants of the linear fast path (see collide_linear).
+template <typename Real>
+struct LinearConsts {
+    Real ux, uy;           // u^ (lattice units)
+    Real ux3, uy3;         // 3 k0 u^
+    Real Qxx, Qxy, Qyy;    // 3 (K1 - k0 I)
+    Real gx, gy;           // 3 (I - K1/2) u^
+    Real k0;
+    Real c0;               // w0 kap / 3,           kap = (9/2)(k2 - k0)
+    Real k6, k6x3;         // -w1 kap / 6, 3 k6
+    Real kd, kdx3;         // -(2/3) w5 kap, 3 kd
+};
+
 // Everything one launch of the sweep needs, passed by value.
 template <typename Real>
 struct SweepParams {
-    const void *fin;       // post-collision populations at step n-1 (9 planes)
-    void *fout;            // post-collision populations at step n
+    const void *fin[9];    // post-collision populations at step n-1, one plane per direction
+    void *fout[9];         // post-collision populations at step n
     Real *phi;             // phi plane: phi^{n-1} on entry, phi^n on exit
     int nx, ny;
-    long long pitch;       // elements between rows
-    long long plane;       // elements between population planes
+    int pitch;             // elements between rows; ny * pitch < 2^31
     int hbb_x, hbb_y;      // 1: bounce-back walls on that axis, 0: periodic
     Real wref[9];          // w_i phi_ref (storage shift)
 
@@ -69,6 +81,7 @@ struct SweepParams {
 
     int first;             // 1: initialisation (f = f_eq(phi), no streaming)
     int *flags;            // bit 0: non-finite phi
+    LinearConsts<Real> lin;
 };
 
 // D2Q9 velocity components and opposite directions, order of the rows of Eq. 85.
@@ -93,6 +106,11 @@ __device__ __forceinline__ Real wall_value(const SweepParams<Real> &p, int side,
     const Real *a = p.wall_arr[side];
     return (a ? a[idx] : p.wall_const[side]) * p.wall_fac;
 }
+
+// Division: IEEE in FP64; the fast reciprocal-based quotient (about 2 ulp) in FP32,
+// well inside the FP32 path's tolerance.
+__device__ __forceinline__ double quot(double a, double b) { return a / b; }
+__device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
 
 // ---------------------------------------------------------------- the collision
 // Moment-space form of Eq. 6 (Eqs. 94, 95, 99 with K2 = k2 Ihat), expanded back
@@ -135,14 +153,14 @@ __device__ __forceinline__ void collide(const SweepParams<Real> &p, Real (&f)[9]
             K1xy = (Real)(-dxy * id);
             K1yy = (Real)(dxx * id);
         } else {
-            const Real id = Real(1) / det;
+            const Real id = quot(Real(1), det);
             K1xx = myy * id;
             K1xy = -mxy * id;
             K1yy = mxx * id;
         }
         if (p.k2_hbb) {
-            const Real k1 = Real(2) / tr;               // 1/k1_eff = tr(K1^-1)/2
-            k2 = Real(8) * (k1 - Real(2)) / (Real(3) * (k1 - Real(4)));
+            // Eq. 62 at k1_eff = 2/tr:  k2 = 8 (k1 - 2) / (3 (k1 - 4)) = (8/3)(tr - 1) / (2 tr - 1)
+            k2 = quot(Real(8) / Real(3) * (tr - Real(1)), Real(2) * tr - Real(1));
         } else {
             k2 = p.k2c;
         }
@@ -215,29 +233,123 @@ __device__ __forceinline__ void equilibrium(const SweepParams<Real> &p, Real phi
     f[8] = w5 * (a5 + Bx - By);
 }
 
-// ---------------------------------------------------------------- the sweep kernel
-template <typename Real, typename S>
-__global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams<Real> p) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= p.nx || y >= p.ny) return;
-    const long long node = (long long)y * p.pitch + x;
-    const S *__restrict__ fin = static_cast<const S *>(p.fin);
-    S *__restrict__ fout = static_cast<S *>(p.fout);
-
-    Real f[9];
-    Real phi_prev = p.phi[node];
-    Real phi;
-    if (p.first) {
-        phi = phi_prev;
-        equilibrium(p, phi, f);
+// ---------------------------------------------------------------- linear fast path
+// For B = u phi, C = phi and constant A (so constant K1 and k2) the collision
+// needs far fewer operations: the equilibrium moments are linear in phi and the
+// weights fold into per-lattice constants (LinearConsts, computed on the host in
+// FP64).  With K2 = k2 Ihat and sigma = nxx + nyy, delta = nxx - nyy:
+//   w_i (a - (9/2)(k2 - k0) H_i) = w_i a + c0 sigma            (rest)
+//                                   w_i a + k6 (sigma +- 3 delta)   (axes)
+//                                   w_i a + kd (sigma +- 3 nxy)     (diagonals)
+// and the first-order and correction terms combine into V = 3(k0 B - (K1 - k0 I) M1neq
+// + (I - K1/2) u dphi).
+template <typename Real, bool K0ONE>
+__device__ __forceinline__ Real collide_linear(const SweepParams<Real> &p, Real (&f)[9], Real phi_prev,
+                                               Real src_spatial, bool first) {
+    const LinearConsts<Real> &L = p.lin;
+    const Real a13 = f[1] + f[3], a24 = f[2] + f[4];
+    const Real s57 = f[5] + f[7], s68 = f[6] + f[8];
+    const Real sd = s57 + s68;
+    const Real phi = (f[0] + sd) + (a13 + a24);
+    const Real b13 = f[1] - f[3], b24 = f[2] - f[4];
+    const Real d57 = f[5] - f[7], d68 = f[6] - f[8];
+    const Real jx = b13 + (d57 - d68);
+    const Real jy = b24 + (d57 + d68);
+    const Real pxy = s57 - s68;
+    const Real sig = fma(Real(-2) / Real(3), phi, fma(Real(2), sd, a13 + a24));
+    const Real del = a13 - a24;
+    const Real mx = fma(-L.ux, phi, jx), my = fma(-L.uy, phi, jy);
+    const Real dphi = first ? Real(0) : phi - phi_prev;
+    const Real Vx = fma(L.gx, dphi, fma(L.ux3, phi, -fma(L.Qxy, my, L.Qxx * mx)));
+    const Real Vy = fma(L.gy, dphi, fma(L.uy3, phi, -fma(L.Qyy, my, L.Qxy * mx)));
+    const Real a = K0ONE ? fma(p.src_val, src_spatial, phi) : fma(p.src_val, src_spatial, L.k0 * phi);
+    const Real w0 = Real(4) / Real(9), w1 = Real(1) / Real(9), w5 = Real(1) / Real(36);
+    Real r[9];
+    r[0] = fma(L.c0, sig, w0 * a);
+    const Real k6s = L.k6 * sig;
+    const Real hx = fma(L.k6x3, del, k6s), hy = fma(-L.k6x3, del, k6s);
+    const Real wa1 = w1 * a;
+    const Real A1 = wa1 + hx, A2 = wa1 + hy;
+    r[1] = fma(w1, Vx, A1);
+    r[3] = fma(-w1, Vx, A1);
+    r[2] = fma(w1, Vy, A2);
+    r[4] = fma(-w1, Vy, A2);
+    const Real kds = L.kd * sig;
+    const Real hp = fma(L.kdx3, pxy, kds), hm = fma(-L.kdx3, pxy, kds);
+    const Real wa5 = w5 * a;
+    const Real P = wa5 + hp, M = wa5 + hm;
+    const Real Vp = Vx + Vy, Vm = Vx - Vy;
+    r[5] = fma(w5, Vp, P);
+    r[7] = fma(-w5, Vp, P);
+    r[6] = fma(-w5, Vm, M);
+    r[8] = fma(w5, Vm, M);
+    if (K0ONE) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = r[i];
     } else {
-        const bool interior = (x > 0) && (x < p.nx - 1) && (y > 0) && (y < p.ny - 1);
-        if (interior) {
+        const Real om = Real(1) - L.k0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = fma(om, f[i], r[i]);
+    }
+    return phi;
+}
+
+// Non-finite test without touching the FP64 pipe: exponent field all ones.
+__device__ __forceinline__ bool not_finite(double v) {
+    return (__double2hiint(v) & 0x7ff00000) == 0x7ff00000;
+}
+__device__ __forceinline__ bool not_finite(float v) {
+    return (__float_as_int(v) & 0x7f800000) == 0x7f800000;
+}
+
+// ---------------------------------------------------------------- the sweep kernel
+// MODE: kGeneral (every coefficient family, runtime flags), kLinear (B = u phi,
+// C = phi, A constant; any k0), kLinearK0One (the same with k0 = 1).
+enum { kGeneral = 0, kLinear = 1, kLinearK0One = 2 };
+// Nodes per thread of the single-lattice sweep: the FP64 sweep is ALU-bound and
+// amortises per-thread set-up over a column of 4 nodes; the HBM-bound FP32
+// sweeps keep one node per thread for more loads in flight.
+template <typename Real> struct RowsPerThread { static constexpr int value = 1; };
+template <> struct RowsPerThread<double> { static constexpr int value = 4; };
+
+template <typename S> struct Shifted { static constexpr bool value = true; };
+template <> struct Shifted<double> { static constexpr bool value = false; };  // FP64 storage is never shifted
+
+// Global loads of data that other SMs rewrite during a persistent launch go
+// through L2 only (L1 is not coherent across SMs); ordinary loads otherwise.
+template <bool L2ONLY, typename T>
+__device__ __forceinline__ T ldg(const T *ptr) {
+    if (L2ONLY) return __ldcg(ptr);
+    return *ptr;
+}
+
+// Sweep `nrows` nodes of column x, rows ybase, ybase + ystride, ...: pull,
+// collide, write back.  Returns the sum over those nodes of (phi^n - phi^{n-1})^2
+// when want_resid is set (steady-state residual), else 0.
+template <typename Real, typename S, int MODE, bool L2ONLY>
+__device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, int ybase, int ystride,
+                                             int nrows, bool want_resid) {
+    constexpr bool kShift = Shifted<S>::value;
+    Real xs = Real(0), xc = Real(0);
+    if (p.src_kind == 2) { xs = p.Xs[x]; xc = p.Xc[x]; }
+    const bool x_inner = (x > 0) && (x < p.nx - 1);
+    double resid = 0.0;
+
+#pragma unroll 1
+    for (int r = 0; r < nrows; ++r) {
+        const int y = ybase + r * ystride;
+        if (y >= p.ny) break;
+        const int node = y * p.pitch + x;
+        Real f[9];
+        const Real phi_prev = ldg<L2ONLY>(p.phi + node);
+        if (p.first) {
+            equilibrium(p, phi_prev, f);
+        } else if (x_inner && y > 0 && y < p.ny - 1) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const long long src = node - (long long)ey_of(i) * p.pitch - ex_of(i);
-                f[i] = Storage<S>::load(fin[(long long)i * p.plane + src]) + p.wref[i];
+                const S *plane = static_cast<const S *>(p.fin[i]);
+                f[i] = Storage<S>::load(ldg<L2ONLY>(plane + (node - ey_of(i) * p.pitch - ex_of(i))));
+                if (kShift) f[i] += p.wref[i];
             }
         } else {
 #pragma unroll
@@ -249,8 +361,9 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
                 if (sy < 0) { if (p.hbb_y) wy = 2; else sy += p.ny; }
                 if (sy >= p.ny) { if (p.hbb_y) wy = 3; else sy -= p.ny; }
                 if (wx < 0 && wy < 0) {
-                    const long long src = (long long)sy * p.pitch + sx;
-                    f[i] = Storage<S>::load(fin[(long long)i * p.plane + src]) + p.wref[i];
+                    const S *plane = static_cast<const S *>(p.fin[i]);
+                    f[i] = Storage<S>::load(ldg<L2ONLY>(plane + (sy * p.pitch + sx)));
+                    if (kShift) f[i] += p.wref[i];
                 } else {
                     // the node's own population leaving towards the wall (direction opp(i))
                     // comes back as direction i (Eqs. 54-56)
@@ -262,25 +375,51 @@ __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ Swee
                         phi_w = wall_value(p, wy, x);
                     else
                         phi_w = wall_value(p, wx, y);
-                    const Real fo = Storage<S>::load(fin[(long long)o * p.plane + node]) + p.wref[o];
+                    const S *oplane = static_cast<const S *>(p.fin[o]);
+                    Real fo = Storage<S>::load(ldg<L2ONLY>(oplane + node));
+                    if (kShift) fo += p.wref[o];
                     f[i] = -fo + wall_term(p, o, phi_w);
                 }
             }
         }
-        phi = ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-    }
 
-    Real src = Real(0);
-    if (p.src_kind == 1) src = Real(1);
-    else if (p.src_kind == 2) src = p.Xs[x] * p.Ys[y] + p.Xc[x] * p.Yc[y];
+        Real src = Real(0);
+        if (p.src_kind == 1) src = Real(1);
+        else if (p.src_kind == 2) src = fma(xs, p.Ys[y], xc * p.Yc[y]);
 
-    collide(p, f, phi, p.first ? phi : phi_prev, src);
+        Real phi;
+        if (MODE == kGeneral) {
+            phi = p.first ? phi_prev
+                          : ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
+            collide(p, f, phi, p.first ? phi : phi_prev, src);
+        } else {
+            phi = collide_linear<Real, MODE == kLinearK0One>(p, f, phi_prev, src, p.first != 0);
+        }
 
 #pragma unroll
-    for (int i = 0; i < 9; ++i)
-        fout[(long long)i * p.plane + node] = Storage<S>::pack(f[i] - p.wref[i]);
-    p.phi[node] = phi;
-    if (!isfinite(phi)) atomicOr(p.flags, 1);
+        for (int i = 0; i < 9; ++i) {
+            S *plane = static_cast<S *>(p.fout[i]);
+            plane[node] = Storage<S>::pack(kShift ? f[i] - p.wref[i] : f[i]);
+        }
+        p.phi[node] = phi;
+        if (not_finite(phi)) atomicOr(p.flags, 1);
+        if (want_resid) {
+            const double d = (double)phi - (double)phi_prev;
+            resid = fma(d, d, resid);
+        }
+    }
+    return resid;
+}
+
+// One sweep of one lattice: 32 x 8 threads per block, each thread sweeps
+// RowsPerThread nodes of its column, rows blockDim.y apart.
+template <typename Real, typename S, int MODE>
+__global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams<Real> p) {
+    constexpr int R = RowsPerThread<Real>::value;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= p.nx) return;
+    const int ybase = blockIdx.y * blockDim.y * R + threadIdx.y;
+    sweep_rows<Real, S, MODE, false>(p, x, ybase, blockDim.y, R, false);
 }
 
 }  // namespace btrt
