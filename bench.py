@@ -43,6 +43,35 @@ def _peaks():
         return 6800.0, "fallback"
 
 
+# FP64 operations (add, mul or fma, one each) per node of the FP64 sweep, counted
+# from the kernel source (collide_linear with k0 = 1 plus the trig source term).
+FP64_OPS_PER_UPDATE_LINEAR = 59
+# GB300 FP64 peak: 1.25 TFLOP/s nominal (profiling recipe) = 0.625 T FMA/s, i.e.
+# 0.625 T FP64 operations/s when every add, mul or fma takes one lane slot.
+FP64_PEAK_TOPS = 0.625
+# DRAM bytes per node of one FP64 sweep launch measured by ncu
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the same kernel; None when
+# the kernel changed after the capture.
+FP64_TRAFFIC_PER_NODE = None
+
+
+def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
+    hbm = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peak_hbm, "unit": "GB/s",
+           "frac": round(achieved_gbs / peak_hbm, 4), "peak_kind": peak_kind,
+           "bytes_per_update": BYTES_PER_UPDATE[args.storage]}
+    kernel = f"sweep_kernel<{args.compute},{args.storage}>"
+    if args.compute != "f64" or args.workload != "mms":
+        return dict(hbm, traffic=None, kernel=kernel)
+    # the FP64 sweep is bound by GB300's FP64 pipe, not by HBM
+    tops = FP64_OPS_PER_UPDATE_LINEAR * nodes / t_launch / 1e12
+    traffic = None if FP64_TRAFFIC_PER_NODE is None else round(FP64_TRAFFIC_PER_NODE * nodes)
+    return {"bound": "alu", "achieved": round(tops, 4), "peak": FP64_PEAK_TOPS,
+            "unit": "T FP64 op/s", "frac": round(tops / FP64_PEAK_TOPS, 4), "traffic": traffic,
+            "ops_per_update": FP64_OPS_PER_UPDATE_LINEAR,
+            "peak_kind": "recipe nominal FP64 1.25 TFLOP/s = 0.625 T op/s (one-off probe measured 1.20)",
+            "kernel": kernel, "hbm_view": hbm}
+
+
 def _cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -192,6 +221,12 @@ def run_gpu(args):
         e2e_mlups = ws * nodes * args.steps / float(e2e_t.item()) / 1e6
 
     extra = {}
+    if not args.no_batched:
+        del lat
+        torch.cuda.empty_cache()
+        extra["batched"] = run_batched(args)
+    if not args.no_serving:
+        extra["serving"] = run_serving(args)
     if rank == 0 and not args.no_cpu_baseline:
         extra["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
@@ -203,11 +238,7 @@ def run_gpu(args):
             "config": {"workload": desc, "nx": p.nx, "ny": p.ny,
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": f"inputs {alg_bytes / 2 / 1e9:.2f} GB read per step >> L2, no flush"},
-            "roofline": {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peak_hbm,
-                         "unit": "GB/s", "frac": round(achieved_gbs / peak_hbm, 4),
-                         "traffic": None, "peak_kind": peak_kind,
-                         "bytes_per_update": BYTES_PER_UPDATE[args.storage],
-                         "kernel": f"sweep_kernel<{args.compute},{args.storage}>"},
+            "roofline": roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind),
             "e2e": None if e2e_mlups is None else {
                 "value": round(e2e_mlups, 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(8 * nodes / args.steps),
@@ -220,6 +251,108 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------- batched
+def run_batched(args, count=512, nsteps=2000, seed=0, plain=True):
+    """Config-4 style batch: `count` instances, side log-uniform in [32, 1024], half
+    periodic Gaussian hills / half HBB manufactured solutions, FP32 compute + FP16
+    shifted storage, `nsteps` steps each: one persistent launch per call (CUDA
+    graph) with an autotuned tile shape, against plain per-instance launches."""
+    import torch
+
+    import workloads as w
+    from paper_1902_09813_gb300 import Batch, Lattice
+
+    probs = w.batched_instances(count=count, seed=seed, nsteps=nsteps)
+    stream = torch.cuda.current_stream()
+    phi0s = [p.phi0() for p in probs]
+    for p, a in zip(probs, phi0s):
+        p.phi_ref = float(a.mean())
+    nodes = sum(p.nx * p.ny for p in probs)
+
+    def make():
+        lats = []
+        for p, a in zip(probs, phi0s):
+            lat = Lattice.from_problem(p, compute="f32", storage="f16", stream=stream)
+            lat.init(a)
+            lats.append(lat)
+        return lats
+
+    # batched: autotune on a throw-away copy (its steps are real steps), then time
+    lats = make()
+    b = Batch(lats, stream=stream)
+    shape = b.autotune(steps_per_trial=3)
+    b.close()
+    del lats, b
+    lats = make()
+    b = Batch(lats, stream=stream)
+    b.set_tiles(*shape)
+    b.step(2)                      # graph capture + warm-up, not timed
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.step(nsteps - 2)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    b.check()
+    t_batch = ev0.elapsed_time(ev1) * 1e-3 * nsteps / (nsteps - 2)
+    batched = [l.phi_host() for l in lats[:8]]
+    b.close()
+    del lats, b
+
+    if not plain:
+        return {"instances": count, "steps": nsteps, "nodes": nodes, "tile": list(shape),
+                "batched_s": round(t_batch, 4),
+                "batched_mlups": round(nodes * nsteps / t_batch / 1e6, 1)}
+    # plain: every instance alone, one launch per step, sequentially
+    lats = make()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for l in lats:
+        l.step(nsteps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    t_plain = ev0.elapsed_time(ev1) * 1e-3
+    same = all(np.array_equal(a, l.phi_host()) for a, l in zip(batched, lats[:8]))
+    del lats
+    return {"instances": count, "steps": nsteps, "nodes": nodes, "tile": list(shape),
+            "batched_s": round(t_batch, 4), "plain_s": round(t_plain, 4),
+            "batched_solves_per_s": round(count / t_batch, 2),
+            "plain_solves_per_s": round(count / t_plain, 2),
+            "batched_mlups": round(nodes * nsteps / t_batch / 1e6, 1),
+            "plain_mlups": round(nodes * nsteps / t_plain / 1e6, 1),
+            "speedup": round(t_plain / t_batch, 3),
+            "batched_equals_plain_bitwise_first8": same,
+            "launch": "step-per-launch graph" if shape[3] else "persistent cooperative",
+            "dtype": "f32 compute, f16 storage"}
+
+
+# ---------------------------------------------------------------------------- serving
+def run_serving(args, rates=(100.0, 500.0, 2000.0), count=96, seed=1):
+    """Config-5 style serving: Poisson arrivals of batched-config instances, each
+    run to ||phi^{n+1} - phi^n||_2 < 1e-8 (checked every 100 steps) or 20000 steps,
+    150 GB admission budget; continuous batching vs sequential plain solves."""
+    import workloads as w
+    from paper_1902_09813_gb300.serve import Server, poisson_trace, serve_sequential, summarize
+
+    probs = w.batched_instances(count=count, seed=seed, nsteps=0)
+    for p in probs:
+        p.phi_ref = float(p.phi0().mean())
+    out = {"requests_per_rate": count, "slice_steps": 100, "max_steps": 20000, "tol": 1e-8,
+           "budget_gb": 150, "dtype": "f32 compute, f16 storage", "rates": {}}
+    for lam in rates:
+        trace = poisson_trace(probs, rate=lam, seed=seed)
+        srv = Server(budget_bytes=150e9, slice_steps=100, max_steps=20000, tol=1e-8)
+        res = srv.run(trace)
+        out["rates"][str(int(lam))] = dict(summarize(res), peak_active=srv.stats["peak_active"],
+                                           slices=srv.stats["slices"])
+    # plain sequential baseline on the first requests of the highest-rate trace
+    nseq = min(count, args.serve_seq)
+    trace = poisson_trace(probs[:nseq], rate=max(rates), seed=seed)
+    seq = serve_sequential(trace, slice_steps=100, max_steps=20000, tol=1e-8)
+    out["sequential_plain"] = summarize(seq)
+    return out
 
 
 # ---------------------------------------------------------------------------- CPU oracle
@@ -278,6 +411,13 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batched_only(args):
+    import torch
+    torch.cuda.set_device(0)
+    print(json.dumps({"batched": run_batched(args, count=args.batch_count, nsteps=args.batch_steps,
+                                             plain=False)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -286,6 +426,13 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-seq", type=int, default=48)
+    ap.add_argument("--batched-only", action="store_true",
+                    help="only the batched persistent launch (for profiling small batches)")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--workload", default="mms", choices=["mms", "nonlinear"])
     ap.add_argument("--n", type=int, default=N_MAIN)
     ap.add_argument("--compute", default="f64", choices=["f64", "f32"])
@@ -297,6 +444,8 @@ def main():
         args.storage = args.compute
     if args.impl == "reference":
         run_reference(args)
+    elif args.batched_only:
+        run_batched_only(args)
     else:
         run_gpu(args)
 

@@ -61,7 +61,7 @@ typedef struct btrt_lattice_s *btrt_lattice;
 
 /* Grid, number formats and the shift of reduced-precision storage. */
 typedef struct {
-    int32_t nx, ny;        /* nodes; 3 <= nx, ny <= 65536                               */
+    int32_t nx, ny;        /* nodes; 3 <= nx, ny <= 65536 and 9 ny roundup(nx, 64) < 2^31 */
     int32_t bc[4];         /* BTRT_BC_* for sides x-, x+, y-, y+; opposite sides match  */
     int32_t compute;       /* BTRT_F64 or BTRT_F32: arithmetic of the sweep             */
     int32_t storage;       /* population storage: F64 (compute F64 only), F32, F16, BF16*/
@@ -119,6 +119,11 @@ btrt_status btrt_init_phi(btrt_lattice L, const void *phi0, int32_t dtype, int32
 /* Advance nsteps time steps (asynchronous on the lattice's stream). */
 btrt_status btrt_step(btrt_lattice L, int64_t nsteps);
 
+/* Advance nsteps >= 1 steps and return ||phi^n - phi^{n-1}||_2 of the last one
+ * (FP64, fixed reduction order; the steady-state measure of the serving loop,
+ * cf. Eq. 64).  Synchronises. */
+btrt_status btrt_step_residual(btrt_lattice L, int64_t nsteps, double *residual);
+
 /* Copy phi (nx*ny values, dtype F64 or F32) to host (on_device = 0, synchronises)
  * or device memory (on_device = 1, asynchronous). */
 btrt_status btrt_read_phi(btrt_lattice L, void *dst, int32_t dtype, int32_t on_device);
@@ -147,8 +152,63 @@ size_t btrt_state_bytes(btrt_lattice L);
 btrt_status btrt_save(btrt_lattice L, void *host_buf, size_t n);
 btrt_status btrt_load(btrt_lattice L, const void *host_buf, size_t n);
 
-/* Release the host-side handle (the workspace stays with the caller). */
+/* Release the host-side handle (the workspace stays with the caller).
+ * BTRT_ESTATE while a batch still references the lattice. */
 btrt_status btrt_destroy(btrt_lattice L);
+
+/* ---------------------------------------------------------------- batches
+ * Many independent lattices of uneven size advanced together: one persistent
+ * cooperative kernel per call (all members, all tiles, every step; a bounded
+ * grid barrier between steps), or one launch per step over all tiles, either
+ * captured in a CUDA graph per (steps, residual) pair and replayed.  Members keep their own workspaces and stay usable with the
+ * single-lattice calls; they must be initialised, share compute and storage
+ * formats and outlive the batch.  Each member's results are bitwise identical to
+ * stepping it alone (the per-node arithmetic does not depend on the tiling). */
+typedef struct btrt_batch_s *btrt_batch;
+
+/* Device workspace (descriptors, tile table, reduction scratch) for a batch of
+ * these members; 0 if the member list is invalid. */
+size_t btrt_batch_workspace_bytes(const btrt_lattice *members, int32_t n);
+
+/* Create a batch over n members in a caller-owned, 256-byte aligned device
+ * workspace.  Synchronises the members' streams; the batch's own work goes to
+ * cuda_stream.  Requires cooperative-launch support. */
+btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_workspace, size_t bytes,
+                              void *cuda_stream, btrt_batch *out);
+
+/* Tile shape: block_x x block_y threads, each sweeping `rows` nodes of its
+ * column.  Candidates: 32x8x1, 32x8x2, 32x8x4, 64x4x1, 64x4x2, 32x4x2.
+ * per_step_launch = 0: persistent launch per call; 1: one launch per step. */
+btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y, int32_t rows,
+                                 int32_t per_step_launch);
+
+/* Pick the fastest candidate (6 tile shapes x 2 launch forms) by timing
+ * steps_per_trial steps of each after one warm-up step.  These are real steps:
+ * on a first tuning every member advances by 12 x (steps_per_trial + 1) steps.
+ * The choice is cached per (members, total nodes, formats) in the process and
+ * reused without timing.  Writes the choice (any pointer may be NULL). */
+btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *block_x, int32_t *block_y,
+                                int32_t *rows, int32_t *per_step_launch);
+
+/* Advance every member nsteps steps (asynchronous; one launch or graph per 4096
+ * steps).  want_residual != 0: also compute each member's ||phi^n - phi^{n-1}||_2
+ * at the last step (fixed order). */
+btrt_status btrt_batch_step(btrt_batch B, int64_t nsteps, int32_t want_residual);
+
+/* Residuals of the last step with want_residual, one per member (host, synchronises). */
+btrt_status btrt_batch_residuals(btrt_batch B, double *out_host);
+
+/* flags: bit 0 non-finite phi in some member, bit 1 a barrier wait gave up.
+ * Returns BTRT_ETIMEOUT or BTRT_EUNSTABLE accordingly.  Synchronises. */
+btrt_status btrt_batch_check(btrt_batch B, int32_t *flags);
+
+/* Bound of every grid-barrier wait, in polls of about 0.1 us (default 2^24).  A
+ * wait that reaches it raises flag bit 1 and ends the launch early.
+ * never_release != 0 makes every barrier unreachable (for testing the timeout). */
+btrt_status btrt_batch_set_wait_limit(btrt_batch B, uint64_t polls, int32_t never_release);
+
+/* Release the batch (synchronises its stream; members stay with the caller). */
+btrt_status btrt_batch_destroy(btrt_batch B);
 
 /* FP64 sum of a phi plane that allocates no device memory -- for callers that
  * cannot call cudaMalloc or lend a workspace: a serving process that reserves

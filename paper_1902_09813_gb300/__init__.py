@@ -10,7 +10,7 @@ from .build import build  # noqa: F401
 
 
 def __getattr__(name):
-    if name in ("Lattice", "grid_desc", "coeffs", "workspace_bytes"):
+    if name in ("Lattice", "Batch", "grid_desc", "coeffs", "workspace_bytes"):
         from . import lattice
         return getattr(lattice, name)
     raise AttributeError(name)

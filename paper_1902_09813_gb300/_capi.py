@@ -53,6 +53,7 @@ SIGNATURES = [
     ("btrt_set_boundary", ctypes.c_int, [_vp, _i32, _dp, _i32]),
     ("btrt_init_phi", ctypes.c_int, [_vp, _vp, _i32, _i32, ctypes.c_double]),
     ("btrt_step", ctypes.c_int, [_vp, _i64]),
+    ("btrt_step_residual", ctypes.c_int, [_vp, _i64, _dp]),
     ("btrt_read_phi", ctypes.c_int, [_vp, _vp, _i32, _i32]),
     ("btrt_read_f", ctypes.c_int, [_vp, _dp, _i32, _i32, _i32, _i32]),
     ("btrt_mass", ctypes.c_int, [_vp, _dp]),
@@ -62,6 +63,16 @@ SIGNATURES = [
     ("btrt_save", ctypes.c_int, [_vp, _vp, _sz]),
     ("btrt_load", ctypes.c_int, [_vp, _vp, _sz]),
     ("btrt_destroy", ctypes.c_int, [_vp]),
+    ("btrt_batch_workspace_bytes", _sz, [ctypes.POINTER(_vp), _i32]),
+    ("btrt_batch_create", ctypes.c_int, [ctypes.POINTER(_vp), _i32, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    ("btrt_batch_set_tiles", ctypes.c_int, [_vp, _i32, _i32, _i32, _i32]),
+    ("btrt_batch_autotune", ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
+                                           ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+    ("btrt_batch_step", ctypes.c_int, [_vp, _i64, _i32]),
+    ("btrt_batch_residuals", ctypes.c_int, [_vp, _dp]),
+    ("btrt_batch_check", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    ("btrt_batch_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_uint64, _i32]),
+    ("btrt_batch_destroy", ctypes.c_int, [_vp]),
     ("btrt_phi_sum_static", ctypes.c_int, [_vp, _i32, _i32, _i32, _i64, _vp, _dp]),
     ("btrt_last_error", ctypes.c_char_p, []),
     ("btrt_version", ctypes.c_char_p, []),

@@ -7,6 +7,7 @@
 // sweep reads buffer `cur` and writes buffer 1 - cur.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -42,29 +43,8 @@ btrt_status fail(btrt_status code, const char *fmt, ...) {
     } while (0)
 
 constexpr size_t kAlign = 256;
-constexpr int kRedBlocks = 1024;     // fixed grid of the FP64 reductions (deterministic order)
-constexpr int kRedThreads = 256;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-size_t elem_size(int fmt) {
-    switch (fmt) {
-    case BTRT_F64: return 8;
-    case BTRT_F32: return 4;
-    case BTRT_F16: return 2;
-    case BTRT_BF16: return 2;
-    default: return 0;
-    }
-}
-
-struct Layout {
-    long long pitch = 0;     // elements per row (f planes and phi plane)
-    long long plane = 0;     // elements per plane
-    size_t fbuf_bytes = 0;   // one buffer of 9 planes
-    size_t off_f[2] = {0, 0};
-    size_t off_phi = 0, off_tab = 0, off_wall = 0, off_red = 0, total = 0;
-    int maxside = 0;
-};
 
 btrt_status check_desc(const btrt_grid_desc *g) {
     if (!g) return fail(BTRT_EINVAL, "null grid description");
@@ -89,8 +69,9 @@ btrt_status check_desc(const btrt_grid_desc *g) {
     if (!std::isfinite(g->phi_ref) || !std::isfinite(g->x0) || !std::isfinite(g->y0))
         return fail(BTRT_EINVAL, "phi_ref, x0, y0 must be finite");
     const long long pitch = (long long)((g->nx + 63) / 64) * 64;
-    if (pitch * (long long)g->ny >= (1LL << 31))
-        return fail(BTRT_EINVAL, "grid %d x %d: a plane must hold fewer than 2^31 nodes", g->nx, g->ny);
+    if (9 * pitch * (long long)g->ny >= (1LL << 31))
+        return fail(BTRT_EINVAL, "grid %d x %d: the nine padded planes must hold fewer than 2^31 values "
+                    "(about 238 M nodes)", g->nx, g->ny);
     return BTRT_OK;
 }
 
@@ -115,6 +96,9 @@ Layout make_layout(const btrt_grid_desc *g) {
     off += align_up(4 * (size_t)L.maxside * sr, kAlign);
     L.off_red = off;
     off += align_up((kRedBlocks + 2) * sizeof(double) + 16, kAlign);
+    L.resid_blocks = sweep_blocks(g->nx, g->ny, g->compute);
+    L.off_resid = off;
+    off += align_up((size_t)L.resid_blocks * sizeof(double), kAlign);
     L.total = off;
     return L;
 }
@@ -179,63 +163,57 @@ void btrt::set_last_error(const char *fmt, ...) {
     g_err = buf;
 }
 
-// ---------------------------------------------------------------- the lattice object
-struct btrt_lattice_s {
-    btrt_grid_desc g;
-    btrt_coeffs c;
-    Layout lay;
-    unsigned char *ws = nullptr;
-    cudaStream_t stream = nullptr;
-    int cur = 0;              // buffer holding the current post-collision populations
-    int64_t step = 0;
-    double t0 = 0.0;
-    bool have_coeffs = false, ready = false;
-    // lattice-unit constants derived from the coefficients
-    double ux = 0, uy = 0, b2 = 0, A0[3] = {0, 0, 0}, K1[3] = {0, 0, 0}, k2 = 1;
-    bool nonlin_A = false;
-    double wall_const[4] = {0, 0, 0, 0};
-    bool wall_is_arr[4] = {false, false, false, false};
-
-    template <typename Real> Real *phi() { return reinterpret_cast<Real *>(ws + lay.off_phi); }
-    void *fbuf(int k) { return ws + lay.off_f[k]; }
-    template <typename Real> Real *tab() { return reinterpret_cast<Real *>(ws + lay.off_tab); }
-    template <typename Real> Real *wall(int side) {
-        return reinterpret_cast<Real *>(ws + lay.off_wall) + (size_t)side * lay.maxside;
+size_t btrt::elem_size(int fmt) {
+    switch (fmt) {
+    case BTRT_F64: return 8;
+    case BTRT_F32: return 4;
+    case BTRT_F16: return 2;
+    case BTRT_BF16: return 2;
+    default: return 0;
     }
-    double *partials() { return reinterpret_cast<double *>(ws + lay.off_red); }
-    double *red_out() { return partials() + kRedBlocks; }
-    int *flags() { return reinterpret_cast<int *>(partials() + kRedBlocks + 2); }
-};
+}
 
-namespace {
+void btrt::step_scalars(btrt_lattice L, int64_t n, bool first, double *src_val, double *wall_fac) {
+    const btrt_grid_desc &g = L->g;
+    const btrt_coeffs &c = L->c;
+    const double tn = L->t0 + (double)n * g.dt;
+    // bounce-back values of the streaming that ends at t_n
+    *wall_fac = c.wall_lam == 0.0 ? 1.0 : std::exp(c.wall_lam * tn);
+    if (c.src_kind == BTRT_SRC_CONST) {
+        *src_val = c.src_const * g.dt;
+    } else if (c.src_kind == BTRT_SRC_TRIG) {
+        // dt S_i + dt^2/2 (S_i^n - S_i^{n-1})/dt = w_i dt (3 S^n - S^{n-1}) / 2 (scheme 2)
+        const double Tn = std::exp(c.src_lam * tn);
+        const double Tp = first ? Tn : std::exp(c.src_lam * (tn - g.dt));
+        *src_val = g.dt * 0.5 * (3.0 * Tn - Tp);
+    } else {
+        *src_val = 0.0;
+    }
+}
 
 template <typename Real>
-void fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool first) {
+void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool first) {
     const btrt_grid_desc &g = L->g;
     const btrt_coeffs &c = L->c;
     std::memset(&p, 0, sizeof p);
-    const size_t sf = elem_size(g.storage);
-    unsigned char *bin = static_cast<unsigned char *>(L->fbuf(L->cur));
-    unsigned char *bout = static_cast<unsigned char *>(L->fbuf(first ? L->cur : 1 - L->cur));
-    for (int i = 0; i < 9; ++i) {
-        p.fin[i] = bin + (size_t)i * L->lay.plane * sf;
-        p.fout[i] = bout + (size_t)i * L->lay.plane * sf;
-    }
+    p.fin = L->fbuf(L->cur);
+    p.fout = L->fbuf(first ? L->cur : 1 - L->cur);
     p.phi = L->phi<Real>();
     p.nx = g.nx;
     p.ny = g.ny;
     p.pitch = (int)L->lay.pitch;
+    p.plane = (int)L->lay.plane;
     p.hbb_x = g.bc[0] == BTRT_BC_HBB;
     p.hbb_y = g.bc[2] == BTRT_BC_HBB;
     const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
     for (int i = 0; i < 9; ++i) p.wref[i] = (Real)(w[i] * g.phi_ref);
-    const double tn = L->t0 + (double)n * g.dt;
     for (int s = 0; s < 4; ++s) {
         p.wall_const[s] = (Real)L->wall_const[s];
         p.wall_arr[s] = L->wall_is_arr[s] ? L->wall<Real>(s) : nullptr;
     }
-    // bounce-back values of the streaming that ends at t_n
-    p.wall_fac = (Real)std::exp(c.wall_lam * tn);
+    double src_val = 0.0, wall_fac = 1.0;
+    step_scalars(L, n, first, &src_val, &wall_fac);
+    p.wall_fac = (Real)wall_fac;
     p.ux = (Real)L->ux;
     p.uy = (Real)L->uy;
     p.b2 = (Real)L->b2;
@@ -254,13 +232,8 @@ void fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool first) {
     p.k2 = (Real)L->k2;
     p.cond_limit = (Real)1.0e4;
     p.src_kind = c.src_kind;
-    if (c.src_kind == BTRT_SRC_CONST) {
-        p.src_val = (Real)(c.src_const * g.dt);
-    } else if (c.src_kind == BTRT_SRC_TRIG) {
-        // dt S_i + dt^2/2 (S_i^n - S_i^{n-1})/dt = w_i dt (3 S^n - S^{n-1}) / 2 (scheme 2)
-        const double Tn = std::exp(c.src_lam * tn);
-        const double Tp = first ? Tn : std::exp(c.src_lam * (tn - g.dt));
-        p.src_val = (Real)(g.dt * 0.5 * (3.0 * Tn - Tp));
+    p.src_val = (Real)src_val;
+    if (c.src_kind == BTRT_SRC_TRIG) {
         Real *tb = L->tab<Real>();
         p.Xs = tb;
         p.Xc = tb + g.nx;
@@ -293,8 +266,11 @@ void fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool first) {
     }
 }
 
+template void btrt::fill_params<double>(btrt_lattice, SweepParams<double> &, int64_t, bool);
+template void btrt::fill_params<float>(btrt_lattice, SweepParams<float> &, int64_t, bool);
+
 // Which compiled variant of the sweep serves these coefficients.
-int sweep_mode(btrt_lattice L) {
+int btrt::sweep_mode(btrt_lattice L) {
     const btrt_coeffs &c = L->c;
     const bool linear = c.b2 == 0.0 && c.c3 == 0.0 && c.a2 == 0.0;
     if (!linear) return kGeneral;
@@ -302,14 +278,18 @@ int sweep_mode(btrt_lattice L) {
     return kLinear;
 }
 
-btrt_status launch(btrt_lattice L, int64_t n, bool first) {
+namespace {
+
+btrt_status launch(btrt_lattice L, int64_t n, bool first, bool resid = false) {
     if (L->g.compute == BTRT_F64) {
         SweepParams<double> p;
         fill_params(L, p, n, first);
+        if (resid) p.resid_partials = L->resid_partials();
         CUDA_TRY(launch_sweep_f64(p, sweep_mode(L), L->stream));
     } else {
         SweepParams<float> p;
         fill_params(L, p, n, first);
+        if (resid) p.resid_partials = L->resid_partials();
         CUDA_TRY(launch_sweep_f32(p, L->g.storage, sweep_mode(L), L->stream));
     }
     return BTRT_OK;
@@ -578,6 +558,30 @@ btrt_status btrt_step(btrt_lattice L, int64_t nsteps) {
     return BTRT_OK;
 }
 
+btrt_status btrt_step_residual(btrt_lattice L, int64_t nsteps, double *residual) {
+    if (!L || !residual) return fail(BTRT_EINVAL, "null argument");
+    if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
+    if (nsteps < 1) return fail(BTRT_EINVAL, "btrt_step_residual needs at least one step");
+    btrt_status st = btrt_step(L, nsteps - 1);
+    if (st != BTRT_OK) return st;
+    st = launch(L, L->step + 1, false, true);
+    if (st != BTRT_OK) return st;
+    L->cur = 1 - L->cur;
+    L->step += 1;
+    // fixed-order FP64 reduction of the per-block partials, then sqrt on the host
+    const long long nb = L->lay.resid_blocks;
+    plane_sum_partials<double><<<kRedBlocks, kRedThreads, 0, L->stream>>>(
+        L->resid_partials(), (int)std::min<long long>(nb, 1 << 30), 1, nb, L->partials());
+    CUDA_TRY(cudaGetLastError());
+    sum_partials<<<1, kRedThreads, 0, L->stream>>>(L->partials(), kRedBlocks, L->red_out());
+    CUDA_TRY(cudaGetLastError());
+    double s2 = 0.0;
+    CUDA_TRY(cudaMemcpyAsync(&s2, L->red_out(), sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+    CUDA_TRY(cudaStreamSynchronize(L->stream));
+    *residual = std::sqrt(s2);
+    return BTRT_OK;
+}
+
 btrt_status btrt_read_phi(btrt_lattice L, void *dst, int32_t dtype, int32_t on_device) {
     if (!L || !dst) return fail(BTRT_EINVAL, "null argument");
     if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
@@ -686,6 +690,7 @@ btrt_status btrt_load(btrt_lattice L, const void *host_buf, size_t n) {
 }
 
 btrt_status btrt_destroy(btrt_lattice L) {
+    if (L && L->batch_refs > 0) return fail(BTRT_ESTATE, "lattice is still a member of %d batch(es)", L->batch_refs);
     delete L;
     return BTRT_OK;
 }

@@ -1,0 +1,646 @@
+// btrt_batch.cu -- many independent lattices of uneven size in one persistent launch.
+//
+// A batch owns a descriptor per member (its sweep parameters and step counter),
+// a table of tiles covering every member, a per-step table of source and wall
+// factors, and two kernel forms over the same tile code:
+//  - persistent: one cooperative launch per call; all resident blocks walk the
+//    tile table for one time step, meet at a grid barrier (bounded wait) and go
+//    on with the next step;
+//  - step-per-launch: one launch per step over all tiles.
+// Either form is captured in a CUDA graph per (steps, residual) pair and
+// replayed.  Members keep their own workspaces; the batch workspace holds only
+// the descriptors, tables and reduction scratch.  btrt_batch_autotune times the
+// candidate tile shapes in both forms on real steps and keeps the fastest.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/btrt.h"
+#include "btrt_internal.h"
+
+using namespace btrt;
+
+namespace {
+
+template <typename Real>
+struct BatchMember {
+    SweepParams<Real> p;       // fin = buffer 0, fout = buffer 1; first = 0
+    long long step;            // completed steps at the start of the launch
+    int cur;                   // buffer holding the current populations at the start
+    int mode;                  // kGeneral or kLinear
+};
+
+constexpr int kMaxSliceSteps = 4096;   // steps per launch (the step table holds this many)
+
+template <typename Real>
+struct BatchArgs {
+    const BatchMember<Real> *members;
+    const int4 *tiles;         // {member, x0, y0, 0}
+    int ntiles;
+    int rows;                  // nodes per thread along y
+    int nsteps;
+    int want_resid;
+    double *tile_partials;     // sum (phi^n - phi^{n-1})^2 per tile, last step
+    unsigned int *barrier;     // arrivals, zeroed before the launch
+    int *err;                  // bit 1: a barrier wait gave up
+    unsigned long long wait_limit;
+    unsigned int barrier_extra;  // added to every barrier target (0; >0 only to test the timeout path)
+    const Real *step_vals;     // [member][table_steps][2]: source factor, wall factor of each step of the launch
+    int table_steps;
+};
+
+// Grid-wide barrier with a bounded wait.  All blocks are co-resident (cooperative
+// launch).  Returns false after raising err bit 1 when the wait gave up.
+__device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int target, int *err,
+                                             unsigned long long limit) {
+    __shared__ int ok;
+    __syncthreads();
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        __threadfence();
+        atomicAdd(count, 1u);
+        int good = 1;
+        unsigned long long polls = 0;
+        while (atomicAdd(count, 0u) < target) {
+            if (++polls > limit) {
+                atomicOr(err, 2);
+                good = 0;
+                break;
+            }
+            __nanosleep(100);
+        }
+        __threadfence();
+        ok = good;
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// One tile of one step: load the member's parameters into shared memory, patch
+// the step-dependent ones (buffer parity, source and wall time factors from the
+// host-computed step table) and sweep the tile's nodes.
+template <typename Real, typename S, bool L2ONLY>
+__device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int k, bool resid,
+                                           SweepParams<Real> &sp, double *red) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    const int4 tile = a.tiles[t];
+    const BatchMember<Real> &M = a.members[tile.x];
+    __syncthreads();   // the previous tile is done with sp
+    {
+        const int *src = reinterpret_cast<const int *>(&M.p);
+        int *dst = reinterpret_cast<int *>(&sp);
+        for (int w = tid; w < (int)(sizeof(SweepParams<Real>) / 4); w += nthr) dst[w] = src[w];
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int cur = (M.cur + k) & 1;
+        const void *b0 = M.p.fin;            // buffer 0
+        void *b1 = M.p.fout;                 // buffer 1
+        sp.fin = cur ? b1 : b0;
+        sp.fout = cur ? const_cast<void *>(b0) : b1;
+    } else if (tid == 32) {
+        const Real *v = a.step_vals + ((size_t)tile.x * a.table_steps + k) * 2;
+        sp.src_val = v[0];
+        sp.wall_fac = v[1];
+        sp.first = 0;
+    }
+    __syncthreads();
+    const int x = tile.y + threadIdx.x;
+    double r = 0.0;
+    if (x < sp.nx) {
+        const int y0 = tile.z + threadIdx.y;
+        if (M.mode == kGeneral) {
+            if (resid) r = sweep_rows<Real, S, kGeneral, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, kGeneral, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+        } else {
+            if (resid) r = sweep_rows<Real, S, kLinear, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, kLinear, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+        }
+    }
+    if (resid) {
+        red[tid] = r;
+        __syncthreads();
+        for (int s = nthr / 2; s > 0; s >>= 1) {
+            if (tid < s) red[tid] += red[tid + s];
+            __syncthreads();
+        }
+        if (tid == 0) a.tile_partials[t] = red[0];
+    }
+}
+
+// Persistent form: every resident block walks the tile table each step; a
+// bounded grid barrier separates the steps.  Population and phi loads go
+// through L2 only, since other SMs rewrote them in the previous step.
+template <typename Real, typename S>
+__global__ void __launch_bounds__(256) batch_kernel(const __grid_constant__ BatchArgs<Real> a) {
+    __shared__ SweepParams<Real> sp;
+    __shared__ double red[256];
+    for (int k = 0; k < a.nsteps; ++k) {
+        const bool resid = a.want_resid && (k == a.nsteps - 1);
+        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, true>(a, t, k, resid, sp, red);
+        if (!grid_barrier(a.barrier, (unsigned)(k + 1) * gridDim.x + a.barrier_extra, a.err, a.wait_limit))
+            return;
+    }
+}
+
+// Step-per-launch form: one launch per step (all of them in one CUDA graph);
+// kernel boundaries order the steps, so no barrier and ordinary cached loads.
+template <typename Real, typename S>
+__global__ void __launch_bounds__(256) batch_step_kernel(const __grid_constant__ BatchArgs<Real> a, int k) {
+    __shared__ SweepParams<Real> sp;
+    __shared__ double red[256];
+    const bool resid = a.want_resid && (k == a.nsteps - 1);
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, false>(a, t, k, resid, sp, red);
+}
+
+// Per-member residual: fixed-order sum of its tiles' partials, then sqrt.
+__global__ void __launch_bounds__(256) member_residual(const double *tile_partials, const int *tile_begin,
+                                                       const int *tile_count, double *out) {
+    __shared__ double sh[256];
+    const int m = blockIdx.x;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < tile_count[m]; k += blockDim.x) acc += tile_partials[tile_begin[m] + k];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[m] = sqrt(sh[0]);
+}
+
+thread_local std::string t_err;
+
+btrt_status bfail(btrt_status code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    set_last_error("%s", buf);
+    return code;
+}
+
+#define BCUDA(expr)                                                                       \
+    do {                                                                                  \
+        cudaError_t e_ = (expr);                                                          \
+        if (e_ != cudaSuccess)                                                            \
+            return bfail(BTRT_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),   \
+                         __FILE__, __LINE__);                                             \
+    } while (0)
+
+size_t up256(size_t v) { return (v + 255) / 256 * 256; }
+
+struct Shape {
+    int bx, by, rows;
+    int per_step;   // 0: persistent launch per call; 1: one launch per step (in a graph)
+};
+const Shape kShapes[] = {{32, 8, 1, 0}, {32, 8, 2, 0}, {32, 8, 4, 0}, {64, 4, 1, 0}, {64, 4, 2, 0}, {32, 4, 2, 0}};
+
+long long tiles_for(const std::vector<btrt_lattice> &m, int bx, int by, int rows) {
+    long long t = 0;
+    for (auto L : m) t += (long long)((L->g.nx + bx - 1) / bx) * ((L->g.ny + by * rows - 1) / (by * rows));
+    return t;
+}
+
+long long max_tiles(const std::vector<btrt_lattice> &m) {
+    long long t = 0;
+    for (const Shape &s : kShapes) t = std::max(t, tiles_for(m, s.bx, s.by, s.rows));
+    return t;
+}
+
+size_t member_bytes(int compute) {
+    return compute == BTRT_F64 ? sizeof(BatchMember<double>) : sizeof(BatchMember<float>);
+}
+
+struct BatchLayout {
+    size_t off_members, off_tiles, off_partials, off_resid, off_tbeg, off_tcnt, off_vals, off_sync, total;
+};
+
+BatchLayout batch_layout(const std::vector<btrt_lattice> &m) {
+    BatchLayout b;
+    const size_t n = m.size();
+    const size_t T = (size_t)max_tiles(m);
+    size_t off = 0;
+    b.off_members = off;
+    off += up256(n * member_bytes(m[0]->g.compute));
+    b.off_tiles = off;
+    off += up256(T * sizeof(int4));
+    b.off_partials = off;
+    off += up256(T * sizeof(double));
+    b.off_resid = off;
+    off += up256(n * sizeof(double));
+    b.off_tbeg = off;
+    off += up256(n * sizeof(int));
+    b.off_tcnt = off;
+    off += up256(n * sizeof(int));
+    b.off_vals = off;
+    off += up256(n * (size_t)kMaxSliceSteps * 2 * (m[0]->g.compute == BTRT_F64 ? 8 : 4));
+    b.off_sync = off;
+    off += 256;
+    b.total = off;
+    return b;
+}
+
+btrt_status check_members(const btrt_lattice *members, int32_t n, std::vector<btrt_lattice> &out) {
+    if (!members || n <= 0) return bfail(BTRT_EINVAL, "a batch needs at least one member");
+    out.assign(members, members + n);
+    for (int k = 0; k < n; ++k) {
+        if (!out[k]) return bfail(BTRT_EINVAL, "member %d is null", k);
+        if (!out[k]->ready) return bfail(BTRT_ESTATE, "member %d is not initialised", k);
+        if (out[k]->g.compute != out[0]->g.compute || out[k]->g.storage != out[0]->g.storage)
+            return bfail(BTRT_EINVAL, "member %d: all members need the same compute and storage formats", k);
+        for (int j = 0; j < k; ++j)
+            if (out[j] == out[k]) return bfail(BTRT_EINVAL, "member %d appears twice", k);
+    }
+    return BTRT_OK;
+}
+
+// autotuner cache: (members, total nodes in millions, compute, storage) -> shape
+std::mutex g_tune_mu;
+std::map<std::tuple<int, long long, int, int>, Shape> g_tune_cache;
+
+}  // namespace
+
+struct btrt_batch_s {
+    std::vector<btrt_lattice> members;
+    int compute = 0, storage = 0;
+    unsigned char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    BatchLayout lay{};
+    Shape shape{32, 8, 1, 0};
+    int ntiles = 0;
+    int grid = 0;              // persistent grid (co-resident blocks)
+    unsigned long long wait_limit = 1ull << 24;
+    unsigned int barrier_extra = 0;
+    bool use_graph = true;
+    bool have_resid = false;
+    std::map<std::pair<long long, int>, cudaGraphExec_t> graphs;
+    std::vector<unsigned char> host_members, host_vals;
+
+    unsigned int *barrier() { return reinterpret_cast<unsigned int *>(ws + lay.off_sync); }
+    int *err() { return reinterpret_cast<int *>(ws + lay.off_sync + 16); }
+
+    void drop_graphs() {
+        for (auto &kv : graphs) cudaGraphExecDestroy(kv.second);
+        graphs.clear();
+    }
+};
+
+namespace {
+
+void *persistent_kernel_for(int compute, int storage) {
+    if (compute == BTRT_F64) return reinterpret_cast<void *>(&batch_kernel<double, double>);
+    switch (storage) {
+    case BTRT_F32: return reinterpret_cast<void *>(&batch_kernel<float, float>);
+    case BTRT_F16: return reinterpret_cast<void *>(&batch_kernel<float, __half>);
+    case BTRT_BF16: return reinterpret_cast<void *>(&batch_kernel<float, __nv_bfloat16>);
+    }
+    return nullptr;
+}
+
+// Tile table for the current shape; also sizes the persistent grid.
+btrt_status build_tiles(btrt_batch B) {
+    const Shape s = B->shape;
+    std::vector<int4> tiles;
+    std::vector<int> beg(B->members.size()), cnt(B->members.size());
+    for (size_t m = 0; m < B->members.size(); ++m) {
+        btrt_lattice L = B->members[m];
+        beg[m] = (int)tiles.size();
+        const int th = s.by * s.rows;
+        for (int y0 = 0; y0 < L->g.ny; y0 += th)
+            for (int x0 = 0; x0 < L->g.nx; x0 += s.bx) tiles.push_back(make_int4((int)m, x0, y0, 0));
+        cnt[m] = (int)tiles.size() - beg[m];
+    }
+    B->ntiles = (int)tiles.size();
+    BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tiles, tiles.data(), tiles.size() * sizeof(int4),
+                          cudaMemcpyHostToDevice, B->stream));
+    BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tbeg, beg.data(), beg.size() * sizeof(int),
+                          cudaMemcpyHostToDevice, B->stream));
+    BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tcnt, cnt.data(), cnt.size() * sizeof(int),
+                          cudaMemcpyHostToDevice, B->stream));
+    BCUDA(cudaStreamSynchronize(B->stream));
+    int dev = 0, sms = 0, per_sm = 0;
+    BCUDA(cudaGetDevice(&dev));
+    BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel_for(B->compute, B->storage),
+                                                        s.bx * s.by, 0));
+    if (per_sm < 1) return bfail(BTRT_ECUDA, "batch kernel cannot be resident");
+    B->grid = per_sm * sms;
+    B->drop_graphs();
+    return BTRT_OK;
+}
+
+// Member descriptors (from the members' host state) and the per-step table of
+// source and wall factors, computed by the same host code as single-lattice steps.
+template <typename Real>
+btrt_status upload_members(btrt_batch B, int nsteps) {
+    const size_t n = B->members.size();
+    B->host_members.resize(n * sizeof(BatchMember<Real>));
+    B->host_vals.resize(n * (size_t)nsteps * 2 * sizeof(Real));
+    BatchMember<Real> *hm = reinterpret_cast<BatchMember<Real> *>(B->host_members.data());
+    Real *hv = reinterpret_cast<Real *>(B->host_vals.data());
+    for (size_t m = 0; m < n; ++m) {
+        btrt_lattice L = B->members[m];
+        BatchMember<Real> d;
+        std::memset(&d, 0, sizeof d);
+        // parameters of the next step with buffer 0 as input; the kernel swaps per parity
+        const int saved = L->cur;
+        L->cur = 0;
+        fill_params<Real>(L, d.p, L->step + 1, false);
+        L->cur = saved;
+        d.step = L->step;
+        d.cur = L->cur;
+        d.mode = sweep_mode(L) == kGeneral ? kGeneral : kLinear;
+        hm[m] = d;
+        for (int k = 0; k < nsteps; ++k) {
+            double sv = 0.0, wf = 1.0;
+            step_scalars(L, L->step + 1 + k, false, &sv, &wf);
+            hv[(m * nsteps + k) * 2] = (Real)sv;
+            hv[(m * nsteps + k) * 2 + 1] = (Real)wf;
+        }
+    }
+    BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_members, hm, n * sizeof(BatchMember<Real>),
+                          cudaMemcpyHostToDevice, B->stream));
+    BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_vals, hv, n * (size_t)nsteps * 2 * sizeof(Real),
+                          cudaMemcpyHostToDevice, B->stream));
+    return BTRT_OK;
+}
+
+template <typename Real>
+BatchArgs<Real> make_args(btrt_batch B, int nsteps, int want_resid) {
+    BatchArgs<Real> a;
+    std::memset(&a, 0, sizeof a);
+    a.members = reinterpret_cast<const BatchMember<Real> *>(B->ws + B->lay.off_members);
+    a.tiles = reinterpret_cast<const int4 *>(B->ws + B->lay.off_tiles);
+    a.ntiles = B->ntiles;
+    a.rows = B->shape.rows;
+    a.nsteps = nsteps;
+    a.want_resid = want_resid;
+    a.tile_partials = reinterpret_cast<double *>(B->ws + B->lay.off_partials);
+    a.barrier = B->barrier();
+    a.err = B->err();
+    a.wait_limit = B->wait_limit;
+    a.barrier_extra = B->barrier_extra;
+    a.step_vals = reinterpret_cast<const Real *>(B->ws + B->lay.off_vals);
+    a.table_steps = nsteps;   // rows of the step table: [member][nsteps][2]
+    return a;
+}
+
+template <typename Real, typename S>
+btrt_status enqueue_typed(btrt_batch B, int nsteps, int want_resid) {
+    BatchArgs<Real> a = make_args<Real>(B, nsteps, want_resid);
+    const dim3 block(B->shape.bx, B->shape.by);
+    if (B->shape.per_step) {
+        const unsigned grid = (unsigned)B->ntiles;
+        for (int k = 0; k < nsteps; ++k) batch_step_kernel<Real, S><<<grid, block, 0, B->stream>>>(a, k);
+        BCUDA(cudaGetLastError());
+        return BTRT_OK;
+    }
+    void *args[] = {&a};
+    BCUDA(cudaMemsetAsync(B->barrier(), 0, sizeof(unsigned int), B->stream));
+    BCUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(&batch_kernel<Real, S>), dim3(B->grid), block,
+                                      args, 0, B->stream));
+    return BTRT_OK;
+}
+
+btrt_status enqueue(btrt_batch B, int nsteps, int want_resid) {
+    if (B->compute == BTRT_F64) return enqueue_typed<double, double>(B, nsteps, want_resid);
+    switch (B->storage) {
+    case BTRT_F32: return enqueue_typed<float, float>(B, nsteps, want_resid);
+    case BTRT_F16: return enqueue_typed<float, __half>(B, nsteps, want_resid);
+    case BTRT_BF16: return enqueue_typed<float, __nv_bfloat16>(B, nsteps, want_resid);
+    }
+    return bfail(BTRT_EINVAL, "unsupported storage format");
+}
+
+// Replay (or capture, then replay) the slice graph; falls back to direct
+// launches if the launch cannot be captured.
+btrt_status run_slice(btrt_batch B, int nsteps, int want_resid) {
+    if (B->use_graph) {
+        auto key = std::make_pair((long long)nsteps, want_resid);
+        auto it = B->graphs.find(key);
+        if (it == B->graphs.end()) {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            bool ok = cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            btrt_status st = BTRT_OK;
+            if (ok) st = enqueue(B, nsteps, want_resid);
+            if (ok) ok = cudaStreamEndCapture(B->stream, &g) == cudaSuccess && st == BTRT_OK;
+            if (ok) ok = cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+            if (g) cudaGraphDestroy(g);
+            if (!ok) {
+                cudaGetLastError();
+                if (ge) cudaGraphExecDestroy(ge);
+                B->use_graph = false;   // capture unsupported here: launch directly from now on
+                return enqueue(B, nsteps, want_resid);
+            }
+            it = B->graphs.emplace(key, ge).first;
+        }
+        BCUDA(cudaGraphLaunch(it->second, B->stream));
+        return BTRT_OK;
+    }
+    return enqueue(B, nsteps, want_resid);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t btrt_batch_workspace_bytes(const btrt_lattice *members, int32_t n) {
+    std::vector<btrt_lattice> m;
+    if (check_members(members, n, m) != BTRT_OK) return 0;
+    return batch_layout(m).total;
+}
+
+btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_workspace, size_t bytes,
+                              void *cuda_stream, btrt_batch *out) {
+    if (!out) return bfail(BTRT_EINVAL, "null output handle");
+    *out = nullptr;
+    std::vector<btrt_lattice> m;
+    btrt_status st = check_members(members, n, m);
+    if (st != BTRT_OK) return st;
+    if (!dev_workspace || ((uintptr_t)dev_workspace) % 256)
+        return bfail(BTRT_EINVAL, "batch workspace must be a 256-byte aligned device pointer");
+    BatchLayout lay = batch_layout(m);
+    if (bytes < lay.total) return bfail(BTRT_ENOMEM, "batch workspace of %zu bytes < required %zu", bytes, lay.total);
+    int coop = 0, dev = 0;
+    BCUDA(cudaGetDevice(&dev));
+    BCUDA(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+    if (!coop) return bfail(BTRT_ECUDA, "device does not support cooperative launches");
+    btrt_batch B = new (std::nothrow) btrt_batch_s();
+    if (!B) return bfail(BTRT_ENOMEM, "host allocation failed");
+    B->members = m;
+    B->compute = m[0]->g.compute;
+    B->storage = m[0]->g.storage;
+    B->ws = static_cast<unsigned char *>(dev_workspace);
+    B->stream = static_cast<cudaStream_t>(cuda_stream);
+    B->lay = lay;
+    // every member's own stream work must be ordered before the batch's
+    for (auto L : m) {
+        cudaError_t e = cudaStreamSynchronize(L->stream);
+        if (e != cudaSuccess) {
+            delete B;
+            return bfail(BTRT_ECUDA, "member stream: %s", cudaGetErrorString(e));
+        }
+    }
+    cudaError_t e = cudaMemsetAsync(B->ws + lay.off_sync, 0, 256, B->stream);
+    if (e != cudaSuccess) {
+        delete B;
+        return bfail(BTRT_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+    st = build_tiles(B);
+    if (st != BTRT_OK) {
+        delete B;
+        return st;
+    }
+    for (auto L : m) L->batch_refs++;
+    *out = B;
+    return BTRT_OK;
+}
+
+btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y, int32_t rows,
+                                 int32_t per_step_launch) {
+    if (!B) return bfail(BTRT_EINVAL, "null batch");
+    bool known = false;
+    for (const Shape &s : kShapes) known |= (s.bx == block_x && s.by == block_y && s.rows == rows);
+    if (!known) return bfail(BTRT_EINVAL, "tile shape %dx%dx%d is not one of the compiled candidates",
+                             block_x, block_y, rows);
+    B->shape = Shape{block_x, block_y, rows, per_step_launch ? 1 : 0};
+    return build_tiles(B);
+}
+
+btrt_status btrt_batch_step(btrt_batch B, int64_t nsteps, int32_t want_residual) {
+    if (!B) return bfail(BTRT_EINVAL, "null batch");
+    if (nsteps < 0) return bfail(BTRT_EINVAL, "negative step count");
+    while (nsteps > 0) {
+        const int chunk = (int)std::min<int64_t>(nsteps, kMaxSliceSteps);
+        const int resid = (want_residual && chunk == nsteps) ? 1 : 0;
+        btrt_status st = B->compute == BTRT_F64 ? upload_members<double>(B, chunk) : upload_members<float>(B, chunk);
+        if (st != BTRT_OK) return st;
+        st = run_slice(B, chunk, resid);
+        if (st != BTRT_OK) return st;
+        if (resid) {
+            member_residual<<<(unsigned)B->members.size(), 256, 0, B->stream>>>(
+                reinterpret_cast<const double *>(B->ws + B->lay.off_partials),
+                reinterpret_cast<const int *>(B->ws + B->lay.off_tbeg),
+                reinterpret_cast<const int *>(B->ws + B->lay.off_tcnt),
+                reinterpret_cast<double *>(B->ws + B->lay.off_resid));
+            BCUDA(cudaGetLastError());
+            B->have_resid = true;
+        }
+        for (auto L : B->members) {
+            L->step += chunk;
+            L->cur = (L->cur + chunk) & 1;
+        }
+        nsteps -= chunk;
+    }
+    return BTRT_OK;
+}
+
+btrt_status btrt_batch_residuals(btrt_batch B, double *out_host) {
+    if (!B || !out_host) return bfail(BTRT_EINVAL, "null argument");
+    if (!B->have_resid) return bfail(BTRT_ESTATE, "no step with want_residual has run");
+    BCUDA(cudaMemcpyAsync(out_host, B->ws + B->lay.off_resid, B->members.size() * sizeof(double),
+                          cudaMemcpyDeviceToHost, B->stream));
+    BCUDA(cudaStreamSynchronize(B->stream));
+    return BTRT_OK;
+}
+
+btrt_status btrt_batch_check(btrt_batch B, int32_t *flags) {
+    if (!B || !flags) return bfail(BTRT_EINVAL, "null argument");
+    int e = 0;
+    BCUDA(cudaMemcpyAsync(&e, B->err(), sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+    BCUDA(cudaStreamSynchronize(B->stream));
+    int f = 0;
+    for (auto L : B->members) {
+        int v = 0;
+        BCUDA(cudaMemcpyAsync(&v, L->flags(), sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+        BCUDA(cudaStreamSynchronize(B->stream));
+        f |= v;
+    }
+    *flags = f | e;
+    if (e & 2) return bfail(BTRT_ETIMEOUT, "a grid barrier wait gave up (limit %llu polls)", B->wait_limit);
+    if (f & 1) return bfail(BTRT_EUNSTABLE, "non-finite phi in a batch member");
+    return BTRT_OK;
+}
+
+btrt_status btrt_batch_set_wait_limit(btrt_batch B, uint64_t polls, int32_t never_release) {
+    if (!B) return bfail(BTRT_EINVAL, "null batch");
+    if (polls == 0) return bfail(BTRT_EINVAL, "wait limit must be positive");
+    B->wait_limit = polls;
+    B->barrier_extra = never_release ? 1u : 0u;
+    B->drop_graphs();
+    return BTRT_OK;
+}
+
+btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *block_x, int32_t *block_y,
+                                int32_t *rows, int32_t *per_step_launch) {
+    if (!B) return bfail(BTRT_EINVAL, "null batch");
+    if (steps_per_trial < 1) return bfail(BTRT_EINVAL, "steps_per_trial must be >= 1");
+    long long nodes = 0;
+    for (auto L : B->members) nodes += (long long)L->g.nx * L->g.ny;
+    const auto key = std::make_tuple((int)B->members.size(), nodes / 1000000, B->compute, B->storage);
+    Shape best{0, 0, 0, 0};
+    {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) best = it->second;
+    }
+    if (best.bx == 0) {
+        cudaEvent_t e0, e1;
+        BCUDA(cudaEventCreate(&e0));
+        BCUDA(cudaEventCreate(&e1));
+        float best_ms = 1e30f;
+        for (int mode = 0; mode < 2; ++mode) {
+            for (const Shape &s : kShapes) {
+                btrt_status st = btrt_batch_set_tiles(B, s.bx, s.by, s.rows, mode);
+                if (st != BTRT_OK) return st;
+                st = btrt_batch_step(B, 1, 0);   // warm-up (and graph capture) for this candidate
+                if (st != BTRT_OK) return st;
+                BCUDA(cudaEventRecord(e0, B->stream));
+                st = btrt_batch_step(B, steps_per_trial, 0);
+                if (st != BTRT_OK) return st;
+                BCUDA(cudaEventRecord(e1, B->stream));
+                BCUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                BCUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = Shape{s.bx, s.by, s.rows, mode};
+                }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[key] = best;
+    }
+    btrt_status st = btrt_batch_set_tiles(B, best.bx, best.by, best.rows, best.per_step);
+    if (st != BTRT_OK) return st;
+    if (block_x) *block_x = best.bx;
+    if (block_y) *block_y = best.by;
+    if (rows) *rows = best.rows;
+    if (per_step_launch) *per_step_launch = best.per_step;
+    return BTRT_OK;
+}
+
+btrt_status btrt_batch_destroy(btrt_batch B) {
+    if (!B) return BTRT_OK;
+    if (B->stream) cudaStreamSynchronize(B->stream);
+    B->drop_graphs();
+    for (auto L : B->members) L->batch_refs--;
+    delete B;
+    return BTRT_OK;
+}
+
+}  // extern "C"

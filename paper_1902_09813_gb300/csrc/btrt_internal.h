@@ -5,9 +5,72 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "../../include/btrt.h"
 #include "btrt_sweep.cuh"
 
 namespace btrt {
+
+constexpr int kRedBlocks = 1024;     // fixed grid of the FP64 reductions (deterministic order)
+constexpr int kRedThreads = 256;
+
+size_t elem_size(int fmt);
+
+// Where each part of a lattice lives in its workspace (byte offsets).
+struct Layout {
+    long long pitch = 0;     // elements per row (f planes and phi plane)
+    long long plane = 0;     // elements per plane
+    size_t fbuf_bytes = 0;   // one buffer of 9 planes
+    size_t off_f[2] = {0, 0};
+    size_t off_phi = 0, off_tab = 0, off_wall = 0, off_red = 0, off_resid = 0, total = 0;
+    int maxside = 0;
+    long long resid_blocks = 0;   // partial slots of a residual sweep (one per block)
+};
+
+}  // namespace btrt
+
+// The host-side lattice object behind btrt_lattice.
+struct btrt_lattice_s {
+    btrt_grid_desc g;
+    btrt_coeffs c;
+    btrt::Layout lay;
+    unsigned char *ws = nullptr;
+    cudaStream_t stream = nullptr;
+    int cur = 0;              // buffer holding the current post-collision populations
+    int64_t step = 0;
+    double t0 = 0.0;
+    bool have_coeffs = false, ready = false;
+    int batch_refs = 0;       // batches that reference this lattice
+    // lattice-unit constants derived from the coefficients
+    double ux = 0, uy = 0, b2 = 0, A0[3] = {0, 0, 0}, K1[3] = {0, 0, 0}, k2 = 1;
+    bool nonlin_A = false;
+    double wall_const[4] = {0, 0, 0, 0};
+    bool wall_is_arr[4] = {false, false, false, false};
+
+    template <typename Real> Real *phi() { return reinterpret_cast<Real *>(ws + lay.off_phi); }
+    void *fbuf(int k) { return ws + lay.off_f[k]; }
+    template <typename Real> Real *tab() { return reinterpret_cast<Real *>(ws + lay.off_tab); }
+    template <typename Real> Real *wall(int side) {
+        return reinterpret_cast<Real *>(ws + lay.off_wall) + (size_t)side * lay.maxside;
+    }
+    double *partials() { return reinterpret_cast<double *>(ws + lay.off_red); }
+    double *resid_partials() { return reinterpret_cast<double *>(ws + lay.off_resid); }
+    double *red_out() { return partials() + btrt::kRedBlocks; }
+    int *flags() { return reinterpret_cast<int *>(partials() + btrt::kRedBlocks + 2); }
+};
+
+namespace btrt {
+
+// Sweep parameters of lattice L for the step that produces step index n
+// (first: the initialising collision at t0).
+template <typename Real> void fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool first);
+// Source factor dt (3 T_n - T_{n-1})/2 (or the constant's dt S) and wall factor
+// exp(wall_lam t_n) of the step producing step index n.
+void step_scalars(btrt_lattice L, int64_t n, bool first, double *src_val, double *wall_fac);
+// Compiled variant (kGeneral / kLinear / kLinearK0One) that serves L's coefficients.
+int sweep_mode(btrt_lattice L);
+
+// Blocks of one single-lattice sweep (32 x 8 threads, RowsPerThread nodes each).
+long long sweep_blocks(int nx, int ny, int compute);
 
 // Launch one sweep (or the initialising collision) for a (compute, storage) pair.
 // compute: 0 = FP64, 1 = FP32; storage: BTRT_F64/F32/F16/BF16.

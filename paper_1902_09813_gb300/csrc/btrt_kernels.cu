@@ -11,6 +11,12 @@ static inline dim3 sweep_grid(int nx, int ny, int rows_per_thread) {
     return dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + rows - 1) / rows), 1);
 }
 
+long long sweep_blocks(int nx, int ny, int compute) {
+    const dim3 g = sweep_grid(nx, ny, compute == BTRT_F64 ? RowsPerThread<double>::value
+                                                          : RowsPerThread<float>::value);
+    return (long long)g.x * g.y;
+}
+
 cudaError_t launch_sweep_f64(const SweepParams<double> &p, int mode, cudaStream_t s) {
     const dim3 g = sweep_grid(p.nx, p.ny, RowsPerThread<double>::value), b = sweep_block();
     switch (mode) {

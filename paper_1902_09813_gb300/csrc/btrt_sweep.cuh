@@ -50,11 +50,12 @@ struct LinearConsts {
 // Everything one launch of the sweep needs, passed by value.
 template <typename Real>
 struct SweepParams {
-    const void *fin[9];    // post-collision populations at step n-1, one plane per direction
-    void *fout[9];         // post-collision populations at step n
+    const void *fin;       // post-collision populations at step n-1: 9 planes, `plane` apart
+    void *fout;            // post-collision populations at step n
     Real *phi;             // phi plane: phi^{n-1} on entry, phi^n on exit
     int nx, ny;
-    int pitch;             // elements between rows; ny * pitch < 2^31
+    int pitch;             // elements between rows
+    int plane;             // elements between population planes; 9 * plane < 2^31
     int hbb_x, hbb_y;      // 1: bounce-back walls on that axis, 0: periodic
     Real wref[9];          // w_i phi_ref (storage shift)
 
@@ -81,6 +82,7 @@ struct SweepParams {
 
     int first;             // 1: initialisation (f = f_eq(phi), no streaming)
     int *flags;            // bit 0: non-finite phi
+    double *resid_partials;  // non-null: per-block sum of (phi^n - phi^{n-1})^2 (single-lattice sweep)
     LinearConsts<Real> lin;
 };
 
@@ -325,11 +327,14 @@ __device__ __forceinline__ T ldg(const T *ptr) {
 
 // Sweep `nrows` nodes of column x, rows ybase, ybase + ystride, ...: pull,
 // collide, write back.  Returns the sum over those nodes of (phi^n - phi^{n-1})^2
-// when want_resid is set (steady-state residual), else 0.
-template <typename Real, typename S, int MODE, bool L2ONLY>
+// when RESID (steady-state residual), else 0.  RESID is a template argument so
+// that no FP64 arithmetic is ever issued (or speculated) in ordinary sweeps.
+template <typename Real, typename S, int MODE, bool L2ONLY, bool RESID>
 __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, int ybase, int ystride,
-                                             int nrows, bool want_resid) {
+                                             int nrows) {
     constexpr bool kShift = Shifted<S>::value;
+    const S *__restrict__ fin = static_cast<const S *>(p.fin);
+    S *__restrict__ fout = static_cast<S *>(p.fout);
     Real xs = Real(0), xc = Real(0);
     if (p.src_kind == 2) { xs = p.Xs[x]; xc = p.Xc[x]; }
     const bool x_inner = (x > 0) && (x < p.nx - 1);
@@ -347,8 +352,7 @@ __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, 
         } else if (x_inner && y > 0 && y < p.ny - 1) {
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const S *plane = static_cast<const S *>(p.fin[i]);
-                f[i] = Storage<S>::load(ldg<L2ONLY>(plane + (node - ey_of(i) * p.pitch - ex_of(i))));
+                f[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + node - ey_of(i) * p.pitch - ex_of(i))));
                 if (kShift) f[i] += p.wref[i];
             }
         } else {
@@ -361,8 +365,7 @@ __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, 
                 if (sy < 0) { if (p.hbb_y) wy = 2; else sy += p.ny; }
                 if (sy >= p.ny) { if (p.hbb_y) wy = 3; else sy -= p.ny; }
                 if (wx < 0 && wy < 0) {
-                    const S *plane = static_cast<const S *>(p.fin[i]);
-                    f[i] = Storage<S>::load(ldg<L2ONLY>(plane + (sy * p.pitch + sx)));
+                    f[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + sy * p.pitch + sx)));
                     if (kShift) f[i] += p.wref[i];
                 } else {
                     // the node's own population leaving towards the wall (direction opp(i))
@@ -375,8 +378,7 @@ __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, 
                         phi_w = wall_value(p, wy, x);
                     else
                         phi_w = wall_value(p, wx, y);
-                    const S *oplane = static_cast<const S *>(p.fin[o]);
-                    Real fo = Storage<S>::load(ldg<L2ONLY>(oplane + node));
+                    Real fo = Storage<S>::load(ldg<L2ONLY>(fin + (o * p.plane + node)));
                     if (kShift) fo += p.wref[o];
                     f[i] = -fo + wall_term(p, o, phi_w);
                 }
@@ -397,13 +399,10 @@ __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, 
         }
 
 #pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            S *plane = static_cast<S *>(p.fout[i]);
-            plane[node] = Storage<S>::pack(kShift ? f[i] - p.wref[i] : f[i]);
-        }
+        for (int i = 0; i < 9; ++i) fout[i * p.plane + node] = Storage<S>::pack(kShift ? f[i] - p.wref[i] : f[i]);
         p.phi[node] = phi;
         if (not_finite(phi)) atomicOr(p.flags, 1);
-        if (want_resid) {
+        if (RESID) {
             const double d = (double)phi - (double)phi_prev;
             resid = fma(d, d, resid);
         }
@@ -417,9 +416,21 @@ template <typename Real, typename S, int MODE>
 __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams<Real> p) {
     constexpr int R = RowsPerThread<Real>::value;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= p.nx) return;
     const int ybase = blockIdx.y * blockDim.y * R + threadIdx.y;
-    sweep_rows<Real, S, MODE, false>(p, x, ybase, blockDim.y, R, false);
+    if (!p.resid_partials) {
+        if (x < p.nx) sweep_rows<Real, S, MODE, false, false>(p, x, ybase, blockDim.y, R);
+        return;
+    }
+    // residual step: every thread joins the fixed-order block reduction
+    __shared__ double red[256];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    red[tid] = x < p.nx ? sweep_rows<Real, S, MODE, false, true>(p, x, ybase, blockDim.y, R) : 0.0;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if (tid < s) red[tid] += red[tid + s];
+        __syncthreads();
+    }
+    if (tid == 0) p.resid_partials[blockIdx.y * gridDim.x + blockIdx.x] = red[0];
 }
 
 }  // namespace btrt

@@ -145,6 +145,12 @@ class Lattice:
         C.check(self.lib.btrt_step(self.handle, int(nsteps)))
         return self
 
+    def step_residual(self, nsteps: int = 1) -> float:
+        """Advance nsteps and return ||phi^n - phi^{n-1}||_2 of the last step."""
+        r = ctypes.c_double()
+        C.check(self.lib.btrt_step_residual(self.handle, int(nsteps), ctypes.byref(r)))
+        return r.value
+
     def phi(self, out: Optional[torch.Tensor] = None, dtype=None) -> torch.Tensor:
         """phi as a device tensor (asynchronous on the lattice stream)."""
         dtype = dtype or self.real_dtype
@@ -201,6 +207,71 @@ class Lattice:
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             self.lib.btrt_destroy(self.handle)
+            self.handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent lattices advanced together by one persistent launch per call
+    (see btrt_batch_* in include/btrt.h)."""
+
+    def __init__(self, lattices, stream=None, device=None):
+        self.lib = C.load()
+        self.members = list(lattices)
+        n = len(self.members)
+        self._handles = (ctypes.c_void_p * n)(*[m.handle.value for m in self.members])
+        self.device = torch.device(device if device is not None else self.members[0].device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        nbytes = self.lib.btrt_batch_workspace_bytes(self._handles, n)
+        if nbytes == 0:
+            raise C.BtrtError(C.EINVAL, self.lib.btrt_last_error().decode())
+        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        C.check(self.lib.btrt_batch_create(self._handles, n, ctypes.c_void_p(self.workspace.data_ptr()),
+                                           int(nbytes), ctypes.c_void_p(self.stream.cuda_stream),
+                                           ctypes.byref(h)))
+        self.handle = h
+
+    def __len__(self):
+        return len(self.members)
+
+    def step(self, nsteps: int, residual: bool = False):
+        C.check(self.lib.btrt_batch_step(self.handle, int(nsteps), 1 if residual else 0))
+        return self
+
+    def residuals(self) -> np.ndarray:
+        out = np.empty(len(self.members), dtype=np.float64)
+        C.check(self.lib.btrt_batch_residuals(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return out
+
+    def set_tiles(self, block_x: int, block_y: int, rows: int, per_step: int = 0):
+        C.check(self.lib.btrt_batch_set_tiles(self.handle, block_x, block_y, rows, per_step))
+        return self
+
+    def autotune(self, steps_per_trial: int = 4):
+        """Returns (block_x, block_y, rows, per_step_launch) of the fastest candidate."""
+        bx, by, r, ps = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        C.check(self.lib.btrt_batch_autotune(self.handle, steps_per_trial, ctypes.byref(bx),
+                                             ctypes.byref(by), ctypes.byref(r), ctypes.byref(ps)))
+        return bx.value, by.value, r.value, ps.value
+
+    def check(self) -> int:
+        flags = ctypes.c_int32()
+        C.check(self.lib.btrt_batch_check(self.handle, ctypes.byref(flags)))
+        return flags.value
+
+    def set_wait_limit(self, polls: int, never_release: bool = False):
+        C.check(self.lib.btrt_batch_set_wait_limit(self.handle, int(polls), 1 if never_release else 0))
+        return self
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            self.lib.btrt_batch_destroy(self.handle)
             self.handle = ctypes.c_void_p()
 
     def __del__(self):

@@ -1,0 +1,172 @@
+"""Continuous-batching solve server for B-TriRT lattices.
+
+Requests (lattice problems) arrive over time.  The server admits them while the
+device-memory budget allows, keeps every admitted lattice resident, and
+advances all active lattices together in slices of ``slice_steps`` steps with
+one persistent batched launch per slice (:class:`~.lattice.Batch`).  At every
+slice boundary it reads each member's steady-state residual
+||phi^{n+1} - phi^n||_2 (computed on the device in the last step of the slice),
+retires the members that converged (residual < tol) or reached ``max_steps``,
+copies their phi to the host, frees their memory and admits waiting requests.
+Requests that arrive while others run therefore join at the next boundary and
+share the device with them.
+
+:func:`serve_sequential` is the plain baseline: the same requests, first come
+first served, one lattice at a time with plain per-step launches and the same
+stopping rule.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+from collections import deque
+from typing import List, Optional
+
+import numpy as np
+import torch
+
+from .lattice import Batch, Lattice, grid_desc, workspace_bytes
+
+
+@dataclasses.dataclass
+class Result:
+    rid: int
+    arrival: float          # seconds since the start of the trace
+    admitted: float
+    finished: float
+    steps: int
+    residual: float
+    phi: np.ndarray
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def _bytes_needed(p, compute, storage) -> int:
+    d = grid_desc(p.nx, p.ny, p.dx, p.dt, p.bc, compute, storage, p.x0, p.y0, p.phi_ref)
+    return workspace_bytes(d)
+
+
+class Server:
+    def __init__(self, budget_bytes: float = 150e9, slice_steps: int = 100, max_steps: int = 20000,
+                 tol: float = 1e-8, compute: str = "f32", storage: str = "f16",
+                 max_active: int = 4096, stream=None, tiles=None):
+        self.budget = float(budget_bytes)
+        self.slice_steps = int(slice_steps)
+        self.max_steps = int(max_steps)
+        self.tol = float(tol)
+        self.compute, self.storage = compute, storage
+        self.max_active = max_active
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.tiles = tiles
+        self.stats = dict(slices=0, rebuilds=0, peak_active=0, peak_bytes=0)
+
+    def run(self, trace) -> List[Result]:
+        """trace: list of (arrival_seconds, problem), arrival-sorted.  Runs in real
+        time: a request becomes visible once the wall clock passes its arrival."""
+        t0 = time.perf_counter()
+        pending = deque((i, a, p) for i, (a, p) in enumerate(trace))
+        waiting = deque()
+        active = []            # [rid, arrival, admitted, lattice, bytes, steps]
+        used = 0.0
+        results: List[Result] = []
+        batch: Optional[Batch] = None
+        dirty = True
+        while pending or waiting or active:
+            now = time.perf_counter() - t0
+            while pending and pending[0][1] <= now:
+                waiting.append(pending.popleft())
+            # admission by memory budget (and a cap on members)
+            while waiting and len(active) < self.max_active:
+                rid, arr, p = waiting[0]
+                need = _bytes_needed(p, self.compute, self.storage)
+                if used + need > self.budget and active:
+                    break
+                waiting.popleft()
+                lat = Lattice.from_problem(p, compute=self.compute, storage=self.storage,
+                                           stream=self.stream)
+                lat.init(p.phi0(), t0=p.t0)
+                used += need
+                active.append([rid, arr, time.perf_counter() - t0, lat, need, 0])
+                dirty = True
+            self.stats["peak_active"] = max(self.stats["peak_active"], len(active))
+            self.stats["peak_bytes"] = max(self.stats["peak_bytes"], used)
+            if not active:
+                if pending:   # idle until the next arrival
+                    time.sleep(max(0.0, min(0.002, pending[0][1] - (time.perf_counter() - t0))))
+                continue
+            if dirty:
+                if batch is not None:
+                    batch.close()
+                batch = Batch([a[3] for a in active], stream=self.stream)
+                if self.tiles:
+                    batch.set_tiles(*self.tiles)
+                self.stats["rebuilds"] += 1
+                dirty = False
+            batch.step(self.slice_steps, residual=True)
+            res = batch.residuals()          # synchronises
+            self.stats["slices"] += 1
+            done_idx = []
+            for k, a in enumerate(active):
+                a[5] += self.slice_steps
+                if res[k] < self.tol or a[5] >= self.max_steps:
+                    done_idx.append(k)
+            if done_idx:
+                for k in reversed(done_idx):
+                    rid, arr, adm, lat, need, steps = active[k]
+                    phi = lat.phi_host()
+                    results.append(Result(rid, arr, adm, time.perf_counter() - t0, steps,
+                                          float(res[k]), phi))
+                    used -= need
+                    del active[k]
+                batch.close()
+                batch = None
+                dirty = True
+        if batch is not None:
+            batch.close()
+        results.sort(key=lambda r: r.rid)
+        return results
+
+
+def serve_sequential(trace, slice_steps: int = 100, max_steps: int = 20000, tol: float = 1e-8,
+                     compute: str = "f32", storage: str = "f16", stream=None) -> List[Result]:
+    """Plain baseline: one request at a time in arrival order, plain per-step
+    launches, the same residual check every slice_steps steps."""
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    results = []
+    for rid, (arr, p) in enumerate(trace):
+        now = time.perf_counter() - t0
+        if now < arr:
+            time.sleep(arr - now)
+        adm = time.perf_counter() - t0
+        lat = Lattice.from_problem(p, compute=compute, storage=storage, stream=stream)
+        lat.init(p.phi0(), t0=p.t0)
+        steps, r = 0, float("inf")
+        while True:
+            r = lat.step_residual(slice_steps)
+            steps += slice_steps
+            if r < tol or steps >= max_steps:
+                break
+        phi = lat.phi_host()
+        results.append(Result(rid, arr, adm, time.perf_counter() - t0, steps, r, phi))
+        del lat
+    return results
+
+
+def poisson_trace(problems, rate: float, seed: int = 0):
+    """Arrival times of a Poisson process of the given rate (requests/s)."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=len(problems)))
+    return [(float(a), p) for a, p in zip(t, problems)]
+
+
+def summarize(results: List[Result]) -> dict:
+    lat = np.array([r.latency for r in results])
+    span = max(r.finished for r in results) - min(r.arrival for r in results)
+    return {"requests": len(results), "solves_per_s": round(len(results) / span, 3),
+            "p50_s": round(float(np.percentile(lat, 50)), 4),
+            "p99_s": round(float(np.percentile(lat, 99)), 4),
+            "mean_steps": round(float(np.mean([r.steps for r in results])), 1),
+            "span_s": round(span, 3)}
