@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "B-TriRT D2Q9 MLUPS & % HBM roofline; served solves/s + p50/p99 vs plain"
 N_MAIN = 8192
-BYTES_PER_UPDATE = {"f64": 160, "f32": 80, "f16": 44, "bf16": 44}
+BYTES_PER_UPDATE = {"f64": 160, "df64": 160, "f32": 80, "f16": 44, "bf16": 44}
 
 
 def _peaks():
@@ -50,9 +50,10 @@ FP64_OPS_PER_UPDATE_LINEAR = 59
 # 0.625 T FP64 operations/s when every add, mul or fma takes one lane slot.
 FP64_PEAK_TOPS = 0.625
 # DRAM bytes per node of one FP64 sweep launch measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the same kernel; None when
-# the kernel changed after the capture.
-FP64_TRAFFIC_PER_NODE = None
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the same kernel at 2048^2
+# (profiles/sweep_f64_mms2048_full.md), scaled to the benchmark by node count;
+# None when the kernel changed after the capture.
+FP64_TRAFFIC_PER_NODE = 148.8
 
 
 def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
@@ -221,8 +222,11 @@ def run_gpu(args):
         e2e_mlups = ws * nodes * args.steps / float(e2e_t.item()) / 1e6
 
     extra = {}
+    del lat
+    torch.cuda.empty_cache()
+    if not args.no_variants:
+        extra["variants"] = run_variants(args)
     if not args.no_batched:
-        del lat
         torch.cuda.empty_cache()
         extra["batched"] = run_batched(args)
     if not args.no_serving:
@@ -251,6 +255,52 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if ws > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------- variants
+def _time_single(p, phi0, compute, storage, steps, warmup):
+    import torch
+    from paper_1902_09813_gb300 import Lattice
+    stream = torch.cuda.Stream()
+    lat = Lattice.from_problem(p, compute=compute, storage=storage, stream=stream)
+    lat.init(phi0)
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lat.check()
+    ms = e0.elapsed_time(e1)
+    nodes = p.nx * p.ny
+    mlups = nodes * steps / (ms * 1e-3) / 1e6
+    peak, _ = _peaks()
+    gbs = BYTES_PER_UPDATE[storage] * mlups * 1e6 / 1e9
+    del lat
+    torch.cuda.empty_cache()
+    return {"mlups": round(mlups, 1), "ms_per_step": round(ms / steps, 4),
+            "algorithmic_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
+
+
+def run_variants(args, steps=200, warmup=5):
+    """The other compute/storage paths at 8192^2: double-word (FP32-pair) arithmetic
+    on the manufactured-solution workload, FP32 compute with FP32/FP16/BF16 shifted
+    storage on the manufactured-solution and nonlinear workloads."""
+    import workloads as w
+    out = {}
+    p = w.mms_sinsin(n=args.n, nsteps=steps)
+    phi0 = p.phi0()
+    out["mms_df64"] = _time_single(p, phi0, "df64", "df64", steps, warmup)
+    for st in ("f32", "f16", "bf16"):
+        out[f"mms_f32_{st}"] = _time_single(p, phi0, "f32", st, steps, warmup)
+    q = w.nonlinear_modes(n=args.n, nsteps=steps)
+    phi0 = q.phi0()
+    q.phi_ref = float(phi0.mean())
+    for st in ("f32", "f16", "bf16"):
+        out[f"nonlinear_f32_{st}"] = _time_single(q, phi0, "f32", st, steps, warmup)
+    out["nonlinear_f64"] = _time_single(q, phi0, "f64", "f64", 50, 3)
+    return out
 
 
 # ---------------------------------------------------------------------------- batched
@@ -427,6 +477,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-seq", type=int, default=48)
     ap.add_argument("--batched-only", action="store_true",
@@ -435,8 +486,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--workload", default="mms", choices=["mms", "nonlinear"])
     ap.add_argument("--n", type=int, default=N_MAIN)
-    ap.add_argument("--compute", default="f64", choices=["f64", "f32"])
-    ap.add_argument("--storage", default=None, choices=["f64", "f32", "f16", "bf16"])
+    ap.add_argument("--compute", default="f64", choices=["f64", "df64", "f32"])
+    ap.add_argument("--storage", default=None, choices=["f64", "df64", "f32", "f16", "bf16"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
