@@ -53,7 +53,7 @@ FP64_PEAK_TOPS = 0.625
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the same kernel at 2048^2
 # (profiles/sweep_f64_mms2048_full.md), scaled to the benchmark by node count;
 # None when the kernel changed after the capture.
-FP64_TRAFFIC_PER_NODE = 148.8
+FP64_TRAFFIC_PER_NODE = None
 
 
 def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
@@ -142,6 +142,19 @@ def _dist():
     return ws, rank, local
 
 
+def aggregate(ms_local: float, units_per_rank: float, device):
+    """Whole-job timing across replicas: the slowest rank's time (MAX over ranks)
+    and the throughput of all ranks' units over that time.  One process: as is."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    if ws > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    return ms, ws * units_per_rank / (ms * 1e-3)
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -174,6 +187,8 @@ def run_gpu(args):
     nodes = p.nx * p.ny
     stream = torch.cuda.Stream()
     lat = Lattice.from_problem(p, compute=args.compute, storage=args.storage, stream=stream)
+    if args.compute == "f32":
+        lat.set_sweep_variant(args.sweep)
     lat.init(phi0)
     # warm-up
     lat.step(args.warmup)
@@ -190,12 +205,9 @@ def run_gpu(args):
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    t_local = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t_local, op=dist.ReduceOp.MAX)
-    ms_max = float(t_local.item())
+    ms_max, lups = aggregate(ms, nodes * args.steps, "cuda")
     lat.check()
-    mlups = ws * nodes * args.steps / (ms_max * 1e-3) / 1e6
+    mlups = lups / 1e6
 
     # dominant kernel: the sweep, one launch per step on `stream`
     t_launch = ms / args.steps * 1e-3
@@ -216,10 +228,8 @@ def run_gpu(args):
         lat.phi(out=out_pinned)
         stream.synchronize()
         e2e_s = time.perf_counter() - t0
-        e2e_t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(e2e_t, op=dist.ReduceOp.MAX)
-        e2e_mlups = ws * nodes * args.steps / float(e2e_t.item()) / 1e6
+        _, e2e_lups = aggregate(e2e_s * 1e3, nodes * args.steps, "cuda")
+        e2e_mlups = e2e_lups / 1e6
 
     extra = {}
     del lat
@@ -258,11 +268,13 @@ def run_gpu(args):
 
 
 # ---------------------------------------------------------------------------- variants
-def _time_single(p, phi0, compute, storage, steps, warmup):
+def _time_single(p, phi0, compute, storage, steps, warmup, variant="plain"):
     import torch
     from paper_1902_09813_gb300 import Lattice
     stream = torch.cuda.Stream()
     lat = Lattice.from_problem(p, compute=compute, storage=storage, stream=stream)
+    if compute == "f32":
+        lat.set_sweep_variant(variant)
     lat.init(phi0)
     lat.step(warmup)
     torch.cuda.synchronize()
@@ -294,11 +306,13 @@ def run_variants(args, steps=200, warmup=5):
     out["mms_df64"] = _time_single(p, phi0, "df64", "df64", steps, warmup)
     for st in ("f32", "f16", "bf16"):
         out[f"mms_f32_{st}"] = _time_single(p, phi0, "f32", st, steps, warmup)
+        out[f"mms_f32_{st}_tma"] = _time_single(p, phi0, "f32", st, steps, warmup, variant="tma")
     q = w.nonlinear_modes(n=args.n, nsteps=steps)
     phi0 = q.phi0()
     q.phi_ref = float(phi0.mean())
     for st in ("f32", "f16", "bf16"):
         out[f"nonlinear_f32_{st}"] = _time_single(q, phi0, "f32", st, steps, warmup)
+        out[f"nonlinear_f32_{st}_tma"] = _time_single(q, phi0, "f32", st, steps, warmup, variant="tma")
     out["nonlinear_f64"] = _time_single(q, phi0, "f64", "f64", 50, 3)
     return out
 
@@ -488,6 +502,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_MAIN)
     ap.add_argument("--compute", default="f64", choices=["f64", "df64", "f32"])
     ap.add_argument("--storage", default=None, choices=["f64", "df64", "f32", "f16", "bf16"])
+    ap.add_argument("--sweep", default="auto", choices=["auto", "plain", "tma"],
+                    help="kernel form of FP32-compute sweeps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

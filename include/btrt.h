@@ -52,9 +52,12 @@ typedef enum {
 } btrt_status;
 
 enum { BTRT_BC_PERIODIC = 0, BTRT_BC_HBB = 1 };                 /* boundary kinds     */
-enum { BTRT_F64 = 0, BTRT_F32 = 1, BTRT_F16 = 2, BTRT_BF16 = 3 };/* number formats     */
+/* number formats; BTRT_DF64 is double-word arithmetic and storage (a value is
+ * the unevaluated sum of two FP32 numbers, ~48 significant bits) */
+enum { BTRT_F64 = 0, BTRT_F32 = 1, BTRT_F16 = 2, BTRT_BF16 = 3, BTRT_DF64 = 4 };
 enum { BTRT_K2_HBB = 0, BTRT_K2_CONST = 1 };                    /* second-order block */
-enum { BTRT_SRC_NONE = 0, BTRT_SRC_CONST = 1, BTRT_SRC_TRIG = 2 };
+enum { BTRT_SRC_NONE = 0, BTRT_SRC_CONST = 1, BTRT_SRC_TRIG = 2, BTRT_SRC_FIELD = 3 };
+enum { BTRT_FIELD_SOURCE = 1, BTRT_FIELD_DIFFUSION = 2 };      /* btrt_grid_desc.fields bits */
 enum { BTRT_SIDE_XMIN = 0, BTRT_SIDE_XMAX = 1, BTRT_SIDE_YMIN = 2, BTRT_SIDE_YMAX = 3 };
 
 typedef struct btrt_lattice_s *btrt_lattice;
@@ -63,11 +66,14 @@ typedef struct btrt_lattice_s *btrt_lattice;
 typedef struct {
     int32_t nx, ny;        /* nodes; 3 <= nx, ny <= 65536 and 9 ny roundup(nx, 64) < 2^31 */
     int32_t bc[4];         /* BTRT_BC_* for sides x-, x+, y-, y+; opposite sides match  */
-    int32_t compute;       /* BTRT_F64 or BTRT_F32: arithmetic of the sweep             */
-    int32_t storage;       /* population storage: F64 (compute F64 only), F32, F16, BF16*/
+    int32_t compute;       /* BTRT_F64, BTRT_DF64 or BTRT_F32: arithmetic of the sweep  */
+    int32_t storage;       /* populations: F64 (F64 compute), DF64 (DF64 compute), or
+                              F32, F16, BF16 (F32 compute)                               */
     double dx, dt;         /* physical spacing and time step (c = dx/dt, cs^2 = c^2/3)  */
     double x0, y0;         /* physical position of the lower-left domain corner         */
     double phi_ref;        /* F32/F16/BF16 storage holds f_i - w_i phi_ref (F64: unshifted) */
+    int32_t fields;        /* BTRT_FIELD_* bits: reserve per-node source / diffusion planes */
+    int32_t reserved;
 } btrt_grid_desc;
 
 /* Coefficients of Eq. 1 and the relaxation parameters (physical units). */
@@ -82,7 +88,8 @@ typedef struct {
     int32_t src_kind;      /* BTRT_SRC_*                                          */
     double k2;             /* used when k2_mode == BTRT_K2_CONST, in (0, 2)       */
     double src_const;      /* BTRT_SRC_CONST: S = src_const                       */
-    double src_lam, src_k; /* BTRT_SRC_TRIG: S = exp(lam t) sum alpha_pq X_p Y_q  */
+    double src_lam, src_k; /* BTRT_SRC_TRIG: S = exp(lam t) sum alpha_pq X_p Y_q;
+                              BTRT_SRC_FIELD: S = exp(lam t) F(x) (btrt_set_source_field) */
     double src_alpha[4];   /*   {ss, sc, cs, cc}: X_s = sin(k x), X_c = cos(k x)  */
     double wall_lam;       /* wall values carry the factor exp(wall_lam t)        */
 } btrt_coeffs;
@@ -108,6 +115,16 @@ btrt_status btrt_set_coeffs(btrt_lattice L, const btrt_coeffs *c);
  * value per boundary node, read from host memory and copied.  The value used at
  * a step is phi_w * exp(wall_lam * t_{n+1}). */
 btrt_status btrt_set_boundary(btrt_lattice L, int32_t side, const double *phi_w_host, int32_t n);
+
+/* Per-node source field F(x) for BTRT_SRC_FIELD: nx*ny values in host memory,
+ * row major; needs BTRT_FIELD_SOURCE in the grid description. */
+btrt_status btrt_set_source_field(btrt_lattice L, const double *F_host);
+
+/* Spatially varying diffusion tensor (physical units, nx*ny values each, row
+ * major, host memory): A(x, phi) = (1 + a2 phi^2) A(x) replaces A0.  Every node's
+ * tensor must be symmetric positive definite.  Needs BTRT_FIELD_DIFFUSION; the
+ * first-order block K1 (Eq. 30) and k2 are then built at every node. */
+btrt_status btrt_set_diffusion_field(btrt_lattice L, const double *Axx, const double *Axy, const double *Ayy);
 
 /* Initial state f_i = f_i^eq(phi0) at time t0 (Sec. 4).  phi0: nx*ny values of
  * dtype BTRT_F64 or BTRT_F32, in host memory (on_device = 0) or device memory
@@ -137,10 +154,19 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst_host, int32_t x0, int32_t y0
  * Synchronises. */
 btrt_status btrt_mass(btrt_lattice L, double *out);
 
-/* Non-finite flag raised by the sweep since the last btrt_init_phi: *flags = 1
- * if any node produced a NaN/Inf phi.  Synchronises; returns BTRT_EUNSTABLE
- * when the flag is set. */
+/* Flags raised by the sweep since the last btrt_init_phi: bit 0 = some node
+ * produced a NaN/Inf phi (returns BTRT_EUNSTABLE), bit 2 = a bounded wait for a
+ * tile copy gave up (returns BTRT_ETIMEOUT).  Synchronises. */
 btrt_status btrt_check(btrt_lattice L, int32_t *flags);
+
+/* Kernel form of the ordinary FP32-compute sweep: BTRT_SWEEP_AUTO (default: the
+ * faster form as measured on GB300, currently the plain one), BTRT_SWEEP_PLAIN
+ * (two nodes per thread, direct global loads served by L1/L2) or BTRT_SWEEP_TMA
+ * (persistent tiles staged in shared memory by TMA with mbarrier pipelining).
+ * Both forms give bitwise identical results.  FP64 and double-word lattices
+ * always use the plain form. */
+enum { BTRT_SWEEP_AUTO = 0, BTRT_SWEEP_PLAIN = 1, BTRT_SWEEP_TMA = 2 };
+btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant);
 
 /* Number of completed steps and the current time t0 + n dt. */
 btrt_status btrt_get_time(btrt_lattice L, int64_t *step, double *t);

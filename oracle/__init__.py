@@ -30,7 +30,7 @@ NQ = 9
 
 _BC = {0: 0, 1: 1}
 _K2 = {"hbb": 0, "const": 1}
-_SRC_KIND = {"none": 0, "const": 1, "trig": 2}
+_SRC_KIND = {"none": 0, "const": 1, "trig": 2, "field": 3}
 
 
 def build(force: bool = False) -> Path:
@@ -66,6 +66,8 @@ class _Problem(ctypes.Structure):
         ("wall", ctypes.c_double * 4),
         ("wall_lam", ctypes.c_double),
         ("wall_arr", ctypes.c_void_p * 4),
+        ("src_field", ctypes.c_void_p),
+        ("A_field", ctypes.c_void_p * 3),
     ]
 
 
@@ -139,6 +141,17 @@ def make_problem(p) -> tuple:
                 a = np.ascontiguousarray(arr, dtype=np.float64)
                 keep.append(a)
                 s.wall_arr[k] = a.ctypes.data
+    if getattr(p, "src_field", None) is not None:
+        a = np.ascontiguousarray(p.src_field, dtype=np.float64)
+        assert a.shape == (p.ny, p.nx)
+        keep.append(a)
+        s.src_field = a.ctypes.data
+    if getattr(p, "A_field", None) is not None:
+        for k in range(3):
+            a = np.ascontiguousarray(p.A_field[k], dtype=np.float64)
+            assert a.shape == (p.ny, p.nx)
+            keep.append(a)
+            s.A_field[k] = a.ctypes.data
     return s, keep
 
 

@@ -65,7 +65,7 @@ static int opposite(int i)
 
 enum { BC_PERIODIC = 0, BC_HBB = 1 };
 enum { K2_HBB = 0, K2_CONST = 1 };
-enum { SRC_NONE = 0, SRC_CONST = 1, SRC_TRIG = 2 };
+enum { SRC_NONE = 0, SRC_CONST = 1, SRC_TRIG = 2, SRC_FIELD = 3 };
 
 typedef struct {
     int32_t nx, ny;
@@ -83,9 +83,20 @@ typedef struct {
     double wall[4];           /* constant wall value per side */
     double wall_lam;          /* wall values carry the time factor exp(wall_lam t) */
     const double *wall_arr[4];/* optional per-node wall values (NULL: constant) */
+    const double *src_field;  /* SRC_FIELD: S = exp(src_lam t) src_field[node] */
+    const double *A_field[3]; /* optional per-node diffusion tensor (xx, xy, yy): A = (1 + a2 phi^2) A(x) */
 } oracle_problem;
 
 /* ---------------------------------------------------------------- coefficients */
+
+/* Row-major index of the node whose cell centre is (x, y). */
+static long node_of(const oracle_problem *p, double x, double y)
+{
+    long ix = lround((x - p->x0) / p->dx - 0.5);
+    long iy = lround((y - p->y0) / p->dx - 0.5);
+    return iy * p->nx + ix;
+}
+
 
 void btrt_oracle_B(const oracle_problem *p, double phi, double B[2])
 {
@@ -109,12 +120,10 @@ void btrt_oracle_A(const oracle_problem *p, double phi, double A[4])
 }
 
 /* K1 from Eq. 30: K1^{-1} = A / (cs^2 dt) + I/2, inverted as a 2x2 matrix. */
-void btrt_oracle_K1(const oracle_problem *p, double phi, double K1[4])
+static void k1_of_A(const oracle_problem *p, const double A[4], double K1[4])
 {
     double c = p->dx / p->dt;
     double cs2 = c * c / 3.0;
-    double A[4];
-    btrt_oracle_A(p, phi, A);
     double M[4];
     for (int k = 0; k < 4; ++k) M[k] = A[k] / (cs2 * p->dt);
     M[0] += 0.5;
@@ -124,6 +133,37 @@ void btrt_oracle_K1(const oracle_problem *p, double phi, double K1[4])
     K1[1] = -M[1] / det;
     K1[2] = -M[2] / det;
     K1[3] = M[0] / det;
+}
+
+/* K1 of Eq. 30 for the uniform tensor A(phi). */
+void btrt_oracle_K1(const oracle_problem *p, double phi, double K1[4])
+{
+    double A[4];
+    btrt_oracle_A(p, phi, A);
+    k1_of_A(p, A, K1);
+}
+
+/* A(x, phi) at the node centred at (x, y): the per-node tensor when one is given. */
+void btrt_oracle_A_at(const oracle_problem *p, double phi, double x, double y, double A[4])
+{
+    if (!p->A_field[0]) {
+        btrt_oracle_A(p, phi, A);
+        return;
+    }
+    long n = node_of(p, x, y);
+    double s = 1.0 + p->a2 * phi * phi;
+    A[0] = s * p->A_field[0][n];
+    A[1] = s * p->A_field[1][n];
+    A[2] = s * p->A_field[1][n];
+    A[3] = s * p->A_field[2][n];
+}
+
+/* K1 from Eq. 30 at the node centred at (x, y). */
+void btrt_oracle_K1_at(const oracle_problem *p, double phi, double x, double y, double K1[4])
+{
+    double A[4];
+    btrt_oracle_A_at(p, phi, x, y, A);
+    k1_of_A(p, A, K1);
 }
 
 /* Eq. 62 */
@@ -145,6 +185,7 @@ double btrt_oracle_source(const oracle_problem *p, double x, double y, double t)
 {
     if (p->src_kind == SRC_NONE) return 0.0;
     if (p->src_kind == SRC_CONST) return p->src_const;
+    if (p->src_kind == SRC_FIELD) return exp(p->src_lam * t) * p->src_field[node_of(p, x, y)];
     double sx = sin(p->src_k * x), cx = cos(p->src_k * x);
     double sy = sin(p->src_k * y), cy = cos(p->src_k * y);
     return exp(p->src_lam * t) * (p->src_alpha[0] * sx * sy + p->src_alpha[1] * sx * cy +
@@ -235,7 +276,7 @@ void btrt_oracle_collide(const oracle_problem *p, const double f[NQ], double phi
     for (int i = 0; i < NQ; ++i) fneq[i] = f[i] - feq[i];
 
     double K1[4];
-    btrt_oracle_K1(p, phi, K1);
+    btrt_oracle_K1_at(p, phi, x, y, K1);
     double k2 = btrt_oracle_k2(p, K1);
     double K2[4] = {k2, k2, k2, k2}; /* K2 = k2 Ihat */
 

@@ -8,11 +8,13 @@ LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libbtrt.so"
 
 OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, -6
 BC_PERIODIC, BC_HBB = 0, 1
-F64, F32, F16, BF16 = 0, 1, 2, 3
+F64, F32, F16, BF16, DF64 = 0, 1, 2, 3, 4
 K2_HBB, K2_CONST = 0, 1
-SRC_NONE, SRC_CONST, SRC_TRIG = 0, 1, 2
+SRC_NONE, SRC_CONST, SRC_TRIG, SRC_FIELD = 0, 1, 2, 3
+FIELD_SOURCE, FIELD_DIFFUSION = 1, 2
+SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA = 0, 1, 2
 
-FORMATS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16}
+FORMATS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "df64": DF64}
 
 
 class GridDesc(ctypes.Structure):
@@ -23,6 +25,7 @@ class GridDesc(ctypes.Structure):
         ("dx", ctypes.c_double), ("dt", ctypes.c_double),
         ("x0", ctypes.c_double), ("y0", ctypes.c_double),
         ("phi_ref", ctypes.c_double),
+        ("fields", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -51,6 +54,8 @@ SIGNATURES = [
     ("btrt_create", ctypes.c_int, [ctypes.POINTER(GridDesc), _vp, _sz, _vp, ctypes.POINTER(_vp)]),
     ("btrt_set_coeffs", ctypes.c_int, [_vp, ctypes.POINTER(Coeffs)]),
     ("btrt_set_boundary", ctypes.c_int, [_vp, _i32, _dp, _i32]),
+    ("btrt_set_source_field", ctypes.c_int, [_vp, _dp]),
+    ("btrt_set_diffusion_field", ctypes.c_int, [_vp, _dp, _dp, _dp]),
     ("btrt_init_phi", ctypes.c_int, [_vp, _vp, _i32, _i32, ctypes.c_double]),
     ("btrt_step", ctypes.c_int, [_vp, _i64]),
     ("btrt_step_residual", ctypes.c_int, [_vp, _i64, _dp]),
@@ -58,6 +63,7 @@ SIGNATURES = [
     ("btrt_read_f", ctypes.c_int, [_vp, _dp, _i32, _i32, _i32, _i32]),
     ("btrt_mass", ctypes.c_int, [_vp, _dp]),
     ("btrt_check", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    ("btrt_set_sweep_variant", ctypes.c_int, [_vp, _i32]),
     ("btrt_get_time", ctypes.c_int, [_vp, ctypes.POINTER(_i64), _dp]),
     ("btrt_state_bytes", _sz, [_vp]),
     ("btrt_save", ctypes.c_int, [_vp, _vp, _sz]),

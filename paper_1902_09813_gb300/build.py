@@ -18,7 +18,10 @@ CSRC = PKG / "csrc"
 OUT = PKG / "_lib"
 LIB = OUT / "libbtrt.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+# -fmad=false: no implicit contraction of a*b + c into an FMA.  The hot paths
+# write their FMAs explicitly, so every kernel form (plain, TMA-staged, batched)
+# rounds each node's arithmetic identically and their results agree bitwise.
+NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-fmad=false", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
               "--expt-relaxed-constexpr", "-I", str(ROOT / "include")] + ARCH
 
 
@@ -65,7 +68,8 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> Path:
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(compile_one, _sources()))
     tmp = str(LIB) + ".tmp"
-    cmd = [nvcc(), "-shared", "-o", tmp] + [str(o) for o in objs] + ARCH + ["-lcudart"]
+    # --no-undefined: a missing template instantiation fails the build, not the first dlopen
+    cmd = [nvcc(), "-shared", "-o", tmp] + [str(o) for o in objs] + ARCH + ["-lcudart", "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -18,6 +18,8 @@
 #include "../../include/btrt.h"
 #include "btrt_internal.h"
 
+#include <cudaTypedefs.h>
+
 using namespace btrt;
 
 namespace {
@@ -46,6 +48,39 @@ constexpr size_t kAlign = 256;
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(ptr);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3-D tensor map over one population buffer: {x: nx, y: ny, plane: 9}.
+bool encode_buffer_map(CUtensorMap *map, void *base, const btrt_grid_desc &g, long long pitch, long long plane,
+                       int box_x, int box_y) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc) return false;
+    const size_t es = elem_size(g.storage);
+    const CUtensorMapDataType dt = g.storage == BTRT_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_UINT16;
+    const cuuint64_t dims[3] = {(cuuint64_t)g.nx, (cuuint64_t)g.ny, 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)(pitch * es), (cuuint64_t)(plane * es)};
+    const cuuint32_t box[3] = {(cuuint32_t)box_x, (cuuint32_t)box_y, 9};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 btrt_status check_desc(const btrt_grid_desc *g) {
     if (!g) return fail(BTRT_EINVAL, "null grid description");
     if (g->nx < 3 || g->ny < 3 || g->nx > 65536 || g->ny > 65536)
@@ -58,16 +93,21 @@ btrt_status check_desc(const btrt_grid_desc *g) {
     if (g->compute == BTRT_F64) {
         if (g->storage != BTRT_F64)
             return fail(BTRT_EINVAL, "FP64 compute requires FP64 storage");
+    } else if (g->compute == BTRT_DF64) {
+        if (g->storage != BTRT_DF64)
+            return fail(BTRT_EINVAL, "double-word compute requires double-word storage");
     } else if (g->compute == BTRT_F32) {
         if (g->storage != BTRT_F32 && g->storage != BTRT_F16 && g->storage != BTRT_BF16)
             return fail(BTRT_EINVAL, "FP32 compute takes F32, F16 or BF16 storage");
     } else {
-        return fail(BTRT_EINVAL, "compute must be BTRT_F64 or BTRT_F32");
+        return fail(BTRT_EINVAL, "compute must be BTRT_F64, BTRT_DF64 or BTRT_F32");
     }
     if (!(g->dx > 0.0) || !(g->dt > 0.0) || !std::isfinite(g->dx) || !std::isfinite(g->dt))
         return fail(BTRT_EINVAL, "dx and dt must be positive and finite");
     if (!std::isfinite(g->phi_ref) || !std::isfinite(g->x0) || !std::isfinite(g->y0))
         return fail(BTRT_EINVAL, "phi_ref, x0, y0 must be finite");
+    if (g->fields & ~(BTRT_FIELD_SOURCE | BTRT_FIELD_DIFFUSION))
+        return fail(BTRT_EINVAL, "unknown field bits 0x%x", g->fields);
     const long long pitch = (long long)((g->nx + 63) / 64) * 64;
     if (9 * pitch * (long long)g->ny >= (1LL << 31))
         return fail(BTRT_EINVAL, "grid %d x %d: the nine padded planes must hold fewer than 2^31 values "
@@ -96,9 +136,17 @@ Layout make_layout(const btrt_grid_desc *g) {
     off += align_up(4 * (size_t)L.maxside * sr, kAlign);
     L.off_red = off;
     off += align_up((kRedBlocks + 2) * sizeof(double) + 16, kAlign);
-    L.resid_blocks = sweep_blocks(g->nx, g->ny, g->compute);
+    L.resid_blocks = sweep_blocks(g->nx, g->ny, g->compute, g->storage);
     L.off_resid = off;
     off += align_up((size_t)L.resid_blocks * sizeof(double), kAlign);
+    if (g->fields & BTRT_FIELD_SOURCE) {
+        L.off_srcf = off;
+        off += align_up((size_t)L.plane * sr, kAlign);
+    }
+    if (g->fields & BTRT_FIELD_DIFFUSION) {
+        L.off_af = off;
+        off += align_up(3 * (size_t)L.plane * sr, kAlign);
+    }
     L.total = off;
     return L;
 }
@@ -109,7 +157,7 @@ __global__ void dense_to_plane(const In *__restrict__ src, Real *__restrict__ ds
                                long long pitch) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    if (x < nx && y < ny) dst[(long long)y * pitch + x] = (Real)src[(long long)y * nx + x];
+    if (x < nx && y < ny) dst[(long long)y * pitch + x] = Real((double)src[(long long)y * nx + x]);
 }
 
 template <typename Real, typename Out>
@@ -117,7 +165,7 @@ __global__ void plane_to_dense(const Real *__restrict__ src, Out *__restrict__ d
                                long long pitch) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
-    if (x < nx && y < ny) dst[(long long)y * nx + x] = (Out)src[(long long)y * pitch + x];
+    if (x < nx && y < ny) dst[(long long)y * nx + x] = (Out) static_cast<double>(src[(long long)y * pitch + x]);
 }
 
 // FP64 sum of a plane: every block owns the rows y = b, b + gridDim.x, ...;
@@ -129,7 +177,7 @@ plane_sum_partials(const Real *__restrict__ a, int nx, int ny, long long pitch, 
     __shared__ double sh[kRedThreads];
     double acc = 0.0;
     for (int y = blockIdx.x; y < ny; y += gridDim.x)
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) acc += (double)a[(long long)y * pitch + x];
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) acc += static_cast<double>(a[(long long)y * pitch + x]);
     sh[threadIdx.x] = acc;
     __syncthreads();
     for (int s = kRedThreads / 2; s > 0; s >>= 1) {
@@ -169,6 +217,7 @@ size_t btrt::elem_size(int fmt) {
     case BTRT_F32: return 4;
     case BTRT_F16: return 2;
     case BTRT_BF16: return 2;
+    case BTRT_DF64: return 8;
     default: return 0;
     }
 }
@@ -181,7 +230,7 @@ void btrt::step_scalars(btrt_lattice L, int64_t n, bool first, double *src_val, 
     *wall_fac = c.wall_lam == 0.0 ? 1.0 : std::exp(c.wall_lam * tn);
     if (c.src_kind == BTRT_SRC_CONST) {
         *src_val = c.src_const * g.dt;
-    } else if (c.src_kind == BTRT_SRC_TRIG) {
+    } else if (c.src_kind == BTRT_SRC_TRIG || c.src_kind == BTRT_SRC_FIELD) {
         // dt S_i + dt^2/2 (S_i^n - S_i^{n-1})/dt = w_i dt (3 S^n - S^{n-1}) / 2 (scheme 2)
         const double Tn = std::exp(c.src_lam * tn);
         const double Tp = first ? Tn : std::exp(c.src_lam * (tn - g.dt));
@@ -233,6 +282,8 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
     p.cond_limit = (Real)1.0e4;
     p.src_kind = c.src_kind;
     p.src_val = (Real)src_val;
+    p.srcF = L->srcf<Real>();
+    p.Af = L->have_af ? L->af<Real>() : nullptr;
     if (c.src_kind == BTRT_SRC_TRIG) {
         Real *tb = L->tab<Real>();
         p.Xs = tb;
@@ -242,12 +293,12 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
     }
     p.first = first ? 1 : 0;
     p.flags = L->flags();
-    // constants of the linear fast path (B = u phi, C = phi, constant A)
+    // constants of the folded collision
     {
         const double k0 = c.k0, K1xx = L->K1[0], K1xy = L->K1[1], K1yy = L->K1[2];
         const double kap = 4.5 * (L->k2 - k0);
         const double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w5 = 1.0 / 36.0;
-        LinearConsts<Real> &q = p.lin;
+        FoldConsts<Real> &q = p.lin;
         q.ux = (Real)L->ux;
         q.uy = (Real)L->uy;
         q.ux3 = (Real)(3.0 * k0 * L->ux);
@@ -258,21 +309,28 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
         q.gx = (Real)(3.0 * ((1.0 - 0.5 * K1xx) * L->ux - 0.5 * K1xy * L->uy));
         q.gy = (Real)(3.0 * (-0.5 * K1xy * L->ux + (1.0 - 0.5 * K1yy) * L->uy));
         q.k0 = (Real)k0;
+        q.om = (Real)(1.0 - k0);
+        q.k0x15 = (Real)(1.5 * k0);
         q.c0 = (Real)(w0 * kap / 3.0);
         q.k6 = (Real)(-w1 * kap / 6.0);
         q.k6x3 = (Real)(-w1 * kap / 2.0);
         q.kd = (Real)(-2.0 * w5 * kap / 3.0);
         q.kdx3 = (Real)(-2.0 * w5 * kap);
+        q.b2h = (Real)(0.5 * L->b2);
+        q.a2x3 = (Real)(3.0 * c.a2);
     }
+    // the storage shift reference (zero for unshifted FP64 / double-word storage)
+    p.phi_ref = (g.storage == BTRT_F64 || g.storage == BTRT_DF64) ? (Real)0.0 : (Real)g.phi_ref;
 }
 
 template void btrt::fill_params<double>(btrt_lattice, SweepParams<double> &, int64_t, bool);
 template void btrt::fill_params<float>(btrt_lattice, SweepParams<float> &, int64_t, bool);
+template void btrt::fill_params<dw>(btrt_lattice, SweepParams<dw> &, int64_t, bool);
 
 // Which compiled variant of the sweep serves these coefficients.
 int btrt::sweep_mode(btrt_lattice L) {
     const btrt_coeffs &c = L->c;
-    const bool linear = c.b2 == 0.0 && c.c3 == 0.0 && c.a2 == 0.0;
+    const bool linear = c.b2 == 0.0 && c.c3 == 0.0 && c.a2 == 0.0 && !L->have_af;
     if (!linear) return kGeneral;
     if (L->g.compute == BTRT_F64 && c.k0 == 1.0) return kLinearK0One;
     return kLinear;
@@ -286,12 +344,36 @@ btrt_status launch(btrt_lattice L, int64_t n, bool first, bool resid = false) {
         fill_params(L, p, n, first);
         if (resid) p.resid_partials = L->resid_partials();
         CUDA_TRY(launch_sweep_f64(p, sweep_mode(L), L->stream));
+    } else if (L->g.compute == BTRT_DF64) {
+        SweepParams<dw> p;
+        fill_params(L, p, n, first);
+        if (resid) p.resid_partials = L->resid_partials();
+        CUDA_TRY(launch_sweep_dw(p, sweep_mode(L), L->stream));
     } else {
         SweepParams<float> p;
         fill_params(L, p, n, first);
         if (resid) p.resid_partials = L->resid_partials();
-        CUDA_TRY(launch_sweep_f32(p, L->g.storage, sweep_mode(L), L->stream));
+        if (!first && !resid && L->have_tma && L->sweep_variant == BTRT_SWEEP_TMA)
+            CUDA_TRY(launch_sweep_tma(p, L->g.storage, sweep_mode(L), &L->tma_in[L->cur], &L->tma_out[1 - L->cur],
+                                      L->stream));
+        else
+            CUDA_TRY(launch_sweep_f32(p, L->g.storage, sweep_mode(L), L->stream));
     }
+    return BTRT_OK;
+}
+
+// Dense host arrays (row major, nx*ny) -> pitched device planes of Real, scaled.
+template <typename Real>
+btrt_status upload_planes(btrt_lattice L, Real *dst, const double *const *src, int nplanes, double scale) {
+    const btrt_grid_desc &g = L->g;
+    std::vector<Real> h((size_t)nplanes * L->lay.plane, Real(0.0));
+    for (int k = 0; k < nplanes; ++k)
+        for (int y = 0; y < g.ny; ++y)
+            for (int x = 0; x < g.nx; ++x)
+                h[(size_t)k * L->lay.plane + (size_t)y * L->lay.pitch + x] =
+                    Real(scale * src[k][(size_t)y * g.nx + x]);
+    CUDA_TRY(cudaMemcpyAsync(dst, h.data(), h.size() * sizeof(Real), cudaMemcpyHostToDevice, L->stream));
+    CUDA_TRY(cudaStreamSynchronize(L->stream));
     return BTRT_OK;
 }
 
@@ -367,7 +449,7 @@ btrt_status copy_phi_out(btrt_lattice L, void *dst, int dtype, int on_device) {
         CUDA_TRY(cudaGetLastError());
         return BTRT_OK;
     }
-    if (dtype == (sizeof(Real) == 8 ? BTRT_F64 : BTRT_F32)) {
+    if (L->g.compute != BTRT_DF64 && dtype == (sizeof(Real) == 8 ? BTRT_F64 : BTRT_F32)) {
         CUDA_TRY(cudaMemcpy2DAsync(dst, g.nx * sizeof(Real), L->phi<Real>(), L->lay.pitch * sizeof(Real),
                                    g.nx * sizeof(Real), g.ny, cudaMemcpyDeviceToHost, L->stream));
         CUDA_TRY(cudaStreamSynchronize(L->stream));
@@ -378,9 +460,9 @@ btrt_status copy_phi_out(btrt_lattice L, void *dst, int dtype, int on_device) {
                                g.nx * sizeof(Real), g.ny, cudaMemcpyDeviceToHost, L->stream));
     CUDA_TRY(cudaStreamSynchronize(L->stream));
     if (dtype == BTRT_F64)
-        for (size_t k = 0; k < n; ++k) ((double *)dst)[k] = (double)h[k];
+        for (size_t k = 0; k < n; ++k) ((double *)dst)[k] = static_cast<double>(h[k]);
     else
-        for (size_t k = 0; k < n; ++k) ((float *)dst)[k] = (float)h[k];
+        for (size_t k = 0; k < n; ++k) ((float *)dst)[k] = (float)static_cast<double>(h[k]);
     return BTRT_OK;
 }
 
@@ -462,6 +544,16 @@ btrt_status btrt_create(const btrt_grid_desc *g, void *dev_workspace, size_t wor
         delete L;
         return fail(BTRT_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     }
+    if (g->compute == BTRT_F32) {
+        int bix, biy, box, boy;
+        tma_box(g->storage, &bix, &biy, &box, &boy);
+        bool ok = true;
+        for (int k = 0; k < 2; ++k) {
+            ok = ok && encode_buffer_map(&L->tma_in[k], L->fbuf(k), *g, lay.pitch, lay.plane, bix, biy);
+            ok = ok && encode_buffer_map(&L->tma_out[k], L->fbuf(k), *g, lay.pitch, lay.plane, box, boy);
+        }
+        L->have_tma = ok;
+    }
     *out = L;
     return BTRT_OK;
 }
@@ -478,8 +570,10 @@ btrt_status btrt_set_coeffs(btrt_lattice L, const btrt_coeffs *c) {
         return fail(BTRT_EINVAL, "unknown k2 mode %d", c->k2_mode);
     if (c->k2_mode == BTRT_K2_CONST && !(c->k2 > 0.0 && c->k2 < 2.0))
         return fail(BTRT_EINVAL, "k2 = %g outside (0, 2)", c->k2);
-    if (c->src_kind < BTRT_SRC_NONE || c->src_kind > BTRT_SRC_TRIG)
+    if (c->src_kind < BTRT_SRC_NONE || c->src_kind > BTRT_SRC_FIELD)
         return fail(BTRT_EINVAL, "unknown source kind %d", c->src_kind);
+    if (c->src_kind == BTRT_SRC_FIELD && !(g.fields & BTRT_FIELD_SOURCE))
+        return fail(BTRT_EINVAL, "BTRT_SRC_FIELD needs BTRT_FIELD_SOURCE in the grid description");
     if (!std::isfinite(c->a2) || c->a2 < 0.0) return fail(BTRT_EINVAL, "a2 must be >= 0");
     L->c = *c;
     // lattice units: B^ = B dt/dx, A^ = A dt/dx^2
@@ -501,7 +595,9 @@ btrt_status btrt_set_coeffs(btrt_lattice L, const btrt_coeffs *c) {
     L->nonlin_A = c->a2 != 0.0;
     L->have_coeffs = true;
     if (c->src_kind == BTRT_SRC_TRIG) {
-        btrt_status st = g.compute == BTRT_F64 ? upload_tables<double>(L) : upload_tables<float>(L);
+        btrt_status st = g.compute == BTRT_F64    ? upload_tables<double>(L)
+                         : g.compute == BTRT_DF64 ? upload_tables<dw>(L)
+                                                  : upload_tables<float>(L);
         if (st != BTRT_OK) return st;
     }
     return BTRT_OK;
@@ -520,20 +616,56 @@ btrt_status btrt_set_boundary(btrt_lattice L, int32_t side, const double *phi_w_
     if (n != len) return fail(BTRT_EINVAL, "side %d takes 1 or %d values, got %d", side, len, n);
     for (int k = 0; k < n; ++k)
         if (!std::isfinite(phi_w_host[k])) return fail(BTRT_EINVAL, "non-finite wall value at %d", k);
-    btrt_status st = L->g.compute == BTRT_F64 ? upload_wall<double>(L, side, phi_w_host, n)
-                                              : upload_wall<float>(L, side, phi_w_host, n);
+    btrt_status st = L->g.compute == BTRT_F64    ? upload_wall<double>(L, side, phi_w_host, n)
+                     : L->g.compute == BTRT_DF64 ? upload_wall<dw>(L, side, phi_w_host, n)
+                                                 : upload_wall<float>(L, side, phi_w_host, n);
     if (st != BTRT_OK) return st;
     L->wall_is_arr[side] = true;
+    return BTRT_OK;
+}
+
+btrt_status btrt_set_source_field(btrt_lattice L, const double *F_host) {
+    if (!L || !F_host) return fail(BTRT_EINVAL, "null argument");
+    if (!(L->g.fields & BTRT_FIELD_SOURCE)) return fail(BTRT_EINVAL, "lattice has no source-field plane");
+    const size_t n = (size_t)L->g.nx * L->g.ny;
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(F_host[k])) return fail(BTRT_EINVAL, "non-finite source value at %zu", k);
+    btrt_status st = L->g.compute == BTRT_F64    ? upload_planes<double>(L, L->srcf<double>(), &F_host, 1, 1.0)
+                     : L->g.compute == BTRT_DF64 ? upload_planes<dw>(L, L->srcf<dw>(), &F_host, 1, 1.0)
+                                                 : upload_planes<float>(L, L->srcf<float>(), &F_host, 1, 1.0);
+    if (st != BTRT_OK) return st;
+    L->have_srcf = true;
+    return BTRT_OK;
+}
+
+btrt_status btrt_set_diffusion_field(btrt_lattice L, const double *Axx, const double *Axy, const double *Ayy) {
+    if (!L || !Axx || !Axy || !Ayy) return fail(BTRT_EINVAL, "null argument");
+    if (!(L->g.fields & BTRT_FIELD_DIFFUSION)) return fail(BTRT_EINVAL, "lattice has no diffusion-field planes");
+    const size_t n = (size_t)L->g.nx * L->g.ny;
+    for (size_t k = 0; k < n; ++k)
+        if (!(Axx[k] > 0.0) || !(Ayy[k] > 0.0) || !(Axx[k] * Ayy[k] - Axy[k] * Axy[k] > 0.0))
+            return fail(BTRT_EINVAL, "diffusion tensor at node %zu is not symmetric positive definite", k);
+    // lattice units: A^ = A dt / dx^2
+    const double sA = L->g.dt / (L->g.dx * L->g.dx);
+    const double *src[3] = {Axx, Axy, Ayy};
+    btrt_status st = L->g.compute == BTRT_F64    ? upload_planes<double>(L, L->af<double>(), src, 3, sA)
+                     : L->g.compute == BTRT_DF64 ? upload_planes<dw>(L, L->af<dw>(), src, 3, sA)
+                                                 : upload_planes<float>(L, L->af<float>(), src, 3, sA);
+    if (st != BTRT_OK) return st;
+    L->have_af = true;
     return BTRT_OK;
 }
 
 btrt_status btrt_init_phi(btrt_lattice L, const void *phi0, int32_t dtype, int32_t on_device, double t0) {
     if (!L || !phi0) return fail(BTRT_EINVAL, "null argument");
     if (!L->have_coeffs) return fail(BTRT_ESTATE, "btrt_set_coeffs must come before btrt_init_phi");
+    if (L->c.src_kind == BTRT_SRC_FIELD && !L->have_srcf)
+        return fail(BTRT_ESTATE, "btrt_set_source_field must come before btrt_init_phi");
     if (dtype != BTRT_F64 && dtype != BTRT_F32) return fail(BTRT_EINVAL, "phi0 dtype must be F64 or F32");
     if (!std::isfinite(t0)) return fail(BTRT_EINVAL, "t0 must be finite");
-    btrt_status st = L->g.compute == BTRT_F64 ? stage_phi0<double>(L, phi0, dtype, on_device)
-                                              : stage_phi0<float>(L, phi0, dtype, on_device);
+    btrt_status st = L->g.compute == BTRT_F64    ? stage_phi0<double>(L, phi0, dtype, on_device)
+                     : L->g.compute == BTRT_DF64 ? stage_phi0<dw>(L, phi0, dtype, on_device)
+                                                 : stage_phi0<float>(L, phi0, dtype, on_device);
     if (st != BTRT_OK) return st;
     L->t0 = t0;
     L->step = 0;
@@ -586,8 +718,9 @@ btrt_status btrt_read_phi(btrt_lattice L, void *dst, int32_t dtype, int32_t on_d
     if (!L || !dst) return fail(BTRT_EINVAL, "null argument");
     if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
     if (dtype != BTRT_F64 && dtype != BTRT_F32) return fail(BTRT_EINVAL, "dtype must be F64 or F32");
-    return L->g.compute == BTRT_F64 ? copy_phi_out<double>(L, dst, dtype, on_device)
-                                    : copy_phi_out<float>(L, dst, dtype, on_device);
+    return L->g.compute == BTRT_F64    ? copy_phi_out<double>(L, dst, dtype, on_device)
+           : L->g.compute == BTRT_DF64 ? copy_phi_out<dw>(L, dst, dtype, on_device)
+                                       : copy_phi_out<float>(L, dst, dtype, on_device);
 }
 
 btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int32_t w, int32_t h) {
@@ -606,11 +739,17 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
                                    cudaMemcpyDeviceToHost, L->stream));
         CUDA_TRY(cudaStreamSynchronize(L->stream));
         // the stored values are rounded from Real = f - w_i phi_ref in the compute precision
-        // FP64 storage is never shifted; FP32 compute shifts by (float)(w_i phi_ref)
-        const double shift = g.storage == BTRT_F64 ? 0.0 : (double)(float)(wts[i] * g.phi_ref);
+        // FP64 and double-word storage are never shifted; FP32 compute shifts by (float)(w_i phi_ref)
+        const double shift = (g.storage == BTRT_F64 || g.storage == BTRT_DF64)
+                                 ? 0.0 : (double)(float)(wts[i] * g.phi_ref);
         for (size_t k = 0; k < (size_t)w * h; ++k) {
             double v;
             if (g.storage == BTRT_F64) std::memcpy(&v, &raw[k * 8], 8);
+            else if (g.storage == BTRT_DF64) {
+                float hl[2];
+                std::memcpy(hl, &raw[k * 8], 8);
+                v = (double)hl[0] + (double)hl[1];
+            }
             else if (g.storage == BTRT_F32) { float fv; std::memcpy(&fv, &raw[k * 4], 4); v = fv; }
             else v = host_half_to_double(g.storage, &raw[k * 2]);
             dst[(size_t)i * w * h + k] = v + shift;
@@ -622,14 +761,27 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
 btrt_status btrt_mass(btrt_lattice L, double *out) {
     if (!L || !out) return fail(BTRT_EINVAL, "null argument");
     if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
-    return L->g.compute == BTRT_F64 ? reduce_phi<double>(L, out) : reduce_phi<float>(L, out);
+    return L->g.compute == BTRT_F64    ? reduce_phi<double>(L, out)
+           : L->g.compute == BTRT_DF64 ? reduce_phi<dw>(L, out)
+                                       : reduce_phi<float>(L, out);
 }
 
 btrt_status btrt_check(btrt_lattice L, int32_t *flags) {
     if (!L || !flags) return fail(BTRT_EINVAL, "null argument");
     CUDA_TRY(cudaMemcpyAsync(flags, L->flags(), sizeof(int32_t), cudaMemcpyDeviceToHost, L->stream));
     CUDA_TRY(cudaStreamSynchronize(L->stream));
+    if (*flags & 4) return fail(BTRT_ETIMEOUT, "a bounded wait for a tile copy gave up");
     if (*flags & 1) return fail(BTRT_EUNSTABLE, "non-finite phi detected (unstable parameters?)");
+    return BTRT_OK;
+}
+
+btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant) {
+    if (!L) return fail(BTRT_EINVAL, "null lattice");
+    if (variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN && variant != BTRT_SWEEP_TMA)
+        return fail(BTRT_EINVAL, "unknown sweep variant %d", variant);
+    if (variant == BTRT_SWEEP_TMA && !L->have_tma)
+        return fail(BTRT_EINVAL, "the TMA sweep serves FP32-compute lattices whose tensor maps could be encoded");
+    L->sweep_variant = variant;
     return BTRT_OK;
 }
 

@@ -119,11 +119,11 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int 
     if (x < sp.nx) {
         const int y0 = tile.z + threadIdx.y;
         if (M.mode == kGeneral) {
-            if (resid) r = sweep_rows<Real, S, kGeneral, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
-            else sweep_rows<Real, S, kGeneral, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+            if (resid) r = sweep_rows<Real, S, kGeneral, 4, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, kGeneral, 4, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
         } else {
-            if (resid) r = sweep_rows<Real, S, kLinear, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
-            else sweep_rows<Real, S, kLinear, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+            if (resid) r = sweep_rows<Real, S, kLinear, 4, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, kLinear, 4, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
         }
     }
     if (resid) {
@@ -257,6 +257,8 @@ btrt_status check_members(const btrt_lattice *members, int32_t n, std::vector<bt
     for (int k = 0; k < n; ++k) {
         if (!out[k]) return bfail(BTRT_EINVAL, "member %d is null", k);
         if (!out[k]->ready) return bfail(BTRT_ESTATE, "member %d is not initialised", k);
+        if (out[k]->g.compute == BTRT_DF64)
+            return bfail(BTRT_EINVAL, "member %d: batches take FP64 or FP32 members", k);
         if (out[k]->g.compute != out[0]->g.compute || out[k]->g.storage != out[0]->g.storage)
             return bfail(BTRT_EINVAL, "member %d: all members need the same compute and storage formats", k);
         for (int j = 0; j < k; ++j)

@@ -22,7 +22,10 @@
 
 namespace btrt {
 
-struct dw {
+// keep the float/double fma overloads visible next to the double-word one
+using ::fma;
+
+struct __align__(8) dw {
     float hi, lo;
 
     dw() = default;

@@ -1,6 +1,7 @@
 // btrt_internal.h -- host-side declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 #include <stdint.h>
@@ -22,6 +23,7 @@ struct Layout {
     size_t fbuf_bytes = 0;   // one buffer of 9 planes
     size_t off_f[2] = {0, 0};
     size_t off_phi = 0, off_tab = 0, off_wall = 0, off_red = 0, off_resid = 0, total = 0;
+    size_t off_srcf = 0, off_af = 0;   // optional field planes (0 when absent)
     int maxside = 0;
     long long resid_blocks = 0;   // partial slots of a residual sweep (one per block)
 };
@@ -45,6 +47,12 @@ struct btrt_lattice_s {
     bool nonlin_A = false;
     double wall_const[4] = {0, 0, 0, 0};
     bool wall_is_arr[4] = {false, false, false, false};
+    // TMA descriptors of the two population buffers (FP32-compute lattices)
+    CUtensorMap tma_in[2];
+    CUtensorMap tma_out[2];
+    bool have_tma = false;
+    int sweep_variant = 0;    // BTRT_SWEEP_AUTO / PLAIN / TMA
+    bool have_srcf = false, have_af = false;   // fields uploaded
 
     template <typename Real> Real *phi() { return reinterpret_cast<Real *>(ws + lay.off_phi); }
     void *fbuf(int k) { return ws + lay.off_f[k]; }
@@ -54,6 +62,8 @@ struct btrt_lattice_s {
     }
     double *partials() { return reinterpret_cast<double *>(ws + lay.off_red); }
     double *resid_partials() { return reinterpret_cast<double *>(ws + lay.off_resid); }
+    template <typename Real> Real *srcf() { return lay.off_srcf ? reinterpret_cast<Real *>(ws + lay.off_srcf) : nullptr; }
+    template <typename Real> Real *af() { return lay.off_af ? reinterpret_cast<Real *>(ws + lay.off_af) : nullptr; }
     double *red_out() { return partials() + btrt::kRedBlocks; }
     int *flags() { return reinterpret_cast<int *>(partials() + btrt::kRedBlocks + 2); }
 };
@@ -69,13 +79,19 @@ void step_scalars(btrt_lattice L, int64_t n, bool first, double *src_val, double
 // Compiled variant (kGeneral / kLinear / kLinearK0One) that serves L's coefficients.
 int sweep_mode(btrt_lattice L);
 
+// TMA-staged sweep (FP32 compute) and the box sizes its tensor maps need.
+cudaError_t launch_sweep_tma(const SweepParams<float> &p, int storage, int mode, const CUtensorMap *in_map,
+                             const CUtensorMap *out_map, cudaStream_t s);
+void tma_box(int storage, int *box_in_x, int *box_in_y, int *box_out_x, int *box_out_y);
+
 // Blocks of one single-lattice sweep (32 x 8 threads, RowsPerThread nodes each).
-long long sweep_blocks(int nx, int ny, int compute);
+long long sweep_blocks(int nx, int ny, int compute, int storage);
 
 // Launch one sweep (or the initialising collision) for a (compute, storage) pair.
 // compute: 0 = FP64, 1 = FP32; storage: BTRT_F64/F32/F16/BF16.
 // mode: kGeneral, kLinear or kLinearK0One (FP64); kGeneral or kLinear (FP32).
 cudaError_t launch_sweep_f64(const SweepParams<double> &p, int mode, cudaStream_t s);
+cudaError_t launch_sweep_dw(const SweepParams<dw> &p, int mode, cudaStream_t s);
 cudaError_t launch_sweep_f32(const SweepParams<float> &p, int storage, int mode, cudaStream_t s);
 
 // Record the thread-local message returned by btrt_last_error (printf format).

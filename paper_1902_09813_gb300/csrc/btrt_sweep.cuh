@@ -12,7 +12,14 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include "btrt_dw.cuh"
+
 namespace btrt {
+
+// A rational constant in the compute type: folded at compile time for
+// float/double, split into its double-word form for dw.
+template <typename Real> __device__ __forceinline__ Real cst(int num, int den) { return Real(num) / Real(den); }
+template <> __device__ __forceinline__ dw cst<dw>(int num, int den) { return dw((double)num / (double)den); }
 
 // ---------------------------------------------------------------- storage types
 template <typename S> struct Storage;
@@ -28,23 +35,29 @@ template <> struct Storage<__half> {
     static __device__ __forceinline__ float load(__half v) { return __half2float(v); }
     static __device__ __forceinline__ __half pack(float v) { return __float2half_rn(v); }
 };
+template <> struct Storage<dw> {
+    static __device__ __forceinline__ dw load(dw v) { return v; }
+    static __device__ __forceinline__ dw pack(dw v) { return v; }
+};
 template <> struct Storage<__nv_bfloat16> {
     static __device__ __forceinline__ float load(__nv_bfloat16 v) { return __bfloat162float(v); }
     static __device__ __forceinline__ __nv_bfloat16 pack(float v) { return __float2bfloat16_rn(v); }
 };
 
 // ---------------------------------------------------------------- parameters
-// Per-lattice constants of the linear fast path (see collide_linear).
+// Per-lattice constants of the folded collision (see collide_fold), computed on
+// the host in FP64.  kap = (9/2)(k2 - k0).
 template <typename Real>
-struct LinearConsts {
+struct FoldConsts {
     Real ux, uy;           // u^ (lattice units)
     Real ux3, uy3;         // 3 k0 u^
-    Real Qxx, Qxy, Qyy;    // 3 (K1 - k0 I)
-    Real gx, gy;           // 3 (I - K1/2) u^
-    Real k0;
-    Real c0;               // w0 kap / 3,           kap = (9/2)(k2 - k0)
+    Real Qxx, Qxy, Qyy;    // 3 (K1 - k0 I)          (constant K1)
+    Real gx, gy;           // 3 (I - K1/2) u^        (constant K1)
+    Real k0, om, k0x15;    // k0, 1 - k0, 1.5 k0
+    Real c0;               // w0 kap / 3             (constant k2)
     Real k6, k6x3;         // -w1 kap / 6, 3 k6
     Real kd, kdx3;         // -(2/3) w5 kap, 3 kd
+    Real b2h, a2x3;        // b2 / 2, 3 a2           (phi-dependent coefficients)
 };
 
 // Everything one launch of the sweep needs, passed by value.
@@ -76,14 +89,17 @@ struct SweepParams {
     Real cond_limit;       // FP32: tr^2/det above this -> invert in FP64
 
     // source
-    int src_kind;          // 0 none, 1 const, 2 trig
-    Real src_val;          // const: S^ ; trig: dt (3 T_n - T_{n-1}) / 2
+    int src_kind;          // 0 none, 1 const, 2 trig, 3 per-node field
+    Real src_val;          // const: S^ ; trig, field: dt (3 T_n - T_{n-1}) / 2
     const Real *Xs, *Xc, *Ys, *Yc;   // trig tables: sin/cos(k x_i), alpha folded into Ys/Yc
+    const Real *srcF;      // field: S(x) per node (pitched plane)
+    const Real *Af;        // non-null: per-node lattice diffusion tensor, planes xx, xy, yy (`plane` apart)
 
     int first;             // 1: initialisation (f = f_eq(phi), no streaming)
     int *flags;            // bit 0: non-finite phi
     double *resid_partials;  // non-null: per-block sum of (phi^n - phi^{n-1})^2 (single-lattice sweep)
-    LinearConsts<Real> lin;
+    Real phi_ref;          // storage shift reference (0 for unshifted storage)
+    FoldConsts<Real> lin;
 };
 
 // D2Q9 velocity components and opposite directions, order of the rows of Eq. 85.
@@ -92,7 +108,7 @@ __host__ __device__ constexpr int ey_of(int i) { return i == 2 || i == 5 || i ==
 __host__ __device__ constexpr int opp_of(int i) { return i == 0 ? 0 : (i <= 4 ? ((i + 1) & 3) + 1 : ((i - 3) & 3) + 5); }
 
 template <typename Real> __device__ __forceinline__ Real wgt(int i) {
-    return i == 0 ? Real(4) / Real(9) : (i <= 4 ? Real(1) / Real(9) : Real(1) / Real(36));
+    return i == 0 ? cst<Real>(4, 9) : (i <= 4 ? cst<Real>(1, 9) : cst<Real>(1, 36));
 }
 
 // 2 x even part of f^eq at the wall value: 2 w_i [phi_w + (C(phi_w) - phi_w)(3|e_i|^2 - 2)/2]
@@ -113,42 +129,91 @@ __device__ __forceinline__ Real wall_value(const SweepParams<Real> &p, int side,
 // well inside the FP32 path's tolerance.
 __device__ __forceinline__ double quot(double a, double b) { return a / b; }
 __device__ __forceinline__ float quot(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ dw quot(dw a, dw b) { return a / b; }
 
 // ---------------------------------------------------------------- the collision
+// Compiled variants: every coefficient family evaluated per node (kGeneral), or
+// B = u phi, C = phi and constant A with any k0 (kLinear) or k0 = 1 (kLinearK0One).
+enum { kGeneral = 0, kLinear = 1, kLinearK0One = 2 };
+
 // Moment-space form of Eq. 6 (Eqs. 94, 95, 99 with K2 = k2 Ihat), expanded back
-// into populations.  f: pre-collision populations; on return f^+.
-template <typename Real>
-__device__ __forceinline__ void collide(const SweepParams<Real> &p, Real (&f)[9], Real phi,
-                                        Real phi_prev, Real src_spatial) {
-    // first and second moments of f
-    const Real d57 = f[5] - f[7];
-    const Real d68 = f[6] - f[8];
-    const Real jx = (f[1] - f[3]) + d57 - d68;
-    const Real jy = (f[2] - f[4]) + d57 + d68;
-    const Real sd = (f[5] + f[7]) + (f[6] + f[8]);
-    const Real pxx = (f[1] + f[3]) + sd;
-    const Real pyy = (f[2] + f[4]) + sd;
-    const Real pxy = (f[5] + f[7]) - (f[6] + f[8]);
+// into populations and written for the values the lattice stores: d_i = f_i
+// (FP64, double-word) or the shifted d_i = f_i - w_i phi_ref (FP32/FP16/BF16).
+// The shift cancels from the first moments and from M2xx - M2yy, enters the
+// trace as phi_ref, and in the outputs only as -k0 w_i phi_ref, which folds into
+// the isotropic term; so the shift costs one add per node instead of eighteen.
+//
+// With sigma = nxx + nyy and delta = nxx - nyy of the non-equilibrium second
+// moments, kap = (9/2)(k2 - k0) and a = k0 (phi - phi_ref) + source:
+//   d_i^+ = (1 - k0) d_i + w_i (a + cC_i) + w_i 3 e_i . V - w_i kap H_i
+//   w0 kap H_0 = -(w0 kap/3) sigma,  w1 kap H_x,y = (w1 kap/6)(sigma +- 3 delta),
+//   w5 kap H_d = (2/3) w5 kap (sigma +- 3 nxy),
+//   V = k0 B - (K1 - k0 I)(M1 - B) + (I - K1/2)(B^n - B^{n-1})    (Eq. 11),
+//   cC_i = (3/2) k0 (C - phi)(|e_i|^2 - 2/3)   (zero when C = phi).
+// MODE selects per-lattice constants (B = u phi, C = phi, constant A: kLinear,
+// kLinearK0One) or per-node coefficient evaluation (kGeneral: nonlinear B, C and
+// A(x, phi) with the first-order block K1 = (3 A^ + I/2)^-1 of Eq. 30 and k2 from
+// Eq. 62 built at every node).  SRC: 0 none, 1 constant, 2 trig table, 3 field,
+// 4 decided at run time.
+template <typename Real, int MODE, int SRC, bool SHIFT>
+__device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&d)[9], Real phi_prev,
+                                             Real srcv, bool first, int node) {
+    const FoldConsts<Real> &L = p.lin;
+    constexpr bool K0ONE = MODE == kLinearK0One;
+    const Real a13 = d[1] + d[3], a24 = d[2] + d[4];
+    const Real s57 = d[5] + d[7], s68 = d[6] + d[8];
+    const Real sd = s57 + s68;
+    const Real a1324 = a13 + a24;
+    const Real phid = (d[0] + sd) + a1324;            // sum of the stored values
+    Real phi = phid;
+    if constexpr (SHIFT) phi = phid + p.phi_ref;
+    const Real b13 = d[1] - d[3], b24 = d[2] - d[4];
+    const Real d57 = d[5] - d[7], d68 = d[6] - d[8];
+    const Real jx = b13 + (d57 - d68);
+    const Real jy = b24 + (d57 + d68);
+    const Real pxy = s57 - s68;
+    const Real del = a13 - a24;
+    const Real dphi = first ? Real(0) : phi - phi_prev;
 
-    // coefficients at phi (Eq. 1 families)
-    const Real hb = Real(0.5) * p.b2 * phi * phi;
-    const Real Bx = p.ux * phi + hb, By = p.uy * phi + hb;
-    const Real hbp = Real(0.5) * p.b2 * phi_prev * phi_prev;
-    const Real dBx = Bx - (p.ux * phi_prev + hbp);
-    const Real dBy = By - (p.uy * phi_prev + hbp);
-    const Real Cm = p.c3 * phi * phi * phi;          // C(phi) - phi
-
-    // first-order block K1 (Eq. 30) and k2 (Eq. 62)
-    Real K1xx = p.K1xx, K1xy = p.K1xy, K1yy = p.K1yy, k2 = p.k2;
-    if (p.nonlin_A) {
-        const Real s3 = Real(3) * (Real(1) + p.a2 * phi * phi);
-        const Real mxx = s3 * p.A0xx + Real(0.5);
-        const Real mxy = s3 * p.A0xy;
-        const Real myy = s3 * p.A0yy + Real(0.5);
+    Real Vx, Vy, c0, k6, k6x3, kd, kdx3;
+    Real cmid = phid;                                   // C - phi_ref
+    Real cc = Real(0);                                  // (3/2) k0 (C - phi)
+    if constexpr (MODE != kGeneral) {
+        const Real mx = fma(-L.ux, phi, jx), my = fma(-L.uy, phi, jy);
+        Vx = fma(L.gx, dphi, fma(L.ux3, phi, -fma(L.Qxy, my, L.Qxx * mx)));
+        Vy = fma(L.gy, dphi, fma(L.uy3, phi, -fma(L.Qyy, my, L.Qxy * mx)));
+        c0 = L.c0;
+        k6 = L.k6;
+        k6x3 = L.k6x3;
+        kd = L.kd;
+        kdx3 = L.kdx3;
+    } else {
+        // coefficients at phi (Eq. 1 families); dB = (u + (b2/2)(phi + phi_prev)) dphi
+        const Real hb = L.b2h * phi * phi;
+        const Real Bx = fma(p.ux, phi, hb), By = fma(p.uy, phi, hb);
+        const Real tb = L.b2h * (phi + phi_prev);
+        const Real dBx = (p.ux + tb) * dphi, dBy = (p.uy + tb) * dphi;
+        const Real Cm = p.c3 * phi * phi * phi;          // C(phi) - phi
+        cmid = phid + Cm;
+        cc = L.k0x15 * Cm;
+        // first-order block K1 = (3 A^ + I/2)^-1 (Eq. 30), A^ = (1 + a2 phi^2) A0^
+        const Real s3 = fma(L.a2x3, phi * phi, Real(3));
+        Real a0xx = p.A0xx, a0xy = p.A0xy, a0yy = p.A0yy;
+        if (p.Af) {   // spatially varying tensor A(x)
+            a0xx = p.Af[node];
+            a0xy = p.Af[p.plane + node];
+            a0yy = p.Af[2 * p.plane + node];
+        }
+        const Real mxx = fma(s3, a0xx, Real(0.5));
+        const Real mxy = s3 * a0xy;
+        const Real myy = fma(s3, a0yy, Real(0.5));
         const Real tr = mxx + myy;
-        const Real det = mxx * myy - mxy * mxy;
-        if (sizeof(Real) == 4 && tr * tr > p.cond_limit * det) {
-            // ill-conditioned block: invert in FP64
+        const Real det = fma(mxx, myy, -(mxy * mxy));
+        Real K1xx, K1xy, K1yy;
+        bool ill = false;
+        if constexpr (sizeof(Real) == 4) ill = tr * tr > p.cond_limit * det;
+        if (ill) {
+            // ill-conditioned FP32 block: invert in FP64
             const double dxx = (double)mxx, dxy = (double)mxy, dyy = (double)myy;
             const double id = 1.0 / (dxx * dyy - dxy * dxy);
             K1xx = (Real)(dyy * id);
@@ -160,70 +225,70 @@ __device__ __forceinline__ void collide(const SweepParams<Real> &p, Real (&f)[9]
             K1xy = -mxy * id;
             K1yy = mxx * id;
         }
-        if (p.k2_hbb) {
-            // Eq. 62 at k1_eff = 2/tr:  k2 = 8 (k1 - 2) / (3 (k1 - 4)) = (8/3)(tr - 1) / (2 tr - 1)
-            k2 = quot(Real(8) / Real(3) * (tr - Real(1)), Real(2) * tr - Real(1));
-        } else {
-            k2 = p.k2c;
-        }
+        // Eq. 62 at k1_eff = 2/tr:  k2 = 8 (k1 - 2) / (3 (k1 - 4)) = (8/3)(tr - 1) / (2 tr - 1)
+        const Real k2 = p.k2_hbb ? quot(cst<Real>(8, 3) * (tr - Real(1)), fma(Real(2), tr, Real(-1))) : p.k2c;
+        const Real kap = cst<Real>(9, 2) * (k2 - L.k0);
+        const Real mx = jx - Bx, my = jy - By;
+        const Real qx = fma(K1xx - L.k0, mx, K1xy * my);
+        const Real qy = fma(K1yy - L.k0, my, K1xy * mx);
+        const Real hx = Real(0.5) * K1xy;
+        const Real gx = fma(Real(1) - Real(0.5) * K1xx, dBx, -(hx * dBy));
+        const Real gy = fma(Real(1) - Real(0.5) * K1yy, dBy, -(hx * dBx));
+        Vx = Real(3) * (fma(L.k0, Bx, gx) - qx);
+        Vy = Real(3) * (fma(L.k0, By, gy) - qy);
+        c0 = cst<Real>(4, 27) * kap;                     // w0 kap / 3
+        k6 = cst<Real>(-1, 54) * kap;                    // -w1 kap / 6
+        k6x3 = cst<Real>(-1, 18) * kap;
+        kd = cst<Real>(-1, 54) * kap;                    // -(2/3) w5 kap
+        kdx3 = cst<Real>(-1, 18) * kap;
     }
-    const Real k0 = p.k0;
-
-    // non-equilibrium moments: M1 - B, M2 - C/3 I (Eq. 9 gives the equilibrium parts)
-    const Real mx = jx - Bx, my = jy - By;
-    const Real c3rd = (phi + Cm) * (Real(1) / Real(3));
-    const Real nxx = pxx - c3rd, nyy = pyy - c3rd, nxy = pxy;
-
-    // (K1 - k0 I) M1neq and (I - K1/2) dB (Eq. 11)
-    const Real qx = (K1xx - k0) * mx + K1xy * my;
-    const Real qy = K1xy * mx + (K1yy - k0) * my;
-    const Real gx = (Real(1) - Real(0.5) * K1xx) * dBx - Real(0.5) * K1xy * dBy;
-    const Real gy = -Real(0.5) * K1xy * dBx + (Real(1) - Real(0.5) * K1yy) * dBy;
-    const Real Vx = Real(3) * (k0 * Bx - qx + gx);
-    const Real Vy = Real(3) * (k0 * By - qy + gy);
-
-    // second-order block: -(9/2)(k2 - k0) H_i
-    const Real kap = Real(4.5) * (k2 - k0);
-    const Real tn = (nxx + nyy) * (Real(1) / Real(3));
-    const Real h0 = kap * tn;
-    const Real hx = -kap * (nxx - tn);             // -(kap)(2 nxx - nyy)/3
-    const Real hy = -kap * (nyy - tn);
-    const Real hdp = -kap * (Real(2) * tn + Real(2) * nxy);
-    const Real hdm = -kap * (Real(2) * tn - Real(2) * nxy);
-
-    // isotropic part: k0 phi + source;  C term: k0 (3/2)(C - phi)(|e|^2 - 2/3)
-    const Real a = k0 * phi + p.src_val * src_spatial;
-    const Real cc = k0 * Real(1.5) * Cm;
-    const Real om = Real(1) - k0;
-    const Real w0 = Real(4) / Real(9), w1 = Real(1) / Real(9), w5 = Real(1) / Real(36);
-
-    const Real a0 = a - cc * (Real(2) / Real(3)) + h0;
-    const Real a1 = a + cc * (Real(1) / Real(3));
-    const Real a5 = a + cc * (Real(4) / Real(3));
+    const Real sig = fma(cst<Real>(-2, 3), cmid, fma(Real(2), sd, a1324));
+    Real a = K0ONE ? phid : L.k0 * phid;
+    if constexpr (SRC != 0) a = fma(p.src_val, srcv, a);
+    const Real w0 = cst<Real>(4, 9), w1 = cst<Real>(1, 9), w5 = cst<Real>(1, 36);
     Real r[9];
-    r[0] = w0 * a0;
-    r[1] = w1 * (a1 + hx + Vx);
-    r[3] = w1 * (a1 + hx - Vx);
-    r[2] = w1 * (a1 + hy + Vy);
-    r[4] = w1 * (a1 + hy - Vy);
-    r[5] = w5 * (a5 + hdp + Vx + Vy);
-    r[7] = w5 * (a5 + hdp - Vx - Vy);
-    r[6] = w5 * (a5 + hdm - Vx + Vy);
-    r[8] = w5 * (a5 + hdm + Vx - Vy);
+    if constexpr (MODE == kGeneral) {
+        r[0] = fma(c0, sig, w0 * fma(cst<Real>(-2, 3), cc, a));
+    } else {
+        r[0] = fma(c0, sig, w0 * a);
+    }
+    const Real k6s = k6 * sig;
+    const Real hxp = fma(k6x3, del, k6s), hyp = fma(-k6x3, del, k6s);
+    const Real wa1 = MODE == kGeneral ? w1 * fma(cst<Real>(1, 3), cc, a) : w1 * a;
+    const Real A1 = wa1 + hxp, A2 = wa1 + hyp;
+    r[1] = fma(w1, Vx, A1);
+    r[3] = fma(-w1, Vx, A1);
+    r[2] = fma(w1, Vy, A2);
+    r[4] = fma(-w1, Vy, A2);
+    const Real kds = kd * sig;
+    const Real hp = fma(kdx3, pxy, kds), hm = fma(-kdx3, pxy, kds);
+    const Real wa5 = MODE == kGeneral ? w5 * fma(cst<Real>(4, 3), cc, a) : w5 * a;
+    const Real P = wa5 + hp, M = wa5 + hm;
+    const Real Vp = Vx + Vy, Vm = Vx - Vy;
+    r[5] = fma(w5, Vp, P);
+    r[7] = fma(-w5, Vp, P);
+    r[6] = fma(-w5, Vm, M);
+    r[8] = fma(w5, Vm, M);
+    if constexpr (K0ONE) {
 #pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = om * f[i] + r[i];
+        for (int i = 0; i < 9; ++i) d[i] = r[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = fma(L.om, d[i], r[i]);
+    }
+    return phi;
 }
 
-// Equilibrium populations (Eq. 7) in lattice units, D = C(phi) I.
-template <typename Real>
+// Equilibrium populations (Eq. 7) in lattice units, D = C(phi) I, in stored form.
+template <typename Real, bool SHIFT>
 __device__ __forceinline__ void equilibrium(const SweepParams<Real> &p, Real phi, Real (&f)[9]) {
     const Real hb = Real(0.5) * p.b2 * phi * phi;
     const Real Bx = Real(3) * (p.ux * phi + hb), By = Real(3) * (p.uy * phi + hb);
     const Real cc = Real(1.5) * p.c3 * phi * phi * phi;
-    const Real w0 = Real(4) / Real(9), w1 = Real(1) / Real(9), w5 = Real(1) / Real(36);
-    const Real a0 = phi - cc * (Real(2) / Real(3));
-    const Real a1 = phi + cc * (Real(1) / Real(3));
-    const Real a5 = phi + cc * (Real(4) / Real(3));
+    const Real w0 = cst<Real>(4, 9), w1 = cst<Real>(1, 9), w5 = cst<Real>(1, 36);
+    const Real a0 = phi - cc * cst<Real>(2, 3);
+    const Real a1 = phi + cc * cst<Real>(1, 3);
+    const Real a5 = phi + cc * cst<Real>(4, 3);
     f[0] = w0 * a0;
     f[1] = w1 * (a1 + Bx);
     f[3] = w1 * (a1 - Bx);
@@ -233,67 +298,10 @@ __device__ __forceinline__ void equilibrium(const SweepParams<Real> &p, Real phi
     f[7] = w5 * (a5 - Bx - By);
     f[6] = w5 * (a5 - Bx + By);
     f[8] = w5 * (a5 + Bx - By);
-}
-
-// ---------------------------------------------------------------- linear fast path
-// For B = u phi, C = phi and constant A (so constant K1 and k2) the collision
-// needs far fewer operations: the equilibrium moments are linear in phi and the
-// weights fold into per-lattice constants (LinearConsts, computed on the host in
-// FP64).  With K2 = k2 Ihat and sigma = nxx + nyy, delta = nxx - nyy:
-//   w_i (a - (9/2)(k2 - k0) H_i) = w_i a + c0 sigma            (rest)
-//                                   w_i a + k6 (sigma +- 3 delta)   (axes)
-//                                   w_i a + kd (sigma +- 3 nxy)     (diagonals)
-// and the first-order and correction terms combine into V = 3(k0 B - (K1 - k0 I) M1neq
-// + (I - K1/2) u dphi).
-template <typename Real, bool K0ONE>
-__device__ __forceinline__ Real collide_linear(const SweepParams<Real> &p, Real (&f)[9], Real phi_prev,
-                                               Real src_spatial, bool first) {
-    const LinearConsts<Real> &L = p.lin;
-    const Real a13 = f[1] + f[3], a24 = f[2] + f[4];
-    const Real s57 = f[5] + f[7], s68 = f[6] + f[8];
-    const Real sd = s57 + s68;
-    const Real phi = (f[0] + sd) + (a13 + a24);
-    const Real b13 = f[1] - f[3], b24 = f[2] - f[4];
-    const Real d57 = f[5] - f[7], d68 = f[6] - f[8];
-    const Real jx = b13 + (d57 - d68);
-    const Real jy = b24 + (d57 + d68);
-    const Real pxy = s57 - s68;
-    const Real sig = fma(Real(-2) / Real(3), phi, fma(Real(2), sd, a13 + a24));
-    const Real del = a13 - a24;
-    const Real mx = fma(-L.ux, phi, jx), my = fma(-L.uy, phi, jy);
-    const Real dphi = first ? Real(0) : phi - phi_prev;
-    const Real Vx = fma(L.gx, dphi, fma(L.ux3, phi, -fma(L.Qxy, my, L.Qxx * mx)));
-    const Real Vy = fma(L.gy, dphi, fma(L.uy3, phi, -fma(L.Qyy, my, L.Qxy * mx)));
-    const Real a = K0ONE ? fma(p.src_val, src_spatial, phi) : fma(p.src_val, src_spatial, L.k0 * phi);
-    const Real w0 = Real(4) / Real(9), w1 = Real(1) / Real(9), w5 = Real(1) / Real(36);
-    Real r[9];
-    r[0] = fma(L.c0, sig, w0 * a);
-    const Real k6s = L.k6 * sig;
-    const Real hx = fma(L.k6x3, del, k6s), hy = fma(-L.k6x3, del, k6s);
-    const Real wa1 = w1 * a;
-    const Real A1 = wa1 + hx, A2 = wa1 + hy;
-    r[1] = fma(w1, Vx, A1);
-    r[3] = fma(-w1, Vx, A1);
-    r[2] = fma(w1, Vy, A2);
-    r[4] = fma(-w1, Vy, A2);
-    const Real kds = L.kd * sig;
-    const Real hp = fma(L.kdx3, pxy, kds), hm = fma(-L.kdx3, pxy, kds);
-    const Real wa5 = w5 * a;
-    const Real P = wa5 + hp, M = wa5 + hm;
-    const Real Vp = Vx + Vy, Vm = Vx - Vy;
-    r[5] = fma(w5, Vp, P);
-    r[7] = fma(-w5, Vp, P);
-    r[6] = fma(-w5, Vm, M);
-    r[8] = fma(w5, Vm, M);
-    if (K0ONE) {
+    if constexpr (SHIFT) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = r[i];
-    } else {
-        const Real om = Real(1) - L.k0;
-#pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = fma(om, f[i], r[i]);
+        for (int i = 0; i < 9; ++i) f[i] = f[i] - p.wref[i];
     }
-    return phi;
 }
 
 // Non-finite test without touching the FP64 pipe: exponent field all ones.
@@ -304,127 +312,174 @@ __device__ __forceinline__ bool not_finite(float v) {
     return (__float_as_int(v) & 0x7f800000) == 0x7f800000;
 }
 
-// ---------------------------------------------------------------- the sweep kernel
-// MODE: kGeneral (every coefficient family, runtime flags), kLinear (B = u phi,
-// C = phi, A constant; any k0), kLinearK0One (the same with k0 = 1).
-enum { kGeneral = 0, kLinear = 1, kLinearK0One = 2 };
-// Nodes per thread of the single-lattice sweep: the FP64 sweep is ALU-bound and
-// amortises per-thread set-up over a column of 4 nodes; the HBM-bound FP32
-// sweeps keep one node per thread for more loads in flight.
-template <typename Real> struct RowsPerThread { static constexpr int value = 1; };
-template <> struct RowsPerThread<double> { static constexpr int value = 4; };
-
 template <typename S> struct Shifted { static constexpr bool value = true; };
 template <> struct Shifted<double> { static constexpr bool value = false; };  // FP64 storage is never shifted
+template <> struct Shifted<dw> { static constexpr bool value = false; };      // nor double-word storage
+
+// Nodes per thread of the single-lattice sweep: the FP64 sweep is ALU-bound and
+// amortises per-thread set-up over a column of 4 nodes; the HBM-bound FP32-storage
+// sweep takes two nodes with both pulls issued before the collisions (loads in
+// flight together, set-up shared); the FP16/BF16-storage sweeps, limited by
+// registers and issue, keep one node per thread.
+template <typename Real, typename S> struct RowsPerThread { static constexpr int value = 1; static constexpr bool unroll = false; };
+template <> struct RowsPerThread<float, float> { static constexpr int value = 2; static constexpr bool unroll = true; };
+template <> struct RowsPerThread<double, double> { static constexpr int value = 4; static constexpr bool unroll = false; };
 
 // Global loads of data that other SMs rewrite during a persistent launch go
 // through L2 only (L1 is not coherent across SMs); ordinary loads otherwise.
 template <bool L2ONLY, typename T>
 __device__ __forceinline__ T ldg(const T *ptr) {
-    if (L2ONLY) return __ldcg(ptr);
-    return *ptr;
+    if constexpr (L2ONLY) return __ldcg(ptr);
+    else return *ptr;
 }
 
-// Sweep `nrows` nodes of column x, rows ybase, ybase + ystride, ...: pull,
-// collide, write back.  Returns the sum over those nodes of (phi^n - phi^{n-1})^2
-// when RESID (steady-state residual), else 0.  RESID is a template argument so
-// that no FP64 arithmetic is ever issued (or speculated) in ordinary sweeps.
-template <typename Real, typename S, int MODE, bool L2ONLY, bool RESID>
-__device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, int ybase, int ystride,
-                                             int nrows) {
+// Pull of a node on the domain boundary: periodic wrap or, for a link that
+// crosses a wall, the node's own population leaving towards it comes back as
+// direction i (half-way bounce-back, Eqs. 54-56).  Stored form in and out.
+template <typename Real, typename S, bool L2ONLY>
+__device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const S *__restrict__ fin, int x,
+                                              int y, int node, Real (&d)[9]) {
     constexpr bool kShift = Shifted<S>::value;
-    const S *__restrict__ fin = static_cast<const S *>(p.fin);
-    S *__restrict__ fout = static_cast<S *>(p.fout);
-    Real xs = Real(0), xc = Real(0);
-    if (p.src_kind == 2) { xs = p.Xs[x]; xc = p.Xc[x]; }
-    const bool x_inner = (x > 0) && (x < p.nx - 1);
-    double resid = 0.0;
-
-#pragma unroll 1
-    for (int r = 0; r < nrows; ++r) {
-        const int y = ybase + r * ystride;
-        if (y >= p.ny) break;
-        const int node = y * p.pitch + x;
-        Real f[9];
-        const Real phi_prev = ldg<L2ONLY>(p.phi + node);
-        if (p.first) {
-            equilibrium(p, phi_prev, f);
-        } else if (x_inner && y > 0 && y < p.ny - 1) {
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                f[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + node - ey_of(i) * p.pitch - ex_of(i))));
-                if (kShift) f[i] += p.wref[i];
-            }
+    for (int i = 0; i < 9; ++i) {
+        int sx = x - ex_of(i), sy = y - ey_of(i);
+        int wx = -1, wy = -1;   // crossed wall side, if any
+        if (sx < 0) { if (p.hbb_x) wx = 0; else sx += p.nx; }
+        if (sx >= p.nx) { if (p.hbb_x) wx = 1; else sx -= p.nx; }
+        if (sy < 0) { if (p.hbb_y) wy = 2; else sy += p.ny; }
+        if (sy >= p.ny) { if (p.hbb_y) wy = 3; else sy -= p.ny; }
+        if (wx < 0 && wy < 0) {
+            d[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + sy * p.pitch + sx)));
         } else {
-#pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                int sx = x - ex_of(i), sy = y - ey_of(i);
-                int wx = -1, wy = -1;   // crossed wall side, if any
-                if (sx < 0) { if (p.hbb_x) wx = 0; else sx += p.nx; }
-                if (sx >= p.nx) { if (p.hbb_x) wx = 1; else sx -= p.nx; }
-                if (sy < 0) { if (p.hbb_y) wy = 2; else sy += p.ny; }
-                if (sy >= p.ny) { if (p.hbb_y) wy = 3; else sy -= p.ny; }
-                if (wx < 0 && wy < 0) {
-                    f[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + sy * p.pitch + sx)));
-                    if (kShift) f[i] += p.wref[i];
-                } else {
-                    // the node's own population leaving towards the wall (direction opp(i))
-                    // comes back as direction i (Eqs. 54-56)
-                    const int o = opp_of(i);
-                    Real phi_w;
-                    if (wx >= 0 && wy >= 0)
-                        phi_w = Real(0.5) * (wall_value(p, wx, y) + wall_value(p, wy, x));
-                    else if (wy >= 0)
-                        phi_w = wall_value(p, wy, x);
-                    else
-                        phi_w = wall_value(p, wx, y);
-                    Real fo = Storage<S>::load(ldg<L2ONLY>(fin + (o * p.plane + node)));
-                    if (kShift) fo += p.wref[o];
-                    f[i] = -fo + wall_term(p, o, phi_w);
-                }
-            }
-        }
-
-        Real src = Real(0);
-        if (p.src_kind == 1) src = Real(1);
-        else if (p.src_kind == 2) src = fma(xs, p.Ys[y], xc * p.Yc[y]);
-
-        Real phi;
-        if (MODE == kGeneral) {
-            phi = p.first ? phi_prev
-                          : ((f[0] + f[1]) + (f[2] + f[3])) + ((f[4] + f[5]) + (f[6] + f[7])) + f[8];
-            collide(p, f, phi, p.first ? phi : phi_prev, src);
-        } else {
-            phi = collide_linear<Real, MODE == kLinearK0One>(p, f, phi_prev, src, p.first != 0);
-        }
-
-#pragma unroll
-        for (int i = 0; i < 9; ++i) fout[i * p.plane + node] = Storage<S>::pack(kShift ? f[i] - p.wref[i] : f[i]);
-        p.phi[node] = phi;
-        if (not_finite(phi)) atomicOr(p.flags, 1);
-        if (RESID) {
-            const double d = (double)phi - (double)phi_prev;
-            resid = fma(d, d, resid);
+            const int o = opp_of(i);
+            Real phi_w;
+            if (wx >= 0 && wy >= 0)
+                phi_w = Real(0.5) * (wall_value(p, wx, y) + wall_value(p, wy, x));
+            else if (wy >= 0)
+                phi_w = wall_value(p, wy, x);
+            else
+                phi_w = wall_value(p, wx, y);
+            const Real dout = Storage<S>::load(ldg<L2ONLY>(fin + (o * p.plane + node)));
+            // f_i = -f_o^+ + wall term; in stored form the two shifts add up to -2 w_i phi_ref
+            Real wt = wall_term(p, o, phi_w);
+            if constexpr (kShift) wt = wt - Real(2) * p.wref[i];
+            d[i] = wt - dout;
         }
     }
+}
+
+// Spatial part of the source at node (x, y) for the compile-time source kind
+// (4: decided at run time).
+template <typename Real, int SRC>
+__device__ __forceinline__ Real source_at(const SweepParams<Real> &p, Real xs, Real xc, int y, int node) {
+    if constexpr (SRC == 1) return Real(1);
+    else if constexpr (SRC == 2) return fma(xs, p.Ys[y], xc * p.Yc[y]);
+    else if constexpr (SRC == 3) return p.srcF[node];
+    else if constexpr (SRC == 4) {
+        if (p.src_kind == 1) return Real(1);
+        if (p.src_kind == 2) return fma(xs, p.Ys[y], xc * p.Yc[y]);
+        if (p.src_kind == 3) return p.srcF[node];
+        return Real(0);
+    } else return Real(0);
+}
+
+// Pull of one node's populations (stored form) and of phi^{n-1}.
+template <typename Real, typename S, bool L2ONLY>
+__device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int y, bool x_inner, Real (&f)[9],
+                                          Real &phi_prev) {
+    constexpr bool kShift = Shifted<S>::value;
+    const S *__restrict__ fin = static_cast<const S *>(p.fin);
+    const int node = y * p.pitch + x;
+    phi_prev = ldg<L2ONLY>(p.phi + node);
+    if (p.first) {
+        equilibrium<Real, kShift>(p, phi_prev, f);
+    } else if (x_inner && y > 0 && y < p.ny - 1) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            f[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + node - ey_of(i) * p.pitch - ex_of(i))));
+    } else {
+        pull_boundary<Real, S, L2ONLY>(p, fin, x, y, node, f);
+    }
+}
+
+// Collision and write-back of one pulled node.  Returns (phi^n - phi^{n-1})^2
+// when RESID.  A non-finite phi sets `bad` (one atomic per thread at the end).
+template <typename Real, typename S, int MODE, int SRC, bool RESID>
+__device__ __forceinline__ double finish_node(const SweepParams<Real> &p, int x, int y, Real xs, Real xc,
+                                              Real (&f)[9], Real phi_prev, bool &bad) {
+    constexpr bool kShift = Shifted<S>::value;
+    S *__restrict__ fout = static_cast<S *>(p.fout);
+    const int node = y * p.pitch + x;
+    const Real src = source_at<Real, SRC>(p, xs, xc, y, node);
+    const Real phi = collide_fold<Real, MODE, SRC, kShift>(p, f, phi_prev, src, p.first != 0, node);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fout[i * p.plane + node] = Storage<S>::pack(f[i]);
+    p.phi[node] = phi;
+    bad |= not_finite(phi);
+    if (RESID) {
+        const double dd = static_cast<double>(phi) - static_cast<double>(phi_prev);
+        return dd * dd;
+    }
+    return 0.0;
+}
+
+// Sweep nodes of column x, rows ybase, ybase + ystride, ...: NR > 0 nodes, with
+// all NR pulls issued before the first collision when UNROLL (their loads are in
+// flight together), or one node after the other; NR == 0: `nrows` nodes decided
+// at run time.  Returns the sum of the nodes' (phi^n - phi^{n-1})^2 when RESID
+// (steady-state residual), else 0.  RESID is a template argument so that no FP64
+// arithmetic is issued (or speculated) in ordinary sweeps.
+template <typename Real, typename S, int MODE, int SRC, bool L2ONLY, bool RESID, int NR = 0, bool UNROLL = false>
+__device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, int ybase, int ystride,
+                                             int nrows) {
+    Real xs = Real(0), xc = Real(0);
+    if (SRC == 2 || (SRC == 4 && p.src_kind == 2)) { xs = p.Xs[x]; xc = p.Xc[x]; }
+    const bool x_inner = (x > 0) && (x < p.nx - 1);
+    double resid = 0.0;
+    bool bad = false;
+    if constexpr (NR > 0 && UNROLL) {
+        Real f[NR][9], phi_prev[NR];
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int y = ybase + r * ystride;
+            if (y < p.ny) pull_node<Real, S, L2ONLY>(p, x, y, x_inner, f[r], phi_prev[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < NR; ++r) {
+            const int y = ybase + r * ystride;
+            if (y < p.ny) resid += finish_node<Real, S, MODE, SRC, RESID>(p, x, y, xs, xc, f[r], phi_prev[r], bad);
+        }
+    } else {
+        const int n = NR > 0 ? NR : nrows;
+#pragma unroll 1
+        for (int r = 0; r < n; ++r) {
+            const int y = ybase + r * ystride;
+            if (y >= p.ny) break;
+            Real f[9], phi_prev;
+            pull_node<Real, S, L2ONLY>(p, x, y, x_inner, f, phi_prev);
+            resid += finish_node<Real, S, MODE, SRC, RESID>(p, x, y, xs, xc, f, phi_prev, bad);
+        }
+    }
+    if (bad) atomicOr(p.flags, 1);
     return resid;
 }
 
 // One sweep of one lattice: 32 x 8 threads per block, each thread sweeps
 // RowsPerThread nodes of its column, rows blockDim.y apart.
-template <typename Real, typename S, int MODE>
+template <typename Real, typename S, int MODE, int SRC>
 __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams<Real> p) {
-    constexpr int R = RowsPerThread<Real>::value;
+    constexpr int R = RowsPerThread<Real, S>::value;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int ybase = blockIdx.y * blockDim.y * R + threadIdx.y;
+    constexpr bool U = RowsPerThread<Real, S>::unroll;
     if (!p.resid_partials) {
-        if (x < p.nx) sweep_rows<Real, S, MODE, false, false>(p, x, ybase, blockDim.y, R);
+        if (x < p.nx) sweep_rows<Real, S, MODE, SRC, false, false, R, U>(p, x, ybase, blockDim.y, R);
         return;
     }
     // residual step: every thread joins the fixed-order block reduction
     __shared__ double red[256];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    red[tid] = x < p.nx ? sweep_rows<Real, S, MODE, false, true>(p, x, ybase, blockDim.y, R) : 0.0;
+    red[tid] = x < p.nx ? sweep_rows<Real, S, MODE, SRC, false, true, R, U>(p, x, ybase, blockDim.y, R) : 0.0;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
         if (tid < s) red[tid] += red[tid + s];

@@ -14,17 +14,18 @@ import torch
 from . import _capi as C
 
 _K2 = {"hbb": C.K2_HBB, "const": C.K2_CONST}
-_SRC = {"none": C.SRC_NONE, "const": C.SRC_CONST, "trig": C.SRC_TRIG}
+_SRC = {"none": C.SRC_NONE, "const": C.SRC_CONST, "trig": C.SRC_TRIG, "field": C.SRC_FIELD}
 
 
 def grid_desc(nx, ny, dx, dt, bc=(0, 0, 0, 0), compute="f64", storage="f64",
-              x0=0.0, y0=0.0, phi_ref=0.0) -> C.GridDesc:
+              x0=0.0, y0=0.0, phi_ref=0.0, fields=0) -> C.GridDesc:
     g = C.GridDesc()
     g.nx, g.ny = int(nx), int(ny)
     for k in range(4):
         g.bc[k] = int(bc[k])
     g.compute, g.storage = C.FORMATS[compute], C.FORMATS[storage]
     g.dx, g.dt, g.x0, g.y0, g.phi_ref = float(dx), float(dt), float(x0), float(y0), float(phi_ref)
+    g.fields = int(fields)
     return g
 
 
@@ -61,7 +62,7 @@ class Lattice:
     """
 
     def __init__(self, desc: C.GridDesc, coef: C.Coeffs, device=None, stream=None,
-                 workspace: Optional[torch.Tensor] = None):
+                 workspace: Optional[torch.Tensor] = None, defer_coeffs: bool = False):
         self.lib = C.load()
         self.desc = desc
         self.coef = coef
@@ -77,18 +78,28 @@ class Lattice:
         C.check(self.lib.btrt_create(ctypes.byref(desc), ctypes.c_void_p(workspace.data_ptr()),
                                      nbytes, ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)))
         self.handle = h
-        C.check(self.lib.btrt_set_coeffs(self.handle, ctypes.byref(coef)))
+        if not defer_coeffs:
+            C.check(self.lib.btrt_set_coeffs(self.handle, ctypes.byref(coef)))
 
     # ------------------------------------------------------------ construction
     @classmethod
     def from_problem(cls, p, compute="f64", storage=None, device=None, stream=None,
                      phi_ref=None) -> "Lattice":
         storage = storage or compute
+        src_field = getattr(p, "src_field", None)
+        A_field = getattr(p, "A_field", None)
+        fields = (C.FIELD_SOURCE if src_field is not None else 0) | \
+                 (C.FIELD_DIFFUSION if A_field is not None else 0)
         desc = grid_desc(p.nx, p.ny, p.dx, p.dt, p.bc, compute, storage, p.x0, p.y0,
-                         p.phi_ref if phi_ref is None else phi_ref)
+                         p.phi_ref if phi_ref is None else phi_ref, fields)
         coef = coeffs(p.u, p.b2, p.c3, p.A0, p.a2, p.k0, p.k2_mode, p.k2, p.source,
                       getattr(p, "wall_lam", 0.0))
-        lat = cls(desc, coef, device=device, stream=stream)
+        lat = cls(desc, coef, device=device, stream=stream, defer_coeffs=True)
+        if src_field is not None:
+            lat.set_source_field(src_field)
+        if A_field is not None:
+            lat.set_diffusion_field(*A_field)
+        C.check(lat.lib.btrt_set_coeffs(lat.handle, ctypes.byref(coef)))
         for side in range(4):
             arrs = getattr(p, "wall_arrays", None)
             if arrs is not None and arrs[side] is not None:
@@ -107,12 +118,32 @@ class Lattice:
 
     @property
     def real_dtype(self):
-        return torch.float64 if self.desc.compute == C.F64 else torch.float32
+        return torch.float32 if self.desc.compute == C.F32 else torch.float64
 
     def set_boundary(self, side: int, values):
         v = np.ascontiguousarray(np.atleast_1d(np.asarray(values, dtype=np.float64)))
         C.check(self.lib.btrt_set_boundary(self.handle, side,
                                            v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), v.size))
+
+    def set_source_field(self, F):
+        a = np.ascontiguousarray(F, dtype=np.float64)
+        assert a.shape == (self.ny, self.nx)
+        C.check(self.lib.btrt_set_source_field(self.handle, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))))
+        return self
+
+    def set_diffusion_field(self, Axx, Axy, Ayy):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (Axx, Axy, Ayy)]
+        for a in arrs:
+            assert a.shape == (self.ny, self.nx)
+        ptrs = [a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) for a in arrs]
+        C.check(self.lib.btrt_set_diffusion_field(self.handle, *ptrs))
+        return self
+
+    def set_sweep_variant(self, variant: str):
+        """'auto', 'plain' or 'tma' (FP32-compute lattices)."""
+        code = {"auto": C.SWEEP_AUTO, "plain": C.SWEEP_PLAIN, "tma": C.SWEEP_TMA}[variant]
+        C.check(self.lib.btrt_set_sweep_variant(self.handle, code))
+        return self
 
     def set_coeffs(self, coef: C.Coeffs):
         self.coef = coef

@@ -209,3 +209,105 @@ def test_full_size_mass_conservation_fp64():
     # both sums carry at most ~N eps |phi| ~ 1e-8 of rounding; a lost or duplicated
     # population would move the mass by O(1e-3) or more
     assert abs(m1 - m0) <= 1e-8
+
+
+# ---------------------------------------------------------------- double-word path
+@pytest.mark.parametrize("case", CASES[:5] + CASES[6:7], ids=lambda c: f"{c[0]}x{c[1]}-bc{''.join(map(str, c[2]))}-{c[4]}")
+def test_df64_random_states(case):
+    """Double-word (FP32-pair) arithmetic meets the FP64 tolerance against the oracle."""
+    nx, ny, bc, nonlin, src, steps = case
+    p = w.random_state_problem(nx, ny, seed=nx * 131 + ny, bc=bc, nonlinear=nonlin, source=src)
+    lat = _gpu_run(p, steps, compute="df64", storage="df64")
+    phi_ref, fpost_ref = _oracle_run(p, steps)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL64
+    assert _rel(lat.read_f(), fpost_ref) <= TOL64
+
+
+@pytest.mark.parametrize("p_fn", [lambda: w.mms_sinsin(n=64), lambda: w.gaussian_hill(),
+                                  lambda: w.nonlinear_modes(n=96, nsteps=60)],
+                         ids=["mms64", "gauss64x500", "nonlinear96"])
+def test_df64_workloads(p_fn):
+    p = p_fn()
+    lat = _gpu_run(p, p.nsteps, compute="df64", storage="df64")
+    phi_ref, _ = _oracle_run(p, p.nsteps)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL64
+
+
+def test_df64_steady_diffusion_exact():
+    p = w.steady_diffusion(n=10, nsteps=30000)
+    lat = _gpu_run(p, p.nsteps, compute="df64", storage="df64")
+    assert w.gre(lat.phi_host(), w.steady_diffusion_exact(p)) < 1e-11
+
+
+# ---------------------------------------------------------------- TMA-staged FP32 sweep
+TMA_CASES = [
+    (100, 37, (0, 0, 0, 0), True, "trig"),
+    (100, 37, (1, 1, 1, 1), True, "trig"),
+    (65, 17, (0, 0, 1, 1), False, "const"),
+    (130, 50, (1, 1, 0, 0), False, "none"),
+    (3, 3, (0, 0, 0, 0), True, "trig"),
+    (200, 33, (1, 1, 1, 1), False, "trig"),
+]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("case", TMA_CASES, ids=lambda c: f"{c[0]}x{c[1]}-bc{''.join(map(str, c[2]))}-{c[4]}")
+def test_tma_sweep_bitwise_equals_plain(case, storage):
+    """The TMA-staged tile kernel and the one-thread-per-node kernel do the same
+    arithmetic on the same values: results are bitwise identical."""
+    nx, ny, bc, nonlin, src = case
+    p = w.random_state_problem(nx, ny, seed=7 * nx + ny, bc=bc, nonlinear=nonlin, source=src)
+    a = _lattice(p, "f32", storage).set_sweep_variant("tma")
+    b = _lattice(p, "f32", storage).set_sweep_variant("plain")
+    a.init(p.phi0()).step(9)
+    b.init(p.phi0()).step(9)
+    assert np.array_equal(a.phi_host(), b.phi_host())
+    assert np.array_equal(a.read_f(), b.read_f())
+    assert a.check() == 0
+
+
+def test_tma_sweep_fp32_matches_oracle_full_size_sample():
+    """FP32 storage through the TMA kernel at 4096^2 against the oracle's
+    single-node step at sampled nodes (FP32 tolerance)."""
+    p = w.nonlinear_modes(n=4096, nsteps=3)
+    lat = _lattice(p, "f32", "f32").set_sweep_variant("tma")
+    lat.init(p.phi0()).step(3)
+    n = p.nx
+    pts = [(0, 0), (n - 1, n - 1), (63, 16), (64, 15), (2000, 1234), (31, 4095)]
+    wins = {pt: _window(lat, *pt) for pt in pts}
+    phi_dev = lat.phi()
+    phi_prev = {pt: float(phi_dev[pt[1], pt[0]].item()) for pt in pts}
+    _, t_now = lat.time()
+    lat.step(1)
+    for pt in pts:
+        fp, _ = oracle.node_step(p, wins[pt], pt[0], pt[1], phi_prev[pt], t_now + p.dt)
+        got = lat.read_f(pt[0], pt[1], 1, 1)[:, 0, 0]
+        assert np.allclose(got, fp, rtol=2e-5, atol=2e-5 * np.abs(fp).max()), pt
+
+
+# ---------------------------------------------------------------- per-node fields
+@pytest.mark.parametrize("walls", [True, False])
+@pytest.mark.parametrize("compute", ["f64", "df64"])
+def test_variable_tensor_field(walls, compute):
+    """Spatially varying diffusion tensor and a per-node source field (Eqs. 73-76)."""
+    p = w.variable_tensor(n=48, alpha=1e-2, walls=walls, t_end=0.3)
+    dt = 20.0 * p.dx ** 2
+    p = p.replace(dt=dt, nsteps=int(round(0.3 / dt)))
+    lat = _gpu_run(p, p.nsteps, compute=compute, storage=compute)
+    phi_ref, _ = _oracle_run(p, p.nsteps)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL64
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_variable_tensor_field_fp32_tma_equals_plain(storage):
+    p = w.variable_tensor(n=70, alpha=1e-2, walls=True, t_end=0.2)
+    dt = 20.0 * p.dx ** 2
+    p = p.replace(dt=dt, nsteps=int(round(0.2 / dt)), phi_ref=0.0)
+    a = _lattice(p, "f32", storage).set_sweep_variant("tma")
+    b = _lattice(p, "f32", storage).set_sweep_variant("plain")
+    a.init(p.phi0()).step(p.nsteps)
+    b.init(p.phi0()).step(p.nsteps)
+    assert np.array_equal(a.phi_host(), b.phi_host())
+    if storage == "f32":
+        phi_ref, _ = _oracle_run(p, p.nsteps)
+        assert _rel(a.phi_host(), phi_ref) <= TOL32

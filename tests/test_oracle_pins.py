@@ -273,3 +273,17 @@ def test_node_step_matches_grid_step(bc):
             fp, phi = oracle.node_step(p, win, ix, iy, phi_prev[iy, ix], t_next)
             assert np.allclose(fp, lat.fpost[:, iy, ix], rtol=0, atol=1e-14)
             assert phi == pytest.approx(lat.phi_prev[iy, ix], abs=1e-14)
+
+
+def test_variable_tensor_second_order():
+    """Spatially varying diffusion tensor with its manufactured source (Sec. 4.2.2,
+    Eqs. 73-76): second order under diffusive scaling (dt = 20 dx^2)."""
+    errs = []
+    for n in (25, 50, 100):
+        p = w.variable_tensor(n=n, alpha=1e-2, walls=True, t_end=0.5)
+        dt = 20.0 * p.dx ** 2
+        p = p.replace(dt=dt, nsteps=int(round(0.5 / dt)))
+        lat = oracle.run(p, nthreads=cpu_threads())
+        errs.append(w.gre(lat.phi(), w.variable_tensor_exact(p, p.nsteps * p.dt)))
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert 3.7 < r1 < 4.3 and 3.7 < r2 < 4.3, errs

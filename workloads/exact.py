@@ -51,3 +51,9 @@ def steady_diffusion_exact(p) -> np.ndarray:
     X, Y = p.coords()
     y = (Y - p.y0) / p.meta["L"]
     return p.meta["phi_bottom"] + p.meta["dphi"] * y * (2.0 - y)
+
+
+def variable_tensor_exact(p, t: float) -> np.ndarray:
+    """phi* = exp((1 - 12 pi^2 alpha) t) sin(2 pi x) sin(2 pi y) (Eq. 76)."""
+    X, Y = p.coords()
+    return math.exp(p.meta["lam"] * t) * np.sin(2 * math.pi * X) * np.sin(2 * math.pi * Y)

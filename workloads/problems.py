@@ -31,7 +31,7 @@ _SIDES = ("x-", "x+", "y-", "y+")
 
 @dataclass
 class Source:
-    kind: str = "none"            # "none" | "const" | "trig"
+    kind: str = "none"            # "none" | "const" | "trig" | "field"
     const: float = 0.0
     lam: float = 0.0              # time factor exp(lam * t)
     k: float = math.pi            # spatial wavenumber of the trig tables
@@ -72,6 +72,8 @@ class Problem:
     wall: tuple = (0.0, 0.0, 0.0, 0.0)   # constant wall value per side
     wall_arrays: Optional[Sequence[Optional[np.ndarray]]] = None   # per-node values along a side
     wall_lam: float = 0.0                # wall values carry the factor exp(wall_lam t)
+    src_field: Optional[np.ndarray] = None    # source kind "field": S = exp(lam t) src_field
+    A_field: Optional[tuple] = None           # per-node diffusion tensor (xx, xy, yy) arrays
     t0: float = 0.0
     nsteps: int = 0
     phi0_fn: Optional[Callable] = None   # phi0(X, Y) -> array
@@ -246,6 +248,31 @@ def linear_cde(n: int = 200, alpha: float = 0.01, u=(0.1, 0.1), c: float = 1.0,
                    source=src, nsteps=int(round(t_end / dt)),
                    phi0_fn=lambda X, Y: np.sin(math.pi * (X + Y)),
                    meta=dict(alpha=alpha, lam=lam), **kw)
+
+
+def variable_tensor(n: int = 100, alpha: float = 1e-2, u=(0.1, 0.1), c: float = 1.0,
+                    t_end: float = 3.0, walls: bool = True) -> Problem:
+    """Anisotropic CDE with a variable diffusion tensor (Sec. 4.2.2, Eqs. 73-76) on
+    the unit square: A = diag(2 - sin(2 pi x) sin(2 pi y), 1) alpha,
+    phi* = exp((1 - 12 pi^2 alpha) t) sin(2 pi x) sin(2 pi y) and the source of
+    Eq. 75 as a per-node field times exp(lam t).  Bounce-back walls with
+    phi_w = 0 (the solution vanishes there), or periodic."""
+    dx = 1.0 / n
+    dt = dx / c
+    lam = 1.0 - 12.0 * math.pi ** 2 * alpha
+    xs = (np.arange(n) + 0.5) * dx
+    X, Y = np.meshgrid(xs, xs)
+    s2x, s2y = np.sin(2 * math.pi * X), np.sin(2 * math.pi * Y)
+    c2x, c2y = np.cos(2 * math.pi * X), np.cos(2 * math.pi * Y)
+    field = (s2x * s2y + 4.0 * alpha * math.pi ** 2 * np.cos(4 * math.pi * X) * s2y ** 2
+             + 2.0 * math.pi * (u[0] * c2x * s2y + u[1] * s2x * c2y))
+    A_field = (alpha * (2.0 - s2x * s2y), np.zeros_like(X), np.full_like(X, alpha))
+    bc = (HBB, HBB, HBB, HBB) if walls else (PERIODIC,) * 4
+    return Problem(name=f"variable_tensor_{n}", nx=n, ny=n, dx=dx, dt=dt, bc=bc, u=tuple(u),
+                   A0=(2.0 * alpha, 0.0, alpha), source=Source(kind="field", lam=lam),
+                   src_field=field, A_field=A_field, nsteps=int(round(t_end / dt)),
+                   phi0_fn=lambda X_, Y_: np.sin(2 * math.pi * X_) * np.sin(2 * math.pi * Y_),
+                   meta=dict(alpha=alpha, lam=lam))
 
 
 def batched_instances(count: int = 512, seed: int = 0, nmin: int = 32, nmax: int = 1024,
