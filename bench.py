@@ -186,7 +186,7 @@ def run_gpu(args):
         p.phi_ref = float(phi0.mean())
     nodes = p.nx * p.ny
     stream = torch.cuda.Stream()
-    lat = Lattice.from_problem(p, compute=args.compute, storage=args.storage, stream=stream)
+    lat = Lattice.from_problem(p, compute=args.compute, storage=args.storage, stream=stream, shift=args.shift)
     if args.compute == "f32":
         lat.set_sweep_variant(args.sweep)
     lat.init(phi0)
@@ -268,11 +268,11 @@ def run_gpu(args):
 
 
 # ---------------------------------------------------------------------------- variants
-def _time_single(p, phi0, compute, storage, steps, warmup, variant="plain"):
+def _time_single(p, phi0, compute, storage, steps, warmup, variant="plain", shift="ref"):
     import torch
     from paper_1902_09813_gb300 import Lattice
     stream = torch.cuda.Stream()
-    lat = Lattice.from_problem(p, compute=compute, storage=storage, stream=stream)
+    lat = Lattice.from_problem(p, compute=compute, storage=storage, stream=stream, shift=shift)
     if compute == "f32":
         lat.set_sweep_variant(variant)
     lat.init(phi0)
@@ -298,7 +298,8 @@ def _time_single(p, phi0, compute, storage, steps, warmup, variant="plain"):
 def run_variants(args, steps=200, warmup=5):
     """The other compute/storage paths at 8192^2: double-word (FP32-pair) arithmetic
     on the manufactured-solution workload, FP32 compute with FP32/FP16/BF16 shifted
-    storage on the manufactured-solution and nonlinear workloads."""
+    storage (reference shift: plain and TMA-staged; local shift: plain) on the
+    manufactured-solution and nonlinear workloads."""
     import workloads as w
     out = {}
     p = w.mms_sinsin(n=args.n, nsteps=steps)
@@ -307,12 +308,14 @@ def run_variants(args, steps=200, warmup=5):
     for st in ("f32", "f16", "bf16"):
         out[f"mms_f32_{st}"] = _time_single(p, phi0, "f32", st, steps, warmup)
         out[f"mms_f32_{st}_tma"] = _time_single(p, phi0, "f32", st, steps, warmup, variant="tma")
+        out[f"mms_f32_{st}_local"] = _time_single(p, phi0, "f32", st, steps, warmup, shift="local")
     q = w.nonlinear_modes(n=args.n, nsteps=steps)
     phi0 = q.phi0()
     q.phi_ref = float(phi0.mean())
     for st in ("f32", "f16", "bf16"):
         out[f"nonlinear_f32_{st}"] = _time_single(q, phi0, "f32", st, steps, warmup)
         out[f"nonlinear_f32_{st}_tma"] = _time_single(q, phi0, "f32", st, steps, warmup, variant="tma")
+        out[f"nonlinear_f32_{st}_local"] = _time_single(q, phi0, "f32", st, steps, warmup, shift="local")
     out["nonlinear_f64"] = _time_single(q, phi0, "f64", "f64", 50, 3)
     return out
 
@@ -389,7 +392,7 @@ def run_batched(args, count=512, nsteps=2000, seed=0, plain=True):
             "speedup": round(t_plain / t_batch, 3),
             "batched_equals_plain_bitwise_first8": same,
             "launch": "step-per-launch graph" if shape[3] else "persistent cooperative",
-            "dtype": "f32 compute, f16 storage"}
+            "dtype": "f32 compute, f16 storage (local shift)"}
 
 
 # ---------------------------------------------------------------------------- serving
@@ -404,7 +407,7 @@ def run_serving(args, rates=(100.0, 500.0, 2000.0), count=96, seed=1):
     for p in probs:
         p.phi_ref = float(p.phi0().mean())
     out = {"requests_per_rate": count, "slice_steps": 100, "max_steps": 20000, "tol": 1e-8,
-           "budget_gb": 150, "dtype": "f32 compute, f16 storage", "rates": {}}
+           "budget_gb": 150, "dtype": "f32 compute, f16 storage (local shift)", "rates": {}}
     for lam in rates:
         trace = poisson_trace(probs, rate=lam, seed=seed)
         srv = Server(budget_bytes=150e9, slice_steps=100, max_steps=20000, tol=1e-8)
@@ -502,6 +505,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_MAIN)
     ap.add_argument("--compute", default="f64", choices=["f64", "df64", "f32"])
     ap.add_argument("--storage", default=None, choices=["f64", "df64", "f32", "f16", "bf16"])
+    ap.add_argument("--shift", default="auto", choices=["auto", "ref", "local"],
+                    help="stored form of F32/F16/BF16 populations")
     ap.add_argument("--sweep", default="auto", choices=["auto", "plain", "tma"],
                     help="kernel form of FP32-compute sweeps")
     args = ap.parse_args()

@@ -59,6 +59,15 @@ enum { BTRT_K2_HBB = 0, BTRT_K2_CONST = 1 };                    /* second-order 
 enum { BTRT_SRC_NONE = 0, BTRT_SRC_CONST = 1, BTRT_SRC_TRIG = 2, BTRT_SRC_FIELD = 3 };
 enum { BTRT_FIELD_SOURCE = 1, BTRT_FIELD_DIFFUSION = 2 };      /* btrt_grid_desc.fields bits */
 enum { BTRT_SIDE_XMIN = 0, BTRT_SIDE_XMAX = 1, BTRT_SIDE_YMIN = 2, BTRT_SIDE_YMAX = 3 };
+/* Stored form of F32/F16/BF16 populations (btrt_grid_desc.shift):
+ *  BTRT_SHIFT_REF    f_i - w_i phi_ref, one reference value per lattice;
+ *  BTRT_SHIFT_LOCAL  f_i^+(x) - w_i phi(x), relative to the phi of the node that
+ *                    wrote the population; the sweep adds w_i phi(x - e_i) back
+ *                    from the previous phi plane.  What is rounded is then of the
+ *                    size of the non-equilibrium part only, which keeps F16/BF16
+ *                    storage far closer to the FP32-storage result.
+ * FP64 and double-word storage are never shifted. */
+enum { BTRT_SHIFT_REF = 0, BTRT_SHIFT_LOCAL = 1 };
 
 typedef struct btrt_lattice_s *btrt_lattice;
 
@@ -71,9 +80,9 @@ typedef struct {
                               F32, F16, BF16 (F32 compute)                               */
     double dx, dt;         /* physical spacing and time step (c = dx/dt, cs^2 = c^2/3)  */
     double x0, y0;         /* physical position of the lower-left domain corner         */
-    double phi_ref;        /* F32/F16/BF16 storage holds f_i - w_i phi_ref (F64: unshifted) */
+    double phi_ref;        /* BTRT_SHIFT_REF: F32/F16/BF16 storage holds f_i - w_i phi_ref  */
     int32_t fields;        /* BTRT_FIELD_* bits: reserve per-node source / diffusion planes */
-    int32_t reserved;
+    int32_t shift;         /* BTRT_SHIFT_REF or BTRT_SHIFT_LOCAL (F32/F16/BF16 storage)   */
 } btrt_grid_desc;
 
 /* Coefficients of Eq. 1 and the relaxation parameters (physical units). */

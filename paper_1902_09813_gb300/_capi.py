@@ -13,6 +13,8 @@ K2_HBB, K2_CONST = 0, 1
 SRC_NONE, SRC_CONST, SRC_TRIG, SRC_FIELD = 0, 1, 2, 3
 FIELD_SOURCE, FIELD_DIFFUSION = 1, 2
 SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA = 0, 1, 2
+SHIFT_REF, SHIFT_LOCAL = 0, 1
+SHIFTS = {"ref": SHIFT_REF, "local": SHIFT_LOCAL}
 
 FORMATS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "df64": DF64}
 
@@ -25,7 +27,7 @@ class GridDesc(ctypes.Structure):
         ("dx", ctypes.c_double), ("dt", ctypes.c_double),
         ("x0", ctypes.c_double), ("y0", ctypes.c_double),
         ("phi_ref", ctypes.c_double),
-        ("fields", ctypes.c_int32), ("reserved", ctypes.c_int32),
+        ("fields", ctypes.c_int32), ("shift", ctypes.c_int32),
     ]
 
 

@@ -108,6 +108,8 @@ btrt_status check_desc(const btrt_grid_desc *g) {
         return fail(BTRT_EINVAL, "phi_ref, x0, y0 must be finite");
     if (g->fields & ~(BTRT_FIELD_SOURCE | BTRT_FIELD_DIFFUSION))
         return fail(BTRT_EINVAL, "unknown field bits 0x%x", g->fields);
+    if (g->shift != BTRT_SHIFT_REF && g->shift != BTRT_SHIFT_LOCAL)
+        return fail(BTRT_EINVAL, "unknown storage shift %d", g->shift);
     const long long pitch = (long long)((g->nx + 63) / 64) * 64;
     if (9 * pitch * (long long)g->ny >= (1LL << 31))
         return fail(BTRT_EINVAL, "grid %d x %d: the nine padded planes must hold fewer than 2^31 values "
@@ -128,8 +130,10 @@ Layout make_layout(const btrt_grid_desc *g) {
     off += L.fbuf_bytes;
     L.off_f[1] = off;
     off += L.fbuf_bytes;
-    L.off_phi = off;
-    off += align_up((size_t)L.plane * sr, kAlign);
+    for (int k = 0; k < 2; ++k) {
+        L.off_phi[k] = off;
+        off += align_up((size_t)L.plane * sr, kAlign);
+    }
     L.off_tab = off;
     off += align_up(2 * ((size_t)g->nx + (size_t)g->ny) * sr, kAlign);
     L.off_wall = off;
@@ -245,9 +249,11 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
     const btrt_grid_desc &g = L->g;
     const btrt_coeffs &c = L->c;
     std::memset(&p, 0, sizeof p);
+    // the initialising collision rewrites the current buffers in place (no streaming)
     p.fin = L->fbuf(L->cur);
     p.fout = L->fbuf(first ? L->cur : 1 - L->cur);
-    p.phi = L->phi<Real>();
+    p.phi_in = L->phi<Real>(L->cur);
+    p.phi_out = L->phi<Real>(first ? L->cur : 1 - L->cur);
     p.nx = g.nx;
     p.ny = g.ny;
     p.pitch = (int)L->lay.pitch;
@@ -255,7 +261,7 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
     p.hbb_x = g.bc[0] == BTRT_BC_HBB;
     p.hbb_y = g.bc[2] == BTRT_BC_HBB;
     const double w[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-    for (int i = 0; i < 9; ++i) p.wref[i] = (Real)(w[i] * g.phi_ref);
+    for (int i = 0; i < 9; ++i) p.wref[i] = shift_of(g) == kShiftRef ? (Real)(w[i] * g.phi_ref) : (Real)0.0;
     for (int s = 0; s < 4; ++s) {
         p.wall_const[s] = (Real)L->wall_const[s];
         p.wall_arr[s] = L->wall_is_arr[s] ? L->wall<Real>(s) : nullptr;
@@ -319,8 +325,8 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
         q.b2h = (Real)(0.5 * L->b2);
         q.a2x3 = (Real)(3.0 * c.a2);
     }
-    // the storage shift reference (zero for unshifted FP64 / double-word storage)
-    p.phi_ref = (g.storage == BTRT_F64 || g.storage == BTRT_DF64) ? (Real)0.0 : (Real)g.phi_ref;
+    // the reference value of kShiftRef storage (zero otherwise)
+    p.phi_ref = shift_of(g) == kShiftRef ? (Real)g.phi_ref : (Real)0.0;
 }
 
 template void btrt::fill_params<double>(btrt_lattice, SweepParams<double> &, int64_t, bool);
@@ -353,11 +359,12 @@ btrt_status launch(btrt_lattice L, int64_t n, bool first, bool resid = false) {
         SweepParams<float> p;
         fill_params(L, p, n, first);
         if (resid) p.resid_partials = L->resid_partials();
+        const int sh = shift_of(L->g);
         if (!first && !resid && L->have_tma && L->sweep_variant == BTRT_SWEEP_TMA)
-            CUDA_TRY(launch_sweep_tma(p, L->g.storage, sweep_mode(L), &L->tma_in[L->cur], &L->tma_out[1 - L->cur],
-                                      L->stream));
+            CUDA_TRY(launch_sweep_tma(p, L->g.storage, sh, sweep_mode(L), &L->tma_in[L->cur],
+                                      &L->tma_out[1 - L->cur], L->stream));
         else
-            CUDA_TRY(launch_sweep_f32(p, L->g.storage, sweep_mode(L), L->stream));
+            CUDA_TRY(launch_sweep_f32(p, L->g.storage, sh, sweep_mode(L), L->stream));
     }
     return BTRT_OK;
 }
@@ -410,6 +417,7 @@ btrt_status upload_wall(btrt_lattice L, int side, const double *v, int n) {
     return BTRT_OK;
 }
 
+// phi0 -> phi plane 0 (the initialising collision then runs with cur = 0).
 template <typename Real>
 btrt_status stage_phi0(btrt_lattice L, const void *phi0, int dtype, int on_device) {
     const btrt_grid_desc &g = L->g;
@@ -424,10 +432,10 @@ btrt_status stage_phi0(btrt_lattice L, const void *phi0, int dtype, int on_devic
     }
     const dim3 blk(256), grd((unsigned)((g.nx + 255) / 256), (unsigned)g.ny);
     if (dtype == BTRT_F64)
-        dense_to_plane<Real, double><<<grd, blk, 0, L->stream>>>((const double *)dev_src, L->phi<Real>(),
+        dense_to_plane<Real, double><<<grd, blk, 0, L->stream>>>((const double *)dev_src, L->phi<Real>(0),
                                                                  g.nx, g.ny, L->lay.pitch);
     else
-        dense_to_plane<Real, float><<<grd, blk, 0, L->stream>>>((const float *)dev_src, L->phi<Real>(),
+        dense_to_plane<Real, float><<<grd, blk, 0, L->stream>>>((const float *)dev_src, L->phi<Real>(0),
                                                                 g.nx, g.ny, L->lay.pitch);
     CUDA_TRY(cudaGetLastError());
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(L->stream));  // host buffer may be reused
@@ -502,7 +510,7 @@ struct StateHeader {
     int32_t nx, ny, compute, storage;
     int64_t step;
     double t0;
-    int32_t cur, pad;
+    int32_t shift, pad;   // storage shift of the saved populations
 };
 
 }  // namespace
@@ -732,16 +740,25 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
     const size_t sf = elem_size(g.storage);
     std::vector<unsigned char> raw((size_t)w * h * sf);
     const double wts[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    const int sh = shift_of(g);
+    std::vector<float> phiw;   // the nodes' phi, for the local shift (FP32 compute)
+    if (sh == kShiftLocal) {
+        phiw.resize((size_t)w * h);
+        CUDA_TRY(cudaMemcpy2DAsync(phiw.data(), w * sizeof(float), L->phi<float>() + (size_t)y0 * L->lay.pitch + x0,
+                                   L->lay.pitch * sizeof(float), w * sizeof(float), h, cudaMemcpyDeviceToHost,
+                                   L->stream));
+        CUDA_TRY(cudaStreamSynchronize(L->stream));
+    }
     for (int i = 0; i < 9; ++i) {
         const unsigned char *src = static_cast<unsigned char *>(L->fbuf(L->cur)) +
                                    ((size_t)i * L->lay.plane + (size_t)y0 * L->lay.pitch + x0) * sf;
         CUDA_TRY(cudaMemcpy2DAsync(raw.data(), w * sf, src, L->lay.pitch * sf, w * sf, h,
                                    cudaMemcpyDeviceToHost, L->stream));
         CUDA_TRY(cudaStreamSynchronize(L->stream));
-        // the stored values are rounded from Real = f - w_i phi_ref in the compute precision
-        // FP64 and double-word storage are never shifted; FP32 compute shifts by (float)(w_i phi_ref)
-        const double shift = (g.storage == BTRT_F64 || g.storage == BTRT_DF64)
-                                 ? 0.0 : (double)(float)(wts[i] * g.phi_ref);
+        // the stored values are rounded from f - w_i phi_ref (reference shift, FP32 compute
+        // shifts by (float)(w_i phi_ref)) or from f^+ - w_i phi(x) (local shift); FP64 and
+        // double-word storage are never shifted
+        const double shift = sh == kShiftRef ? (double)(float)(wts[i] * g.phi_ref) : 0.0;
         for (size_t k = 0; k < (size_t)w * h; ++k) {
             double v;
             if (g.storage == BTRT_F64) std::memcpy(&v, &raw[k * 8], 8);
@@ -752,7 +769,8 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
             }
             else if (g.storage == BTRT_F32) { float fv; std::memcpy(&fv, &raw[k * 4], 4); v = fv; }
             else v = host_half_to_double(g.storage, &raw[k * 2]);
-            dst[(size_t)i * w * h + k] = v + shift;
+            const double loc = sh == kShiftLocal ? wts[i] * (double)phiw[k] : 0.0;
+            dst[(size_t)i * w * h + k] = v + shift + loc;
         }
     }
     return BTRT_OK;
@@ -803,7 +821,8 @@ btrt_status btrt_save(btrt_lattice L, void *host_buf, size_t n) {
     if (n < btrt_state_bytes(L)) return fail(BTRT_ENOMEM, "buffer of %zu bytes too small", n);
     StateHeader h;
     std::memset(&h, 0, sizeof h);
-    std::memcpy(h.magic, "BTRTST1", 8);
+    std::memcpy(h.magic, "BTRTST2", 8);
+    h.shift = L->g.shift;
     h.nx = L->g.nx;
     h.ny = L->g.ny;
     h.compute = L->g.compute;
@@ -813,7 +832,7 @@ btrt_status btrt_save(btrt_lattice L, void *host_buf, size_t n) {
     std::memcpy(host_buf, &h, sizeof h);
     unsigned char *p = static_cast<unsigned char *>(host_buf) + sizeof h;
     CUDA_TRY(cudaMemcpyAsync(p, L->fbuf(L->cur), L->lay.fbuf_bytes, cudaMemcpyDeviceToHost, L->stream));
-    CUDA_TRY(cudaMemcpyAsync(p + L->lay.fbuf_bytes, L->ws + L->lay.off_phi,
+    CUDA_TRY(cudaMemcpyAsync(p + L->lay.fbuf_bytes, L->ws + L->lay.off_phi[L->cur],
                              (size_t)L->lay.plane * elem_size(L->g.compute), cudaMemcpyDeviceToHost, L->stream));
     CUDA_TRY(cudaStreamSynchronize(L->stream));
     return BTRT_OK;
@@ -825,13 +844,13 @@ btrt_status btrt_load(btrt_lattice L, const void *host_buf, size_t n) {
     if (n < btrt_state_bytes(L)) return fail(BTRT_ENOMEM, "buffer of %zu bytes too small", n);
     StateHeader h;
     std::memcpy(&h, host_buf, sizeof h);
-    if (std::memcmp(h.magic, "BTRTST1", 8) != 0 || h.nx != L->g.nx || h.ny != L->g.ny ||
-        h.compute != L->g.compute || h.storage != L->g.storage)
+    if (std::memcmp(h.magic, "BTRTST2", 8) != 0 || h.nx != L->g.nx || h.ny != L->g.ny ||
+        h.compute != L->g.compute || h.storage != L->g.storage || h.shift != L->g.shift)
         return fail(BTRT_EINVAL, "state does not match this lattice");
     const unsigned char *p = static_cast<const unsigned char *>(host_buf) + sizeof h;
     L->cur = 0;
     CUDA_TRY(cudaMemcpyAsync(L->fbuf(0), p, L->lay.fbuf_bytes, cudaMemcpyHostToDevice, L->stream));
-    CUDA_TRY(cudaMemcpyAsync(L->ws + L->lay.off_phi, p + L->lay.fbuf_bytes,
+    CUDA_TRY(cudaMemcpyAsync(L->ws + L->lay.off_phi[0], p + L->lay.fbuf_bytes,
                              (size_t)L->lay.plane * elem_size(L->g.compute), cudaMemcpyHostToDevice, L->stream));
     CUDA_TRY(cudaMemsetAsync(L->flags(), 0, 16, L->stream));
     CUDA_TRY(cudaStreamSynchronize(L->stream));

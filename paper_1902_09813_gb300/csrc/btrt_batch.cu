@@ -33,7 +33,7 @@ namespace {
 
 template <typename Real>
 struct BatchMember {
-    SweepParams<Real> p;       // fin = buffer 0, fout = buffer 1; first = 0
+    SweepParams<Real> p;       // fin, phi_in = buffers 0; fout, phi_out = buffers 1; first = 0
     long long step;            // completed steps at the start of the launch
     int cur;                   // buffer holding the current populations at the start
     int mode;                  // kGeneral or kLinear
@@ -87,7 +87,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int t
 // One tile of one step: load the member's parameters into shared memory, patch
 // the step-dependent ones (buffer parity, source and wall time factors from the
 // host-computed step table) and sweep the tile's nodes.
-template <typename Real, typename S, bool L2ONLY>
+template <typename Real, typename S, int SH, bool L2ONLY>
 __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int k, bool resid,
                                            SweepParams<Real> &sp, double *red) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -107,6 +107,10 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int 
         void *b1 = M.p.fout;                 // buffer 1
         sp.fin = cur ? b1 : b0;
         sp.fout = cur ? const_cast<void *>(b0) : b1;
+        const Real *q0 = M.p.phi_in;         // phi plane 0
+        Real *q1 = M.p.phi_out;              // phi plane 1
+        sp.phi_in = cur ? q1 : q0;
+        sp.phi_out = cur ? const_cast<Real *>(q0) : q1;
     } else if (tid == 32) {
         const Real *v = a.step_vals + ((size_t)tile.x * a.table_steps + k) * 2;
         sp.src_val = v[0];
@@ -119,11 +123,11 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int 
     if (x < sp.nx) {
         const int y0 = tile.z + threadIdx.y;
         if (M.mode == kGeneral) {
-            if (resid) r = sweep_rows<Real, S, kGeneral, 4, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
-            else sweep_rows<Real, S, kGeneral, 4, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+            if (resid) r = sweep_rows<Real, S, SH, kGeneral, 4, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, SH, kGeneral, 4, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
         } else {
-            if (resid) r = sweep_rows<Real, S, kLinear, 4, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
-            else sweep_rows<Real, S, kLinear, 4, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+            if (resid) r = sweep_rows<Real, S, SH, kLinear, 4, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, SH, kLinear, 4, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
         }
     }
     if (resid) {
@@ -140,13 +144,13 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int 
 // Persistent form: every resident block walks the tile table each step; a
 // bounded grid barrier separates the steps.  Population and phi loads go
 // through L2 only, since other SMs rewrote them in the previous step.
-template <typename Real, typename S>
+template <typename Real, typename S, int SH>
 __global__ void __launch_bounds__(256) batch_kernel(const __grid_constant__ BatchArgs<Real> a) {
     __shared__ SweepParams<Real> sp;
     __shared__ double red[256];
     for (int k = 0; k < a.nsteps; ++k) {
         const bool resid = a.want_resid && (k == a.nsteps - 1);
-        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, true>(a, t, k, resid, sp, red);
+        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, SH, true>(a, t, k, resid, sp, red);
         if (!grid_barrier(a.barrier, (unsigned)(k + 1) * gridDim.x + a.barrier_extra, a.err, a.wait_limit))
             return;
     }
@@ -154,12 +158,12 @@ __global__ void __launch_bounds__(256) batch_kernel(const __grid_constant__ Batc
 
 // Step-per-launch form: one launch per step (all of them in one CUDA graph);
 // kernel boundaries order the steps, so no barrier and ordinary cached loads.
-template <typename Real, typename S>
+template <typename Real, typename S, int SH>
 __global__ void __launch_bounds__(256) batch_step_kernel(const __grid_constant__ BatchArgs<Real> a, int k) {
     __shared__ SweepParams<Real> sp;
     __shared__ double red[256];
     const bool resid = a.want_resid && (k == a.nsteps - 1);
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, false>(a, t, k, resid, sp, red);
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, SH, false>(a, t, k, resid, sp, red);
 }
 
 // Per-member residual: fixed-order sum of its tiles' partials, then sqrt.
@@ -259,23 +263,24 @@ btrt_status check_members(const btrt_lattice *members, int32_t n, std::vector<bt
         if (!out[k]->ready) return bfail(BTRT_ESTATE, "member %d is not initialised", k);
         if (out[k]->g.compute == BTRT_DF64)
             return bfail(BTRT_EINVAL, "member %d: batches take FP64 or FP32 members", k);
-        if (out[k]->g.compute != out[0]->g.compute || out[k]->g.storage != out[0]->g.storage)
-            return bfail(BTRT_EINVAL, "member %d: all members need the same compute and storage formats", k);
+        if (out[k]->g.compute != out[0]->g.compute || out[k]->g.storage != out[0]->g.storage ||
+            shift_of(out[k]->g) != shift_of(out[0]->g))
+            return bfail(BTRT_EINVAL, "member %d: all members need the same compute and storage formats and shift", k);
         for (int j = 0; j < k; ++j)
             if (out[j] == out[k]) return bfail(BTRT_EINVAL, "member %d appears twice", k);
     }
     return BTRT_OK;
 }
 
-// autotuner cache: (members, total nodes in millions, compute, storage) -> shape
+// autotuner cache: (members, total nodes in millions, compute, storage, shift) -> shape
 std::mutex g_tune_mu;
-std::map<std::tuple<int, long long, int, int>, Shape> g_tune_cache;
+std::map<std::tuple<int, long long, int, int, int>, Shape> g_tune_cache;
 
 }  // namespace
 
 struct btrt_batch_s {
     std::vector<btrt_lattice> members;
-    int compute = 0, storage = 0;
+    int compute = 0, storage = 0, shift = 0;
     unsigned char *ws = nullptr;
     cudaStream_t stream = nullptr;
     BatchLayout lay{};
@@ -300,14 +305,19 @@ struct btrt_batch_s {
 
 namespace {
 
-void *persistent_kernel_for(int compute, int storage) {
-    if (compute == BTRT_F64) return reinterpret_cast<void *>(&batch_kernel<double, double>);
+template <int SH>
+void *persistent_kernel_sh(int storage) {
     switch (storage) {
-    case BTRT_F32: return reinterpret_cast<void *>(&batch_kernel<float, float>);
-    case BTRT_F16: return reinterpret_cast<void *>(&batch_kernel<float, __half>);
-    case BTRT_BF16: return reinterpret_cast<void *>(&batch_kernel<float, __nv_bfloat16>);
+    case BTRT_F32: return reinterpret_cast<void *>(&batch_kernel<float, float, SH>);
+    case BTRT_F16: return reinterpret_cast<void *>(&batch_kernel<float, __half, SH>);
+    case BTRT_BF16: return reinterpret_cast<void *>(&batch_kernel<float, __nv_bfloat16, SH>);
     }
     return nullptr;
+}
+
+void *persistent_kernel_for(int compute, int storage, int shift) {
+    if (compute == BTRT_F64) return reinterpret_cast<void *>(&batch_kernel<double, double, kShiftNone>);
+    return shift == kShiftLocal ? persistent_kernel_sh<kShiftLocal>(storage) : persistent_kernel_sh<kShiftRef>(storage);
 }
 
 // Tile table for the current shape; also sizes the persistent grid.
@@ -334,7 +344,7 @@ btrt_status build_tiles(btrt_batch B) {
     int dev = 0, sms = 0, per_sm = 0;
     BCUDA(cudaGetDevice(&dev));
     BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel_for(B->compute, B->storage),
+    BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel_for(B->compute, B->storage, B->shift),
                                                         s.bx * s.by, 0));
     if (per_sm < 1) return bfail(BTRT_ECUDA, "batch kernel cannot be resident");
     B->grid = per_sm * sms;
@@ -398,31 +408,37 @@ BatchArgs<Real> make_args(btrt_batch B, int nsteps, int want_resid) {
     return a;
 }
 
-template <typename Real, typename S>
+template <typename Real, typename S, int SH>
 btrt_status enqueue_typed(btrt_batch B, int nsteps, int want_resid) {
     BatchArgs<Real> a = make_args<Real>(B, nsteps, want_resid);
     const dim3 block(B->shape.bx, B->shape.by);
     if (B->shape.per_step) {
         const unsigned grid = (unsigned)B->ntiles;
-        for (int k = 0; k < nsteps; ++k) batch_step_kernel<Real, S><<<grid, block, 0, B->stream>>>(a, k);
+        for (int k = 0; k < nsteps; ++k) batch_step_kernel<Real, S, SH><<<grid, block, 0, B->stream>>>(a, k);
         BCUDA(cudaGetLastError());
         return BTRT_OK;
     }
     void *args[] = {&a};
     BCUDA(cudaMemsetAsync(B->barrier(), 0, sizeof(unsigned int), B->stream));
-    BCUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(&batch_kernel<Real, S>), dim3(B->grid), block,
+    BCUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(&batch_kernel<Real, S, SH>), dim3(B->grid), block,
                                       args, 0, B->stream));
     return BTRT_OK;
 }
 
-btrt_status enqueue(btrt_batch B, int nsteps, int want_resid) {
-    if (B->compute == BTRT_F64) return enqueue_typed<double, double>(B, nsteps, want_resid);
+template <int SH>
+btrt_status enqueue_sh(btrt_batch B, int nsteps, int want_resid) {
     switch (B->storage) {
-    case BTRT_F32: return enqueue_typed<float, float>(B, nsteps, want_resid);
-    case BTRT_F16: return enqueue_typed<float, __half>(B, nsteps, want_resid);
-    case BTRT_BF16: return enqueue_typed<float, __nv_bfloat16>(B, nsteps, want_resid);
+    case BTRT_F32: return enqueue_typed<float, float, SH>(B, nsteps, want_resid);
+    case BTRT_F16: return enqueue_typed<float, __half, SH>(B, nsteps, want_resid);
+    case BTRT_BF16: return enqueue_typed<float, __nv_bfloat16, SH>(B, nsteps, want_resid);
     }
     return bfail(BTRT_EINVAL, "unsupported storage format");
+}
+
+btrt_status enqueue(btrt_batch B, int nsteps, int want_resid) {
+    if (B->compute == BTRT_F64) return enqueue_typed<double, double, kShiftNone>(B, nsteps, want_resid);
+    return B->shift == kShiftLocal ? enqueue_sh<kShiftLocal>(B, nsteps, want_resid)
+                                   : enqueue_sh<kShiftRef>(B, nsteps, want_resid);
 }
 
 // Replay (or capture, then replay) the slice graph; falls back to direct
@@ -484,6 +500,7 @@ btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_
     B->members = m;
     B->compute = m[0]->g.compute;
     B->storage = m[0]->g.storage;
+    B->shift = shift_of(m[0]->g);
     B->ws = static_cast<unsigned char *>(dev_workspace);
     B->stream = static_cast<cudaStream_t>(cuda_stream);
     B->lay = lay;
@@ -591,7 +608,7 @@ btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *
     if (steps_per_trial < 1) return bfail(BTRT_EINVAL, "steps_per_trial must be >= 1");
     long long nodes = 0;
     for (auto L : B->members) nodes += (long long)L->g.nx * L->g.ny;
-    const auto key = std::make_tuple((int)B->members.size(), nodes / 1000000, B->compute, B->storage);
+    const auto key = std::make_tuple((int)B->members.size(), nodes / 1000000, B->compute, B->storage, B->shift);
     Shape best{0, 0, 0, 0};
     {
         std::lock_guard<std::mutex> lock(g_tune_mu);

@@ -22,7 +22,8 @@ struct Layout {
     long long plane = 0;     // elements per plane
     size_t fbuf_bytes = 0;   // one buffer of 9 planes
     size_t off_f[2] = {0, 0};
-    size_t off_phi = 0, off_tab = 0, off_wall = 0, off_red = 0, off_resid = 0, total = 0;
+    size_t off_phi[2] = {0, 0};   // phi planes, double-buffered with the populations
+    size_t off_tab = 0, off_wall = 0, off_red = 0, off_resid = 0, total = 0;
     size_t off_srcf = 0, off_af = 0;   // optional field planes (0 when absent)
     int maxside = 0;
     long long resid_blocks = 0;   // partial slots of a residual sweep (one per block)
@@ -54,7 +55,9 @@ struct btrt_lattice_s {
     int sweep_variant = 0;    // BTRT_SWEEP_AUTO / PLAIN / TMA
     bool have_srcf = false, have_af = false;   // fields uploaded
 
-    template <typename Real> Real *phi() { return reinterpret_cast<Real *>(ws + lay.off_phi); }
+    // phi plane k; phi<Real>() is the current one (written with the populations of buffer cur)
+    template <typename Real> Real *phi(int k) { return reinterpret_cast<Real *>(ws + lay.off_phi[k]); }
+    template <typename Real> Real *phi() { return phi<Real>(cur); }
     void *fbuf(int k) { return ws + lay.off_f[k]; }
     template <typename Real> Real *tab() { return reinterpret_cast<Real *>(ws + lay.off_tab); }
     template <typename Real> Real *wall(int side) {
@@ -79,9 +82,23 @@ void step_scalars(btrt_lattice L, int64_t n, bool first, double *src_val, double
 // Compiled variant (kGeneral / kLinear / kLinearK0One) that serves L's coefficients.
 int sweep_mode(btrt_lattice L);
 
+// Threads of a single-lattice sweep block, and its grid: 32 x 8 threads, each
+// sweeping rows_per_thread nodes of its column.
+inline dim3 sweep_block() { return dim3(32, 8, 1); }
+inline dim3 sweep_grid(int nx, int ny, int rows_per_thread) {
+    const int rows = 8 * rows_per_thread;
+    return dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + rows - 1) / rows), 1);
+}
+
+// Storage shift of a lattice (kShiftNone for FP64 / double-word storage).
+inline int shift_of(const btrt_grid_desc &g) {
+    if (g.storage == BTRT_F64 || g.storage == BTRT_DF64) return kShiftNone;
+    return g.shift == BTRT_SHIFT_LOCAL ? kShiftLocal : kShiftRef;
+}
+
 // TMA-staged sweep (FP32 compute) and the box sizes its tensor maps need.
-cudaError_t launch_sweep_tma(const SweepParams<float> &p, int storage, int mode, const CUtensorMap *in_map,
-                             const CUtensorMap *out_map, cudaStream_t s);
+cudaError_t launch_sweep_tma(const SweepParams<float> &p, int storage, int shift, int mode,
+                             const CUtensorMap *in_map, const CUtensorMap *out_map, cudaStream_t s);
 void tma_box(int storage, int *box_in_x, int *box_in_y, int *box_out_x, int *box_out_y);
 
 // Blocks of one single-lattice sweep (32 x 8 threads, RowsPerThread nodes each).
@@ -92,7 +109,7 @@ long long sweep_blocks(int nx, int ny, int compute, int storage);
 // mode: kGeneral, kLinear or kLinearK0One (FP64); kGeneral or kLinear (FP32).
 cudaError_t launch_sweep_f64(const SweepParams<double> &p, int mode, cudaStream_t s);
 cudaError_t launch_sweep_dw(const SweepParams<dw> &p, int mode, cudaStream_t s);
-cudaError_t launch_sweep_f32(const SweepParams<float> &p, int storage, int mode, cudaStream_t s);
+cudaError_t launch_sweep_f32(const SweepParams<float> &p, int storage, int shift, int mode, cudaStream_t s);
 
 // Record the thread-local message returned by btrt_last_error (printf format).
 void set_last_error(const char *fmt, ...);

@@ -1,0 +1,92 @@
+// btrt_launch.cuh -- launch helpers of the FP32-compute sweeps, instantiated per
+// storage format in their own translation units (btrt_sweep_*.cu) so that the
+// many compiled variants build in parallel.
+#pragma once
+
+#include <algorithm>
+
+#include "btrt_internal.h"
+#include "btrt_tma.cuh"
+
+namespace btrt {
+
+// Dispatch on the source kind so that each compiled sweep carries only its own
+// source arithmetic.
+template <typename Real, typename S, int SH, int MODE>
+inline void launch_src(const SweepParams<Real> &p, dim3 g, dim3 b, cudaStream_t s) {
+    switch (p.src_kind) {
+    case 0: sweep_kernel<Real, S, SH, MODE, 0><<<g, b, 0, s>>>(p); break;
+    case 1: sweep_kernel<Real, S, SH, MODE, 1><<<g, b, 0, s>>>(p); break;
+    case 2: sweep_kernel<Real, S, SH, MODE, 2><<<g, b, 0, s>>>(p); break;
+    default: sweep_kernel<Real, S, SH, MODE, 3><<<g, b, 0, s>>>(p); break;
+    }
+}
+
+// Plain FP32-compute sweep for storage S: shift x {kGeneral, kLinear} x source.
+template <typename S>
+cudaError_t launch_f32_storage(const SweepParams<float> &p, int shift, int mode, cudaStream_t s) {
+    const dim3 g = sweep_grid(p.nx, p.ny, RowsPerThread<float, S>::value), b = sweep_block();
+    const bool lin = mode != kGeneral;
+    if (shift == kShiftLocal) {
+        if (lin) launch_src<float, S, kShiftLocal, kLinear>(p, g, b, s);
+        else launch_src<float, S, kShiftLocal, kGeneral>(p, g, b, s);
+    } else {
+        if (lin) launch_src<float, S, kShiftRef, kLinear>(p, g, b, s);
+        else launch_src<float, S, kShiftRef, kGeneral>(p, g, b, s);
+    }
+    return cudaGetLastError();
+}
+
+// TMA-staged sweep: a persistent grid of at most (resident blocks per SM) x SMs.
+template <typename S, int SH, int MODE, int SRC>
+cudaError_t launch_tma_src(const SweepParams<float> &p, const CUtensorMap *in_map, const CUtensorMap *out_map,
+                           cudaStream_t s) {
+    using G = TmaGeom<S>;
+    static bool configured = false;   // one attribute call per instantiation
+    static int per_sm = 0, sms = 0;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(sweep_tma_kernel<S, SH, MODE, SRC>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
+        if (e != cudaSuccess) return e;
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_tma_kernel<S, SH, MODE, SRC>,
+                                                              G::THREADS, G::SMEM);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaErrorInvalidConfiguration;
+        configured = true;
+    }
+    const int ntx = (p.nx + G::TX - 1) / G::TX;
+    const int nty = (p.ny + G::TY - 1) / G::TY;
+    const int ntiles = ntx * nty;
+    const int grid = std::min(ntiles, per_sm * sms);
+    sweep_tma_kernel<S, SH, MODE, SRC><<<grid, G::THREADS, G::SMEM, s>>>(p, *in_map, *out_map, ntx, ntiles,
+                                                                        1u << 22);
+    return cudaGetLastError();
+}
+
+template <typename S, int SH, int MODE>
+cudaError_t launch_tma_mode(const SweepParams<float> &p, const CUtensorMap *in_map, const CUtensorMap *out_map,
+                            cudaStream_t s) {
+    switch (p.src_kind) {
+    case 0: return launch_tma_src<S, SH, MODE, 0>(p, in_map, out_map, s);
+    case 1: return launch_tma_src<S, SH, MODE, 1>(p, in_map, out_map, s);
+    case 2: return launch_tma_src<S, SH, MODE, 2>(p, in_map, out_map, s);
+    default: return launch_tma_src<S, SH, MODE, 3>(p, in_map, out_map, s);
+    }
+}
+
+template <typename S>
+cudaError_t launch_tma_storage(const SweepParams<float> &p, int shift, int mode, const CUtensorMap *in_map,
+                               const CUtensorMap *out_map, cudaStream_t s) {
+    const bool lin = mode != kGeneral;
+    if (shift == kShiftLocal)
+        return lin ? launch_tma_mode<S, kShiftLocal, kLinear>(p, in_map, out_map, s)
+                   : launch_tma_mode<S, kShiftLocal, kGeneral>(p, in_map, out_map, s);
+    return lin ? launch_tma_mode<S, kShiftRef, kLinear>(p, in_map, out_map, s)
+               : launch_tma_mode<S, kShiftRef, kGeneral>(p, in_map, out_map, s);
+}
+
+}  // namespace btrt

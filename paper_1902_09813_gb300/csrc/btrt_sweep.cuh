@@ -5,7 +5,16 @@
 // (Eq. 38 read backwards), replaces links that cross a bounce-back wall by
 // -f_opp^+(x) + 2 w_i phi_w (Eqs. 54-56), collides with the moment-space form
 // of Eq. 6 (Eqs. 94-95, 99) and writes f^+ back to its own slot of the other
-// buffer, together with phi.
+// buffer, together with phi (the phi plane is double-buffered like f).
+//
+// Stored form of the populations (SH):
+//   kShiftNone   FP64 and double-word storage: f_i itself;
+//   kShiftRef    f_i - w_i phi_ref with one reference value per lattice;
+//   kShiftLocal  f_i^+(x) - w_i phi^n(x), the deviation from w_i times the phi of
+//                the node that wrote it.  The puller adds w_i phi^n(x - e_i) back
+//                from the previous phi plane.  What is rounded to the storage
+//                format is then of the size of the non-equilibrium and convective
+//                parts only, not of phi itself.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -65,12 +74,13 @@ template <typename Real>
 struct SweepParams {
     const void *fin;       // post-collision populations at step n-1: 9 planes, `plane` apart
     void *fout;            // post-collision populations at step n
-    Real *phi;             // phi plane: phi^{n-1} on entry, phi^n on exit
+    const Real *phi_in;    // phi^{n-1} (the phi of the nodes that wrote fin)
+    Real *phi_out;         // phi^n (equal to phi_in for the initialising collision)
     int nx, ny;
     int pitch;             // elements between rows
     int plane;             // elements between population planes; 9 * plane < 2^31
     int hbb_x, hbb_y;      // 1: bounce-back walls on that axis, 0: periodic
-    Real wref[9];          // w_i phi_ref (storage shift)
+    Real wref[9];          // w_i phi_ref (kShiftRef storage)
 
     // walls (phi_w per side; arrays may be null) and the time factor of this step
     Real wall_const[4];
@@ -98,7 +108,7 @@ struct SweepParams {
     int first;             // 1: initialisation (f = f_eq(phi), no streaming)
     int *flags;            // bit 0: non-finite phi
     double *resid_partials;  // non-null: per-block sum of (phi^n - phi^{n-1})^2 (single-lattice sweep)
-    Real phi_ref;          // storage shift reference (0 for unshifted storage)
+    Real phi_ref;          // kShiftRef: the reference value (0 otherwise)
     FoldConsts<Real> lin;
 };
 
@@ -135,16 +145,18 @@ __device__ __forceinline__ dw quot(dw a, dw b) { return a / b; }
 // Compiled variants: every coefficient family evaluated per node (kGeneral), or
 // B = u phi, C = phi and constant A with any k0 (kLinear) or k0 = 1 (kLinearK0One).
 enum { kGeneral = 0, kLinear = 1, kLinearK0One = 2 };
+// Stored form of the populations (see the top of this file).
+enum { kShiftNone = 0, kShiftRef = 1, kShiftLocal = 2 };
 
 // Moment-space form of Eq. 6 (Eqs. 94, 95, 99 with K2 = k2 Ihat), expanded back
-// into populations and written for the values the lattice stores: d_i = f_i
-// (FP64, double-word) or the shifted d_i = f_i - w_i phi_ref (FP32/FP16/BF16).
-// The shift cancels from the first moments and from M2xx - M2yy, enters the
-// trace as phi_ref, and in the outputs only as -k0 w_i phi_ref, which folds into
+// into populations and written for shifted values d_i = f_i - w_i rs: rs = 0
+// (kShiftNone), rs = phi_ref (kShiftRef) or rs = phi^{n-1} of this node
+// (kShiftLocal).  The shift cancels from the first moments and from M2xx - M2yy,
+// enters the trace as rs, and in the outputs only as -k0 w_i rs, which folds into
 // the isotropic term; so the shift costs one add per node instead of eighteen.
 //
 // With sigma = nxx + nyy and delta = nxx - nyy of the non-equilibrium second
-// moments, kap = (9/2)(k2 - k0) and a = k0 (phi - phi_ref) + source:
+// moments, kap = (9/2)(k2 - k0) and a = k0 (phi - rs) + source:
 //   d_i^+ = (1 - k0) d_i + w_i (a + cC_i) + w_i 3 e_i . V - w_i kap H_i
 //   w0 kap H_0 = -(w0 kap/3) sigma,  w1 kap H_x,y = (w1 kap/6)(sigma +- 3 delta),
 //   w5 kap H_d = (2/3) w5 kap (sigma +- 3 nxy),
@@ -154,29 +166,31 @@ enum { kGeneral = 0, kLinear = 1, kLinearK0One = 2 };
 // kLinearK0One) or per-node coefficient evaluation (kGeneral: nonlinear B, C and
 // A(x, phi) with the first-order block K1 = (3 A^ + I/2)^-1 of Eq. 30 and k2 from
 // Eq. 62 built at every node).  SRC: 0 none, 1 constant, 2 trig table, 3 field,
-// 4 decided at run time.
-template <typename Real, int MODE, int SRC, bool SHIFT>
-__device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&d)[9], Real phi_prev,
-                                             Real srcv, bool first, int node) {
+// 4 decided at run time.  Returns phi; phid_out = phi - rs as summed from the d_i.
+template <typename Real, int MODE, int SRC, int SH>
+__device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&d)[9], Real rs, Real phi_prev,
+                                             Real srcv, bool first, int node, Real &phid_out) {
     const FoldConsts<Real> &L = p.lin;
     constexpr bool K0ONE = MODE == kLinearK0One;
     const Real a13 = d[1] + d[3], a24 = d[2] + d[4];
     const Real s57 = d[5] + d[7], s68 = d[6] + d[8];
     const Real sd = s57 + s68;
     const Real a1324 = a13 + a24;
-    const Real phid = (d[0] + sd) + a1324;            // sum of the stored values
+    const Real phid = (d[0] + sd) + a1324;            // phi - rs
+    phid_out = phid;
     Real phi = phid;
-    if constexpr (SHIFT) phi = phid + p.phi_ref;
+    if constexpr (SH != kShiftNone) phi = phid + rs;
     const Real b13 = d[1] - d[3], b24 = d[2] - d[4];
     const Real d57 = d[5] - d[7], d68 = d[6] - d[8];
     const Real jx = b13 + (d57 - d68);
     const Real jy = b24 + (d57 + d68);
     const Real pxy = s57 - s68;
     const Real del = a13 - a24;
-    const Real dphi = first ? Real(0) : phi - phi_prev;
+    // phi^n - phi^{n-1}; with the local shift rs = phi^{n-1}, so it is phid itself
+    const Real dphi = first ? Real(0) : (SH == kShiftLocal ? phid : phi - phi_prev);
 
     Real Vx, Vy, c0, k6, k6x3, kd, kdx3;
-    Real cmid = phid;                                   // C - phi_ref
+    Real cmid = phid;                                   // C - rs
     Real cc = Real(0);                                  // (3/2) k0 (C - phi)
     if constexpr (MODE != kGeneral) {
         const Real mx = fma(-L.ux, phi, jx), my = fma(-L.uy, phi, jy);
@@ -279,8 +293,9 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
     return phi;
 }
 
-// Equilibrium populations (Eq. 7) in lattice units, D = C(phi) I, in stored form.
-template <typename Real, bool SHIFT>
+// Equilibrium populations (Eq. 7) in lattice units, D = C(phi) I, shifted by
+// w_i rs as the collision expects (rs = phi for the local shift).
+template <typename Real, int SH>
 __device__ __forceinline__ void equilibrium(const SweepParams<Real> &p, Real phi, Real (&f)[9]) {
     const Real hb = Real(0.5) * p.b2 * phi * phi;
     const Real Bx = Real(3) * (p.ux * phi + hb), By = Real(3) * (p.uy * phi + hb);
@@ -298,9 +313,12 @@ __device__ __forceinline__ void equilibrium(const SweepParams<Real> &p, Real phi
     f[7] = w5 * (a5 - Bx - By);
     f[6] = w5 * (a5 - Bx + By);
     f[8] = w5 * (a5 + Bx - By);
-    if constexpr (SHIFT) {
+    if constexpr (SH == kShiftRef) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = f[i] - p.wref[i];
+    } else if constexpr (SH == kShiftLocal) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = fma(-wgt<Real>(i), phi, f[i]);
     }
 }
 
@@ -312,18 +330,40 @@ __device__ __forceinline__ bool not_finite(float v) {
     return (__float_as_int(v) & 0x7f800000) == 0x7f800000;
 }
 
-template <typename S> struct Shifted { static constexpr bool value = true; };
-template <> struct Shifted<double> { static constexpr bool value = false; };  // FP64 storage is never shifted
-template <> struct Shifted<dw> { static constexpr bool value = false; };      // nor double-word storage
+// FP64 and double-word storage are never shifted; the other formats take the
+// shift the lattice was created with.
+template <typename S, int SH> struct ShiftOf { static constexpr int value = SH; };
+template <int SH> struct ShiftOf<double, SH> { static constexpr int value = kShiftNone; };
+template <int SH> struct ShiftOf<dw, SH> { static constexpr int value = kShiftNone; };
 
 // Nodes per thread of the single-lattice sweep: the FP64 sweep is ALU-bound and
 // amortises per-thread set-up over a column of 4 nodes; the HBM-bound FP32-storage
 // sweep takes two nodes with both pulls issued before the collisions (loads in
 // flight together, set-up shared); the FP16/BF16-storage sweeps, limited by
-// registers and issue, keep one node per thread.
-template <typename Real, typename S> struct RowsPerThread { static constexpr int value = 1; static constexpr bool unroll = false; };
-template <> struct RowsPerThread<float, float> { static constexpr int value = 2; static constexpr bool unroll = true; };
+// registers and issue, keep one node per thread.  The BTRT_ROWS_* macros
+// override the counts at build time (tuning).
+#ifndef BTRT_ROWS_S32
+#define BTRT_ROWS_S32 2
+#endif
+#ifndef BTRT_UNROLL_S32
+#define BTRT_UNROLL_S32 1
+#endif
+#ifndef BTRT_ROWS_S16
+#define BTRT_ROWS_S16 1
+#endif
+#ifndef BTRT_UNROLL_S16
+#define BTRT_UNROLL_S16 0
+#endif
+template <typename Real, typename S> struct RowsPerThread {
+    static constexpr int value = BTRT_ROWS_S16;
+    static constexpr bool unroll = BTRT_UNROLL_S16 != 0;
+};
+template <> struct RowsPerThread<float, float> {
+    static constexpr int value = BTRT_ROWS_S32;
+    static constexpr bool unroll = BTRT_UNROLL_S32 != 0;
+};
 template <> struct RowsPerThread<double, double> { static constexpr int value = 4; static constexpr bool unroll = false; };
+template <> struct RowsPerThread<dw, dw> { static constexpr int value = 1; static constexpr bool unroll = false; };
 
 // Global loads of data that other SMs rewrite during a persistent launch go
 // through L2 only (L1 is not coherent across SMs); ordinary loads otherwise.
@@ -335,11 +375,11 @@ __device__ __forceinline__ T ldg(const T *ptr) {
 
 // Pull of a node on the domain boundary: periodic wrap or, for a link that
 // crosses a wall, the node's own population leaving towards it comes back as
-// direction i (half-way bounce-back, Eqs. 54-56).  Stored form in and out.
-template <typename Real, typename S, bool L2ONLY>
+// direction i (half-way bounce-back, Eqs. 54-56).  Out: d_i = f_i - w_i rs with
+// rs = phi_prev (the node's phi^{n-1}) for the local shift.
+template <typename Real, typename S, int SH, bool L2ONLY>
 __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const S *__restrict__ fin, int x,
-                                              int y, int node, Real (&d)[9]) {
-    constexpr bool kShift = Shifted<S>::value;
+                                              int y, int node, Real phi_prev, Real (&d)[9]) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         int sx = x - ex_of(i), sy = y - ey_of(i);
@@ -349,7 +389,10 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
         if (sy < 0) { if (p.hbb_y) wy = 2; else sy += p.ny; }
         if (sy >= p.ny) { if (p.hbb_y) wy = 3; else sy -= p.ny; }
         if (wx < 0 && wy < 0) {
-            d[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + sy * p.pitch + sx)));
+            const int src = sy * p.pitch + sx;
+            d[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + src)));
+            if constexpr (SH == kShiftLocal)
+                if (i != 0) d[i] = fma(wgt<Real>(i), ldg<L2ONLY>(p.phi_in + src) - phi_prev, d[i]);
         } else {
             const int o = opp_of(i);
             Real phi_w;
@@ -360,9 +403,11 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
             else
                 phi_w = wall_value(p, wx, y);
             const Real dout = Storage<S>::load(ldg<L2ONLY>(fin + (o * p.plane + node)));
-            // f_i = -f_o^+ + wall term; in stored form the two shifts add up to -2 w_i phi_ref
+            // f_i = -f_o^+ + wall term; in shifted form the two shifts add up to -2 w_i rs
+            // (for the local shift f_o^+ was stored relative to this node's own phi^{n-1} = rs)
             Real wt = wall_term(p, o, phi_w);
-            if constexpr (kShift) wt = wt - Real(2) * p.wref[i];
+            if constexpr (SH == kShiftRef) wt = wt - Real(2) * p.wref[i];
+            if constexpr (SH == kShiftLocal) wt = fma(Real(-2) * wgt<Real>(i), phi_prev, wt);
             d[i] = wt - dout;
         }
     }
@@ -383,38 +428,51 @@ __device__ __forceinline__ Real source_at(const SweepParams<Real> &p, Real xs, R
     } else return Real(0);
 }
 
-// Pull of one node's populations (stored form) and of phi^{n-1}.
-template <typename Real, typename S, bool L2ONLY>
+// Pull of one node's populations (shifted form, see collide_fold) and of phi^{n-1}.
+template <typename Real, typename S, int SH, bool L2ONLY>
 __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int y, bool x_inner, Real (&f)[9],
                                           Real &phi_prev) {
-    constexpr bool kShift = Shifted<S>::value;
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
     const int node = y * p.pitch + x;
-    phi_prev = ldg<L2ONLY>(p.phi + node);
+    phi_prev = ldg<L2ONLY>(p.phi_in + node);
     if (p.first) {
-        equilibrium<Real, kShift>(p, phi_prev, f);
+        equilibrium<Real, SH>(p, phi_prev, f);
     } else if (x_inner && y > 0 && y < p.ny - 1) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
             f[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + node - ey_of(i) * p.pitch - ex_of(i))));
+        if constexpr (SH == kShiftLocal) {
+#pragma unroll
+            for (int i = 1; i < 9; ++i)
+                f[i] = fma(wgt<Real>(i), ldg<L2ONLY>(p.phi_in + (node - ey_of(i) * p.pitch - ex_of(i))) - phi_prev,
+                           f[i]);
+        }
     } else {
-        pull_boundary<Real, S, L2ONLY>(p, fin, x, y, node, f);
+        pull_boundary<Real, S, SH, L2ONLY>(p, fin, x, y, node, phi_prev, f);
     }
+}
+
+// Shifted post-collision value d_i^+ = f_i^+ - w_i rs -> the stored form.
+template <typename Real, typename S, int SH>
+__device__ __forceinline__ S store_value(int i, Real d, Real phid) {
+    if constexpr (SH == kShiftLocal) return Storage<S>::pack(fma(-wgt<Real>(i), phid, d));
+    else return Storage<S>::pack(d);
 }
 
 // Collision and write-back of one pulled node.  Returns (phi^n - phi^{n-1})^2
 // when RESID.  A non-finite phi sets `bad` (one atomic per thread at the end).
-template <typename Real, typename S, int MODE, int SRC, bool RESID>
+template <typename Real, typename S, int SH, int MODE, int SRC, bool RESID>
 __device__ __forceinline__ double finish_node(const SweepParams<Real> &p, int x, int y, Real xs, Real xc,
                                               Real (&f)[9], Real phi_prev, bool &bad) {
-    constexpr bool kShift = Shifted<S>::value;
     S *__restrict__ fout = static_cast<S *>(p.fout);
     const int node = y * p.pitch + x;
     const Real src = source_at<Real, SRC>(p, xs, xc, y, node);
-    const Real phi = collide_fold<Real, MODE, SRC, kShift>(p, f, phi_prev, src, p.first != 0, node);
+    const Real rs = SH == kShiftLocal ? phi_prev : p.phi_ref;
+    Real phid;
+    const Real phi = collide_fold<Real, MODE, SRC, SH>(p, f, rs, phi_prev, src, p.first != 0, node, phid);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fout[i * p.plane + node] = Storage<S>::pack(f[i]);
-    p.phi[node] = phi;
+    for (int i = 0; i < 9; ++i) fout[i * p.plane + node] = store_value<Real, S, SH>(i, f[i], phid);
+    p.phi_out[node] = phi;
     bad |= not_finite(phi);
     if (RESID) {
         const double dd = static_cast<double>(phi) - static_cast<double>(phi_prev);
@@ -429,7 +487,8 @@ __device__ __forceinline__ double finish_node(const SweepParams<Real> &p, int x,
 // at run time.  Returns the sum of the nodes' (phi^n - phi^{n-1})^2 when RESID
 // (steady-state residual), else 0.  RESID is a template argument so that no FP64
 // arithmetic is issued (or speculated) in ordinary sweeps.
-template <typename Real, typename S, int MODE, int SRC, bool L2ONLY, bool RESID, int NR = 0, bool UNROLL = false>
+template <typename Real, typename S, int SH, int MODE, int SRC, bool L2ONLY, bool RESID, int NR = 0,
+          bool UNROLL = false>
 __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, int ybase, int ystride,
                                              int nrows) {
     Real xs = Real(0), xc = Real(0);
@@ -442,12 +501,13 @@ __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, 
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const int y = ybase + r * ystride;
-            if (y < p.ny) pull_node<Real, S, L2ONLY>(p, x, y, x_inner, f[r], phi_prev[r]);
+            if (y < p.ny) pull_node<Real, S, SH, L2ONLY>(p, x, y, x_inner, f[r], phi_prev[r]);
         }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const int y = ybase + r * ystride;
-            if (y < p.ny) resid += finish_node<Real, S, MODE, SRC, RESID>(p, x, y, xs, xc, f[r], phi_prev[r], bad);
+            if (y < p.ny)
+                resid += finish_node<Real, S, SH, MODE, SRC, RESID>(p, x, y, xs, xc, f[r], phi_prev[r], bad);
         }
     } else {
         const int n = NR > 0 ? NR : nrows;
@@ -456,8 +516,8 @@ __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, 
             const int y = ybase + r * ystride;
             if (y >= p.ny) break;
             Real f[9], phi_prev;
-            pull_node<Real, S, L2ONLY>(p, x, y, x_inner, f, phi_prev);
-            resid += finish_node<Real, S, MODE, SRC, RESID>(p, x, y, xs, xc, f, phi_prev, bad);
+            pull_node<Real, S, SH, L2ONLY>(p, x, y, x_inner, f, phi_prev);
+            resid += finish_node<Real, S, SH, MODE, SRC, RESID>(p, x, y, xs, xc, f, phi_prev, bad);
         }
     }
     if (bad) atomicOr(p.flags, 1);
@@ -466,20 +526,20 @@ __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, 
 
 // One sweep of one lattice: 32 x 8 threads per block, each thread sweeps
 // RowsPerThread nodes of its column, rows blockDim.y apart.
-template <typename Real, typename S, int MODE, int SRC>
+template <typename Real, typename S, int SH, int MODE, int SRC>
 __global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams<Real> p) {
     constexpr int R = RowsPerThread<Real, S>::value;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int ybase = blockIdx.y * blockDim.y * R + threadIdx.y;
     constexpr bool U = RowsPerThread<Real, S>::unroll;
     if (!p.resid_partials) {
-        if (x < p.nx) sweep_rows<Real, S, MODE, SRC, false, false, R, U>(p, x, ybase, blockDim.y, R);
+        if (x < p.nx) sweep_rows<Real, S, SH, MODE, SRC, false, false, R, U>(p, x, ybase, blockDim.y, R);
         return;
     }
     // residual step: every thread joins the fixed-order block reduction
     __shared__ double red[256];
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    red[tid] = x < p.nx ? sweep_rows<Real, S, MODE, SRC, false, true, R, U>(p, x, ybase, blockDim.y, R) : 0.0;
+    red[tid] = x < p.nx ? sweep_rows<Real, S, SH, MODE, SRC, false, true, R, U>(p, x, ybase, blockDim.y, R) : 0.0;
     __syncthreads();
     for (int s = 128; s > 0; s >>= 1) {
         if (tid < s) red[tid] += red[tid + s];

@@ -9,7 +9,8 @@
 // writes the post-collision populations into an output tile that one 3-D TMA
 // store sends back to global memory (clipped at the grid edge).  Nodes on the
 // domain boundary take the ordinary global-memory path with periodic wrap or
-// bounce-back.  Every mbarrier wait is bounded; on expiry the block raises flag
+// bounce-back.  With the local storage shift the neighbours' phi^{n-1} values
+// come through L1 from the previous phi plane.  Every mbarrier wait is bounded; on expiry the block raises flag
 // bit 2, waits (bounded) for its own copies and returns.
 #pragma once
 
@@ -81,13 +82,12 @@ __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wa
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
-template <typename S, int MODE, int SRC>
+template <typename S, int SH, int MODE, int SRC>
 __global__ void __launch_bounds__(256) sweep_tma_kernel(const __grid_constant__ SweepParams<float> p,
                                                         const __grid_constant__ CUtensorMap in_map,
                                                         const __grid_constant__ CUtensorMap out_map, int ntx,
                                                         int ntiles, uint32_t wait_limit) {
     using G = TmaGeom<S>;
-    constexpr bool kShift = Shifted<S>::value;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     // TMA destinations and sources start on 128-byte boundaries
     unsigned char *smem = smem_raw + ((128u - (smem_addr(smem_raw) & 127u)) & 127u);
@@ -151,20 +151,27 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(const __grid_constant__ 
             if (x >= p.nx || y >= p.ny) continue;
             const int node = y * p.pitch + x;
             float f[9];
-            const float phi_prev = p.phi[node];
+            const float phi_prev = p.phi_in[node];
             if (x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1) {
                 const S *base = tin + (ly + 1) * G::BX + (lx + G::PAD);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[i] = Storage<S>::load(base[i * G::BY * G::BX - ey_of(i) * G::BX - ex_of(i)]);
+                if constexpr (SH == kShiftLocal) {
+#pragma unroll
+                    for (int i = 1; i < 9; ++i)
+                        f[i] = fma(wgt<float>(i), p.phi_in[node - ey_of(i) * p.pitch - ex_of(i)] - phi_prev, f[i]);
+                }
             } else {
-                pull_boundary<float, S, false>(p, fin, x, y, node, f);
+                pull_boundary<float, S, SH, false>(p, fin, x, y, node, phi_prev, f);
             }
             const float src = source_at<float, SRC>(p, xs, xc, y, node);
-            const float phi = collide_fold<float, MODE, SRC, kShift>(p, f, phi_prev, src, false, node);
+            const float rs = SH == kShiftLocal ? phi_prev : p.phi_ref;
+            float phid;
+            const float phi = collide_fold<float, MODE, SRC, SH>(p, f, rs, phi_prev, src, false, node, phid);
             S *o = out_tile + ly * G::TX + lx;
 #pragma unroll
-            for (int i = 0; i < 9; ++i) o[i * G::TY * G::TX] = Storage<S>::pack(f[i]);
-            p.phi[node] = phi;
+            for (int i = 0; i < 9; ++i) o[i * G::TY * G::TX] = store_value<float, S, SH>(i, f[i], phid);
+            p.phi_out[node] = phi;
             if (not_finite(phi)) atomicOr(p.flags, 1);
         }
         fence_proxy_async_smem();

@@ -18,7 +18,7 @@ _SRC = {"none": C.SRC_NONE, "const": C.SRC_CONST, "trig": C.SRC_TRIG, "field": C
 
 
 def grid_desc(nx, ny, dx, dt, bc=(0, 0, 0, 0), compute="f64", storage="f64",
-              x0=0.0, y0=0.0, phi_ref=0.0, fields=0) -> C.GridDesc:
+              x0=0.0, y0=0.0, phi_ref=0.0, fields=0, shift="ref") -> C.GridDesc:
     g = C.GridDesc()
     g.nx, g.ny = int(nx), int(ny)
     for k in range(4):
@@ -26,6 +26,7 @@ def grid_desc(nx, ny, dx, dt, bc=(0, 0, 0, 0), compute="f64", storage="f64",
     g.compute, g.storage = C.FORMATS[compute], C.FORMATS[storage]
     g.dx, g.dt, g.x0, g.y0, g.phi_ref = float(dx), float(dt), float(x0), float(y0), float(phi_ref)
     g.fields = int(fields)
+    g.shift = C.SHIFTS[shift]
     return g
 
 
@@ -84,14 +85,20 @@ class Lattice:
     # ------------------------------------------------------------ construction
     @classmethod
     def from_problem(cls, p, compute="f64", storage=None, device=None, stream=None,
-                     phi_ref=None) -> "Lattice":
+                     phi_ref=None, shift="auto") -> "Lattice":
+        """shift: stored form of F32/F16/BF16 populations -- "ref" (f - w_i phi_ref),
+        "local" (f^+ - w_i phi of the writing node) or "auto" (local for the 16-bit
+        formats, whose rounding it keeps well below the discretisation error; ref
+        for FP32 storage)."""
         storage = storage or compute
+        if shift == "auto":
+            shift = "local" if storage in ("f16", "bf16") else "ref"
         src_field = getattr(p, "src_field", None)
         A_field = getattr(p, "A_field", None)
         fields = (C.FIELD_SOURCE if src_field is not None else 0) | \
                  (C.FIELD_DIFFUSION if A_field is not None else 0)
         desc = grid_desc(p.nx, p.ny, p.dx, p.dt, p.bc, compute, storage, p.x0, p.y0,
-                         p.phi_ref if phi_ref is None else phi_ref, fields)
+                         p.phi_ref if phi_ref is None else phi_ref, fields, shift)
         coef = coeffs(p.u, p.b2, p.c3, p.A0, p.a2, p.k0, p.k2_mode, p.k2, p.source,
                       getattr(p, "wall_lam", 0.0))
         lat = cls(desc, coef, device=device, stream=stream, defer_coeffs=True)

@@ -44,6 +44,7 @@ class Result:
 
 
 def _bytes_needed(p, compute, storage) -> int:
+    # the workspace size does not depend on the stored form
     d = grid_desc(p.nx, p.ny, p.dx, p.dt, p.bc, compute, storage, p.x0, p.y0, p.phi_ref)
     return workspace_bytes(d)
 
@@ -51,12 +52,12 @@ def _bytes_needed(p, compute, storage) -> int:
 class Server:
     def __init__(self, budget_bytes: float = 150e9, slice_steps: int = 100, max_steps: int = 20000,
                  tol: float = 1e-8, compute: str = "f32", storage: str = "f16",
-                 max_active: int = 4096, stream=None, tiles=None):
+                 max_active: int = 4096, stream=None, tiles=None, shift: str = "auto"):
         self.budget = float(budget_bytes)
         self.slice_steps = int(slice_steps)
         self.max_steps = int(max_steps)
         self.tol = float(tol)
-        self.compute, self.storage = compute, storage
+        self.compute, self.storage, self.shift = compute, storage, shift
         self.max_active = max_active
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.tiles = tiles
@@ -85,7 +86,7 @@ class Server:
                     break
                 waiting.popleft()
                 lat = Lattice.from_problem(p, compute=self.compute, storage=self.storage,
-                                           stream=self.stream)
+                                           stream=self.stream, shift=self.shift)
                 lat.init(p.phi0(), t0=p.t0)
                 used += need
                 active.append([rid, arr, time.perf_counter() - t0, lat, need, 0])
@@ -130,7 +131,8 @@ class Server:
 
 
 def serve_sequential(trace, slice_steps: int = 100, max_steps: int = 20000, tol: float = 1e-8,
-                     compute: str = "f32", storage: str = "f16", stream=None) -> List[Result]:
+                     compute: str = "f32", storage: str = "f16", stream=None,
+                     shift: str = "auto") -> List[Result]:
     """Plain baseline: one request at a time in arrival order, plain per-step
     launches, the same residual check every slice_steps steps."""
     stream = stream if stream is not None else torch.cuda.current_stream()
@@ -141,7 +143,7 @@ def serve_sequential(trace, slice_steps: int = 100, max_steps: int = 20000, tol:
         if now < arr:
             time.sleep(arr - now)
         adm = time.perf_counter() - t0
-        lat = Lattice.from_problem(p, compute=compute, storage=storage, stream=stream)
+        lat = Lattice.from_problem(p, compute=compute, storage=storage, stream=stream, shift=shift)
         lat.init(p.phi0(), t0=p.t0)
         steps, r = 0, float("inf")
         while True:

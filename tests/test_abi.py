@@ -60,7 +60,8 @@ def test_workspace_layout(lib):
     n = lib.btrt_workspace_bytes(ctypes.byref(d))
     pitch = 64
     fbuf = 9 * pitch * 48 * 8
-    assert n >= 2 * fbuf + pitch * 48 * 8
+    # two population buffers and two phi planes (double-buffered together)
+    assert n >= 2 * fbuf + 2 * pitch * 48 * 8
     assert n % 256 == 0
     d16 = _desc(compute="f32", storage="f16")
     n16 = lib.btrt_workspace_bytes(ctypes.byref(d16))
@@ -75,6 +76,15 @@ def test_invalid_descriptions_rejected(lib, kw):
     d = _desc(**kw)
     assert lib.btrt_workspace_bytes(ctypes.byref(d)) == 0
     assert len(lib.btrt_last_error()) > 0
+
+
+def test_unknown_storage_shift_rejected(lib):
+    d = _desc(compute="f32", storage="f16")
+    d.shift = 2
+    assert lib.btrt_workspace_bytes(ctypes.byref(d)) == 0
+    assert b"shift" in lib.btrt_last_error()
+    d.shift = 1
+    assert lib.btrt_workspace_bytes(ctypes.byref(d)) > 0
 
 
 def test_create_rejects_null_workspace(lib):

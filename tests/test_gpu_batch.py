@@ -21,21 +21,24 @@ def _mix(compute="f32", storage="f16", count=10, seed=3):
     return probs
 
 
-def _make(p, compute, storage):
+def _make(p, compute, storage, shift="ref"):
     import torch
     from paper_1902_09813_gb300 import Lattice
-    lat = Lattice.from_problem(p, compute=compute, storage=storage, stream=torch.cuda.current_stream())
+    lat = Lattice.from_problem(p, compute=compute, storage=storage, stream=torch.cuda.current_stream(),
+                               shift=shift)
     lat.init(p.phi0(), t0=p.t0)
     return lat
 
 
-@pytest.mark.parametrize("compute,storage", [("f32", "f16"), ("f32", "f32"), ("f32", "bf16"), ("f64", "f64")])
-def test_alone_equals_in_mix_bitwise(compute, storage):
+@pytest.mark.parametrize("compute,storage,shift", [("f32", "f16", "ref"), ("f32", "f32", "ref"),
+                                                  ("f32", "bf16", "ref"), ("f64", "f64", "ref"),
+                                                  ("f32", "f16", "local"), ("f32", "bf16", "local")])
+def test_alone_equals_in_mix_bitwise(compute, storage, shift):
     from paper_1902_09813_gb300 import Batch
     probs = _mix(compute, storage)
     steps = 17
-    alone = [_make(p, compute, storage).step(steps) for p in probs]
-    mixed = [_make(p, compute, storage) for p in probs]
+    alone = [_make(p, compute, storage, shift).step(steps) for p in probs]
+    mixed = [_make(p, compute, storage, shift) for p in probs]
     b = Batch(mixed)
     b.step(5).step(12)
     b.set_tiles(32, 8, 2, 1).step(3)
