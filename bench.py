@@ -236,6 +236,8 @@ def run_gpu(args):
     torch.cuda.empty_cache()
     if not args.no_variants:
         extra["variants"] = run_variants(args)
+    if not args.no_accuracy:
+        extra["accuracy"] = run_accuracy(args)
     if not args.no_batched:
         torch.cuda.empty_cache()
         extra["batched"] = run_batched(args)
@@ -317,6 +319,54 @@ def run_variants(args, steps=200, warmup=5):
         out[f"nonlinear_f32_{st}_tma"] = _time_single(q, phi0, "f32", st, steps, warmup, variant="tma")
         out[f"nonlinear_f32_{st}_local"] = _time_single(q, phi0, "f32", st, steps, warmup, shift="local")
     out["nonlinear_f64"] = _time_single(q, phi0, "f64", "f64", 50, 3)
+    return out
+
+
+# ---------------------------------------------------------------------------- accuracy
+def _final_phi(p, phi0, compute, storage, steps, shift="ref"):
+    import torch
+    from paper_1902_09813_gb300 import Lattice
+    lat = Lattice.from_problem(p, compute=compute, storage=storage, shift=shift)
+    lat.init(phi0, t0=p.t0).step(steps)
+    out = lat.phi_host()
+    lat.check()
+    del lat
+    torch.cuda.empty_cache()
+    return out
+
+
+REDUCED = [("df64", "df64", "ref"), ("f32", "f32", "ref"), ("f32", "f32", "local"), ("f32", "f16", "ref"),
+           ("f32", "f16", "local"), ("f32", "bf16", "ref"), ("f32", "bf16", "local")]
+
+
+def run_accuracy(args):
+    """Error of each reduced-precision path: relative L2 against the FP64 sweep on
+    the nonlinear 16-mode workload (2048^2, 1000 steps; the FP64 sweep matches the
+    FP64 oracle to 1e-11 in the parity tests), and the discretisation error (GRE)
+    against the closed forms of the Gaussian hill (64^2, 500 steps) and the
+    manufactured solution (128^2) next to the FP64 sweep's."""
+    import workloads as w
+
+    def key(c, s, sh):
+        return c if c == "df64" else f"{c}_{s}_{sh}"
+
+    out = {"reference": "FP64 sweep (= FP64 oracle to 1e-11)"}
+    q = w.nonlinear_modes(n=2048, nsteps=1000)
+    phi0 = q.phi0()
+    q.phi_ref = float(phi0.mean())
+    ref = _final_phi(q, phi0, "f64", "f64", 1000)
+    out["nonlinear_2048_1000_rel_l2"] = {key(c, s, sh): float(f"{w.rel_l2(_final_phi(q, phi0, c, s, 1000, sh), ref):.3e}")
+                                         for c, s, sh in REDUCED}
+    closed = {"hill_64": (w.gaussian_hill(), lambda p: w.gaussian_hill_exact(p, p.nsteps * p.dt)),
+              "mms_128": (w.mms_sinsin(n=128), lambda p: w.mms_sinsin_exact(p, p.t0 + p.nsteps * p.dt))}
+    for name, (p, exact) in closed.items():
+        phi0 = p.phi0()
+        p.phi_ref = float(phi0.mean())
+        ex = exact(p)
+        g = {"f64": float(f"{w.gre(_final_phi(p, phi0, 'f64', 'f64', p.nsteps), ex):.4e}")}
+        for c, s, sh in REDUCED:
+            g[key(c, s, sh)] = float(f"{w.gre(_final_phi(p, phi0, c, s, p.nsteps, sh), ex):.4e}")
+        out[f"{name}_gre"] = g
     return out
 
 
@@ -496,6 +546,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--serve-seq", type=int, default=48)
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched persistent launch (for profiling small batches)")

@@ -5,9 +5,11 @@
  *
  * The equation solved is
  *     d_t phi + div B(phi) = div( A(phi) grad C(phi) ) + S(x, t)            (Eq. 1, Eq. 29)
- * with B(phi) = u phi + b2 (phi^2/2)(1,1), C(phi) = phi + c3 phi^3 (the paper's
- * D = C I), A(phi) = (1 + a2 phi^2) A0, and S = 0, a constant, or a separable
- * trigonometric field exp(lam t) sum_pq alpha_pq X_p(k x) Y_q(k y).
+ * with B(phi) = u phi + b2 (phi^q/q) d (q = 2 and d = (1,1) by default),
+ * C(phi) = phi + c3 phi^3 (the paper's D = C I), A(phi) = (1 + a2 phi^2) A0, and
+ * S = 0, a constant, a separable trigonometric field exp(lam t) sum_pq
+ * alpha_pq X_p(k x) Y_q(k y), a per-node field exp(lam t) F(x), or the reaction
+ * term rate phi (1 - phi^exp) of the Burgers-Fisher equation (Eq. 67).
  *
  * One time step is one fused sweep (stream + collide, Eq. 38 with Eq. 6):
  * pull the nine populations, take phi, evaluate B, C, A, build the first-order
@@ -56,7 +58,7 @@ enum { BTRT_BC_PERIODIC = 0, BTRT_BC_HBB = 1 };                 /* boundary kind
  * the unevaluated sum of two FP32 numbers, ~48 significant bits) */
 enum { BTRT_F64 = 0, BTRT_F32 = 1, BTRT_F16 = 2, BTRT_BF16 = 3, BTRT_DF64 = 4 };
 enum { BTRT_K2_HBB = 0, BTRT_K2_CONST = 1 };                    /* second-order block */
-enum { BTRT_SRC_NONE = 0, BTRT_SRC_CONST = 1, BTRT_SRC_TRIG = 2, BTRT_SRC_FIELD = 3 };
+enum { BTRT_SRC_NONE = 0, BTRT_SRC_CONST = 1, BTRT_SRC_TRIG = 2, BTRT_SRC_FIELD = 3, BTRT_SRC_REACTION = 4 };
 enum { BTRT_FIELD_SOURCE = 1, BTRT_FIELD_DIFFUSION = 2 };      /* btrt_grid_desc.fields bits */
 enum { BTRT_SIDE_XMIN = 0, BTRT_SIDE_XMAX = 1, BTRT_SIDE_YMIN = 2, BTRT_SIDE_YMAX = 3 };
 /* Stored form of F32/F16/BF16 populations (btrt_grid_desc.shift):
@@ -87,7 +89,7 @@ typedef struct {
 
 /* Coefficients of Eq. 1 and the relaxation parameters (physical units). */
 typedef struct {
-    double u[2];           /* B(phi) = u phi + b2 (phi^2/2)(1,1)                 */
+    double u[2];           /* B(phi) = u phi + b2 (phi^q / q) (d_x, d_y)         */
     double b2;
     double c3;             /* C(phi) = phi + c3 phi^3                             */
     double A0[3];          /* A(phi) = (1 + a2 phi^2) A0; A0 = {xx, xy, yy}, SPD  */
@@ -101,6 +103,14 @@ typedef struct {
                               BTRT_SRC_FIELD: S = exp(lam t) F(x) (btrt_set_source_field) */
     double src_alpha[4];   /*   {ss, sc, cs, cc}: X_s = sin(k x), X_c = cos(k x)  */
     double wall_lam;       /* wall values carry the factor exp(wall_lam t)        */
+    double b_dir[2];       /* d of the power-law flux term; {0, 0} selects (1, 1) */
+    double b_q;            /* its exponent q >= 1 (0 selects 2); for q != 2 the power
+                              is taken of max(phi, 0)                              */
+    double react_rate;     /* BTRT_SRC_REACTION: S = react_rate phi (1 - phi^react_exp),
+                              with the same scheme-2 time derivative as the other
+                              sources, S^{n-1} taken at phi^{n-1}                 */
+    double react_exp;      /*   > 0; for an exponent other than 2 the power is taken
+                              of max(phi, 0)                                       */
 } btrt_coeffs;
 
 /* Bytes of device workspace a lattice with this description needs.  Returns 0

@@ -30,7 +30,7 @@ NQ = 9
 
 _BC = {0: 0, 1: 1}
 _K2 = {"hbb": 0, "const": 1}
-_SRC_KIND = {"none": 0, "const": 1, "trig": 2, "field": 3}
+_SRC_KIND = {"none": 0, "const": 1, "trig": 2, "field": 3, "reaction": 4}
 
 
 def build(force: bool = False) -> Path:
@@ -68,6 +68,8 @@ class _Problem(ctypes.Structure):
         ("wall_arr", ctypes.c_void_p * 4),
         ("src_field", ctypes.c_void_p),
         ("A_field", ctypes.c_void_p * 3),
+        ("b_dir", ctypes.c_double * 2), ("b_q", ctypes.c_double),
+        ("react_rate", ctypes.c_double), ("react_exp", ctypes.c_double),
     ]
 
 
@@ -93,7 +95,7 @@ def lib():
         L.btrt_oracle_k2_from_k1.restype = d
         L.btrt_oracle_k2.argtypes = [P, dp]
         L.btrt_oracle_k2.restype = d
-        L.btrt_oracle_source.argtypes = [P, d, d, d]
+        L.btrt_oracle_source.argtypes = [P, d, d, d, d]
         L.btrt_oracle_source.restype = d
         L.btrt_oracle_feq.argtypes = [P, d, dp]
         L.btrt_oracle_relax.argtypes = [d, dp, dp, d, dp, dp]
@@ -130,6 +132,9 @@ def make_problem(p) -> tuple:
     src = p.source
     s.src_kind = _SRC_KIND[src.kind]
     s.src_const, s.src_lam, s.src_k = src.const, src.lam, src.k
+    s.react_rate, s.react_exp = src.const, getattr(src, "exp", 1.0)
+    s.b_dir[0], s.b_dir[1] = getattr(p, "b_dir", (1.0, 1.0))
+    s.b_q = getattr(p, "b_q", 2.0)
     for k in range(4):
         s.src_alpha[k] = src.alpha[k]
         s.wall[k] = p.wall[k]
@@ -170,6 +175,14 @@ class OracleLattice:
         self.step_index = 0
         self.t0 = problem.t0
         del n
+        # walls re-evaluated every step (time-dependent Dirichlet data): the C
+        # struct points at these arrays, refilled before each step
+        self._walls = None
+        if getattr(problem, "wall_fn", None) is not None:
+            self._walls = [np.array(a, dtype=np.float64) for a in problem.wall_arrays_at(problem.t0)]
+            for k, a in enumerate(self._walls):
+                self.s.wall_arr[k] = a.ctypes.data
+            self.s.wall_lam = 0.0
 
     def init(self, phi0=None):
         if phi0 is None:
@@ -184,9 +197,18 @@ class OracleLattice:
         return self.t0 + self.step_index * self.problem.dt
 
     def step(self, nsteps: int = 1):
-        lib().btrt_oracle_run(ctypes.byref(self.s), _ptr(self.f), _ptr(self.fpost),
-                              _ptr(self.phi_prev), self.t0, self.step_index, nsteps, self.nthreads)
-        self.step_index += nsteps
+        if self._walls is None:
+            lib().btrt_oracle_run(ctypes.byref(self.s), _ptr(self.f), _ptr(self.fpost),
+                                  _ptr(self.phi_prev), self.t0, self.step_index, nsteps, self.nthreads)
+            self.step_index += nsteps
+            return self
+        for _ in range(nsteps):
+            # the wall value of the step from t_n to t_{n+1} is taken at t_{n+1}
+            for a, v in zip(self._walls, self.problem.wall_arrays_at(self.t + self.problem.dt)):
+                a[:] = v
+            lib().btrt_oracle_run(ctypes.byref(self.s), _ptr(self.f), _ptr(self.fpost),
+                                  _ptr(self.phi_prev), self.t0, self.step_index, 1, self.nthreads)
+            self.step_index += 1
         return self
 
     def phi(self) -> np.ndarray:
@@ -246,9 +268,9 @@ def C(problem, phi: float) -> float:
     return lib().btrt_oracle_C(ctypes.byref(s), phi)
 
 
-def source(problem, x: float, y: float, t: float) -> float:
+def source(problem, x: float, y: float, t: float, phi: float = 0.0) -> float:
     s, keep = make_problem(problem)
-    return lib().btrt_oracle_source(ctypes.byref(s), x, y, t)
+    return lib().btrt_oracle_source(ctypes.byref(s), x, y, t, phi)
 
 
 def node_step(problem, win, ix: int, iy: int, phi_prev: float, t_next: float):

@@ -65,13 +65,13 @@ static int opposite(int i)
 
 enum { BC_PERIODIC = 0, BC_HBB = 1 };
 enum { K2_HBB = 0, K2_CONST = 1 };
-enum { SRC_NONE = 0, SRC_CONST = 1, SRC_TRIG = 2, SRC_FIELD = 3 };
+enum { SRC_NONE = 0, SRC_CONST = 1, SRC_TRIG = 2, SRC_FIELD = 3, SRC_REACTION = 4 };
 
 typedef struct {
     int32_t nx, ny;
     int32_t bc[4];            /* sides x-, x+, y-, y+ */
     double dx, dt, x0, y0;
-    double u[2], b2;          /* B(phi) = u phi + b2 phi^2/2 (1,1) */
+    double u[2], b2;          /* B(phi) = u phi + b2 (phi^q / q) (d_x, d_y) */
     double c3;                /* C(phi) = phi + c3 phi^3           */
     double A0[3], a2;         /* A(phi) = (1 + a2 phi^2) A0, (xx, xy, yy) */
     double k0;
@@ -85,6 +85,9 @@ typedef struct {
     const double *wall_arr[4];/* optional per-node wall values (NULL: constant) */
     const double *src_field;  /* SRC_FIELD: S = exp(src_lam t) src_field[node] */
     const double *A_field[3]; /* optional per-node diffusion tensor (xx, xy, yy): A = (1 + a2 phi^2) A(x) */
+    double b_dir[2];          /* direction (d_x, d_y) of the power-law flux term */
+    double b_q;               /* its exponent q (2: the quadratic family)      */
+    double react_rate, react_exp; /* SRC_REACTION: S = rate phi (1 - phi^exp)  */
 } oracle_problem;
 
 /* ---------------------------------------------------------------- coefficients */
@@ -98,10 +101,23 @@ static long node_of(const oracle_problem *p, double x, double y)
 }
 
 
+/* phi^q; for q != 2 the power is taken of max(phi, 0): the power-law terms of
+ * Eq. 67 are defined for phi >= 0 and an undershoot below 0 next to a steep
+ * front would otherwise give a non-finite value. */
+static double phi_pow(double phi, double q)
+{
+    if (q == 2.0) return phi * phi;
+    return pow(phi > 0.0 ? phi : 0.0, q);
+}
+
+/* Eq. 1 flux family: B(phi) = u phi + b2 (phi^q / q) (d_x, d_y); q = 2 with
+ * d = (1, 1) is the quadratic flux of the nonlinear tests, q = delta + 1 with
+ * d = (1, 0) the Burgers-Fisher flux of Eq. 67 in conservative form. */
 void btrt_oracle_B(const oracle_problem *p, double phi, double B[2])
 {
-    B[0] = p->u[0] * phi + p->b2 * 0.5 * phi * phi;
-    B[1] = p->u[1] * phi + p->b2 * 0.5 * phi * phi;
+    double g = phi_pow(phi, p->b_q) / p->b_q;
+    B[0] = p->u[0] * phi + p->b2 * p->b_dir[0] * g;
+    B[1] = p->u[1] * phi + p->b2 * p->b_dir[1] * g;
 }
 
 double btrt_oracle_C(const oracle_problem *p, double phi)
@@ -181,10 +197,12 @@ double btrt_oracle_k2(const oracle_problem *p, const double K1[4])
     return btrt_oracle_k2_from_k1(2.0 / tr_inv);
 }
 
-double btrt_oracle_source(const oracle_problem *p, double x, double y, double t)
+/* S(x, t, phi); the reaction kind is the logistic-type term of Eq. 67. */
+double btrt_oracle_source(const oracle_problem *p, double x, double y, double t, double phi)
 {
     if (p->src_kind == SRC_NONE) return 0.0;
     if (p->src_kind == SRC_CONST) return p->src_const;
+    if (p->src_kind == SRC_REACTION) return p->react_rate * phi * (1.0 - phi_pow(phi, p->react_exp));
     if (p->src_kind == SRC_FIELD) return exp(p->src_lam * t) * p->src_field[node_of(p, x, y)];
     double sx = sin(p->src_k * x), cx = cos(p->src_k * x);
     double sy = sin(p->src_k * y), cy = cos(p->src_k * y);
@@ -295,8 +313,8 @@ void btrt_oracle_collide(const oracle_problem *p, const double f[NQ], double phi
         for (int b = 0; b < 2; ++b) Gv[a] += (((a == b) ? 1.0 : 0.0) - 0.5 * K1[2 * a + b]) * dtB[b];
     }
 
-    double S = btrt_oracle_source(p, x, y, t);
-    double Sprev = btrt_oracle_source(p, x, y, t_prev);
+    double S = btrt_oracle_source(p, x, y, t, phi);
+    double Sprev = btrt_oracle_source(p, x, y, t_prev, phi_prev);
 
     for (int i = 0; i < NQ; ++i) {
         double ci[2] = {c * EX[i], c * EY[i]};

@@ -10,7 +10,7 @@ OK, EINVAL, ENOMEM, ECUDA, EUNSTABLE, ETIMEOUT, ESTATE = 0, -1, -2, -3, -4, -5, 
 BC_PERIODIC, BC_HBB = 0, 1
 F64, F32, F16, BF16, DF64 = 0, 1, 2, 3, 4
 K2_HBB, K2_CONST = 0, 1
-SRC_NONE, SRC_CONST, SRC_TRIG, SRC_FIELD = 0, 1, 2, 3
+SRC_NONE, SRC_CONST, SRC_TRIG, SRC_FIELD, SRC_REACTION = 0, 1, 2, 3, 4
 FIELD_SOURCE, FIELD_DIFFUSION = 1, 2
 SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA = 0, 1, 2
 SHIFT_REF, SHIFT_LOCAL = 0, 1
@@ -39,6 +39,8 @@ class Coeffs(ctypes.Structure):
         ("k2", ctypes.c_double), ("src_const", ctypes.c_double),
         ("src_lam", ctypes.c_double), ("src_k", ctypes.c_double),
         ("src_alpha", ctypes.c_double * 4), ("wall_lam", ctypes.c_double),
+        ("b_dir", ctypes.c_double * 2), ("b_q", ctypes.c_double),
+        ("react_rate", ctypes.c_double), ("react_exp", ctypes.c_double),
     ]
 
 

@@ -234,6 +234,8 @@ void btrt::step_scalars(btrt_lattice L, int64_t n, bool first, double *src_val, 
     *wall_fac = c.wall_lam == 0.0 ? 1.0 : std::exp(c.wall_lam * tn);
     if (c.src_kind == BTRT_SRC_CONST) {
         *src_val = c.src_const * g.dt;
+    } else if (c.src_kind == BTRT_SRC_REACTION) {
+        *src_val = g.dt;   // times (3 S(phi^n) - S(phi^{n-1})) / 2, evaluated per node
     } else if (c.src_kind == BTRT_SRC_TRIG || c.src_kind == BTRT_SRC_FIELD) {
         // dt S_i + dt^2/2 (S_i^n - S_i^{n-1})/dt = w_i dt (3 S^n - S^{n-1}) / 2 (scheme 2)
         const double Tn = std::exp(c.src_lam * tn);
@@ -272,6 +274,13 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
     p.ux = (Real)L->ux;
     p.uy = (Real)L->uy;
     p.b2 = (Real)L->b2;
+    p.bgx = (Real)L->bgx;
+    p.bgy = (Real)L->bgy;
+    p.bq = (Real)L->bq;
+    p.bq2 = L->bq == 2.0 ? 1 : 0;
+    p.react_rate = (Real)c.react_rate;
+    p.react_exp = (Real)c.react_exp;
+    p.react2 = c.react_exp == 2.0 ? 1 : 0;
     p.c3 = (Real)c.c3;
     p.A0xx = (Real)L->A0[0];
     p.A0xy = (Real)L->A0[1];
@@ -322,7 +331,6 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
         q.k6x3 = (Real)(-w1 * kap / 2.0);
         q.kd = (Real)(-2.0 * w5 * kap / 3.0);
         q.kdx3 = (Real)(-2.0 * w5 * kap);
-        q.b2h = (Real)(0.5 * L->b2);
         q.a2x3 = (Real)(3.0 * c.a2);
     }
     // the reference value of kShiftRef storage (zero otherwise)
@@ -578,8 +586,14 @@ btrt_status btrt_set_coeffs(btrt_lattice L, const btrt_coeffs *c) {
         return fail(BTRT_EINVAL, "unknown k2 mode %d", c->k2_mode);
     if (c->k2_mode == BTRT_K2_CONST && !(c->k2 > 0.0 && c->k2 < 2.0))
         return fail(BTRT_EINVAL, "k2 = %g outside (0, 2)", c->k2);
-    if (c->src_kind < BTRT_SRC_NONE || c->src_kind > BTRT_SRC_FIELD)
+    if (c->src_kind < BTRT_SRC_NONE || c->src_kind > BTRT_SRC_REACTION)
         return fail(BTRT_EINVAL, "unknown source kind %d", c->src_kind);
+    if (c->src_kind == BTRT_SRC_REACTION && (!std::isfinite(c->react_rate) || !(c->react_exp > 0.0)))
+        return fail(BTRT_EINVAL, "reaction source needs a finite rate and an exponent > 0");
+    if (!(c->b_q == 0.0 || (c->b_q >= 1.0 && std::isfinite(c->b_q))))
+        return fail(BTRT_EINVAL, "flux exponent b_q = %g: must be 0 (default 2) or >= 1", c->b_q);
+    if (!std::isfinite(c->b_dir[0]) || !std::isfinite(c->b_dir[1]))
+        return fail(BTRT_EINVAL, "non-finite flux direction");
     if (c->src_kind == BTRT_SRC_FIELD && !(g.fields & BTRT_FIELD_SOURCE))
         return fail(BTRT_EINVAL, "BTRT_SRC_FIELD needs BTRT_FIELD_SOURCE in the grid description");
     if (!std::isfinite(c->a2) || c->a2 < 0.0) return fail(BTRT_EINVAL, "a2 must be >= 0");
@@ -588,6 +602,12 @@ btrt_status btrt_set_coeffs(btrt_lattice L, const btrt_coeffs *c) {
     L->ux = c->u[0] / cl;
     L->uy = c->u[1] / cl;
     L->b2 = c->b2 / cl;
+    // power-law flux b2 (phi^q / q) d -> bg phi^q in lattice units
+    const double q = c->b_q == 0.0 ? 2.0 : c->b_q;
+    const bool dflt = c->b_dir[0] == 0.0 && c->b_dir[1] == 0.0;
+    L->bq = q;
+    L->bgx = L->b2 * (dflt ? 1.0 : c->b_dir[0]) / q;
+    L->bgy = L->b2 * (dflt ? 1.0 : c->b_dir[1]) / q;
     const double sA = g.dt / (g.dx * g.dx);
     L->A0[0] = axx * sA;
     L->A0[1] = axy * sA;

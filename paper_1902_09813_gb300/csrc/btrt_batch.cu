@@ -123,11 +123,11 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int 
     if (x < sp.nx) {
         const int y0 = tile.z + threadIdx.y;
         if (M.mode == kGeneral) {
-            if (resid) r = sweep_rows<Real, S, SH, kGeneral, 4, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
-            else sweep_rows<Real, S, SH, kGeneral, 4, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+            if (resid) r = sweep_rows<Real, S, SH, kGeneral, kSrcRuntime, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, SH, kGeneral, kSrcRuntime, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
         } else {
-            if (resid) r = sweep_rows<Real, S, SH, kLinear, 4, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
-            else sweep_rows<Real, S, SH, kLinear, 4, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+            if (resid) r = sweep_rows<Real, S, SH, kLinear, kSrcRuntime, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, SH, kLinear, kSrcRuntime, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
         }
     }
     if (resid) {

@@ -45,6 +45,7 @@ struct btrt_lattice_s {
     int batch_refs = 0;       // batches that reference this lattice
     // lattice-unit constants derived from the coefficients
     double ux = 0, uy = 0, b2 = 0, A0[3] = {0, 0, 0}, K1[3] = {0, 0, 0}, k2 = 1;
+    double bgx = 0, bgy = 0, bq = 2;   // power-law flux in lattice units: B^ += bg phi^q
     bool nonlin_A = false;
     double wall_const[4] = {0, 0, 0, 0};
     bool wall_is_arr[4] = {false, false, false, false};

@@ -31,7 +31,8 @@ static void launch_unshifted(const SweepParams<Real> &p, dim3 g, dim3 b, cudaStr
     case 0: sweep_kernel<Real, Real, kShiftNone, MODE, 0><<<g, b, 0, s>>>(p); break;
     case 1: sweep_kernel<Real, Real, kShiftNone, MODE, 1><<<g, b, 0, s>>>(p); break;
     case 2: sweep_kernel<Real, Real, kShiftNone, MODE, 2><<<g, b, 0, s>>>(p); break;
-    default: sweep_kernel<Real, Real, kShiftNone, MODE, 3><<<g, b, 0, s>>>(p); break;
+    case 3: sweep_kernel<Real, Real, kShiftNone, MODE, 3><<<g, b, 0, s>>>(p); break;
+    default: sweep_kernel<Real, Real, kShiftNone, MODE, kSrcReaction><<<g, b, 0, s>>>(p); break;
     }
 }
 

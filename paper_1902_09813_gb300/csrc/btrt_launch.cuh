@@ -18,7 +18,8 @@ inline void launch_src(const SweepParams<Real> &p, dim3 g, dim3 b, cudaStream_t 
     case 0: sweep_kernel<Real, S, SH, MODE, 0><<<g, b, 0, s>>>(p); break;
     case 1: sweep_kernel<Real, S, SH, MODE, 1><<<g, b, 0, s>>>(p); break;
     case 2: sweep_kernel<Real, S, SH, MODE, 2><<<g, b, 0, s>>>(p); break;
-    default: sweep_kernel<Real, S, SH, MODE, 3><<<g, b, 0, s>>>(p); break;
+    case 3: sweep_kernel<Real, S, SH, MODE, 3><<<g, b, 0, s>>>(p); break;
+    default: sweep_kernel<Real, S, SH, MODE, kSrcReaction><<<g, b, 0, s>>>(p); break;
     }
 }
 
@@ -74,7 +75,8 @@ cudaError_t launch_tma_mode(const SweepParams<float> &p, const CUtensorMap *in_m
     case 0: return launch_tma_src<S, SH, MODE, 0>(p, in_map, out_map, s);
     case 1: return launch_tma_src<S, SH, MODE, 1>(p, in_map, out_map, s);
     case 2: return launch_tma_src<S, SH, MODE, 2>(p, in_map, out_map, s);
-    default: return launch_tma_src<S, SH, MODE, 3>(p, in_map, out_map, s);
+    case 3: return launch_tma_src<S, SH, MODE, 3>(p, in_map, out_map, s);
+    default: return launch_tma_src<S, SH, MODE, kSrcReaction>(p, in_map, out_map, s);
     }
 }
 

@@ -66,7 +66,7 @@ struct FoldConsts {
     Real c0;               // w0 kap / 3             (constant k2)
     Real k6, k6x3;         // -w1 kap / 6, 3 k6
     Real kd, kdx3;         // -(2/3) w5 kap, 3 kd
-    Real b2h, a2x3;        // b2 / 2, 3 a2           (phi-dependent coefficients)
+    Real a2x3;             // 3 a2                   (phi-dependent coefficients)
 };
 
 // Everything one launch of the sweep needs, passed by value.
@@ -88,7 +88,10 @@ struct SweepParams {
     Real wall_fac;
 
     // coefficients in lattice units
-    Real ux, uy, b2, c3;   // B = u phi + b2 phi^2/2 (1,1); C = phi + c3 phi^3
+    Real ux, uy, b2, c3;   // B = u phi + b2 (phi^q / q) d; C = phi + c3 phi^3
+    Real bgx, bgy;         // b2 d / q: B = u phi + bg phi^q
+    Real bq;               // q
+    int bq2;               // 1: q == 2 (phi^q = phi phi)
     Real A0xx, A0xy, A0yy, a2;
     Real k0;
     int nonlin_A;          // 1: A depends on phi -> K1, k2 built per node
@@ -99,8 +102,10 @@ struct SweepParams {
     Real cond_limit;       // FP32: tr^2/det above this -> invert in FP64
 
     // source
-    int src_kind;          // 0 none, 1 const, 2 trig, 3 per-node field
-    Real src_val;          // const: S^ ; trig, field: dt (3 T_n - T_{n-1}) / 2
+    int src_kind;          // 0 none, 1 const, 2 trig, 3 per-node field, 4 reaction
+    Real src_val;          // const: S^ ; trig, field: dt (3 T_n - T_{n-1}) / 2; reaction: dt
+    Real react_rate, react_exp;   // reaction: S = rate phi (1 - phi^exp)
+    int react2;                   // 1: exp == 2 (phi^exp = phi phi)
     const Real *Xs, *Xc, *Ys, *Yc;   // trig tables: sin/cos(k x_i), alpha folded into Ys/Yc
     const Real *srcF;      // field: S(x) per node (pitched plane)
     const Real *Af;        // non-null: per-node lattice diffusion tensor, planes xx, xy, yy (`plane` apart)
@@ -147,6 +152,30 @@ __device__ __forceinline__ dw quot(dw a, dw b) { return a / b; }
 enum { kGeneral = 0, kLinear = 1, kLinearK0One = 2 };
 // Stored form of the populations (see the top of this file).
 enum { kShiftNone = 0, kShiftRef = 1, kShiftLocal = 2 };
+// Source kinds (compile-time SRC); kSrcRuntime decides per lattice at run time.
+enum { kSrcNone = 0, kSrcConst = 1, kSrcTrig = 2, kSrcField = 3, kSrcReaction = 4, kSrcRuntime = 5 };
+
+// max(x, 0)^q for the power-law flux (q != 2) and the reaction term: those
+// terms are defined for phi >= 0, and an undershoot next to a steep front must
+// not turn into a non-finite value.
+__device__ __forceinline__ float powr(float x, float q) { return powf(fmaxf(x, 0.0f), q); }
+__device__ __forceinline__ double powr(double x, double q) { return pow(fmax(x, 0.0), q); }
+__device__ __forceinline__ dw powr(dw x, dw q) {
+    return dw(pow(fmax(static_cast<double>(x), 0.0), static_cast<double>(q)));
+}
+
+// phi^q / q times q, i.e. phi^q (q == 2: one product).
+template <typename Real>
+__device__ __forceinline__ Real flux_pow(const SweepParams<Real> &p, Real phi) {
+    return p.bq2 ? phi * phi : powr(phi, p.bq);
+}
+
+// Reaction term S = rate phi (1 - phi^exp) (Eq. 67); exp == 2 takes phi phi.
+template <typename Real>
+__device__ __forceinline__ Real reaction(const SweepParams<Real> &p, Real phi) {
+    const Real pe = p.react2 ? phi * phi : powr(phi, p.react_exp);
+    return p.react_rate * phi * (Real(1) - pe);
+}
 
 // Moment-space form of Eq. 6 (Eqs. 94, 95, 99 with K2 = k2 Ihat), expanded back
 // into populations and written for shifted values d_i = f_i - w_i rs: rs = 0
@@ -202,11 +231,25 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
         kd = L.kd;
         kdx3 = L.kdx3;
     } else {
-        // coefficients at phi (Eq. 1 families); dB = (u + (b2/2)(phi + phi_prev)) dphi
-        const Real hb = L.b2h * phi * phi;
-        const Real Bx = fma(p.ux, phi, hb), By = fma(p.uy, phi, hb);
-        const Real tb = L.b2h * (phi + phi_prev);
-        const Real dBx = (p.ux + tb) * dphi, dBy = (p.uy + tb) * dphi;
+        // coefficients at phi (Eq. 1 families): B = u phi + bg phi^q and
+        // dB = B(phi) - B(phi_prev) = u dphi + bg (phi^q - phi_prev^q), for q = 2
+        // factored as bg (phi + phi_prev) dphi
+        Real Bx, By, dBx, dBy;
+        if (p.bq2) {
+            const Real p2 = phi * phi;
+            Bx = fma(p.ux, phi, p.bgx * p2);
+            By = fma(p.uy, phi, p.bgy * p2);
+            const Real sp = phi + phi_prev;
+            dBx = fma(p.bgx, sp, p.ux) * dphi;
+            dBy = fma(p.bgy, sp, p.uy) * dphi;
+        } else {
+            const Real gq = powr(phi, p.bq);
+            const Real dg = first ? Real(0) : gq - powr(phi_prev, p.bq);
+            Bx = fma(p.ux, phi, p.bgx * gq);
+            By = fma(p.uy, phi, p.bgy * gq);
+            dBx = fma(p.ux, dphi, p.bgx * dg);
+            dBy = fma(p.uy, dphi, p.bgy * dg);
+        }
         const Real Cm = p.c3 * phi * phi * phi;          // C(phi) - phi
         cmid = phid + Cm;
         cc = L.k0x15 * Cm;
@@ -258,6 +301,14 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
     }
     const Real sig = fma(cst<Real>(-2, 3), cmid, fma(Real(2), sd, a1324));
     Real a = K0ONE ? phid : L.k0 * phid;
+    if constexpr (SRC == kSrcReaction || SRC == kSrcRuntime) {
+        // phi-dependent source: (3 S(phi^n) - S(phi^{n-1})) / 2 (scheme 2), S^{-1} = S^0 at start
+        if (SRC == kSrcReaction || p.src_kind == kSrcReaction) {
+            const Real Sn = reaction(p, phi);
+            const Real Sp = first ? Sn : reaction(p, phi_prev);
+            srcv = fma(Real(1.5), Sn, Real(-0.5) * Sp);
+        }
+    }
     if constexpr (SRC != 0) a = fma(p.src_val, srcv, a);
     const Real w0 = cst<Real>(4, 9), w1 = cst<Real>(1, 9), w5 = cst<Real>(1, 36);
     Real r[9];
@@ -297,8 +348,8 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
 // w_i rs as the collision expects (rs = phi for the local shift).
 template <typename Real, int SH>
 __device__ __forceinline__ void equilibrium(const SweepParams<Real> &p, Real phi, Real (&f)[9]) {
-    const Real hb = Real(0.5) * p.b2 * phi * phi;
-    const Real Bx = Real(3) * (p.ux * phi + hb), By = Real(3) * (p.uy * phi + hb);
+    const Real g = flux_pow(p, phi);
+    const Real Bx = Real(3) * fma(p.ux, phi, p.bgx * g), By = Real(3) * fma(p.uy, phi, p.bgy * g);
     const Real cc = Real(1.5) * p.c3 * phi * phi * phi;
     const Real w0 = cst<Real>(4, 9), w1 = cst<Real>(1, 9), w5 = cst<Real>(1, 36);
     const Real a0 = phi - cc * cst<Real>(2, 3);
@@ -414,16 +465,16 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
 }
 
 // Spatial part of the source at node (x, y) for the compile-time source kind
-// (4: decided at run time).
+// (the reaction term depends on phi and is evaluated in the collision).
 template <typename Real, int SRC>
 __device__ __forceinline__ Real source_at(const SweepParams<Real> &p, Real xs, Real xc, int y, int node) {
-    if constexpr (SRC == 1) return Real(1);
-    else if constexpr (SRC == 2) return fma(xs, p.Ys[y], xc * p.Yc[y]);
-    else if constexpr (SRC == 3) return p.srcF[node];
-    else if constexpr (SRC == 4) {
-        if (p.src_kind == 1) return Real(1);
-        if (p.src_kind == 2) return fma(xs, p.Ys[y], xc * p.Yc[y]);
-        if (p.src_kind == 3) return p.srcF[node];
+    if constexpr (SRC == kSrcConst) return Real(1);
+    else if constexpr (SRC == kSrcTrig) return fma(xs, p.Ys[y], xc * p.Yc[y]);
+    else if constexpr (SRC == kSrcField) return p.srcF[node];
+    else if constexpr (SRC == kSrcRuntime) {
+        if (p.src_kind == kSrcConst) return Real(1);
+        if (p.src_kind == kSrcTrig) return fma(xs, p.Ys[y], xc * p.Yc[y]);
+        if (p.src_kind == kSrcField) return p.srcF[node];
         return Real(0);
     } else return Real(0);
 }
@@ -492,7 +543,7 @@ template <typename Real, typename S, int SH, int MODE, int SRC, bool L2ONLY, boo
 __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, int ybase, int ystride,
                                              int nrows) {
     Real xs = Real(0), xc = Real(0);
-    if (SRC == 2 || (SRC == 4 && p.src_kind == 2)) { xs = p.Xs[x]; xc = p.Xc[x]; }
+    if (SRC == kSrcTrig || (SRC == kSrcRuntime && p.src_kind == kSrcTrig)) { xs = p.Xs[x]; xc = p.Xc[x]; }
     const bool x_inner = (x > 0) && (x < p.nx - 1);
     double resid = 0.0;
     bool bad = false;

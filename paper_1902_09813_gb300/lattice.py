@@ -14,7 +14,8 @@ import torch
 from . import _capi as C
 
 _K2 = {"hbb": C.K2_HBB, "const": C.K2_CONST}
-_SRC = {"none": C.SRC_NONE, "const": C.SRC_CONST, "trig": C.SRC_TRIG, "field": C.SRC_FIELD}
+_SRC = {"none": C.SRC_NONE, "const": C.SRC_CONST, "trig": C.SRC_TRIG, "field": C.SRC_FIELD,
+        "reaction": C.SRC_REACTION}
 
 
 def grid_desc(nx, ny, dx, dt, bc=(0, 0, 0, 0), compute="f64", storage="f64",
@@ -31,7 +32,7 @@ def grid_desc(nx, ny, dx, dt, bc=(0, 0, 0, 0), compute="f64", storage="f64",
 
 
 def coeffs(u=(0.0, 0.0), b2=0.0, c3=0.0, A0=(0.0, 0.0, 0.0), a2=0.0, k0=1.0, k2_mode="hbb",
-           k2=1.0, source=None, wall_lam=0.0) -> C.Coeffs:
+           k2=1.0, source=None, wall_lam=0.0, b_dir=(1.0, 1.0), b_q=2.0) -> C.Coeffs:
     c = C.Coeffs()
     c.u[0], c.u[1] = float(u[0]), float(u[1])
     c.b2, c.c3, c.a2, c.k0 = float(b2), float(c3), float(a2), float(k0)
@@ -44,7 +45,11 @@ def coeffs(u=(0.0, 0.0), b2=0.0, c3=0.0, A0=(0.0, 0.0, 0.0), a2=0.0, k0=1.0, k2_
         c.src_const, c.src_lam, c.src_k = float(source.const), float(source.lam), float(source.k)
         for k in range(4):
             c.src_alpha[k] = float(source.alpha[k])
+        if source.kind == "reaction":
+            c.react_rate, c.react_exp = float(source.const), float(source.exp)
     c.wall_lam = float(wall_lam)
+    c.b_dir[0], c.b_dir[1] = float(b_dir[0]), float(b_dir[1])
+    c.b_q = float(b_q)
     return c
 
 
@@ -100,20 +105,33 @@ class Lattice:
         desc = grid_desc(p.nx, p.ny, p.dx, p.dt, p.bc, compute, storage, p.x0, p.y0,
                          p.phi_ref if phi_ref is None else phi_ref, fields, shift)
         coef = coeffs(p.u, p.b2, p.c3, p.A0, p.a2, p.k0, p.k2_mode, p.k2, p.source,
-                      getattr(p, "wall_lam", 0.0))
+                      getattr(p, "wall_lam", 0.0), getattr(p, "b_dir", (1.0, 1.0)), getattr(p, "b_q", 2.0))
         lat = cls(desc, coef, device=device, stream=stream, defer_coeffs=True)
         if src_field is not None:
             lat.set_source_field(src_field)
         if A_field is not None:
             lat.set_diffusion_field(*A_field)
         C.check(lat.lib.btrt_set_coeffs(lat.handle, ctypes.byref(coef)))
+        wall_fn_arrs = p.wall_arrays_at(p.t0 + p.dt) if getattr(p, "wall_fn", None) is not None else None
         for side in range(4):
             arrs = getattr(p, "wall_arrays", None)
-            if arrs is not None and arrs[side] is not None:
+            if wall_fn_arrs is not None:
+                lat.set_boundary(side, wall_fn_arrs[side])
+            elif arrs is not None and arrs[side] is not None:
                 lat.set_boundary(side, arrs[side])
             else:
                 lat.set_boundary(side, [p.wall[side]])
         return lat
+
+    def step_walls(self, p, nsteps: int = 1):
+        """Advance nsteps with wall values re-evaluated from p.wall_fn before every
+        step (at the step's end time, as the bounce-back rule takes them)."""
+        for _ in range(nsteps):
+            _, t = self.time()
+            for side, v in enumerate(p.wall_arrays_at(t + p.dt)):
+                self.set_boundary(side, v)
+            self.step(1)
+        return self
 
     @property
     def nx(self):

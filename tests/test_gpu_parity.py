@@ -311,3 +311,45 @@ def test_variable_tensor_field_fp32_tma_equals_plain(storage):
     if storage == "f32":
         phi_ref, _ = _oracle_run(p, p.nsteps)
         assert _rel(a.phi_host(), phi_ref) <= TOL32
+
+
+# ---------------------------------------------------------------- power-law flux, reaction source
+BF_CASES = [
+    (40, 33, (0, 0, 0, 0), "reaction", 2.5),
+    (40, 33, (1, 1, 1, 1), "reaction", 2.0),
+    (37, 29, (1, 1, 0, 0), "trig", 1.5),
+    (3, 3, (0, 0, 0, 0), "reaction", 3.0),
+]
+
+
+@pytest.mark.parametrize("case", BF_CASES, ids=lambda c: f"{c[0]}x{c[1]}-bc{''.join(map(str, c[2]))}-{c[3]}-q{c[4]}")
+@pytest.mark.parametrize("compute", ["f64", "df64"])
+def test_power_flux_reaction_random_states(case, compute):
+    nx, ny, bc, src, q = case
+    p = w.random_state_problem(nx, ny, seed=3 * nx + ny, bc=bc, nonlinear=True, source=src, flux_q=q)
+    lat = _gpu_run(p, 10, compute=compute, storage=compute)
+    phi_ref, fpost_ref = _oracle_run(p, 10)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL64
+    assert _rel(lat.read_f(), fpost_ref) <= TOL64
+
+
+@pytest.mark.parametrize("compute,storage,tol", [("f64", "f64", TOL64), ("df64", "df64", TOL64),
+                                                 ("f32", "f32", TOL32)])
+def test_burgers_fisher_walls_per_step(compute, storage, tol):
+    """Burgers-Fisher (Eq. 67) on [-1, 2]^2 with bounce-back walls re-evaluated
+    from the exact solution before every step."""
+    p = w.burgers_fisher(n=60, a=2.0, alpha=0.05, t_end=0.25)
+    lat = _lattice(p, compute, storage)
+    lat.init(p.phi0(), t0=p.t0).step_walls(p, p.nsteps)
+    o = oracle.OracleLattice(p, nthreads=cpu_threads()).init().step(p.nsteps)
+    assert _rel(lat.phi_host(), o.phi()) <= tol
+    assert lat.check() == 0
+
+
+def test_burgers_fisher_f16_storage_error():
+    """FP16 storage (local shift) keeps the closed-form error within 1 % of FP64's."""
+    p = w.burgers_fisher(n=120, a=2.0, alpha=0.05, t_end=1.0)
+    ex = w.burgers_fisher_exact(p, p.nsteps * p.dt)
+    g64 = w.gre(_lattice(p, "f64").init(p.phi0()).step_walls(p, p.nsteps).phi_host(), ex)
+    g16 = w.gre(_lattice(p, "f32", "f16").init(p.phi0()).step_walls(p, p.nsteps).phi_host(), ex)
+    assert abs(g16 - g64) <= 0.01 * g64, (g64, g16)

@@ -33,6 +33,11 @@ MUTATIONS = {
     "K1_half": ("M[0] += 0.5;", "M[0] += 0.25;"),
     "A_offdiag": ("A[1] = s * p->A0[1];", "A[1] = -s * p->A0[1];"),
     "wall_time": ("link_target(p, ix, iy, i, t + p->dt,", "link_target(p, ix, iy, i, t,"),
+    "reaction_sign": ("return p->react_rate * phi * (1.0 - phi_pow(phi, p->react_exp));",
+                      "return p->react_rate * phi * (1.0 + phi_pow(phi, p->react_exp));"),
+    "flux_direction": ("B[0] = p->u[0] * phi + p->b2 * p->b_dir[0] * g;",
+                       "B[0] = p->u[0] * phi + p->b2 * p->b_dir[1] * g;"),
+    "flux_exponent_scale": ("double g = phi_pow(phi, p->b_q) / p->b_q;", "double g = phi_pow(phi, p->b_q) / 2.0;"),
 }
 
 
@@ -54,6 +59,7 @@ def test_pins_catch_mutation(name, tmp_path):
         subprocess.run(cmd, check=True, capture_output=True)
     env = dict(os.environ, BTRT_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_burgers_fisher.py")],
                        env=env, capture_output=True, text=True, cwd=ROOT, timeout=600)
     assert r.returncode != 0, f"mutation {name} survived the pins:\n{r.stdout[-2000:]}"

@@ -8,10 +8,11 @@ It contains none of the lattice Boltzmann arithmetic; both the CPU oracle
 from .problems import (  # noqa: F401
     Problem, Source, PERIODIC, HBB,
     gaussian_hill, mms_sinsin, nonlinear_modes, steady_diffusion, linear_cde, variable_tensor,
+    burgers_fisher, burgers_fisher_solution,
     batched_instances, random_state_problem,
 )
 from .exact import (  # noqa: F401
     gaussian_hill_exact, mms_sinsin_exact, steady_diffusion_exact, linear_cde_exact,
-    variable_tensor_exact,
+    variable_tensor_exact, burgers_fisher_exact,
 )
 from .metrics import gre, rel_l2  # noqa: F401

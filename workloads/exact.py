@@ -57,3 +57,11 @@ def variable_tensor_exact(p, t: float) -> np.ndarray:
     """phi* = exp((1 - 12 pi^2 alpha) t) sin(2 pi x) sin(2 pi y) (Eq. 76)."""
     X, Y = p.coords()
     return math.exp(p.meta["lam"] * t) * np.sin(2 * math.pi * X) * np.sin(2 * math.pi * Y)
+
+
+def burgers_fisher_exact(p, t: float) -> np.ndarray:
+    """Eq. 68 (with the corrected wave speed, see burgers_fisher_solution)."""
+    from .problems import burgers_fisher_solution
+    X, Y = p.coords()
+    m = p.meta
+    return burgers_fisher_solution(X, Y, t, m["a"], m["alpha"], m["b"], m["delta"])

@@ -5,10 +5,11 @@
 with the coefficient families used by the paper's tests (Sec. 4) and by the
 synthetic workloads of this project:
 
-    B(phi) = u phi + b2 (phi^2 / 2) (1, 1)
+    B(phi) = u phi + b2 (phi^q / q) (d_x, d_y)   (q = 2, d = (1, 1) unless stated)
     C(phi) = phi + c3 phi^3                      (paper: D(x,phi,t) = C(phi) I)
     A(phi) = (1 + a2 phi^2) A0,  A0 symmetric positive definite
     S(x,t) = 0 | const | exp(lam t) sum_pq alpha_pq X_p(k x) Y_q(k y)   (X,Y in {sin, cos})
+           | rate phi (1 - phi^exp)              (reaction term of Eq. 67)
 
 All quantities are physical; nodes are cell-centred, x_i = x0 + (i + 1/2) dx
 (the half-way bounce-back analysis places the wall half a cell outside the
@@ -31,8 +32,9 @@ _SIDES = ("x-", "x+", "y-", "y+")
 
 @dataclass
 class Source:
-    kind: str = "none"            # "none" | "const" | "trig" | "field"
-    const: float = 0.0
+    kind: str = "none"            # "none" | "const" | "trig" | "field" | "reaction"
+    const: float = 0.0            # const: S; reaction: the rate
+    exp: float = 1.0              # reaction: S = const phi (1 - phi^exp)
     lam: float = 0.0              # time factor exp(lam * t)
     k: float = math.pi            # spatial wavenumber of the trig tables
     alpha: tuple = (0.0, 0.0, 0.0, 0.0)   # (ss, sc, cs, cc): X_p(kx) Y_q(ky)
@@ -62,6 +64,8 @@ class Problem:
     bc: tuple = (PERIODIC, PERIODIC, PERIODIC, PERIODIC)   # x-, x+, y-, y+
     u: tuple = (0.0, 0.0)
     b2: float = 0.0
+    b_dir: tuple = (1.0, 1.0)            # direction of the power-law flux term
+    b_q: float = 2.0                     # its exponent
     c3: float = 0.0
     A0: tuple = (0.0, 0.0, 0.0)          # (xx, xy, yy)
     a2: float = 0.0
@@ -72,6 +76,7 @@ class Problem:
     wall: tuple = (0.0, 0.0, 0.0, 0.0)   # constant wall value per side
     wall_arrays: Optional[Sequence[Optional[np.ndarray]]] = None   # per-node values along a side
     wall_lam: float = 0.0                # wall values carry the factor exp(wall_lam t)
+    wall_fn: Optional[Callable] = None   # (x, y, t) -> wall value, re-evaluated every step
     src_field: Optional[np.ndarray] = None    # source kind "field": S = exp(lam t) src_field
     A_field: Optional[tuple] = None           # per-node diffusion tensor (xx, xy, yy) arrays
     t0: float = 0.0
@@ -110,7 +115,20 @@ class Problem:
     def lattice_speed(self, phi_max: float) -> float:
         """max |B'(phi)| dt/dx over |phi| <= phi_max (advective Courant number)."""
         ux, uy = self.u
-        return (max(abs(ux), abs(uy)) + abs(self.b2) * phi_max) * self.dt / self.dx
+        slope = abs(self.b2) * max(abs(self.b_dir[0]), abs(self.b_dir[1])) * phi_max ** (self.b_q - 1.0)
+        return (max(abs(ux), abs(uy)) + slope) * self.dt / self.dx
+
+    def wall_arrays_at(self, t: float):
+        """Wall values along the four sides at time t from wall_fn (x-, x+: one
+        per row at the row centres; y-, y+: one per column)."""
+        xs = self.x0 + (np.arange(self.nx) + 0.5) * self.dx
+        ys = self.y0 + (np.arange(self.ny) + 0.5) * self.dx
+        x1, y1 = self.x0 + self.nx * self.dx, self.y0 + self.ny * self.dx
+        f = self.wall_fn
+        return [np.asarray(f(np.full_like(ys, self.x0), ys, t), dtype=np.float64),
+                np.asarray(f(np.full_like(ys, x1), ys, t), dtype=np.float64),
+                np.asarray(f(xs, np.full_like(xs, self.y0), t), dtype=np.float64),
+                np.asarray(f(xs, np.full_like(xs, y1), t), dtype=np.float64)]
 
 
 def _rot_tensor(l1: float, l2: float, theta: float) -> tuple:
@@ -250,6 +268,39 @@ def linear_cde(n: int = 200, alpha: float = 0.01, u=(0.1, 0.1), c: float = 1.0,
                    meta=dict(alpha=alpha, lam=lam), **kw)
 
 
+def burgers_fisher_solution(x, y, t, a: float, alpha: float, b: float, delta: float):
+    """Travelling-wave solution of the Burgers-Fisher equation (Eq. 67, convection
+    along x only, diffusion alpha in both directions):
+        phi = [1/2 + 1/2 tanh(A (x + y - omega t))]^(1/delta),
+        A = -a delta / (4 alpha (delta + 1)),
+        omega = a / (delta + 1) + 2 b alpha (delta + 1) / a.
+    Eq. 69 prints omega = (a^2 + 2 b alpha (delta + 1)) / (a (delta + 1)); the
+    wave satisfies Eq. 67 only with (delta + 1)^2 in that numerator (checked by
+    substitution), which is the omega above."""
+    A = -a * delta / (4.0 * alpha * (delta + 1.0))
+    om = a / (delta + 1.0) + 2.0 * b * alpha * (delta + 1.0) / a
+    return (0.5 + 0.5 * np.tanh(A * (x + y - om * t))) ** (1.0 / delta)
+
+
+def burgers_fisher(n: int = 120, a: float = 2.0, alpha: float = 0.05, b: float = 0.05,
+                   delta: float = 1.5, c: float = 5.0, t_end: float = 1.0, k2_mode: str = "hbb",
+                   k2: float = 1.0) -> Problem:
+    """Burgers-Fisher equation (Sec. 4.1.3, Eq. 67) on [-1, 2]^2 with n x n nodes:
+    B = a phi^(delta+1)/(delta+1) (1, 0) (the conservative form of a phi^delta d_x phi),
+    A = alpha I, S = b phi (1 - phi^delta); bounce-back walls carrying the exact
+    solution, re-evaluated at every step (wall_fn); phi0 the exact solution at t = 0."""
+    dx = 3.0 / n
+    dt = dx / c
+    sol = lambda X, Y, t: burgers_fisher_solution(X, Y, t, a, alpha, b, delta)  # noqa: E731
+    return Problem(name=f"burgers_fisher_{n}", nx=n, ny=n, dx=dx, dt=dt, x0=-1.0, y0=-1.0,
+                   bc=(HBB, HBB, HBB, HBB), u=(0.0, 0.0), b2=a, b_dir=(1.0, 0.0), b_q=delta + 1.0,
+                   A0=(alpha, 0.0, alpha), k2_mode=k2_mode, k2=k2,
+                   source=Source(kind="reaction", const=b, exp=delta),
+                   wall_fn=sol, nsteps=int(round(t_end / dt)),
+                   phi0_fn=lambda X, Y: sol(X, Y, 0.0),
+                   meta=dict(a=a, alpha=alpha, b=b, delta=delta))
+
+
 def variable_tensor(n: int = 100, alpha: float = 1e-2, u=(0.1, 0.1), c: float = 1.0,
                     t_end: float = 3.0, walls: bool = True) -> Problem:
     """Anisotropic CDE with a variable diffusion tensor (Sec. 4.2.2, Eqs. 73-76) on
@@ -306,10 +357,11 @@ def batched_instances(count: int = 512, seed: int = 0, nmin: int = 32, nmax: int
 
 
 def random_state_problem(nx: int, ny: int, seed: int = 0, bc=(PERIODIC,) * 4,
-                         nonlinear: bool = True, source: str = "trig") -> Problem:
+                         nonlinear: bool = True, source: str = "trig", flux_q: float = 2.0) -> Problem:
     """A generic seeded problem for parity tests: random coefficients within the
     stable range, a smooth random initial field, optional walls with random
-    constant values and a trig source."""
+    constant values and a trig, constant or reaction source; flux_q != 2 gives
+    the power-law flux b2 (phi^q / q)(1, -1/2)."""
     rng = np.random.default_rng(seed)
     l1, l2 = rng.uniform(0.01, 0.08, size=2)
     th = rng.uniform(0.0, math.pi)
@@ -333,6 +385,8 @@ def random_state_problem(nx: int, ny: int, seed: int = 0, bc=(PERIODIC,) * 4,
                      alpha=tuple(rng.uniform(-1e-3, 1e-3, size=4)))
     elif source == "const":
         src = Source(kind="const", const=float(rng.uniform(-1e-3, 1e-3)))
+    elif source == "reaction":
+        src = Source(kind="reaction", const=float(rng.uniform(0.01, 0.05)), exp=float(rng.uniform(1.0, 2.0)))
     else:
         src = Source()
     wall = tuple(float(v) for v in rng.uniform(0.2, 1.2, size=4))
@@ -340,4 +394,5 @@ def random_state_problem(nx: int, ny: int, seed: int = 0, bc=(PERIODIC,) * 4,
                    bc=tuple(bc), u=u, b2=(0.05 if nonlinear else 0.0),
                    c3=(0.02 if nonlinear else 0.0), A0=A0, a2=(0.3 if nonlinear else 0.0),
                    k0=float(rng.uniform(0.8, 1.2)), source=src, wall=wall,
+                   b_q=float(flux_q), b_dir=((1.0, 1.0) if flux_q == 2.0 else (1.0, -0.5)),
                    nsteps=8, phi0_fn=phi0, phi_ref=base)
