@@ -16,3 +16,7 @@ from .exact import (  # noqa: F401
     variable_tensor_exact, burgers_fisher_exact,
 )
 from .metrics import gre, rel_l2  # noqa: F401
+from .problems3 import (  # noqa: F401
+    Problem3, gaussian_hill3, steady_diffusion3, random_state_problem3, rot_tensor3,
+    gaussian_hill3_exact, steady_diffusion3_exact,
+)
