@@ -319,7 +319,50 @@ def run_variants(args, steps=200, warmup=5):
         out[f"nonlinear_f32_{st}_tma"] = _time_single(q, phi0, "f32", st, steps, warmup, variant="tma")
         out[f"nonlinear_f32_{st}_local"] = _time_single(q, phi0, "f32", st, steps, warmup, shift="local")
     out["nonlinear_f64"] = _time_single(q, phi0, "f64", "f64", 50, 3)
+    out.update(run_d3q19(args))
     return out
+
+
+BYTES_PER_UPDATE_3D = {"f64": 2 * (19 * 8 + 8), "f32": 2 * (19 * 4 + 4), "f16": 2 * (19 * 2 + 4),
+                       "bf16": 2 * (19 * 2 + 4)}
+N_3D = 384
+
+
+def _time_single3(p, compute, storage, steps, warmup, shift="auto"):
+    import torch
+    from paper_1902_09813_gb300 import Lattice3
+    stream = torch.cuda.Stream()
+    lat = Lattice3.from_problem(p, compute=compute, storage=storage, stream=stream, shift=shift)
+    lat.init(p.phi0())
+    lat.step(warmup)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    lat.check()
+    ms = e0.elapsed_time(e1)
+    nodes = p.nx * p.ny * p.nz
+    mlups = nodes * steps / (ms * 1e-3) / 1e6
+    peak, _ = _peaks()
+    gbs = BYTES_PER_UPDATE_3D[storage] * mlups * 1e6 / 1e9
+    lat.close()
+    del lat
+    torch.cuda.empty_cache()
+    return {"mlups": round(mlups, 1), "ms_per_step": round(ms / steps, 4), "algorithmic_gbs": round(gbs, 1),
+            "hbm_frac": round(gbs / peak, 4), "bytes_per_update": BYTES_PER_UPDATE_3D[storage]}
+
+
+def run_d3q19(args, n=N_3D):
+    """The D3Q19 sweep on an n^3 periodic box (advected anisotropic Gaussian hill,
+    lattice units): FP64, FP32 storage, FP16 storage with the local shift."""
+    import workloads as w
+    p = w.gaussian_hill3(n=n, sigma0=n / 16.0, u=(0.05, -0.03, 0.02),
+                         A0=(0.02, 0.004, 0.0, 0.015, -0.003, 0.01), nsteps=0)
+    return {f"d3q19_{n}_f64": _time_single3(p, "f64", "f64", 30, 3),
+            f"d3q19_{n}_f32_f32": _time_single3(p, "f32", "f32", 100, 5),
+            f"d3q19_{n}_f32_f16_local": _time_single3(p, "f32", "f16", 100, 5, shift="local")}
 
 
 # ---------------------------------------------------------------------------- accuracy
@@ -550,6 +593,8 @@ def main():
     ap.add_argument("--serve-seq", type=int, default=48)
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched persistent launch (for profiling small batches)")
+    ap.add_argument("--d3q19-only", action="store_true",
+                    help="only the D3Q19 sweep on an n^3 box (--n, --compute, --storage, --shift, --steps)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--workload", default="mms", choices=["mms", "nonlinear"])
@@ -569,6 +614,12 @@ def main():
         run_reference(args)
     elif args.batched_only:
         run_batched_only(args)
+    elif args.d3q19_only:
+        import workloads as w
+        p = w.gaussian_hill3(n=args.n, sigma0=args.n / 16.0, u=(0.05, -0.03, 0.02),
+                             A0=(0.02, 0.004, 0.0, 0.015, -0.003, 0.01), nsteps=0)
+        r = _time_single3(p, args.compute, args.storage, args.steps, args.warmup, shift=args.shift)
+        print(json.dumps({"d3q19": r, "n": args.n, "compute": args.compute, "storage": args.storage}), flush=True)
     else:
         run_gpu(args)
 

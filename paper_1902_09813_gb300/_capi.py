@@ -44,6 +44,30 @@ class Coeffs(ctypes.Structure):
     ]
 
 
+class GridDesc3(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+        ("bc", ctypes.c_int32 * 6),
+        ("compute", ctypes.c_int32), ("storage", ctypes.c_int32),
+        ("shift", ctypes.c_int32), ("fields", ctypes.c_int32),
+        ("dx", ctypes.c_double), ("dt", ctypes.c_double),
+        ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+        ("phi_ref", ctypes.c_double),
+    ]
+
+
+class Coeffs3(ctypes.Structure):
+    _fields_ = [
+        ("u", ctypes.c_double * 3), ("b2", ctypes.c_double), ("b_dir", ctypes.c_double * 3),
+        ("b_q", ctypes.c_double), ("c3", ctypes.c_double),
+        ("A0", ctypes.c_double * 6), ("a2", ctypes.c_double), ("k0", ctypes.c_double),
+        ("k2_mode", ctypes.c_int32), ("src_kind", ctypes.c_int32),
+        ("k2", ctypes.c_double), ("src_const", ctypes.c_double), ("src_lam", ctypes.c_double),
+        ("react_rate", ctypes.c_double), ("react_exp", ctypes.c_double),
+        ("wall", ctypes.c_double * 6), ("wall_lam", ctypes.c_double),
+    ]
+
+
 class BtrtError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"btrt error {code}: {msg}")
@@ -84,6 +108,18 @@ SIGNATURES = [
     ("btrt_batch_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_uint64, _i32]),
     ("btrt_batch_destroy", ctypes.c_int, [_vp]),
     ("btrt_phi_sum_static", ctypes.c_int, [_vp, _i32, _i32, _i32, _i64, _vp, _dp]),
+    ("btrt3_workspace_bytes", _sz, [ctypes.POINTER(GridDesc3)]),
+    ("btrt3_create", ctypes.c_int, [ctypes.POINTER(GridDesc3), _vp, _sz, _vp, ctypes.POINTER(_vp)]),
+    ("btrt3_set_coeffs", ctypes.c_int, [_vp, ctypes.POINTER(Coeffs3)]),
+    ("btrt3_set_source_field", ctypes.c_int, [_vp, _dp]),
+    ("btrt3_init_phi", ctypes.c_int, [_vp, _vp, _i32, _i32, ctypes.c_double]),
+    ("btrt3_step", ctypes.c_int, [_vp, _i64]),
+    ("btrt3_read_phi", ctypes.c_int, [_vp, _vp, _i32, _i32]),
+    ("btrt3_read_f", ctypes.c_int, [_vp, _dp, _i32, _i32, _i32, _i32, _i32, _i32]),
+    ("btrt3_mass", ctypes.c_int, [_vp, _dp]),
+    ("btrt3_check", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    ("btrt3_get_time", ctypes.c_int, [_vp, ctypes.POINTER(_i64), _dp]),
+    ("btrt3_destroy", ctypes.c_int, [_vp]),
     ("btrt_last_error", ctypes.c_char_p, []),
     ("btrt_version", ctypes.c_char_p, []),
 ]

@@ -1,0 +1,348 @@
+// btrt_sweep3.cuh -- device side of the fused B-TriRT sweep on the D3Q19 lattice.
+//
+// Same scheme as the D2Q9 sweep in three dimensions (the appendix's D3Q19
+// relaxation matrix S_f = diag(k0, K1, k2 I_6, k0 I_9) with a 3x3 first-order
+// block K1 = (3 A^ + I/2)^-1 from Eq. 30, k2 from Eq. 62 at the mean rate
+// 1/k1_eff = tr(K1^-1)/3, the correction of Eq. 11 and scheme-2 sources).  One
+// thread owns one node; the sweep pulls f_i(x) = f_i^+(x - c_i), replaces links
+// that cross bounce-back faces (one face, or two at an edge: mean of their
+// values) by -f_opp^+(x) + wall term, collides in moment space and writes f^+
+// and phi to the other buffers.  Lattice units (c = 1, cs^2 = 1/3).
+//
+// Velocity order (columns of Eq. 86): 0 rest; 1, 2 = +-x; 3, 4 = +-y; 5, 6 = +-z;
+// 7 (1,1,0) 8 (-1,1,0) 9 (1,-1,0) 10 (-1,-1,0); 11 (1,0,1) 12 (-1,0,1)
+// 13 (1,0,-1) 14 (-1,0,-1); 15 (0,1,1) 16 (0,-1,1) 17 (0,1,-1) 18 (0,-1,-1).
+// Weights 1/3, 1/18, 1/36.  Populations are stored in the forms of the D2Q9
+// sweep (unshifted FP64, or FP32/FP16/BF16 shifted by w_i phi_ref or by w_i phi
+// of the writing node).
+#pragma once
+
+#include "btrt_sweep.cuh"
+
+namespace btrt {
+
+__host__ __device__ constexpr int cx3(int i) {
+    return (i == 1 || i == 7 || i == 9 || i == 11 || i == 13) ? 1
+           : (i == 2 || i == 8 || i == 10 || i == 12 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy3(int i) {
+    return (i == 3 || i == 7 || i == 8 || i == 15 || i == 17) ? 1
+           : (i == 4 || i == 9 || i == 10 || i == 16 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz3(int i) {
+    return (i == 5 || i == 11 || i == 12 || i == 15 || i == 16) ? 1
+           : (i == 6 || i == 13 || i == 14 || i == 17 || i == 18) ? -1 : 0;
+}
+// opposite directions (checked against cx3/cy3/cz3 by a static assertion below)
+__host__ __device__ constexpr int opposite3(int i) {
+    constexpr int o[19] = {0, 2, 1, 4, 3, 6, 5, 10, 9, 8, 7, 14, 13, 12, 11, 18, 17, 16, 15};
+    return o[i];
+}
+__host__ __device__ constexpr bool opposites_ok() {
+    for (int i = 0; i < 19; ++i) {
+        const int o = opposite3(i);
+        if (cx3(o) != -cx3(i) || cy3(o) != -cy3(i) || cz3(o) != -cz3(i)) return false;
+    }
+    return true;
+}
+static_assert(opposites_ok(), "D3Q19 opposite table");
+
+template <typename Real> __device__ __forceinline__ Real wgt3(int i) {
+    return i == 0 ? cst<Real>(1, 3) : (i <= 6 ? cst<Real>(1, 18) : cst<Real>(1, 36));
+}
+
+template <typename Real>
+struct Sweep3Params {
+    const void *fin;       // post-collision populations of the previous step: 19 planes, `plane` apart
+    void *fout;
+    const Real *phi_in;    // phi of the nodes that wrote fin
+    Real *phi_out;
+    int nx, ny, nz;
+    int pitch;             // elements between rows
+    int slab;              // elements between z layers (pitch * ny)
+    int plane;             // elements between population planes; 19 * plane < 2^31
+    int hbb_x, hbb_y, hbb_z;
+    Real wall[6];          // wall value per face (x-, x+, y-, y+, z-, z+), times wall_fac
+    Real wall_fac;
+    Real wref[3];          // w phi_ref for |c|^2 = 0, 1, 2 (reference shift)
+    Real phi_ref;
+
+    Real ux, uy, uz;       // B = u phi + bg phi^q
+    Real bgx, bgy, bgz, bq;
+    int bq2;
+    Real c3;               // C = phi + c3 phi^3
+    Real A0[6];            // xx, xy, xz, yy, yz, zz (lattice units)
+    Real a2;
+    Real k0, om;           // k0, 1 - k0
+    int nonlin;            // 1: A depends on phi (K1, k2 per node) or B, C nonlinear
+    int k2_hbb;
+    Real k2c;
+    Real K1[6];            // constant K1 (symmetric) and k2 when A is constant
+    Real k2;
+    Real cond_limit;       // FP32: tr^3 > cond_limit det -> invert in FP64
+
+    int src_kind;          // 0 none, 1 const, 3 per-node field, 4 reaction
+    Real src_val;          // dt S (const), dt (3 T_n - T_{n-1}) / 2 (field), dt (reaction)
+    const Real *srcF;      // field: F(x) per node (pitched)
+    Real react_rate, react_exp;
+    int react2;
+
+    int first;
+    int *flags;            // bit 0: non-finite phi
+};
+
+template <typename Real>
+__device__ __forceinline__ Real wall3_term(const Sweep3Params<Real> &p, int n2, Real phi_w) {
+    // 2 x even part of f^eq at phi_w: 2 w [phi_w + (C - phi_w)(3/2)(|c|^2 - 1)]
+    const Real w = n2 == 0 ? cst<Real>(1, 3) : (n2 == 1 ? cst<Real>(1, 18) : cst<Real>(1, 36));
+    const Real dC = p.c3 * phi_w * phi_w * phi_w;
+    return Real(2) * w * fma(dC, Real(1.5) * Real(n2 - 1), phi_w);
+}
+
+// Shifted equilibrium (Eq. 7, D = C I) for the initialising collision.
+template <typename Real, int SH>
+__device__ __forceinline__ void equilibrium3(const Sweep3Params<Real> &p, Real phi, Real (&f)[19]) {
+    const Real g = p.bq2 ? phi * phi : powr(phi, p.bq);
+    const Real Bx = Real(3) * fma(p.ux, phi, p.bgx * g);
+    const Real By = Real(3) * fma(p.uy, phi, p.bgy * g);
+    const Real Bz = Real(3) * fma(p.uz, phi, p.bgz * g);
+    const Real Cm = Real(1.5) * p.c3 * phi * phi * phi;   // (3/2)(C - phi)
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const int n2 = cx3(i) * cx3(i) + cy3(i) * cy3(i) + cz3(i) * cz3(i);
+        Real v = fma(Cm, Real(n2 - 1), phi);
+        v = v + Real(cx3(i)) * Bx + Real(cy3(i)) * By + Real(cz3(i)) * Bz;
+        f[i] = wgt3<Real>(i) * v;
+        if constexpr (SH == kShiftRef) f[i] = f[i] - p.wref[n2];
+        if constexpr (SH == kShiftLocal) f[i] = fma(-wgt3<Real>(i), phi, f[i]);
+    }
+}
+
+// Moment-space collision of one node in shifted form d_i = f_i - w_i rs
+// (rs = 0, phi_ref or phi^{n-1} of the node):
+//   d_i^+ = (1 - k0) d_i + w_i [a + cC_i + 3 c_i.V - kap H_i],
+//   a = k0 (phi - rs) + source, cC_i = (3/2) k0 (C - phi)(|c_i|^2 - 1),
+//   V = k0 B - (K1 - k0 I)(M1) + (I - K1/2) dB, M1 = j - B,
+//   H_i = c_i c_i : M2 - tr(M2)/3, M2 = Pi - (C - rs)/3 I, kap = (9/2)(k2 - k0).
+// Returns phi; phid = phi - rs.
+template <typename Real, int MODE, int SRC, int SH>
+__device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[19], Real rs, Real phi_prev,
+                                         Real srcv, bool first, Real &phid_out) {
+    // moments of the shifted populations
+    const Real ax = d[1] + d[2], ay = d[3] + d[4], az = d[5] + d[6];
+    const Real sxy = (d[7] + d[8]) + (d[9] + d[10]);
+    const Real sxz = (d[11] + d[12]) + (d[13] + d[14]);
+    const Real syz = (d[15] + d[16]) + (d[17] + d[18]);
+    const Real phid = ((d[0] + (ax + ay)) + (az + sxy)) + (sxz + syz);
+    phid_out = phid;
+    Real phi = phid;
+    if constexpr (SH != kShiftNone) phi = phid + rs;
+    const Real jx = (d[1] - d[2]) + ((d[7] - d[8]) + (d[9] - d[10])) + ((d[11] - d[12]) + (d[13] - d[14]));
+    const Real jy = (d[3] - d[4]) + ((d[7] + d[8]) - (d[9] + d[10])) + ((d[15] - d[16]) + (d[17] - d[18]));
+    const Real jz = (d[5] - d[6]) + ((d[11] + d[12]) - (d[13] + d[14])) + ((d[15] + d[16]) - (d[17] + d[18]));
+    const Real Pxx = (ax + sxy) + sxz, Pyy = (ay + sxy) + syz, Pzz = (az + sxz) + syz;
+    const Real Pxy = (d[7] - d[8]) - (d[9] - d[10]);
+    const Real Pxz = (d[11] - d[12]) - (d[13] - d[14]);
+    const Real Pyz = (d[15] - d[16]) - (d[17] - d[18]);
+    const Real dphi = first ? Real(0) : (SH == kShiftLocal ? phid : phi - phi_prev);
+
+    // coefficients
+    Real Bx, By, Bz, dBx, dBy, dBz, Cm = Real(0);
+    if constexpr (MODE != kGeneral) {
+        Bx = p.ux * phi; By = p.uy * phi; Bz = p.uz * phi;
+        dBx = p.ux * dphi; dBy = p.uy * dphi; dBz = p.uz * dphi;
+    } else if (p.bq2) {
+        const Real p2 = phi * phi;
+        Bx = fma(p.ux, phi, p.bgx * p2);
+        By = fma(p.uy, phi, p.bgy * p2);
+        Bz = fma(p.uz, phi, p.bgz * p2);
+        const Real sp = phi + phi_prev;
+        dBx = fma(p.bgx, sp, p.ux) * dphi;
+        dBy = fma(p.bgy, sp, p.uy) * dphi;
+        dBz = fma(p.bgz, sp, p.uz) * dphi;
+    } else {
+        const Real gq = powr(phi, p.bq);
+        const Real dg = first ? Real(0) : gq - powr(phi_prev, p.bq);
+        Bx = fma(p.ux, phi, p.bgx * gq);
+        By = fma(p.uy, phi, p.bgy * gq);
+        Bz = fma(p.uz, phi, p.bgz * gq);
+        dBx = fma(p.ux, dphi, p.bgx * dg);
+        dBy = fma(p.uy, dphi, p.bgy * dg);
+        dBz = fma(p.uz, dphi, p.bgz * dg);
+    }
+    Real Kxx, Kxy, Kxz, Kyy, Kyz, Kzz, k2;
+    if constexpr (MODE == kGeneral) {
+        Cm = p.c3 * phi * phi * phi;
+        // K1 = (3 A^ + I/2)^-1, A^ = (1 + a2 phi^2) A0^ (Eq. 30), symmetric 3x3 by cofactors
+        const Real s3 = fma(Real(3) * p.a2, phi * phi, Real(3));
+        const Real mxx = fma(s3, p.A0[0], Real(0.5)), mxy = s3 * p.A0[1], mxz = s3 * p.A0[2];
+        const Real myy = fma(s3, p.A0[3], Real(0.5)), myz = s3 * p.A0[4];
+        const Real mzz = fma(s3, p.A0[5], Real(0.5));
+        const Real cxx = fma(myy, mzz, -(myz * myz));
+        const Real cxy = fma(mxz, myz, -(mxy * mzz));
+        const Real cxz = fma(mxy, myz, -(mxz * myy));
+        const Real cyy = fma(mxx, mzz, -(mxz * mxz));
+        const Real cyz = fma(mxy, mxz, -(mxx * myz));
+        const Real czz = fma(mxx, myy, -(mxy * mxy));
+        const Real det = fma(mxx, cxx, fma(mxy, cxy, mxz * cxz));
+        const Real tr = (mxx + myy) + mzz;
+        bool ill = false;
+        if constexpr (sizeof(Real) == 4) ill = tr * tr * tr > p.cond_limit * det;
+        if (ill) {
+            // ill-conditioned FP32 block: cofactors and determinant again in FP64
+            const double dxx = mxx, dxy = mxy, dxz = mxz, dyy = myy, dyz = myz, dzz = mzz;
+            const double ex = dyy * dzz - dyz * dyz, exy = dxz * dyz - dxy * dzz, exz = dxy * dyz - dxz * dyy;
+            const double ey = dxx * dzz - dxz * dxz, eyz = dxy * dxz - dxx * dyz, ez = dxx * dyy - dxy * dxy;
+            const double id = 1.0 / (dxx * ex + dxy * exy + dxz * exz);
+            Kxx = (Real)(ex * id); Kxy = (Real)(exy * id); Kxz = (Real)(exz * id);
+            Kyy = (Real)(ey * id); Kyz = (Real)(eyz * id); Kzz = (Real)(ez * id);
+        } else {
+            const Real id = quot(Real(1), det);
+            Kxx = cxx * id; Kxy = cxy * id; Kxz = cxz * id;
+            Kyy = cyy * id; Kyz = cyz * id; Kzz = czz * id;
+        }
+        // Eq. 62 at k1_eff = 3/tr:  k2 = (8/3)(2 tr - 3) / (4 tr - 3)
+        k2 = p.k2_hbb ? quot(cst<Real>(8, 3) * fma(Real(2), tr, Real(-3)), fma(Real(4), tr, Real(-3))) : p.k2c;
+    } else {
+        Kxx = p.K1[0]; Kxy = p.K1[1]; Kxz = p.K1[2]; Kyy = p.K1[3]; Kyz = p.K1[4]; Kzz = p.K1[5];
+        k2 = p.k2;
+    }
+    // V = k0 B - (K1 - k0 I) M1 + (I - K1/2) dB
+    const Real mx = jx - Bx, my = jy - By, mz = jz - Bz;
+    const Real k0 = p.k0;
+    const Real qx = fma(Kxx - k0, mx, fma(Kxy, my, Kxz * mz));
+    const Real qy = fma(Kxy, mx, fma(Kyy - k0, my, Kyz * mz));
+    const Real qz = fma(Kxz, mx, fma(Kyz, my, (Kzz - k0) * mz));
+    const Real hx = fma(Real(-0.5), fma(Kxx, dBx, fma(Kxy, dBy, Kxz * dBz)), dBx);
+    const Real hy = fma(Real(-0.5), fma(Kxy, dBx, fma(Kyy, dBy, Kyz * dBz)), dBy);
+    const Real hz = fma(Real(-0.5), fma(Kxz, dBx, fma(Kyz, dBy, Kzz * dBz)), dBz);
+    const Real Vx = Real(3) * (fma(k0, Bx, hx) - qx);
+    const Real Vy = Real(3) * (fma(k0, By, hy) - qy);
+    const Real Vz = Real(3) * (fma(k0, Bz, hz) - qz);
+
+    // second-order non-equilibrium moments, H_i pieces
+    const Real cmid = phid + Cm;                                  // C - rs
+    const Real third = cst<Real>(1, 3);
+    const Real Mxx = fma(-third, cmid, Pxx), Myy = fma(-third, cmid, Pyy), Mzz = fma(-third, cmid, Pzz);
+    const Real trM = (Mxx + Myy) + Mzz;
+    const Real t3 = third * trM;
+    const Real kap = cst<Real>(9, 2) * (k2 - k0);
+
+    Real a = k0 * phid;
+    if constexpr (SRC == kSrcReaction || SRC == kSrcRuntime) {
+        if (SRC == kSrcReaction || p.src_kind == kSrcReaction) {
+            const Real Sn = p.react_rate * phi * (Real(1) - (p.react2 ? phi * phi : powr(phi, p.react_exp)));
+            const Real Sp = first ? Sn
+                                  : p.react_rate * phi_prev *
+                                        (Real(1) - (p.react2 ? phi_prev * phi_prev : powr(phi_prev, p.react_exp)));
+            srcv = fma(Real(1.5), Sn, Real(-0.5) * Sp);
+        }
+    }
+    if constexpr (SRC != kSrcNone) a = fma(p.src_val, srcv, a);
+    const Real cC = Real(1.5) * k0 * Cm;                          // (3/2) k0 (C - phi)
+
+    const Real w0 = cst<Real>(1, 3), w1 = cst<Real>(1, 18), w2 = cst<Real>(1, 36);
+    Real r[19];
+    r[0] = w0 * (a - cC + kap * t3);
+    // axis directions: H = M_aa - tr/3
+    const Real bx = w1 * fma(-kap, Mxx - t3, a), by = w1 * fma(-kap, Myy - t3, a), bz = w1 * fma(-kap, Mzz - t3, a);
+    const Real v1x = w1 * Vx, v1y = w1 * Vy, v1z = w1 * Vz;
+    r[1] = bx + v1x; r[2] = bx - v1x;
+    r[3] = by + v1y; r[4] = by - v1y;
+    r[5] = bz + v1z; r[6] = bz - v1z;
+    // face diagonals: H = M_aa + M_bb +- 2 M_ab - tr/3
+    const Real ac = a + cC;
+    const Real bxy = w2 * fma(-kap, (Mxx + Myy) - t3, ac);
+    const Real bxz = w2 * fma(-kap, (Mxx + Mzz) - t3, ac);
+    const Real byz = w2 * fma(-kap, (Myy + Mzz) - t3, ac);
+    const Real pxy = w2 * Real(2) * kap * Pxy, pxz = w2 * Real(2) * kap * Pxz, pyz = w2 * Real(2) * kap * Pyz;
+    const Real vxpy = w2 * (Vx + Vy), vxmy = w2 * (Vx - Vy);
+    const Real vxpz = w2 * (Vx + Vz), vxmz = w2 * (Vx - Vz);
+    const Real vypz = w2 * (Vy + Vz), vymz = w2 * (Vy - Vz);
+    r[7] = (bxy - pxy) + vxpy;  r[10] = (bxy - pxy) - vxpy;
+    r[8] = (bxy + pxy) - vxmy;  r[9] = (bxy + pxy) + vxmy;
+    r[11] = (bxz - pxz) + vxpz; r[14] = (bxz - pxz) - vxpz;
+    r[12] = (bxz + pxz) - vxmz; r[13] = (bxz + pxz) + vxmz;
+    r[15] = (byz - pyz) + vypz; r[18] = (byz - pyz) - vypz;
+    r[16] = (byz + pyz) - vymz; r[17] = (byz + pyz) + vymz;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) d[i] = fma(p.om, d[i], r[i]);
+    return phi;
+}
+
+// Pull of a node with at least one neighbour across the domain boundary.
+template <typename Real, typename S, int SH>
+__device__ __forceinline__ void pull3_boundary(const Sweep3Params<Real> &p, const S *__restrict__ fin, int x, int y,
+                                               int z, int node, Real phi_prev, Real (&d)[19]) {
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        int sx = x - cx3(i), sy = y - cy3(i), sz = z - cz3(i);
+        Real wsum = Real(0);
+        int crossed = 0;
+        if (sx < 0) { if (p.hbb_x) { wsum += p.wall[0]; ++crossed; } else sx += p.nx; }
+        if (sx >= p.nx) { if (p.hbb_x) { wsum += p.wall[1]; ++crossed; } else sx -= p.nx; }
+        if (sy < 0) { if (p.hbb_y) { wsum += p.wall[2]; ++crossed; } else sy += p.ny; }
+        if (sy >= p.ny) { if (p.hbb_y) { wsum += p.wall[3]; ++crossed; } else sy -= p.ny; }
+        if (sz < 0) { if (p.hbb_z) { wsum += p.wall[4]; ++crossed; } else sz += p.nz; }
+        if (sz >= p.nz) { if (p.hbb_z) { wsum += p.wall[5]; ++crossed; } else sz -= p.nz; }
+        if (!crossed) {
+            const int src = sz * p.slab + sy * p.pitch + sx;
+            d[i] = Storage<S>::load(fin[i * p.plane + src]);
+            if constexpr (SH == kShiftLocal)
+                if (i != 0) d[i] = fma(wgt3<Real>(i), p.phi_in[src] - phi_prev, d[i]);
+        } else {
+            const int o = opposite3(i);
+            const int n2 = cx3(i) * cx3(i) + cy3(i) * cy3(i) + cz3(i) * cz3(i);
+            const Real phi_w = (crossed == 1 ? wsum : Real(0.5) * wsum) * p.wall_fac;
+            const Real dout = Storage<S>::load(fin[o * p.plane + node]);
+            Real wt = wall3_term(p, n2, phi_w);
+            if constexpr (SH == kShiftRef) wt = wt - Real(2) * p.wref[n2];
+            if constexpr (SH == kShiftLocal) wt = fma(Real(-2) * wgt3<Real>(i), phi_prev, wt);
+            d[i] = wt - dout;
+        }
+    }
+}
+
+template <typename Real, typename S, int SH, int MODE, int SRC>
+__global__ void __launch_bounds__(256) sweep3_kernel(const __grid_constant__ Sweep3Params<Real> p) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= p.nx || y >= p.ny) return;
+    const S *__restrict__ fin = static_cast<const S *>(p.fin);
+    S *__restrict__ fout = static_cast<S *>(p.fout);
+    const int node = z * p.slab + y * p.pitch + x;
+    const Real phi_prev = p.phi_in[node];
+    Real d[19];
+    if (p.first) {
+        equilibrium3<Real, SH>(p, phi_prev, d);
+    } else if (x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1) {
+#pragma unroll
+        for (int i = 0; i < 19; ++i)
+            d[i] = Storage<S>::load(fin[i * p.plane + node - cz3(i) * p.slab - cy3(i) * p.pitch - cx3(i)]);
+        if constexpr (SH == kShiftLocal) {
+#pragma unroll
+            for (int i = 1; i < 19; ++i)
+                d[i] = fma(wgt3<Real>(i), p.phi_in[node - cz3(i) * p.slab - cy3(i) * p.pitch - cx3(i)] - phi_prev,
+                           d[i]);
+        }
+    } else {
+        pull3_boundary<Real, S, SH>(p, fin, x, y, z, node, phi_prev, d);
+    }
+    Real srcv = Real(0);
+    if constexpr (SRC == kSrcConst) srcv = Real(1);
+    if constexpr (SRC == kSrcField) srcv = p.srcF[node];
+    const Real rs = SH == kShiftLocal ? phi_prev : p.phi_ref;
+    Real phid;
+    const Real phi = collide3<Real, MODE, SRC, SH>(p, d, rs, phi_prev, srcv, p.first != 0, phid);
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        Real v = d[i];
+        if constexpr (SH == kShiftLocal) v = fma(-wgt3<Real>(i), phid, v);
+        fout[i * p.plane + node] = Storage<S>::pack(v);
+    }
+    p.phi_out[node] = phi;
+    if (not_finite(phi)) atomicOr(p.flags, 1);
+}
+
+}  // namespace btrt

@@ -16,7 +16,7 @@ def _declared_symbols():
     for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        for m in re.finditer(r"\b(btrt_[a-z0-9_]+)\s*\(", text):
+        for m in re.finditer(r"\b(btrt3?_[a-z0-9_]+)\s*\(", text):
             names.add(m.group(1))
     return sorted(names)
 
@@ -32,7 +32,8 @@ def lib():
 def test_header_declares_entry_points():
     names = _declared_symbols()
     for expect in ("btrt_create", "btrt_step", "btrt_set_coeffs", "btrt_set_boundary",
-                   "btrt_init_phi", "btrt_read_phi", "btrt_mass", "btrt_workspace_bytes"):
+                   "btrt_init_phi", "btrt_read_phi", "btrt_mass", "btrt_workspace_bytes",
+                   "btrt3_create", "btrt3_step", "btrt3_set_coeffs", "btrt3_read_f"):
         assert expect in names
 
 
