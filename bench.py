@@ -59,6 +59,7 @@ FP64_TRAFFIC_PER_NODE = 149.0
 def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
     hbm = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peak_hbm, "unit": "GB/s",
            "frac": round(achieved_gbs / peak_hbm, 4), "peak_kind": peak_kind,
+           "frac_of_nominal_8tbs": round(achieved_gbs / 8000.0, 4),
            "bytes_per_update": BYTES_PER_UPDATE[args.storage]}
     kernel = f"sweep_kernel<{args.compute},{args.storage}>"
     if args.compute != "f64" or args.workload != "mms":
@@ -494,7 +495,7 @@ def run_serving(args, rates=(100.0, 500.0, 2000.0), count=96, seed=1):
     run to ||phi^{n+1} - phi^n||_2 < 1e-8 (checked every 100 steps) or 20000 steps,
     150 GB admission budget; continuous batching vs sequential plain solves."""
     import workloads as w
-    from paper_1902_09813_gb300.serve import Server, poisson_trace, serve_sequential, summarize
+    from paper_1902_09813_gb300.serve import Server, depth_series, poisson_trace, serve_sequential, summarize
 
     probs = w.batched_instances(count=count, seed=seed, nsteps=0)
     for p in probs:
@@ -506,7 +507,8 @@ def run_serving(args, rates=(100.0, 500.0, 2000.0), count=96, seed=1):
         srv = Server(budget_bytes=150e9, slice_steps=100, max_steps=20000, tol=1e-8)
         res = srv.run(trace)
         out["rates"][str(int(lam))] = dict(summarize(res), peak_active=srv.stats["peak_active"],
-                                           slices=srv.stats["slices"])
+                                           slices=srv.stats["slices"],
+                                           depth_t_active_waiting=depth_series(srv.depth))
     # plain sequential baseline on the first requests of the highest-rate trace
     nseq = min(count, args.serve_seq)
     trace = poisson_trace(probs[:nseq], rate=max(rates), seed=seed)
@@ -524,21 +526,30 @@ def _oracle_sample(n_side: int):
     return p.replace(nx=n_side, ny=n_side)
 
 
-def cpu_baseline(args, seconds: float = 12.0):
+def _oracle_rate(n_side: int, threads: int, seconds: float):
     import oracle
-    cores = _cores()
-    p = _oracle_sample(1024)
-    lat = oracle.OracleLattice(p, nthreads=cores).init()
+    p = _oracle_sample(n_side)
+    lat = oracle.OracleLattice(p, nthreads=threads).init()
     lat.step(1)
     steps, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < seconds:
         lat.step(2)
         steps += 2
     el = time.perf_counter() - t0
-    return {"value": round(p.nx * p.ny * steps / el / 1e6, 3), "unit": "MLUPS", "cores": cores,
-            "kind": "oracle",
+    return p, steps, el, p.nx * p.ny * steps / el / 1e6
+
+
+def cpu_baseline(args, seconds: float = 12.0):
+    """The FP64 oracle on the host cores (all of them, OpenMP over rows), plus a
+    short single-thread sample."""
+    cores = _cores()
+    p, steps, el, mlups = _oracle_rate(1024, cores, seconds)
+    _, steps1, el1, mlups1 = _oracle_rate(256, 1, 4.0)
+    return {"value": round(mlups, 3), "unit": "MLUPS", "cores": cores, "kind": "oracle",
+            "single_thread_mlups": round(mlups1, 3),
             "sample": f"{p.nx}x{p.ny} patch of the benchmark lattice (same dx, dt, coefficients, "
-                      f"walls), {steps} steps, {el:.1f} s, OpenMP over rows"}
+                      f"walls), {steps} steps, {el:.1f} s, OpenMP over rows; single thread: 256x256 patch, "
+                      f"{steps1} steps, {el1:.1f} s"}
 
 
 def run_reference(args):

@@ -193,7 +193,8 @@ void step_scalars3(btrt3_lattice L, int64_t n, bool first, double *src_val, doub
 
 int mode3(btrt3_lattice L) {
     const btrt3_coeffs &c = L->c;
-    return (c.b2 == 0.0 && c.c3 == 0.0 && c.a2 == 0.0) ? kLinear : kGeneral;
+    if (c.b2 != 0.0 || c.c3 != 0.0 || c.a2 != 0.0) return kGeneral;
+    return c.k0 == 1.0 ? kLinearK0One : kLinear;
 }
 
 template <typename Real>
@@ -234,6 +235,16 @@ void fill3(btrt3_lattice L, Sweep3Params<Real> &p, int64_t n, bool first) {
     for (int k = 0; k < 6; ++k) {
         p.A0[k] = (Real)L->A0[k];
         p.K1[k] = (Real)L->K1[k];
+    }
+    {
+        // constant-coefficient fold: K1 u and (I - K1/2) u
+        const double *K = L->K1, *u = L->u;
+        const double Ku[3] = {K[0] * u[0] + K[1] * u[1] + K[2] * u[2], K[1] * u[0] + K[3] * u[1] + K[4] * u[2],
+                              K[2] * u[0] + K[4] * u[1] + K[5] * u[2]};
+        for (int k = 0; k < 3; ++k) {
+            p.Ku[k] = (Real)Ku[k];
+            p.gu[k] = (Real)(u[k] - 0.5 * Ku[k]);
+        }
     }
     p.a2 = (Real)c.a2;
     p.k0 = (Real)c.k0;

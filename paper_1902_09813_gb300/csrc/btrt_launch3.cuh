@@ -28,6 +28,7 @@ inline void launch3_src(const Sweep3Params<Real> &p, cudaStream_t s) {
 template <typename Real, typename S, int SH>
 inline cudaError_t launch3_mode(const Sweep3Params<Real> &p, int mode, cudaStream_t s) {
     if (mode == kGeneral) launch3_src<Real, S, SH, kGeneral>(p, s);
+    else if (mode == kLinearK0One) launch3_src<Real, S, SH, kLinearK0One>(p, s);
     else launch3_src<Real, S, SH, kLinear>(p, s);
     return cudaGetLastError();
 }

@@ -413,7 +413,19 @@ template <> struct RowsPerThread<float, float> {
     static constexpr int value = BTRT_ROWS_S32;
     static constexpr bool unroll = BTRT_UNROLL_S32 != 0;
 };
-template <> struct RowsPerThread<double, double> { static constexpr int value = 4; static constexpr bool unroll = false; };
+#ifndef BTRT_ROWS_F64
+#define BTRT_ROWS_F64 4
+#endif
+#ifndef BTRT_MINBLOCKS_F64
+#define BTRT_MINBLOCKS_F64 0
+#endif
+template <> struct RowsPerThread<double, double> {
+    static constexpr int value = BTRT_ROWS_F64;
+    static constexpr bool unroll = false;
+};
+// Minimum resident blocks per SM requested from the compiler (register budget).
+template <typename Real> struct MinBlocks { static constexpr int value = 0; };
+template <> struct MinBlocks<double> { static constexpr int value = BTRT_MINBLOCKS_F64; };
 template <> struct RowsPerThread<dw, dw> { static constexpr int value = 1; static constexpr bool unroll = false; };
 
 // Global loads of data that other SMs rewrite during a persistent launch go
@@ -578,7 +590,7 @@ __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, 
 // One sweep of one lattice: 32 x 8 threads per block, each thread sweeps
 // RowsPerThread nodes of its column, rows blockDim.y apart.
 template <typename Real, typename S, int SH, int MODE, int SRC>
-__global__ void __launch_bounds__(256) sweep_kernel(const __grid_constant__ SweepParams<Real> p) {
+__global__ void __launch_bounds__(256, MinBlocks<Real>::value) sweep_kernel(const __grid_constant__ SweepParams<Real> p) {
     constexpr int R = RowsPerThread<Real, S>::value;
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int ybase = blockIdx.y * blockDim.y * R + threadIdx.y;

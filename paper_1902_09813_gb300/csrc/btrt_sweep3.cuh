@@ -79,6 +79,8 @@ struct Sweep3Params {
     Real k2c;
     Real K1[6];            // constant K1 (symmetric) and k2 when A is constant
     Real k2;
+    Real Ku[3];            // constant-coefficient fold: K1 u (B = u phi)
+    Real gu[3];            //   and (I - K1/2) u
     Real cond_limit;       // FP32: tr^3 > cond_limit det -> invert in FP64
 
     int src_kind;          // 0 none, 1 const, 3 per-node field, 4 reaction
@@ -149,8 +151,7 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
     // coefficients
     Real Bx, By, Bz, dBx, dBy, dBz, Cm = Real(0);
     if constexpr (MODE != kGeneral) {
-        Bx = p.ux * phi; By = p.uy * phi; Bz = p.uz * phi;
-        dBx = p.ux * dphi; dBy = p.uy * dphi; dBz = p.uz * dphi;
+        Bx = By = Bz = dBx = dBy = dBz = Real(0);   // folded into Ku, gu below
     } else if (p.bq2) {
         const Real p2 = phi * phi;
         Bx = fma(p.ux, phi, p.bgx * p2);
@@ -207,18 +208,30 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
         Kxx = p.K1[0]; Kxy = p.K1[1]; Kxz = p.K1[2]; Kyy = p.K1[3]; Kyz = p.K1[4]; Kzz = p.K1[5];
         k2 = p.k2;
     }
-    // V = k0 B - (K1 - k0 I) M1 + (I - K1/2) dB
-    const Real mx = jx - Bx, my = jy - By, mz = jz - Bz;
+    // V = k0 B - (K1 - k0 I) M1 + (I - K1/2) dB (times 3 below)
     const Real k0 = p.k0;
-    const Real qx = fma(Kxx - k0, mx, fma(Kxy, my, Kxz * mz));
-    const Real qy = fma(Kxy, mx, fma(Kyy - k0, my, Kyz * mz));
-    const Real qz = fma(Kxz, mx, fma(Kyz, my, (Kzz - k0) * mz));
-    const Real hx = fma(Real(-0.5), fma(Kxx, dBx, fma(Kxy, dBy, Kxz * dBz)), dBx);
-    const Real hy = fma(Real(-0.5), fma(Kxy, dBx, fma(Kyy, dBy, Kyz * dBz)), dBy);
-    const Real hz = fma(Real(-0.5), fma(Kxz, dBx, fma(Kyz, dBy, Kzz * dBz)), dBz);
-    const Real Vx = Real(3) * (fma(k0, Bx, hx) - qx);
-    const Real Vy = Real(3) * (fma(k0, By, hy) - qy);
-    const Real Vz = Real(3) * (fma(k0, Bz, hz) - qz);
+    Real Vx, Vy, Vz;
+    if constexpr (MODE == kGeneral) {
+        const Real mx = jx - Bx, my = jy - By, mz = jz - Bz;
+        const Real qx = fma(Kxx - k0, mx, fma(Kxy, my, Kxz * mz));
+        const Real qy = fma(Kxy, mx, fma(Kyy - k0, my, Kyz * mz));
+        const Real qz = fma(Kxz, mx, fma(Kyz, my, (Kzz - k0) * mz));
+        const Real hx = fma(Real(-0.5), fma(Kxx, dBx, fma(Kxy, dBy, Kxz * dBz)), dBx);
+        const Real hy = fma(Real(-0.5), fma(Kxy, dBx, fma(Kyy, dBy, Kyz * dBz)), dBy);
+        const Real hz = fma(Real(-0.5), fma(Kxz, dBx, fma(Kyz, dBy, Kzz * dBz)), dBz);
+        Vx = Real(3) * (fma(k0, Bx, hx) - qx);
+        Vy = Real(3) * (fma(k0, By, hy) - qy);
+        Vz = Real(3) * (fma(k0, Bz, hz) - qz);
+    } else {
+        // constant K1, B = u phi: V = K1 u phi - (K1 - k0 I) j + (I - K1/2) u dphi
+        (void)Bx; (void)By; (void)Bz; (void)dBx; (void)dBy; (void)dBz;
+        const Real qx = fma(Kxx - k0, jx, fma(Kxy, jy, Kxz * jz));
+        const Real qy = fma(Kxy, jx, fma(Kyy - k0, jy, Kyz * jz));
+        const Real qz = fma(Kxz, jx, fma(Kyz, jy, (Kzz - k0) * jz));
+        Vx = Real(3) * (fma(p.gu[0], dphi, fma(p.Ku[0], phi, -qx)));
+        Vy = Real(3) * (fma(p.gu[1], dphi, fma(p.Ku[1], phi, -qy)));
+        Vz = Real(3) * (fma(p.gu[2], dphi, fma(p.Ku[2], phi, -qz)));
+    }
 
     // second-order non-equilibrium moments, H_i pieces
     const Real cmid = phid + Cm;                                  // C - rs
@@ -228,7 +241,7 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
     const Real t3 = third * trM;
     const Real kap = cst<Real>(9, 2) * (k2 - k0);
 
-    Real a = k0 * phid;
+    Real a = MODE == kLinearK0One ? phid : k0 * phid;
     if constexpr (SRC == kSrcReaction || SRC == kSrcRuntime) {
         if (SRC == kSrcReaction || p.src_kind == kSrcReaction) {
             const Real Sn = p.react_rate * phi * (Real(1) - (p.react2 ? phi * phi : powr(phi, p.react_exp)));
@@ -265,8 +278,13 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
     r[12] = (bxz + pxz) - vxmz; r[13] = (bxz + pxz) + vxmz;
     r[15] = (byz - pyz) + vypz; r[18] = (byz - pyz) - vypz;
     r[16] = (byz + pyz) - vymz; r[17] = (byz + pyz) + vymz;
+    if constexpr (MODE == kLinearK0One) {
 #pragma unroll
-    for (int i = 0; i < 19; ++i) d[i] = fma(p.om, d[i], r[i]);
+        for (int i = 0; i < 19; ++i) d[i] = r[i];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 19; ++i) d[i] = fma(p.om, d[i], r[i]);
+    }
     return phi;
 }
 

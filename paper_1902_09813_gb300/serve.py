@@ -62,6 +62,7 @@ class Server:
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.tiles = tiles
         self.stats = dict(slices=0, rebuilds=0, peak_active=0, peak_bytes=0)
+        self.depth = []        # (t, active, waiting) at every slice
 
     def run(self, trace) -> List[Result]:
         """trace: list of (arrival_seconds, problem), arrival-sorted.  Runs in real
@@ -108,6 +109,7 @@ class Server:
             batch.step(self.slice_steps, residual=True)
             res = batch.residuals()          # synchronises
             self.stats["slices"] += 1
+            self.depth.append((round(time.perf_counter() - t0, 4), len(active), len(waiting) + len(pending)))
             done_idx = []
             for k, a in enumerate(active):
                 a[5] += self.slice_steps
@@ -162,6 +164,17 @@ def poisson_trace(problems, rate: float, seed: int = 0):
     rng = np.random.default_rng(seed)
     t = np.cumsum(rng.exponential(1.0 / rate, size=len(problems)))
     return [(float(a), p) for a, p in zip(t, problems)]
+
+
+def depth_series(depth, points: int = 16) -> list:
+    """Queue depth over time, thinned to about `points` samples: [t, active, waiting]."""
+    if not depth:
+        return []
+    stride = max(1, len(depth) // points)
+    out = [list(d) for d in depth[::stride]]
+    if out[-1] != list(depth[-1]):
+        out.append(list(depth[-1]))
+    return out
 
 
 def summarize(results: List[Result]) -> dict:

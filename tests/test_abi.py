@@ -98,3 +98,38 @@ def test_create_rejects_null_workspace(lib):
 
 def test_version(lib):
     assert b"sm_103a" in lib.btrt_version()
+
+
+def _desc3(**kw):
+    from paper_1902_09813_gb300.lattice3 import grid_desc3
+    base = dict(nx=32, ny=24, nz=16, dx=1.0, dt=1.0, bc=(0, 0, 1, 1, 0, 0), compute="f64", storage="f64")
+    base.update(kw)
+    return grid_desc3(**base)
+
+
+def test_d3q19_workspace_layout(lib):
+    d = _desc3()
+    n = lib.btrt3_workspace_bytes(ctypes.byref(d))
+    plane = 64 * 24 * 16
+    assert n >= 2 * 19 * plane * 8 + 2 * plane * 8 and n % 256 == 0
+    d16 = _desc3(compute="f32", storage="f16", shift="local")
+    assert 0 < lib.btrt3_workspace_bytes(ctypes.byref(d16)) < n
+
+
+@pytest.mark.parametrize("kw", [dict(nz=2), dict(nx=1), dict(bc=(0, 1, 0, 0, 0, 0)), dict(bc=(0, 0, 0, 0, 1, 0)),
+                                dict(compute="df64", storage="df64"), dict(compute="f32", storage="f64"),
+                                dict(compute="f64", storage="f16"), dict(dx=0.0),
+                                dict(nx=1024, ny=1024, nz=200)])
+def test_invalid_d3q19_descriptions_rejected(lib, kw):
+    d = _desc3(**kw)
+    assert lib.btrt3_workspace_bytes(ctypes.byref(d)) == 0
+    assert len(lib.btrt_last_error()) > 0
+
+
+def test_d3q19_rejects_unknown_shift_and_fields(lib):
+    d = _desc3(compute="f32", storage="f16")
+    d.shift = 3
+    assert lib.btrt3_workspace_bytes(ctypes.byref(d)) == 0
+    d = _desc3()
+    d.fields = 2      # no diffusion-field planes in 3-D
+    assert lib.btrt3_workspace_bytes(ctypes.byref(d)) == 0
