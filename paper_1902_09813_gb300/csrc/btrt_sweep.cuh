@@ -423,9 +423,14 @@ template <> struct RowsPerThread<double, double> {
     static constexpr int value = BTRT_ROWS_F64;
     static constexpr bool unroll = false;
 };
-// Minimum resident blocks per SM requested from the compiler (register budget).
+#ifndef BTRT_MINBLOCKS_F32
+#define BTRT_MINBLOCKS_F32 0
+#endif
+// Minimum resident blocks per SM requested from the compiler (register budget);
+// 0 leaves the choice to the compiler.
 template <typename Real> struct MinBlocks { static constexpr int value = 0; };
 template <> struct MinBlocks<double> { static constexpr int value = BTRT_MINBLOCKS_F64; };
+template <> struct MinBlocks<float> { static constexpr int value = BTRT_MINBLOCKS_F32; };
 template <> struct RowsPerThread<dw, dw> { static constexpr int value = 1; static constexpr bool unroll = false; };
 
 // Global loads of data that other SMs rewrite during a persistent launch go
