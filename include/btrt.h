@@ -175,7 +175,8 @@ btrt_status btrt_mass(btrt_lattice L, double *out);
 
 /* Flags raised by the sweep since the last btrt_init_phi: bit 0 = some node
  * produced a NaN/Inf phi (returns BTRT_EUNSTABLE), bit 2 = a bounded wait for a
- * tile copy gave up (returns BTRT_ETIMEOUT).  Synchronises. */
+ * tile copy gave up (returns BTRT_ETIMEOUT), bit 3 = an index check of a
+ * -DBTRT_DEBUG_BOUNDS build failed (returns BTRT_ECUDA).  Synchronises. */
 btrt_status btrt_check(btrt_lattice L, int32_t *flags);
 
 /* Kernel form of the ordinary FP32-compute sweep: BTRT_SWEEP_AUTO (default: the
@@ -243,9 +244,15 @@ btrt_status btrt_batch_step(btrt_batch B, int64_t nsteps, int32_t want_residual)
 /* Residuals of the last step with want_residual, one per member (host, synchronises). */
 btrt_status btrt_batch_residuals(btrt_batch B, double *out_host);
 
-/* flags: bit 0 non-finite phi in some member, bit 1 a barrier wait gave up.
+/* flags: bit 0 non-finite phi in some member, bit 1 a barrier wait gave up,
+ * bit 3 an index check of a -DBTRT_DEBUG_BOUNDS build failed (BTRT_ECUDA).
  * Returns BTRT_ETIMEOUT or BTRT_EUNSTABLE accordingly.  Synchronises. */
 btrt_status btrt_batch_check(btrt_batch B, int32_t *flags);
+
+/* Each member's device flags (bit 0: non-finite phi), in member order, into
+ * out_host[n]: lets a caller retire only the members that failed.  Synchronises
+ * the batch stream. */
+btrt_status btrt_batch_member_flags(btrt_batch B, int32_t *out_host);
 
 /* Bound of every grid-barrier wait, in polls of about 0.1 us (default 2^24).  A
  * wait that reaches it raises flag bit 1 and ends the launch early.

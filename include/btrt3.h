@@ -103,7 +103,8 @@ btrt_status btrt3_read_f(btrt3_lattice L, double *dst, int32_t x0, int32_t y0, i
 /* FP64 sum of phi over the box (fixed-order reduction).  Synchronises. */
 btrt_status btrt3_mass(btrt3_lattice L, double *out);
 
-/* Device flags (bit 0: a non-finite phi was produced -> BTRT_EUNSTABLE).  Synchronises. */
+/* Device flags (bit 0: a non-finite phi was produced -> BTRT_EUNSTABLE; bit 3: an
+ * index check of a -DBTRT_DEBUG_BOUNDS build failed -> BTRT_ECUDA).  Synchronises. */
 btrt_status btrt3_check(btrt3_lattice L, int32_t *flags);
 
 /* Steps taken since btrt3_init_phi and the current time t0 + step dt. */

@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import ctypes
+import os
 from pathlib import Path
 
 LIB_PATH = Path(__file__).resolve().parent / "_lib" / "libbtrt.so"
@@ -105,6 +106,7 @@ SIGNATURES = [
     ("btrt_batch_step", ctypes.c_int, [_vp, _i64, _i32]),
     ("btrt_batch_residuals", ctypes.c_int, [_vp, _dp]),
     ("btrt_batch_check", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    ("btrt_batch_member_flags", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     ("btrt_batch_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_uint64, _i32]),
     ("btrt_batch_destroy", ctypes.c_int, [_vp]),
     ("btrt_phi_sum_static", ctypes.c_int, [_vp, _i32, _i32, _i32, _i64, _vp, _dp]),
@@ -132,10 +134,13 @@ def load():
     fallback implementation."""
     global _lib
     if _lib is None:
-        if not LIB_PATH.exists():
-            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+        # BTRT_LIBRARY selects another build of the same library (the index-checked
+        # debug build in the tests); unset, the in-tree build is used
+        path = Path(os.environ.get("BTRT_LIBRARY") or LIB_PATH)
+        if not path.exists():
+            raise RuntimeError(f"{path} is missing: build it with "
                                "`python -c 'import __graft_entry__ as g; g.build()'`")
-        lib = ctypes.CDLL(str(LIB_PATH))
+        lib = ctypes.CDLL(str(path))
         for name, res, args in SIGNATURES:
             fn = getattr(lib, name)
             fn.restype = res

@@ -40,18 +40,21 @@ def _deps():
     return list(CSRC.glob("*")) + list((ROOT / "include").glob("*.h")) + [Path(__file__)]
 
 
-def up_to_date() -> bool:
-    if not LIB.exists():
+def up_to_date(lib: Path = LIB) -> bool:
+    if not lib.exists():
         return False
-    t = LIB.stat().st_mtime
+    t = lib.stat().st_mtime
     return all(p.stat().st_mtime <= t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra=None) -> Path:
-    if not force and up_to_date():
-        return LIB
-    OUT.mkdir(exist_ok=True)
-    objdir = OUT / "obj"
+def build(force: bool = False, verbose: bool = False, extra=None, lib: Path = LIB) -> Path:
+    """Compile every csrc/*.cu and link `lib`.  `extra` adds nvcc flags (for example
+    -DBTRT_DEBUG_BOUNDS for the index-checked build, linked to another path)."""
+    lib = Path(lib)
+    if not force and up_to_date(lib):
+        return lib
+    lib.parent.mkdir(parents=True, exist_ok=True)
+    objdir = lib.parent / "obj"
     objdir.mkdir(exist_ok=True)
     flags = NVCC_FLAGS + list(extra or [])
 
@@ -67,14 +70,23 @@ def build(force: bool = False, verbose: bool = False, extra=None) -> Path:
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 2)) as ex:
         objs = list(ex.map(compile_one, _sources()))
-    tmp = str(LIB) + ".tmp"
+    tmp = str(lib) + ".tmp"
     # --no-undefined: a missing template instantiation fails the build, not the first dlopen
     cmd = [nvcc(), "-shared", "-o", tmp] + [str(o) for o in objs] + ARCH + ["-lcudart", "-Xlinker", "--no-undefined"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
+
+
+DEBUG_LIB = OUT / "debug" / "libbtrt.so"
+
+
+def build_debug(force: bool = False) -> Path:
+    """The index-checked build (every global access of the sweeps checks its index
+    and raises flag bit 3 instead of faulting), for tests on tiny grids."""
+    return build(force=force, extra=["-DBTRT_DEBUG_BOUNDS"], lib=DEBUG_LIB)
 
 
 if __name__ == "__main__":

@@ -472,6 +472,7 @@ btrt_status btrt3_set_source_field(btrt3_lattice L, const double *F) {
 }
 
 btrt_status btrt3_init_phi(btrt3_lattice L, const void *phi0, int32_t dtype, int32_t on_device, double t0) {
+    NvtxRange range("btrt3_init_phi");
     if (!L || !phi0) return fail3(BTRT_EINVAL, "null argument");
     if (!L->have_coeffs) return fail3(BTRT_ESTATE, "btrt3_set_coeffs must come before btrt3_init_phi");
     if (L->c.src_kind == BTRT_SRC_FIELD && !L->have_srcf)
@@ -492,6 +493,7 @@ btrt_status btrt3_init_phi(btrt3_lattice L, const void *phi0, int32_t dtype, int
 }
 
 btrt_status btrt3_step(btrt3_lattice L, int64_t nsteps) {
+    NvtxRange range("btrt3_step");
     if (!L) return fail3(BTRT_EINVAL, "null lattice");
     if (!L->ready) return fail3(BTRT_ESTATE, "lattice not initialised");
     if (nsteps < 0) return fail3(BTRT_EINVAL, "negative step count");
@@ -571,6 +573,7 @@ btrt_status btrt3_check(btrt3_lattice L, int32_t *flags) {
     if (!L || !flags) return fail3(BTRT_EINVAL, "null argument");
     CUDA3_TRY(cudaMemcpyAsync(flags, L->flags(), sizeof(int32_t), cudaMemcpyDeviceToHost, L->stream));
     CUDA3_TRY(cudaStreamSynchronize(L->stream));
+    if (*flags & 8) return fail3(BTRT_ECUDA, "an index check of the debug build failed (flag bit 3)");
     if (*flags & 1) return fail3(BTRT_EUNSTABLE, "non-finite phi detected (unstable parameters?)");
     return BTRT_OK;
 }

@@ -685,6 +685,7 @@ btrt_status btrt_set_diffusion_field(btrt_lattice L, const double *Axx, const do
 }
 
 btrt_status btrt_init_phi(btrt_lattice L, const void *phi0, int32_t dtype, int32_t on_device, double t0) {
+    NvtxRange range("btrt_init_phi");
     if (!L || !phi0) return fail(BTRT_EINVAL, "null argument");
     if (!L->have_coeffs) return fail(BTRT_ESTATE, "btrt_set_coeffs must come before btrt_init_phi");
     if (L->c.src_kind == BTRT_SRC_FIELD && !L->have_srcf)
@@ -706,6 +707,7 @@ btrt_status btrt_init_phi(btrt_lattice L, const void *phi0, int32_t dtype, int32
 }
 
 btrt_status btrt_step(btrt_lattice L, int64_t nsteps) {
+    NvtxRange range("btrt_step");
     if (!L) return fail(BTRT_EINVAL, "null lattice");
     if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
     if (nsteps < 0) return fail(BTRT_EINVAL, "negative step count");
@@ -719,6 +721,7 @@ btrt_status btrt_step(btrt_lattice L, int64_t nsteps) {
 }
 
 btrt_status btrt_step_residual(btrt_lattice L, int64_t nsteps, double *residual) {
+    NvtxRange range("btrt_step_residual");
     if (!L || !residual) return fail(BTRT_EINVAL, "null argument");
     if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
     if (nsteps < 1) return fail(BTRT_EINVAL, "btrt_step_residual needs at least one step");
@@ -808,6 +811,7 @@ btrt_status btrt_check(btrt_lattice L, int32_t *flags) {
     if (!L || !flags) return fail(BTRT_EINVAL, "null argument");
     CUDA_TRY(cudaMemcpyAsync(flags, L->flags(), sizeof(int32_t), cudaMemcpyDeviceToHost, L->stream));
     CUDA_TRY(cudaStreamSynchronize(L->stream));
+    if (*flags & 8) return fail(BTRT_ECUDA, "an index check of the debug build failed (flag bit 3)");
     if (*flags & 4) return fail(BTRT_ETIMEOUT, "a bounded wait for a tile copy gave up");
     if (*flags & 1) return fail(BTRT_EUNSTABLE, "non-finite phi detected (unstable parameters?)");
     return BTRT_OK;

@@ -166,6 +166,13 @@ __global__ void __launch_bounds__(256) batch_step_kernel(const __grid_constant__
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, SH, false>(a, t, k, resid, sp, red);
 }
 
+// Each member's device flags (bit 0: non-finite phi) gathered into one array.
+template <typename Real>
+__global__ void gather_member_flags(const BatchMember<Real> *members, int n, int *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = *members[k].p.flags;
+}
+
 // Per-member residual: fixed-order sum of its tiles' partials, then sqrt.
 __global__ void __launch_bounds__(256) member_residual(const double *tile_partials, const int *tile_begin,
                                                        const int *tile_count, double *out) {
@@ -227,7 +234,7 @@ size_t member_bytes(int compute) {
 }
 
 struct BatchLayout {
-    size_t off_members, off_tiles, off_partials, off_resid, off_tbeg, off_tcnt, off_vals, off_sync, total;
+    size_t off_members, off_tiles, off_partials, off_resid, off_tbeg, off_tcnt, off_vals, off_mflags, off_sync, total;
 };
 
 BatchLayout batch_layout(const std::vector<btrt_lattice> &m) {
@@ -249,6 +256,8 @@ BatchLayout batch_layout(const std::vector<btrt_lattice> &m) {
     off += up256(n * sizeof(int));
     b.off_vals = off;
     off += up256(n * (size_t)kMaxSliceSteps * 2 * (m[0]->g.compute == BTRT_F64 ? 8 : 4));
+    b.off_mflags = off;
+    off += up256(n * sizeof(int));
     b.off_sync = off;
     off += 256;
     b.total = off;
@@ -539,6 +548,7 @@ btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y,
 }
 
 btrt_status btrt_batch_step(btrt_batch B, int64_t nsteps, int32_t want_residual) {
+    NvtxRange range("btrt_batch_step");
     if (!B) return bfail(BTRT_EINVAL, "null batch");
     if (nsteps < 0) return bfail(BTRT_EINVAL, "negative step count");
     while (nsteps > 0) {
@@ -588,8 +598,26 @@ btrt_status btrt_batch_check(btrt_batch B, int32_t *flags) {
         f |= v;
     }
     *flags = f | e;
+    if (f & 8) return bfail(BTRT_ECUDA, "an index check of the debug build failed (flag bit 3)");
     if (e & 2) return bfail(BTRT_ETIMEOUT, "a grid barrier wait gave up (limit %llu polls)", B->wait_limit);
     if (f & 1) return bfail(BTRT_EUNSTABLE, "non-finite phi in a batch member");
+    return BTRT_OK;
+}
+
+btrt_status btrt_batch_member_flags(btrt_batch B, int32_t *out_host) {
+    if (!B || !out_host) return bfail(BTRT_EINVAL, "null argument");
+    const int n = (int)B->members.size();
+    int *dflags = reinterpret_cast<int *>(B->ws + B->lay.off_mflags);
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (B->compute == BTRT_F64)
+        gather_member_flags<double><<<grid, 256, 0, B->stream>>>(
+            reinterpret_cast<const BatchMember<double> *>(B->ws + B->lay.off_members), n, dflags);
+    else
+        gather_member_flags<float><<<grid, 256, 0, B->stream>>>(
+            reinterpret_cast<const BatchMember<float> *>(B->ws + B->lay.off_members), n, dflags);
+    BCUDA(cudaGetLastError());
+    BCUDA(cudaMemcpyAsync(out_host, dflags, n * sizeof(int), cudaMemcpyDeviceToHost, B->stream));
+    BCUDA(cudaStreamSynchronize(B->stream));
     return BTRT_OK;
 }
 
@@ -604,6 +632,7 @@ btrt_status btrt_batch_set_wait_limit(btrt_batch B, uint64_t polls, int32_t neve
 
 btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *block_x, int32_t *block_y,
                                 int32_t *rows, int32_t *per_step_launch) {
+    NvtxRange range("btrt_batch_autotune");
     if (!B) return bfail(BTRT_EINVAL, "null batch");
     if (steps_per_trial < 1) return bfail(BTRT_EINVAL, "steps_per_trial must be >= 1");
     long long nodes = 0;

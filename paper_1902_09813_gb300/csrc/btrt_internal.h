@@ -3,6 +3,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stddef.h>
 #include <stdint.h>
 
@@ -114,5 +115,14 @@ cudaError_t launch_sweep_f32(const SweepParams<float> &p, int storage, int shift
 
 // Record the thread-local message returned by btrt_last_error (printf format).
 void set_last_error(const char *fmt, ...);
+
+// NVTX range around a host entry point (visible in Nsight timelines; no cost
+// beyond a function-pointer test when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 }  // namespace btrt

@@ -53,6 +53,24 @@ template <> struct Storage<__nv_bfloat16> {
     static __device__ __forceinline__ __nv_bfloat16 pack(float v) { return __float2bfloat16_rn(v); }
 };
 
+// ---------------------------------------------------------------- debug index checks
+// Built with -DBTRT_DEBUG_BOUNDS, every global access of the sweeps checks its
+// element index against the array's extent; an index outside it raises flag
+// bit 3 and the access goes to element 0 instead (no fault, no trap).  The
+// ordinary build compiles the check away.
+#ifdef BTRT_DEBUG_BOUNDS
+__device__ __forceinline__ long long checked_index(int *flags, long long idx, long long n) {
+    if (idx < 0 || idx >= n) {
+        atomicOr(flags, 8);
+        return 0;
+    }
+    return idx;
+}
+#define BTRT_IX(flags, idx, n) ::btrt::checked_index((flags), (long long)(idx), (long long)(n))
+#else
+#define BTRT_IX(flags, idx, n) (idx)
+#endif
+
 // ---------------------------------------------------------------- parameters
 // Per-lattice constants of the folded collision (see collide_fold), computed on
 // the host in FP64.  kap = (9/2)(k2 - k0).
@@ -137,7 +155,7 @@ __device__ __forceinline__ Real wall_term(const SweepParams<Real> &p, int i, Rea
 template <typename Real>
 __device__ __forceinline__ Real wall_value(const SweepParams<Real> &p, int side, int idx) {
     const Real *a = p.wall_arr[side];
-    return (a ? a[idx] : p.wall_const[side]) * p.wall_fac;
+    return (a ? a[BTRT_IX(p.flags, idx, side < 2 ? p.ny : p.nx)] : p.wall_const[side]) * p.wall_fac;
 }
 
 // Division: IEEE in FP64; the fast reciprocal-based quotient (about 2 ulp) in FP32,
@@ -257,9 +275,9 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
         const Real s3 = fma(L.a2x3, phi * phi, Real(3));
         Real a0xx = p.A0xx, a0xy = p.A0xy, a0yy = p.A0yy;
         if (p.Af) {   // spatially varying tensor A(x)
-            a0xx = p.Af[node];
-            a0xy = p.Af[p.plane + node];
-            a0yy = p.Af[2 * p.plane + node];
+            a0xx = p.Af[BTRT_IX(p.flags, node, p.plane)];
+            a0xy = p.Af[BTRT_IX(p.flags, p.plane + node, 3 * p.plane)];
+            a0yy = p.Af[BTRT_IX(p.flags, 2 * p.plane + node, 3 * p.plane)];
         }
         const Real mxx = fma(s3, a0xx, Real(0.5));
         const Real mxy = s3 * a0xy;
@@ -458,9 +476,9 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
         if (sy >= p.ny) { if (p.hbb_y) wy = 3; else sy -= p.ny; }
         if (wx < 0 && wy < 0) {
             const int src = sy * p.pitch + sx;
-            d[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + src)));
+            d[i] = Storage<S>::load(ldg<L2ONLY>(fin + BTRT_IX(p.flags, i * p.plane + src, 9 * p.plane)));
             if constexpr (SH == kShiftLocal)
-                if (i != 0) d[i] = fma(wgt<Real>(i), ldg<L2ONLY>(p.phi_in + src) - phi_prev, d[i]);
+                if (i != 0) d[i] = fma(wgt<Real>(i), ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, src, p.plane)) - phi_prev, d[i]);
         } else {
             const int o = opp_of(i);
             Real phi_w;
@@ -470,7 +488,7 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
                 phi_w = wall_value(p, wy, x);
             else
                 phi_w = wall_value(p, wx, y);
-            const Real dout = Storage<S>::load(ldg<L2ONLY>(fin + (o * p.plane + node)));
+            const Real dout = Storage<S>::load(ldg<L2ONLY>(fin + BTRT_IX(p.flags, o * p.plane + node, 9 * p.plane)));
             // f_i = -f_o^+ + wall term; in shifted form the two shifts add up to -2 w_i rs
             // (for the local shift f_o^+ was stored relative to this node's own phi^{n-1} = rs)
             Real wt = wall_term(p, o, phi_w);
@@ -486,12 +504,12 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
 template <typename Real, int SRC>
 __device__ __forceinline__ Real source_at(const SweepParams<Real> &p, Real xs, Real xc, int y, int node) {
     if constexpr (SRC == kSrcConst) return Real(1);
-    else if constexpr (SRC == kSrcTrig) return fma(xs, p.Ys[y], xc * p.Yc[y]);
-    else if constexpr (SRC == kSrcField) return p.srcF[node];
+    else if constexpr (SRC == kSrcTrig) return fma(xs, p.Ys[BTRT_IX(p.flags, y, p.ny)], xc * p.Yc[BTRT_IX(p.flags, y, p.ny)]);
+    else if constexpr (SRC == kSrcField) return p.srcF[BTRT_IX(p.flags, node, p.plane)];
     else if constexpr (SRC == kSrcRuntime) {
         if (p.src_kind == kSrcConst) return Real(1);
-        if (p.src_kind == kSrcTrig) return fma(xs, p.Ys[y], xc * p.Yc[y]);
-        if (p.src_kind == kSrcField) return p.srcF[node];
+        if (p.src_kind == kSrcTrig) return fma(xs, p.Ys[BTRT_IX(p.flags, y, p.ny)], xc * p.Yc[BTRT_IX(p.flags, y, p.ny)]);
+        if (p.src_kind == kSrcField) return p.srcF[BTRT_IX(p.flags, node, p.plane)];
         return Real(0);
     } else return Real(0);
 }
@@ -502,17 +520,20 @@ __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int
                                           Real &phi_prev) {
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
     const int node = y * p.pitch + x;
-    phi_prev = ldg<L2ONLY>(p.phi_in + node);
+    phi_prev = ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, node, p.plane));
     if (p.first) {
         equilibrium<Real, SH>(p, phi_prev, f);
     } else if (x_inner && y > 0 && y < p.ny - 1) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            f[i] = Storage<S>::load(ldg<L2ONLY>(fin + (i * p.plane + node - ey_of(i) * p.pitch - ex_of(i))));
+            f[i] = Storage<S>::load(
+                ldg<L2ONLY>(fin + BTRT_IX(p.flags, i * p.plane + node - ey_of(i) * p.pitch - ex_of(i), 9 * p.plane)));
         if constexpr (SH == kShiftLocal) {
 #pragma unroll
             for (int i = 1; i < 9; ++i)
-                f[i] = fma(wgt<Real>(i), ldg<L2ONLY>(p.phi_in + (node - ey_of(i) * p.pitch - ex_of(i))) - phi_prev,
+                f[i] = fma(wgt<Real>(i),
+                           ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, node - ey_of(i) * p.pitch - ex_of(i), p.plane)) -
+                               phi_prev,
                            f[i]);
         }
     } else {
@@ -539,8 +560,8 @@ __device__ __forceinline__ double finish_node(const SweepParams<Real> &p, int x,
     Real phid;
     const Real phi = collide_fold<Real, MODE, SRC, SH>(p, f, rs, phi_prev, src, p.first != 0, node, phid);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fout[i * p.plane + node] = store_value<Real, S, SH>(i, f[i], phid);
-    p.phi_out[node] = phi;
+    for (int i = 0; i < 9; ++i) fout[BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)] = store_value<Real, S, SH>(i, f[i], phid);
+    p.phi_out[BTRT_IX(p.flags, node, p.plane)] = phi;
     bad |= not_finite(phi);
     if (RESID) {
         const double dd = static_cast<double>(phi) - static_cast<double>(phi_prev);
@@ -560,7 +581,10 @@ template <typename Real, typename S, int SH, int MODE, int SRC, bool L2ONLY, boo
 __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, int ybase, int ystride,
                                              int nrows) {
     Real xs = Real(0), xc = Real(0);
-    if (SRC == kSrcTrig || (SRC == kSrcRuntime && p.src_kind == kSrcTrig)) { xs = p.Xs[x]; xc = p.Xc[x]; }
+    if (SRC == kSrcTrig || (SRC == kSrcRuntime && p.src_kind == kSrcTrig)) {
+        xs = p.Xs[BTRT_IX(p.flags, x, p.nx)];
+        xc = p.Xc[BTRT_IX(p.flags, x, p.nx)];
+    }
     const bool x_inner = (x > 0) && (x < p.nx - 1);
     double resid = 0.0;
     bool bad = false;

@@ -305,14 +305,14 @@ __device__ __forceinline__ void pull3_boundary(const Sweep3Params<Real> &p, cons
         if (sz >= p.nz) { if (p.hbb_z) { wsum += p.wall[5]; ++crossed; } else sz -= p.nz; }
         if (!crossed) {
             const int src = sz * p.slab + sy * p.pitch + sx;
-            d[i] = Storage<S>::load(fin[i * p.plane + src]);
+            d[i] = Storage<S>::load(fin[BTRT_IX(p.flags, i * p.plane + src, 19 * p.plane)]);
             if constexpr (SH == kShiftLocal)
-                if (i != 0) d[i] = fma(wgt3<Real>(i), p.phi_in[src] - phi_prev, d[i]);
+                if (i != 0) d[i] = fma(wgt3<Real>(i), p.phi_in[BTRT_IX(p.flags, src, p.plane)] - phi_prev, d[i]);
         } else {
             const int o = opposite3(i);
             const int n2 = cx3(i) * cx3(i) + cy3(i) * cy3(i) + cz3(i) * cz3(i);
             const Real phi_w = (crossed == 1 ? wsum : Real(0.5) * wsum) * p.wall_fac;
-            const Real dout = Storage<S>::load(fin[o * p.plane + node]);
+            const Real dout = Storage<S>::load(fin[BTRT_IX(p.flags, o * p.plane + node, 19 * p.plane)]);
             Real wt = wall3_term(p, n2, phi_w);
             if constexpr (SH == kShiftRef) wt = wt - Real(2) * p.wref[n2];
             if constexpr (SH == kShiftLocal) wt = fma(Real(-2) * wgt3<Real>(i), phi_prev, wt);
@@ -330,18 +330,21 @@ __global__ void __launch_bounds__(256) sweep3_kernel(const __grid_constant__ Swe
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
     S *__restrict__ fout = static_cast<S *>(p.fout);
     const int node = z * p.slab + y * p.pitch + x;
-    const Real phi_prev = p.phi_in[node];
+    const Real phi_prev = p.phi_in[BTRT_IX(p.flags, node, p.plane)];
     Real d[19];
     if (p.first) {
         equilibrium3<Real, SH>(p, phi_prev, d);
     } else if (x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1 && z > 0 && z < p.nz - 1) {
 #pragma unroll
         for (int i = 0; i < 19; ++i)
-            d[i] = Storage<S>::load(fin[i * p.plane + node - cz3(i) * p.slab - cy3(i) * p.pitch - cx3(i)]);
+            d[i] = Storage<S>::load(
+                fin[BTRT_IX(p.flags, i * p.plane + node - cz3(i) * p.slab - cy3(i) * p.pitch - cx3(i), 19 * p.plane)]);
         if constexpr (SH == kShiftLocal) {
 #pragma unroll
             for (int i = 1; i < 19; ++i)
-                d[i] = fma(wgt3<Real>(i), p.phi_in[node - cz3(i) * p.slab - cy3(i) * p.pitch - cx3(i)] - phi_prev,
+                d[i] = fma(wgt3<Real>(i),
+                           p.phi_in[BTRT_IX(p.flags, node - cz3(i) * p.slab - cy3(i) * p.pitch - cx3(i), p.plane)] -
+                               phi_prev,
                            d[i]);
         }
     } else {
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(256) sweep3_kernel(const __grid_constant__ Swe
     }
     Real srcv = Real(0);
     if constexpr (SRC == kSrcConst) srcv = Real(1);
-    if constexpr (SRC == kSrcField) srcv = p.srcF[node];
+    if constexpr (SRC == kSrcField) srcv = p.srcF[BTRT_IX(p.flags, node, p.plane)];
     const Real rs = SH == kShiftLocal ? phi_prev : p.phi_ref;
     Real phid;
     const Real phi = collide3<Real, MODE, SRC, SH>(p, d, rs, phi_prev, srcv, p.first != 0, phid);
@@ -357,9 +360,9 @@ __global__ void __launch_bounds__(256) sweep3_kernel(const __grid_constant__ Swe
     for (int i = 0; i < 19; ++i) {
         Real v = d[i];
         if constexpr (SH == kShiftLocal) v = fma(-wgt3<Real>(i), phid, v);
-        fout[i * p.plane + node] = Storage<S>::pack(v);
+        fout[BTRT_IX(p.flags, i * p.plane + node, 19 * p.plane)] = Storage<S>::pack(v);
     }
-    p.phi_out[node] = phi;
+    p.phi_out[BTRT_IX(p.flags, node, p.plane)] = phi;
     if (not_finite(phi)) atomicOr(p.flags, 1);
 }
 

@@ -143,7 +143,10 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(const __grid_constant__ 
         const S *tin = in_tile(s);
         const int x = x0 + lx;
         float xs = 0.f, xc = 0.f;
-        if (SRC == 2 && x < p.nx) { xs = p.Xs[x]; xc = p.Xc[x]; }
+        if (SRC == 2 && x < p.nx) {
+            xs = p.Xs[BTRT_IX(p.flags, x, p.nx)];
+            xc = p.Xc[BTRT_IX(p.flags, x, p.nx)];
+        }
 #pragma unroll 1
         for (int r = 0; r < G::ROWS; ++r) {
             const int ly = ly0 + r * YSTEP;
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(const __grid_constant__ 
             if (x >= p.nx || y >= p.ny) continue;
             const int node = y * p.pitch + x;
             float f[9];
-            const float phi_prev = p.phi_in[node];
+            const float phi_prev = p.phi_in[BTRT_IX(p.flags, node, p.plane)];
             if (x > 0 && x < p.nx - 1 && y > 0 && y < p.ny - 1) {
                 const S *base = tin + (ly + 1) * G::BX + (lx + G::PAD);
 #pragma unroll
@@ -159,7 +162,9 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(const __grid_constant__ 
                 if constexpr (SH == kShiftLocal) {
 #pragma unroll
                     for (int i = 1; i < 9; ++i)
-                        f[i] = fma(wgt<float>(i), p.phi_in[node - ey_of(i) * p.pitch - ex_of(i)] - phi_prev, f[i]);
+                        f[i] = fma(wgt<float>(i),
+                                   p.phi_in[BTRT_IX(p.flags, node - ey_of(i) * p.pitch - ex_of(i), p.plane)] - phi_prev,
+                                   f[i]);
                 }
             } else {
                 pull_boundary<float, S, SH, false>(p, fin, x, y, node, phi_prev, f);
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(256) sweep_tma_kernel(const __grid_constant__ 
             S *o = out_tile + ly * G::TX + lx;
 #pragma unroll
             for (int i = 0; i < 9; ++i) o[i * G::TY * G::TX] = store_value<float, S, SH>(i, f[i], phid);
-            p.phi_out[node] = phi;
+            p.phi_out[BTRT_IX(p.flags, node, p.plane)] = phi;
             if (not_finite(phi)) atomicOr(p.flags, 1);
         }
         fence_proxy_async_smem();

@@ -243,6 +243,12 @@ class Lattice:
         C.check(self.lib.btrt_check(self.handle, ctypes.byref(flags)))
         return flags.value
 
+    def flags(self) -> int:
+        """The device flags without raising (bit 0: non-finite phi, bit 2: a tile-copy wait gave up)."""
+        flags = ctypes.c_int32()
+        self.lib.btrt_check(self.handle, ctypes.byref(flags))
+        return flags.value
+
     def time(self):
         s = ctypes.c_int64()
         t = ctypes.c_double()
@@ -299,6 +305,12 @@ class Batch:
     def step(self, nsteps: int, residual: bool = False):
         C.check(self.lib.btrt_batch_step(self.handle, int(nsteps), 1 if residual else 0))
         return self
+
+    def member_flags(self) -> np.ndarray:
+        """Each member's device flags (bit 0: non-finite phi)."""
+        out = np.zeros(len(self.members), dtype=np.int32)
+        C.check(self.lib.btrt_batch_member_flags(self.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))))
+        return out
 
     def residuals(self) -> np.ndarray:
         out = np.empty(len(self.members), dtype=np.float64)

@@ -143,6 +143,12 @@ class Lattice3:
         C.check(self.lib.btrt3_mass(self.handle, ctypes.byref(v)))
         return v.value
 
+    def flags(self) -> int:
+        """Device flags without raising (bit 0: non-finite phi, bit 3: debug index check)."""
+        f = ctypes.c_int32()
+        self.lib.btrt3_check(self.handle, ctypes.byref(f))
+        return f.value
+
     def check(self) -> int:
         f = ctypes.c_int32()
         C.check(self.lib.btrt3_check(self.handle, ctypes.byref(f)))

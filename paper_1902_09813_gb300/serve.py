@@ -37,6 +37,7 @@ class Result:
     steps: int
     residual: float
     phi: np.ndarray
+    status: str = "done"     # "unstable": a non-finite phi appeared; the request was retired alone
 
     @property
     def latency(self) -> float:
@@ -108,19 +109,20 @@ class Server:
                 dirty = False
             batch.step(self.slice_steps, residual=True)
             res = batch.residuals()          # synchronises
+            bad = batch.member_flags() & 1   # non-finite phi in that member only
             self.stats["slices"] += 1
             self.depth.append((round(time.perf_counter() - t0, 4), len(active), len(waiting) + len(pending)))
             done_idx = []
             for k, a in enumerate(active):
                 a[5] += self.slice_steps
-                if res[k] < self.tol or a[5] >= self.max_steps:
+                if bad[k] or res[k] < self.tol or a[5] >= self.max_steps:
                     done_idx.append(k)
             if done_idx:
                 for k in reversed(done_idx):
                     rid, arr, adm, lat, need, steps = active[k]
                     phi = lat.phi_host()
                     results.append(Result(rid, arr, adm, time.perf_counter() - t0, steps,
-                                          float(res[k]), phi))
+                                          float(res[k]), phi, "unstable" if bad[k] else "done"))
                     used -= need
                     del active[k]
                 batch.close()
@@ -147,14 +149,17 @@ def serve_sequential(trace, slice_steps: int = 100, max_steps: int = 20000, tol:
         adm = time.perf_counter() - t0
         lat = Lattice.from_problem(p, compute=compute, storage=storage, stream=stream, shift=shift)
         lat.init(p.phi0(), t0=p.t0)
-        steps, r = 0, float("inf")
+        steps, r, status = 0, float("inf"), "done"
         while True:
             r = lat.step_residual(slice_steps)
             steps += slice_steps
+            if lat.flags() & 1:
+                status = "unstable"
+                break
             if r < tol or steps >= max_steps:
                 break
         phi = lat.phi_host()
-        results.append(Result(rid, arr, adm, time.perf_counter() - t0, steps, r, phi))
+        results.append(Result(rid, arr, adm, time.perf_counter() - t0, steps, r, phi, status))
         del lat
     return results
 

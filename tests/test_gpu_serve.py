@@ -63,3 +63,25 @@ def test_serve_budget_limits_admission():
     assert len(res) == 6
     assert srv.stats["peak_bytes"] <= 2.5 * need
     assert srv.stats["peak_active"] < len(probs)      # the budget held some requests back
+
+
+def test_unstable_request_is_retired_alone():
+    """A request whose initial field holds a NaN (a failure made on the host) is
+    reported as unstable after its first slice; the others complete and equal
+    their solves alone, in the server and in the sequential baseline."""
+    from paper_1902_09813_gb300.serve import Server, poisson_trace, serve_sequential
+    probs = _problems(count=5, seed=13)
+    bad = probs[2]
+    arr = bad.phi0()
+    arr[3, 4] = float("nan")
+    probs[2] = bad.replace(phi0_fn=None, phi0_array=arr)
+    trace = poisson_trace(probs, rate=1e6, seed=4)
+    srv = Server(slice_steps=10, max_steps=40, tol=1e-30)
+    res = srv.run(trace)
+    seq = serve_sequential(trace, slice_steps=10, max_steps=40, tol=1e-30)
+    for out in (res, seq):
+        assert [r.status for r in out] == ["done", "done", "unstable", "done", "done"]
+        assert out[2].steps == 10
+        for k in (0, 1, 3, 4):
+            assert out[k].steps == 40
+            assert np.array_equal(out[k].phi, _alone(probs[k], 40))
