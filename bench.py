@@ -235,6 +235,11 @@ def run_gpu(args):
     extra = {}
     del lat
     torch.cuda.empty_cache()
+    if ws > 1:
+        # the per-GPU characterisations (variants, accuracy, batching, serving, CPU oracle)
+        # are reported at N = 1; replicas only time the headline sweep
+        args.no_variants = args.no_accuracy = args.no_batched = args.no_serving = True
+        args.no_cpu_baseline = True
     if not args.no_variants:
         extra["variants"] = run_variants(args)
     if not args.no_accuracy:
