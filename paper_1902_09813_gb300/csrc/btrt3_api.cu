@@ -337,22 +337,6 @@ btrt_status mass3(btrt3_lattice L, double *out) {
     return BTRT_OK;
 }
 
-double half_bits_to_double(int fmt, const unsigned char *p) {
-    uint16_t b;
-    std::memcpy(&b, p, 2);
-    if (fmt == BTRT_BF16) {
-        uint32_t u = (uint32_t)b << 16;
-        float f;
-        std::memcpy(&f, &u, 4);
-        return f;
-    }
-    const int sign = (b >> 15) & 1, e = (b >> 10) & 31, m = b & 1023;
-    double v;
-    if (e == 0) v = std::ldexp((double)m, -24);
-    else if (e == 31) v = m ? NAN : INFINITY;
-    else v = std::ldexp((double)(m | 1024), e - 25);
-    return sign ? -v : v;
-}
 
 }  // namespace
 

@@ -215,6 +215,24 @@ void btrt::set_last_error(const char *fmt, ...) {
     g_err = buf;
 }
 
+double btrt::half_bits_to_double(int fmt, const unsigned char *p) {
+    uint16_t b;
+    std::memcpy(&b, p, 2);
+    if (fmt == BTRT_BF16) {
+        uint32_t u = (uint32_t)b << 16;
+        float f;
+        std::memcpy(&f, &u, 4);
+        return f;
+    }
+    // IEEE binary16 -> double, by its definition
+    const int sign = (b >> 15) & 1, e = (b >> 10) & 31, m = b & 1023;
+    double v;
+    if (e == 0) v = std::ldexp((double)m, -24);
+    else if (e == 31) v = m ? NAN : INFINITY;
+    else v = std::ldexp((double)(m | 1024), e - 25);
+    return sign ? -v : v;
+}
+
 size_t btrt::elem_size(int fmt) {
     switch (fmt) {
     case BTRT_F64: return 8;
@@ -495,23 +513,6 @@ btrt_status reduce_phi(btrt_lattice L, double *out) {
     return BTRT_OK;
 }
 
-double host_half_to_double(int fmt, const unsigned char *p) {
-    uint16_t b;
-    std::memcpy(&b, p, 2);
-    if (fmt == BTRT_BF16) {
-        uint32_t u = (uint32_t)b << 16;
-        float f;
-        std::memcpy(&f, &u, 4);
-        return f;
-    }
-    // IEEE binary16 -> double, by its definition
-    const int sign = (b >> 15) & 1, e = (b >> 10) & 31, m = b & 1023;
-    double v;
-    if (e == 0) v = std::ldexp((double)m, -24);
-    else if (e == 31) v = m ? NAN : INFINITY;
-    else v = std::ldexp((double)(m | 1024), e - 25);
-    return sign ? -v : v;
-}
 
 struct StateHeader {
     char magic[8];
@@ -791,7 +792,7 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
                 v = (double)hl[0] + (double)hl[1];
             }
             else if (g.storage == BTRT_F32) { float fv; std::memcpy(&fv, &raw[k * 4], 4); v = fv; }
-            else v = host_half_to_double(g.storage, &raw[k * 2]);
+            else v = half_bits_to_double(g.storage, &raw[k * 2]);
             const double loc = sh == kShiftLocal ? wts[i] * (double)phiw[k] : 0.0;
             dst[(size_t)i * w * h + k] = v + shift + loc;
         }

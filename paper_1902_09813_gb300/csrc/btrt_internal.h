@@ -16,6 +16,8 @@ constexpr int kRedBlocks = 1024;     // fixed grid of the FP64 reductions (deter
 constexpr int kRedThreads = 256;
 
 size_t elem_size(int fmt);
+// A stored FP16 (IEEE binary16, by its definition) or BF16 value as a double.
+double half_bits_to_double(int fmt, const unsigned char *p);
 
 // Where each part of a lattice lives in its workspace (byte offsets).
 struct Layout {
