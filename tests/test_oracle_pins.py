@@ -275,6 +275,19 @@ def test_node_step_matches_grid_step(bc):
             assert phi == pytest.approx(lat.phi_prev[iy, ix], abs=1e-14)
 
 
+@pytest.mark.parametrize("alpha,n,key,tol", [(1e-4, 200, "gre_table6_a1e-4_dx200", 0.06),
+                                             (1e-6, 200, "gre_table6_a1e-6_dx200", 0.06),
+                                             (1e-6, 400, "gre_table6_a1e-6_dx400", 0.06)])
+def test_table6_variable_tensor_small_alpha(alpha, n, key, tol):
+    """Table 6 (Sec. 4.2.2): periodic unit square, c = 1, t = 3, u = (0.1, 0.1), and
+    k2 = 1 as the paper sets for its anisotropic runs."""
+    from conftest import paper_value
+    p = w.variable_tensor(n=n, alpha=alpha, walls=False, t_end=3.0).replace(k2_mode="const", k2=1.0)
+    lat = oracle.run(p, nthreads=cpu_threads())
+    err = w.gre(lat.phi(), w.variable_tensor_exact(p, p.nsteps * p.dt))
+    assert err == pytest.approx(paper_value(key), rel=tol)
+
+
 def test_variable_tensor_second_order():
     """Spatially varying diffusion tensor with its manufactured source (Sec. 4.2.2,
     Eqs. 73-76): second order under diffusive scaling (dt = 20 dx^2)."""
