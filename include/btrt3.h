@@ -107,6 +107,14 @@ btrt_status btrt3_mass(btrt3_lattice L, double *out);
  * index check of a -DBTRT_DEBUG_BOUNDS build failed -> BTRT_ECUDA).  Synchronises. */
 btrt_status btrt3_check(btrt3_lattice L, int32_t *flags);
 
+/* Checkpoint: bytes of a saved state (header, the current populations in their
+ * stored form, phi), the save (synchronises) and the load into a lattice of the
+ * same grid, formats and shift (coefficients must be set first).  A resumed run
+ * continues bitwise as the uninterrupted one. */
+size_t btrt3_state_bytes(btrt3_lattice L);
+btrt_status btrt3_save(btrt3_lattice L, void *host_buf, size_t n);
+btrt_status btrt3_load(btrt3_lattice L, const void *host_buf, size_t n);
+
 /* Steps taken since btrt3_init_phi and the current time t0 + step dt. */
 btrt_status btrt3_get_time(btrt3_lattice L, int64_t *step, double *t);
 

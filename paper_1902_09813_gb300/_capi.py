@@ -121,6 +121,9 @@ SIGNATURES = [
     ("btrt3_mass", ctypes.c_int, [_vp, _dp]),
     ("btrt3_check", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     ("btrt3_get_time", ctypes.c_int, [_vp, ctypes.POINTER(_i64), _dp]),
+    ("btrt3_state_bytes", _sz, [_vp]),
+    ("btrt3_save", ctypes.c_int, [_vp, _vp, _sz]),
+    ("btrt3_load", ctypes.c_int, [_vp, _vp, _sz]),
     ("btrt3_destroy", ctypes.c_int, [_vp]),
     ("btrt_last_error", ctypes.c_char_p, []),
     ("btrt_version", ctypes.c_char_p, []),

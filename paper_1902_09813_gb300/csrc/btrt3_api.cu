@@ -562,6 +562,66 @@ btrt_status btrt3_check(btrt3_lattice L, int32_t *flags) {
     return BTRT_OK;
 }
 
+namespace {
+struct State3Header {
+    char magic[8];
+    int32_t nx, ny, nz, compute, storage, shift;
+    int64_t step;
+    double t0;
+};
+}  // namespace
+
+size_t btrt3_state_bytes(btrt3_lattice L) {
+    if (!L) return 0;
+    return sizeof(State3Header) + L->lay.fbuf_bytes + (size_t)L->lay.plane * elem_size(L->g.compute);
+}
+
+btrt_status btrt3_save(btrt3_lattice L, void *host_buf, size_t n) {
+    if (!L || !host_buf) return fail3(BTRT_EINVAL, "null argument");
+    if (!L->ready) return fail3(BTRT_ESTATE, "lattice not initialised");
+    if (n < btrt3_state_bytes(L)) return fail3(BTRT_ENOMEM, "buffer too small");
+    State3Header h;
+    std::memset(&h, 0, sizeof h);
+    std::memcpy(h.magic, "BTRT3S1", 8);
+    h.nx = L->g.nx;
+    h.ny = L->g.ny;
+    h.nz = L->g.nz;
+    h.compute = L->g.compute;
+    h.storage = L->g.storage;
+    h.shift = L->g.shift;
+    h.step = L->step;
+    h.t0 = L->t0;
+    std::memcpy(host_buf, &h, sizeof h);
+    unsigned char *p = static_cast<unsigned char *>(host_buf) + sizeof h;
+    CUDA3_TRY(cudaMemcpyAsync(p, L->fbuf(L->cur), L->lay.fbuf_bytes, cudaMemcpyDeviceToHost, L->stream));
+    CUDA3_TRY(cudaMemcpyAsync(p + L->lay.fbuf_bytes, L->ws + L->lay.off_phi[L->cur],
+                              (size_t)L->lay.plane * elem_size(L->g.compute), cudaMemcpyDeviceToHost, L->stream));
+    CUDA3_TRY(cudaStreamSynchronize(L->stream));
+    return BTRT_OK;
+}
+
+btrt_status btrt3_load(btrt3_lattice L, const void *host_buf, size_t n) {
+    if (!L || !host_buf) return fail3(BTRT_EINVAL, "null argument");
+    if (!L->have_coeffs) return fail3(BTRT_ESTATE, "btrt3_set_coeffs must come before btrt3_load");
+    if (n < btrt3_state_bytes(L)) return fail3(BTRT_ENOMEM, "buffer too small");
+    State3Header h;
+    std::memcpy(&h, host_buf, sizeof h);
+    if (std::memcmp(h.magic, "BTRT3S1", 8) != 0 || h.nx != L->g.nx || h.ny != L->g.ny || h.nz != L->g.nz ||
+        h.compute != L->g.compute || h.storage != L->g.storage || h.shift != L->g.shift)
+        return fail3(BTRT_EINVAL, "state does not match this lattice");
+    const unsigned char *p = static_cast<const unsigned char *>(host_buf) + sizeof h;
+    L->cur = 0;
+    CUDA3_TRY(cudaMemcpyAsync(L->fbuf(0), p, L->lay.fbuf_bytes, cudaMemcpyHostToDevice, L->stream));
+    CUDA3_TRY(cudaMemcpyAsync(L->ws + L->lay.off_phi[0], p + L->lay.fbuf_bytes,
+                              (size_t)L->lay.plane * elem_size(L->g.compute), cudaMemcpyHostToDevice, L->stream));
+    CUDA3_TRY(cudaMemsetAsync(L->flags(), 0, 16, L->stream));
+    CUDA3_TRY(cudaStreamSynchronize(L->stream));
+    L->step = h.step;
+    L->t0 = h.t0;
+    L->ready = true;
+    return BTRT_OK;
+}
+
 btrt_status btrt3_get_time(btrt3_lattice L, int64_t *step, double *t) {
     if (!L) return fail3(BTRT_EINVAL, "null lattice");
     if (step) *step = L->step;

@@ -159,6 +159,17 @@ class Lattice3:
         C.check(self.lib.btrt3_get_time(self.handle, ctypes.byref(s), ctypes.byref(t)))
         return s.value, t.value
 
+    def save(self) -> bytes:
+        n = self.lib.btrt3_state_bytes(self.handle)
+        buf = ctypes.create_string_buffer(n)
+        C.check(self.lib.btrt3_save(self.handle, buf, n))
+        return buf.raw
+
+    def load(self, state: bytes):
+        buf = ctypes.create_string_buffer(state, len(state))
+        C.check(self.lib.btrt3_load(self.handle, buf, len(state)))
+        return self
+
     def close(self):
         if getattr(self, "handle", None) is not None and self.handle.value:
             self.lib.btrt3_destroy(self.handle)

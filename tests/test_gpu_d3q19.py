@@ -152,3 +152,15 @@ def test_nonfinite_flag():
         lat.check()
     assert e.value.code == C.EUNSTABLE
     assert _lattice(p).init(p.phi0()).step(3).check() == 0
+
+
+@pytest.mark.parametrize("compute,storage", [("f64", "f64"), ("f32", "f16")])
+def test_checkpoint_resume_bitwise(compute, storage):
+    p = w.random_state_problem3(11, 9, 7, seed=6, bc=(1, 1, 0, 0, 1, 1), nonlinear=True, source="reaction")
+    a = _lattice(p, compute, storage).init(p.phi0()).step(5)
+    state = a.save()
+    a.step(4)
+    b = _lattice(p, compute, storage).load(state).step(4)
+    assert np.array_equal(a.phi_host(), b.phi_host())
+    assert np.array_equal(a.read_f(), b.read_f())
+    assert a.time() == b.time()
