@@ -164,3 +164,15 @@ def test_checkpoint_resume_bitwise(compute, storage):
     assert np.array_equal(a.phi_host(), b.phi_host())
     assert np.array_equal(a.read_f(), b.read_f())
     assert a.time() == b.time()
+
+
+def test_fp32_ill_conditioned_first_order_block():
+    """A 3-D tensor with eigenvalues (1e4, 1e-3, 2e-3): the FP32 sweep inverts the
+    ill-conditioned blocks in FP64 and meets the FP32 tolerance."""
+    p = w.random_state_problem3(12, 10, 9, seed=14, bc=(0, 0, 1, 1, 0, 0), nonlinear=True, source="none")
+    p = p.replace(A0=w.rot_tensor3((1.0e4, 1.0e-3, 2.0e-3), (0.3, 0.7, 1.1)), a2=0.3)
+    steps = 8
+    lat = _lattice(p, "f32", "f32", "ref").init(p.phi0()).step(steps)
+    phi, _ = _oracle(p, steps)
+    assert _rel(lat.phi_host(), phi) <= TOL32
+    assert lat.check() == 0

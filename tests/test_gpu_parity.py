@@ -358,3 +358,17 @@ def test_burgers_fisher_reduced_storage_error():
     g16 = w.gre(_lattice(p, "f32", "f16").init(p.phi0()).step_walls(p, p.nsteps).phi_host(), ex)
     assert abs(g32 - g64) <= 0.01 * g64, (g64, g32)
     assert abs(g16 - g64) <= 0.05 * g64, (g64, g16)
+
+
+def test_fp32_ill_conditioned_first_order_block():
+    """A diffusion tensor with eigenvalues 1e4 and 1e-3 (lattice units) makes the
+    per-node block 3 A^ + I/2 ill-conditioned (tr^2/det ~ 6e4); the FP32 sweep
+    inverts such blocks in FP64 and still meets the FP32 tolerance."""
+    from workloads.problems import _rot_tensor
+    p = w.random_state_problem(40, 33, seed=12, bc=(1, 1, 0, 0), nonlinear=True, source="none")
+    p = p.replace(A0=_rot_tensor(1.0e4, 1.0e-3, 0.4), a2=0.3)
+    steps = 10
+    lat = _gpu_run(p, steps, compute="f32", storage="f32")
+    phi_ref, _ = _oracle_run(p, steps)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL32
+    assert lat.check() == 0
