@@ -326,6 +326,36 @@ def run_variants(args, steps=200, warmup=5):
         out[f"nonlinear_f32_{st}_local"] = _time_single(q, phi0, "f32", st, steps, warmup, shift="local")
     out["nonlinear_f64"] = _time_single(q, phi0, "f64", "f64", 50, 3)
     out.update(run_d3q19(args))
+    out.update(run_extended(args))
+    return out
+
+
+def run_extended(args, n=4096, steps=100):
+    """The extended coefficient paths at n^2: per-node diffusion tensor and source
+    fields (the variable-tensor problem, Eqs. 73-76; 4 field planes read per
+    update), and the Burgers-Fisher power-law flux with the reaction source
+    (Eq. 67, periodic copy of the problem; pow() per node)."""
+    import workloads as w
+    out = {}
+    vt = w.variable_tensor(n=n, alpha=1e-2, walls=True, t_end=0.0)
+    vt = vt.replace(dt=20.0 * vt.dx ** 2)
+    phi0 = vt.phi0()
+    for comp, st in (("f64", "f64"), ("f32", "f32")):
+        r = _time_single(vt, phi0, comp, st, steps, 3)
+        field_b = 4 * (8 if comp == "f64" else 4)
+        gbs = (BYTES_PER_UPDATE[st] + field_b) * r["mlups"] * 1e6 / 1e9
+        peak, _ = _peaks()
+        r.update(bytes_per_update=BYTES_PER_UPDATE[st] + field_b, algorithmic_gbs=round(gbs, 1),
+                 hbm_frac=round(gbs / peak, 4))
+        out[f"fields_{n}_{comp}_{st}"] = r
+    # Burgers-Fisher coefficients on a periodic square with a smooth periodic field in [0.1, 0.9]
+    bf = w.burgers_fisher(n=n, a=2.0, alpha=0.05).replace(
+        bc=(0, 0, 0, 0), wall_fn=None,
+        phi0_fn=lambda X, Y: 0.5 + 0.4 * np.sin(2 * np.pi * X / 3.0) * np.sin(2 * np.pi * Y / 3.0))
+    phi0 = bf.phi0()
+    for comp, st in (("f64", "f64"), ("f32", "f32"), ("f32", "f16")):
+        out[f"burgers_fisher_{n}_{comp}_{st}"] = _time_single(bf, phi0, comp, st, steps, 3,
+                                                             shift="local" if st == "f16" else "ref")
     return out
 
 

@@ -254,6 +254,8 @@ void fill3(btrt3_lattice L, Sweep3Params<Real> &p, int64_t n, bool first) {
     p.k2c = (Real)c.k2;
     p.k2 = (Real)L->k2;
     p.cond_limit = (Real)1.0e6;
+    for (int k = 0; k < 6; ++k) p.A0d[k] = L->A0[k];
+    p.a2d = c.a2;
     p.src_kind = c.src_kind;
     p.src_val = (Real)sv;
     p.srcF = L->srcf<Real>();

@@ -313,6 +313,8 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
     p.K1yy = (Real)L->K1[2];
     p.k2 = (Real)L->k2;
     p.cond_limit = (Real)1.0e4;
+    for (int k = 0; k < 3; ++k) p.A0d[k] = L->A0[k];
+    p.a2d = c.a2;
     p.src_kind = c.src_kind;
     p.src_val = (Real)src_val;
     p.srcF = L->srcf<Real>();

@@ -117,7 +117,8 @@ struct SweepParams {
     Real k2c;              // constant k2
     Real K1xx, K1xy, K1yy; // K1 when A is constant (symmetric)
     Real k2;               // k2 when A is constant
-    Real cond_limit;       // FP32: tr^2/det above this -> invert in FP64
+    Real cond_limit;       // FP32: tr^2/det above this -> build and invert the block in FP64
+    double A0d[3], a2d;    // A0^ and a2 in FP64 for that path
 
     // source
     int src_kind;          // 0 none, 1 const, 2 trig, 3 per-node field, 4 reaction
@@ -288,8 +289,18 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
         bool ill = false;
         if constexpr (sizeof(Real) == 4) ill = tr * tr > p.cond_limit * det;
         if (ill) {
-            // ill-conditioned FP32 block: invert in FP64
-            const double dxx = (double)mxx, dxy = (double)mxy, dyy = (double)myy;
+            // ill-conditioned FP32 block: build it again from FP64 coefficients (the
+            // FP32-rounded entries would carry errors the condition number amplifies)
+            // and invert it in FP64
+            const double ph = static_cast<double>(phi);
+            const double s3d = 3.0 + 3.0 * p.a2d * ph * ph;
+            double bxx = p.A0d[0], bxy = p.A0d[1], byy = p.A0d[2];
+            if (p.Af) {
+                bxx = (double)a0xx;
+                bxy = (double)a0xy;
+                byy = (double)a0yy;
+            }
+            const double dxx = s3d * bxx + 0.5, dxy = s3d * bxy, dyy = s3d * byy + 0.5;
             const double id = 1.0 / (dxx * dyy - dxy * dxy);
             K1xx = (Real)(dyy * id);
             K1xy = (Real)(-dxy * id);

@@ -81,7 +81,8 @@ struct Sweep3Params {
     Real k2;
     Real Ku[3];            // constant-coefficient fold: K1 u (B = u phi)
     Real gu[3];            //   and (I - K1/2) u
-    Real cond_limit;       // FP32: tr^3 > cond_limit det -> invert in FP64
+    Real cond_limit;       // FP32: tr^3 > cond_limit det -> build and invert the block in FP64
+    double A0d[6], a2d;    // A0^ and a2 in FP64 for that path
 
     int src_kind;          // 0 none, 1 const, 3 per-node field, 4 reaction
     Real src_val;          // dt S (const), dt (3 T_n - T_{n-1}) / 2 (field), dt (reaction)
@@ -190,8 +191,12 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
         bool ill = false;
         if constexpr (sizeof(Real) == 4) ill = tr * tr * tr > p.cond_limit * det;
         if (ill) {
-            // ill-conditioned FP32 block: cofactors and determinant again in FP64
-            const double dxx = mxx, dxy = mxy, dxz = mxz, dyy = myy, dyz = myz, dzz = mzz;
+            // ill-conditioned FP32 block: rebuilt from FP64 coefficients (FP32-rounded
+            // entries carry errors the condition number amplifies), inverted in FP64
+            const double ph = static_cast<double>(phi);
+            const double s3d = 3.0 + 3.0 * p.a2d * ph * ph;
+            const double dxx = s3d * p.A0d[0] + 0.5, dxy = s3d * p.A0d[1], dxz = s3d * p.A0d[2];
+            const double dyy = s3d * p.A0d[3] + 0.5, dyz = s3d * p.A0d[4], dzz = s3d * p.A0d[5] + 0.5;
             const double ex = dyy * dzz - dyz * dyz, exy = dxz * dyz - dxy * dzz, exz = dxy * dyz - dxz * dyy;
             const double ey = dxx * dzz - dxz * dxz, eyz = dxy * dxz - dxx * dyz, ez = dxx * dyy - dxy * dxy;
             const double id = 1.0 / (dxx * ex + dxy * exy + dxz * exz);

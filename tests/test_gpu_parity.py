@@ -372,3 +372,21 @@ def test_fp32_ill_conditioned_first_order_block():
     phi_ref, _ = _oracle_run(p, steps)
     assert _rel(lat.phi_host(), phi_ref) <= TOL32
     assert lat.check() == 0
+
+
+@pytest.mark.parametrize("model", ["lbgk", "mlbm", "rlbm", "ob-trirt"])
+def test_table1_presets_match_oracle(model):
+    """The comparison models of Table 1 run through the same kernels (k0 != 1,
+    constant k2): GPU equals the oracle on the walled Table 3 problem and the
+    Burgers-Fisher problem of Table 4."""
+    from paper_1902_09813_gb300.presets import relaxation_preset
+    p = w.linear_cde(n=50, alpha=0.01, u=(0.1, 0.1), c=5.0, t_end=0.1, walls=True)
+    p = p.replace(**relaxation_preset(model, p.A0, p.dx, p.dt))
+    lat = _gpu_run(p, p.nsteps)
+    phi_ref, _ = _oracle_run(p, p.nsteps)
+    assert _rel(lat.phi_host(), phi_ref) <= TOL64
+    q = w.burgers_fisher(n=40, a=2.0, alpha=0.05, t_end=0.2)
+    q = q.replace(**relaxation_preset(model, q.A0, q.dx, q.dt))
+    lat = _lattice(q).init(q.phi0(), t0=q.t0).step_walls(q, q.nsteps)
+    o = oracle.OracleLattice(q, nthreads=cpu_threads()).init().step(q.nsteps)
+    assert _rel(lat.phi_host(), o.phi()) <= TOL64
