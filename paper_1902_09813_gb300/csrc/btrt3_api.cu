@@ -262,6 +262,8 @@ void fill3(btrt3_lattice L, Sweep3Params<Real> &p, int64_t n, bool first) {
     p.react_rate = (Real)c.react_rate;
     p.react_exp = (Real)c.react_exp;
     p.react2 = c.react_exp == 2.0 ? 1 : 0;
+    half_split(L->bq, &p.bq_n, &p.bq_h);
+    half_split(c.react_exp, &p.re_n, &p.re_h);
     p.first = first ? 1 : 0;
     p.flags = L->flags();
 }

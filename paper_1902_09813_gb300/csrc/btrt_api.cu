@@ -299,6 +299,8 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
     p.react_rate = (Real)c.react_rate;
     p.react_exp = (Real)c.react_exp;
     p.react2 = c.react_exp == 2.0 ? 1 : 0;
+    half_split(L->bq, &p.bq_n, &p.bq_h);
+    half_split(c.react_exp, &p.re_n, &p.re_h);
     p.c3 = (Real)c.c3;
     p.A0xx = (Real)L->A0[0];
     p.A0xy = (Real)L->A0[1];

@@ -94,6 +94,19 @@ inline dim3 sweep_grid(int nx, int ny, int rows_per_thread) {
     return dim3((unsigned)((nx + 31) / 32), (unsigned)((ny + rows - 1) / rows), 1);
 }
 
+// Exponent q as n + h/2 (n in [0, 8], h in {0, 1}) when it has that form, so the
+// kernels take products and one square root; otherwise n = -1 (pow).
+inline void half_split(double q, int *n, int *h) {
+    const double t = 2.0 * q;
+    if (q >= 0.0 && q <= 8.5 && t == (double)(long long)t) {
+        *n = (int)(t / 2);
+        *h = (int)((long long)t % 2);
+    } else {
+        *n = -1;
+        *h = 0;
+    }
+}
+
 // Storage shift of a lattice (kShiftNone for FP64 / double-word storage).
 inline int shift_of(const btrt_grid_desc &g) {
     if (g.storage == BTRT_F64 || g.storage == BTRT_DF64) return kShiftNone;

@@ -110,6 +110,7 @@ struct SweepParams {
     Real bgx, bgy;         // b2 d / q: B = u phi + bg phi^q
     Real bq;               // q
     int bq2;               // 1: q == 2 (phi^q = phi phi)
+    int bq_n, bq_h;        // q = bq_n + bq_h / 2 (bq_n >= 0) -> products and a square root; bq_n < 0: pow
     Real A0xx, A0xy, A0yy, a2;
     Real k0;
     int nonlin_A;          // 1: A depends on phi -> K1, k2 built per node
@@ -125,6 +126,7 @@ struct SweepParams {
     Real src_val;          // const: S^ ; trig, field: dt (3 T_n - T_{n-1}) / 2; reaction: dt
     Real react_rate, react_exp;   // reaction: S = rate phi (1 - phi^exp)
     int react2;                   // 1: exp == 2 (phi^exp = phi phi)
+    int re_n, re_h;               // exp = re_n + re_h / 2 as for the flux exponent
     const Real *Xs, *Xc, *Ys, *Yc;   // trig tables: sin/cos(k x_i), alpha folded into Ys/Yc
     const Real *srcF;      // field: S(x) per node (pitched plane)
     const Real *Af;        // non-null: per-node lattice diffusion tensor, planes xx, xy, yy (`plane` apart)
@@ -183,16 +185,35 @@ __device__ __forceinline__ dw powr(dw x, dw q) {
     return dw(pow(fmax(static_cast<double>(x), 0.0), static_cast<double>(q)));
 }
 
+// max(x, 0)^(n + h/2) for a whole or half-whole exponent: n products and one
+// square root (the exponents of Eq. 67 in the paper's tests are 1.5 and 2.5);
+// n < 0 falls back to powr.
+__device__ __forceinline__ float not_negative(float x) { return fmaxf(x, 0.0f); }
+__device__ __forceinline__ double not_negative(double x) { return fmax(x, 0.0); }
+__device__ __forceinline__ dw not_negative(dw x) { return x.hi > 0.0f ? x : dw(0.0f, 0.0f); }
+__device__ __forceinline__ float sqrt_r(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrt_r(double x) { return sqrt(x); }
+__device__ __forceinline__ dw sqrt_r(dw x) { return dw(sqrt(static_cast<double>(x))); }
+template <typename Real>
+__device__ __forceinline__ Real pow_half(Real x, Real q, int n, int h) {
+    if (n < 0) return powr(x, q);
+    const Real xp = not_negative(x);
+    Real r = Real(1);
+    for (int k = 0; k < n; ++k) r = r * xp;
+    if (h) r = r * sqrt_r(xp);
+    return r;
+}
+
 // phi^q / q times q, i.e. phi^q (q == 2: one product).
 template <typename Real>
 __device__ __forceinline__ Real flux_pow(const SweepParams<Real> &p, Real phi) {
-    return p.bq2 ? phi * phi : powr(phi, p.bq);
+    return p.bq2 ? phi * phi : pow_half(phi, p.bq, p.bq_n, p.bq_h);
 }
 
 // Reaction term S = rate phi (1 - phi^exp) (Eq. 67); exp == 2 takes phi phi.
 template <typename Real>
 __device__ __forceinline__ Real reaction(const SweepParams<Real> &p, Real phi) {
-    const Real pe = p.react2 ? phi * phi : powr(phi, p.react_exp);
+    const Real pe = p.react2 ? phi * phi : pow_half(phi, p.react_exp, p.re_n, p.re_h);
     return p.react_rate * phi * (Real(1) - pe);
 }
 
@@ -262,8 +283,8 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
             dBx = fma(p.bgx, sp, p.ux) * dphi;
             dBy = fma(p.bgy, sp, p.uy) * dphi;
         } else {
-            const Real gq = powr(phi, p.bq);
-            const Real dg = first ? Real(0) : gq - powr(phi_prev, p.bq);
+            const Real gq = pow_half(phi, p.bq, p.bq_n, p.bq_h);
+            const Real dg = first ? Real(0) : gq - pow_half(phi_prev, p.bq, p.bq_n, p.bq_h);
             Bx = fma(p.ux, phi, p.bgx * gq);
             By = fma(p.uy, phi, p.bgy * gq);
             dBx = fma(p.ux, dphi, p.bgx * dg);

@@ -70,6 +70,7 @@ struct Sweep3Params {
     Real ux, uy, uz;       // B = u phi + bg phi^q
     Real bgx, bgy, bgz, bq;
     int bq2;
+    int bq_n, bq_h;        // q = bq_n + bq_h / 2 when bq_n >= 0 (products and a square root)
     Real c3;               // C = phi + c3 phi^3
     Real A0[6];            // xx, xy, xz, yy, yz, zz (lattice units)
     Real a2;
@@ -89,6 +90,7 @@ struct Sweep3Params {
     const Real *srcF;      // field: F(x) per node (pitched)
     Real react_rate, react_exp;
     int react2;
+    int re_n, re_h;
 
     int first;
     int *flags;            // bit 0: non-finite phi
@@ -105,7 +107,7 @@ __device__ __forceinline__ Real wall3_term(const Sweep3Params<Real> &p, int n2, 
 // Shifted equilibrium (Eq. 7, D = C I) for the initialising collision.
 template <typename Real, int SH>
 __device__ __forceinline__ void equilibrium3(const Sweep3Params<Real> &p, Real phi, Real (&f)[19]) {
-    const Real g = p.bq2 ? phi * phi : powr(phi, p.bq);
+    const Real g = p.bq2 ? phi * phi : pow_half(phi, p.bq, p.bq_n, p.bq_h);
     const Real Bx = Real(3) * fma(p.ux, phi, p.bgx * g);
     const Real By = Real(3) * fma(p.uy, phi, p.bgy * g);
     const Real Bz = Real(3) * fma(p.uz, phi, p.bgz * g);
@@ -163,8 +165,8 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
         dBy = fma(p.bgy, sp, p.uy) * dphi;
         dBz = fma(p.bgz, sp, p.uz) * dphi;
     } else {
-        const Real gq = powr(phi, p.bq);
-        const Real dg = first ? Real(0) : gq - powr(phi_prev, p.bq);
+        const Real gq = pow_half(phi, p.bq, p.bq_n, p.bq_h);
+        const Real dg = first ? Real(0) : gq - pow_half(phi_prev, p.bq, p.bq_n, p.bq_h);
         Bx = fma(p.ux, phi, p.bgx * gq);
         By = fma(p.uy, phi, p.bgy * gq);
         Bz = fma(p.uz, phi, p.bgz * gq);
@@ -249,10 +251,12 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
     Real a = MODE == kLinearK0One ? phid : k0 * phid;
     if constexpr (SRC == kSrcReaction || SRC == kSrcRuntime) {
         if (SRC == kSrcReaction || p.src_kind == kSrcReaction) {
-            const Real Sn = p.react_rate * phi * (Real(1) - (p.react2 ? phi * phi : powr(phi, p.react_exp)));
+            const Real Sn =
+                p.react_rate * phi * (Real(1) - (p.react2 ? phi * phi : pow_half(phi, p.react_exp, p.re_n, p.re_h)));
             const Real Sp = first ? Sn
                                   : p.react_rate * phi_prev *
-                                        (Real(1) - (p.react2 ? phi_prev * phi_prev : powr(phi_prev, p.react_exp)));
+                                        (Real(1) - (p.react2 ? phi_prev * phi_prev
+                                                             : pow_half(phi_prev, p.react_exp, p.re_n, p.re_h)));
             srcv = fma(Real(1.5), Sn, Real(-0.5) * Sp);
         }
     }
