@@ -53,7 +53,7 @@ FP64_PEAK_TOPS = 0.625
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the same kernel at 2048^2
 # (profiles/sweep_f64_mms2048_full.md), scaled to the benchmark by node count;
 # None when the kernel changed after the capture.
-FP64_TRAFFIC_PER_NODE = 149.0
+FP64_TRAFFIC_PER_NODE = 149.1
 
 
 def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
