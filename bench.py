@@ -317,6 +317,7 @@ def run_variants(args, steps=200, warmup=5):
         out[f"mms_f32_{st}"] = _time_single(p, phi0, "f32", st, steps, warmup)
         out[f"mms_f32_{st}_tma"] = _time_single(p, phi0, "f32", st, steps, warmup, variant="tma")
         out[f"mms_f32_{st}_local"] = _time_single(p, phi0, "f32", st, steps, warmup, shift="local")
+    out["mms_f32_f32_tb2"] = _time_single(p, phi0, "f32", "f32", steps, warmup, variant="tb2")
     q = w.nonlinear_modes(n=args.n, nsteps=steps)
     phi0 = q.phi0()
     q.phi_ref = float(phi0.mean())
@@ -324,6 +325,7 @@ def run_variants(args, steps=200, warmup=5):
         out[f"nonlinear_f32_{st}"] = _time_single(q, phi0, "f32", st, steps, warmup)
         out[f"nonlinear_f32_{st}_tma"] = _time_single(q, phi0, "f32", st, steps, warmup, variant="tma")
         out[f"nonlinear_f32_{st}_local"] = _time_single(q, phi0, "f32", st, steps, warmup, shift="local")
+    out["nonlinear_f32_f32_tb2"] = _time_single(q, phi0, "f32", "f32", steps, warmup, variant="tb2")
     out["nonlinear_f64"] = _time_single(q, phi0, "f64", "f64", 50, 3)
     out.update(run_d3q19(args))
     out.update(run_extended(args))
@@ -649,7 +651,7 @@ def main():
     ap.add_argument("--storage", default=None, choices=["f64", "df64", "f32", "f16", "bf16"])
     ap.add_argument("--shift", default="auto", choices=["auto", "ref", "local"],
                     help="stored form of F32/F16/BF16 populations")
-    ap.add_argument("--sweep", default="auto", choices=["auto", "plain", "tma"],
+    ap.add_argument("--sweep", default="auto", choices=["auto", "plain", "tma", "tb2"],
                     help="kernel form of FP32-compute sweeps")
     args = ap.parse_args()
     if args.warmup < 3:

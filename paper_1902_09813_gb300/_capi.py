@@ -13,7 +13,7 @@ F64, F32, F16, BF16, DF64 = 0, 1, 2, 3, 4
 K2_HBB, K2_CONST = 0, 1
 SRC_NONE, SRC_CONST, SRC_TRIG, SRC_FIELD, SRC_REACTION = 0, 1, 2, 3, 4
 FIELD_SOURCE, FIELD_DIFFUSION = 1, 2
-SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA = 0, 1, 2
+SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA, SWEEP_TB2 = 0, 1, 2, 3
 SHIFT_REF, SHIFT_LOCAL = 0, 1
 SHIFTS = {"ref": SHIFT_REF, "local": SHIFT_LOCAL}
 

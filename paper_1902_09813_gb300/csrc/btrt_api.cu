@@ -716,6 +716,17 @@ btrt_status btrt_step(btrt_lattice L, int64_t nsteps) {
     if (!L) return fail(BTRT_EINVAL, "null lattice");
     if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
     if (nsteps < 0) return fail(BTRT_EINVAL, "negative step count");
+    if (L->sweep_variant == BTRT_SWEEP_TB2) {
+        // pairs of steps in one launch: inputs from buffer cur, outputs to the other
+        for (; nsteps >= 2; nsteps -= 2) {
+            SweepParams<float> pa, pb;
+            fill_params(L, pa, L->step + 1, false);
+            fill_params(L, pb, L->step + 2, false);
+            CUDA_TRY(launch_sweep_tb2(pa, pb, sweep_mode(L), L->stream));
+            L->cur = 1 - L->cur;
+            L->step += 2;
+        }
+    }
     for (int64_t k = 0; k < nsteps; ++k) {
         btrt_status st = launch(L, L->step + 1, false);
         if (st != BTRT_OK) return st;
@@ -824,8 +835,12 @@ btrt_status btrt_check(btrt_lattice L, int32_t *flags) {
 
 btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant) {
     if (!L) return fail(BTRT_EINVAL, "null lattice");
-    if (variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN && variant != BTRT_SWEEP_TMA)
+    if (variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN && variant != BTRT_SWEEP_TMA &&
+        variant != BTRT_SWEEP_TB2)
         return fail(BTRT_EINVAL, "unknown sweep variant %d", variant);
+    if (variant == BTRT_SWEEP_TB2 &&
+        (L->g.compute != BTRT_F32 || L->g.storage != BTRT_F32 || L->g.shift != BTRT_SHIFT_REF))
+        return fail(BTRT_EINVAL, "the two-step sweep serves FP32 compute with FP32 storage and the reference shift");
     if (variant == BTRT_SWEEP_TMA && !L->have_tma)
         return fail(BTRT_EINVAL, "the TMA sweep serves FP32-compute lattices whose tensor maps could be encoded");
     L->sweep_variant = variant;

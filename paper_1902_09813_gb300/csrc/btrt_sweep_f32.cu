@@ -13,4 +13,8 @@ cudaError_t launch_sweep_tma_f32(const SweepParams<float> &p, int shift, int mod
     return launch_tma_storage<float>(p, shift, mode, in_map, out_map, s);
 }
 
+cudaError_t launch_sweep_tb2(const SweepParams<float> &pa, const SweepParams<float> &pb, int mode, cudaStream_t s) {
+    return launch_tb2_storage<float>(pa, pb, mode, s);
+}
+
 }  // namespace btrt

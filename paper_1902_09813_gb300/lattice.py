@@ -165,8 +165,9 @@ class Lattice:
         return self
 
     def set_sweep_variant(self, variant: str):
-        """'auto', 'plain' or 'tma' (FP32-compute lattices)."""
-        code = {"auto": C.SWEEP_AUTO, "plain": C.SWEEP_PLAIN, "tma": C.SWEEP_TMA}[variant]
+        """'auto', 'plain', 'tma' or 'tb2' (two steps per launch; FP32 storage,
+        reference shift) for FP32-compute lattices."""
+        code = {"auto": C.SWEEP_AUTO, "plain": C.SWEEP_PLAIN, "tma": C.SWEEP_TMA, "tb2": C.SWEEP_TB2}[variant]
         C.check(self.lib.btrt_set_sweep_variant(self.handle, code))
         return self
 

@@ -390,3 +390,68 @@ def test_table1_presets_match_oracle(model):
     lat = _lattice(q).init(q.phi0(), t0=q.t0).step_walls(q, q.nsteps)
     o = oracle.OracleLattice(q, nthreads=cpu_threads()).init().step(q.nsteps)
     assert _rel(lat.phi_host(), o.phi()) <= TOL64
+
+
+# ---------------------------------------------------------------- two steps per launch
+TB_CASES = [
+    (100, 37, (0, 0, 0, 0), True, "trig"),
+    (100, 37, (1, 1, 1, 1), True, "trig"),
+    (65, 17, (0, 0, 1, 1), False, "const"),
+    (130, 50, (1, 1, 0, 0), False, "none"),
+    (3, 3, (0, 0, 0, 0), True, "trig"),
+    (3, 3, (1, 1, 1, 1), True, "const"),
+    (5, 97, (1, 1, 0, 0), True, "reaction"),
+    (33, 17, (0, 0, 0, 0), True, "reaction"),
+]
+
+
+@pytest.mark.parametrize("steps", [9, 10])
+@pytest.mark.parametrize("case", TB_CASES, ids=lambda c: f"{c[0]}x{c[1]}-bc{''.join(map(str, c[2]))}-{c[4]}")
+def test_tb2_sweep_bitwise_equals_plain(case, steps):
+    """Two steps per launch (first step kept in shared memory) and one step per
+    launch do the same arithmetic node by node: results are bitwise identical,
+    for odd step counts too (the last step runs in the plain form)."""
+    nx, ny, bc, nonlin, src = case
+    p = w.random_state_problem(nx, ny, seed=3 * nx + ny, bc=bc, nonlinear=nonlin, source=src,
+                               flux_q=2.5 if src == "reaction" else 2.0)
+    a = _lattice(p, "f32", "f32", shift="ref").set_sweep_variant("tb2")
+    b = _lattice(p, "f32", "f32", shift="ref").set_sweep_variant("plain")
+    a.init(p.phi0(), t0=p.t0).step(steps)
+    b.init(p.phi0(), t0=p.t0).step(steps)
+    assert np.array_equal(a.phi_host(), b.phi_host())
+    assert np.array_equal(a.read_f(), b.read_f())
+    assert a.time() == b.time()
+    assert a.check() == 0
+
+
+def test_tb2_fields_and_large_ragged_grid():
+    """Per-node tensor and source fields, and a 4099 x 4093 grid (ragged tiles at
+    both far edges): bitwise equal to the one-step sweep; the residual step
+    after two-step launches also matches."""
+    p = w.variable_tensor(n=70, alpha=1e-2, walls=True, t_end=0.2)
+    p = p.replace(dt=20.0 * p.dx ** 2, nsteps=11, phi_ref=0.0)
+    a = _lattice(p, "f32", "f32", shift="ref").set_sweep_variant("tb2")
+    b = _lattice(p, "f32", "f32", shift="ref").set_sweep_variant("plain")
+    a.init(p.phi0()).step(p.nsteps)
+    b.init(p.phi0()).step(p.nsteps)
+    assert np.array_equal(a.phi_host(), b.phi_host())
+    assert a.step_residual(5) == b.step_residual(5)
+    q = w.nonlinear_modes(n=4096, nsteps=4).replace(nx=4099, ny=4093)
+    a = _lattice(q, "f32", "f32", shift="ref").set_sweep_variant("tb2")
+    a.init(q.phi0()).step(4)
+    pa = a.phi_host()
+    del a
+    b = _lattice(q, "f32", "f32", shift="ref").set_sweep_variant("plain")
+    b.init(q.phi0()).step(4)
+    assert np.array_equal(pa, b.phi_host())
+
+
+def test_tb2_rejects_other_storage():
+    from paper_1902_09813_gb300 import _capi as C
+    p = w.random_state_problem(20, 20, seed=2)
+    with pytest.raises(C.BtrtError):
+        _lattice(p, "f32", "f16").set_sweep_variant("tb2")
+    with pytest.raises(C.BtrtError):
+        _lattice(p, "f32", "f32", shift="local").set_sweep_variant("tb2")
+    with pytest.raises(C.BtrtError):
+        _lattice(p, "f64").set_sweep_variant("tb2")
