@@ -50,6 +50,14 @@ __device__ __forceinline__ bool tb_coord(int &g, int n, int wall) {
 __device__ __forceinline__ void tb_pull(const SweepParams<float> &p, const float *reg, int rw, int rh, int lx,
                                         int ly, int gx, int gy, float (&d)[9]) {
     const int plane = rw * rh;
+    // no link of a node one or more nodes away from every bounce-back wall crosses one
+    const bool inner = (!p.hbb_x || (gx > 0 && gx < p.nx - 1)) && (!p.hbb_y || (gy > 0 && gy < p.ny - 1));
+    if (inner) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            d[i] = reg[BTRT_IX(p.flags, i * plane + (ly - ey_of(i)) * rw + (lx - ex_of(i)), 9 * plane)];
+        return;
+    }
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         const int sx = gx - ex_of(i), sy = gy - ey_of(i);
