@@ -44,16 +44,17 @@ def _peaks():
 
 
 # FP64 operations (add, mul or fma, one each) per node of the FP64 sweep, counted
-# from the kernel source (collide_linear with k0 = 1 plus the trig source term).
-FP64_OPS_PER_UPDATE_LINEAR = 59
-# GB300 FP64 peak: 1.25 TFLOP/s nominal (profiling recipe) = 0.625 T FMA/s, i.e.
+# from the kernel source (collide_fold in the k0 = 1 constant-coefficient form
+# plus the trig source term): 20 adds (moments 18, V +- 2), 25 FMAs, 6 multiplies.
+FP64_OPS_PER_UPDATE_LINEAR = 51
+# GB300 FP64 peak: 1.25 TFLOP/s nominal = 0.625 T FMA/s, i.e.
 # 0.625 T FP64 operations/s when every add, mul or fma takes one lane slot.
 FP64_PEAK_TOPS = 0.625
 # DRAM bytes per node of one FP64 sweep launch measured by ncu
 # (dram__bytes_read.sum + dram__bytes_write.sum) on the same kernel at 2048^2
 # (profiles/sweep_f64_mms2048_full.md), scaled to the benchmark by node count;
 # None when the kernel changed after the capture.
-FP64_TRAFFIC_PER_NODE = 149.1
+FP64_TRAFFIC_PER_NODE = 149.3
 
 
 def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):

@@ -253,6 +253,21 @@ void fill3(btrt3_lattice L, Sweep3Params<Real> &p, int64_t n, bool first) {
     p.k2_hbb = c.k2_mode == BTRT_K2_HBB;
     p.k2c = (Real)c.k2;
     p.k2 = (Real)L->k2;
+    {
+        const double k0 = c.k0, dk = L->k2 - k0;
+        p.Q[0] = (Real)(L->K1[0] - k0);
+        p.Q[1] = (Real)(L->K1[3] - k0);
+        p.Q[2] = (Real)(L->K1[5] - k0);
+        p.ka[0] = (Real)(1.5 * dk);
+        p.ka[1] = (Real)(0.25 * dk);
+        p.ka[2] = (Real)(0.125 * dk);
+        p.kak[0] = (Real)(-1.5 * k0);
+        p.kak[1] = (Real)(-0.25 * k0);
+        p.kak[2] = (Real)(-0.125 * k0);
+        p.a2x3 = (Real)(3.0 * c.a2);
+        p.k0x15 = (Real)(1.5 * k0);
+        p.k0_one = k0 == 1.0 ? 1 : 0;
+    }
     p.cond_limit = (Real)1.0e6;
     for (int k = 0; k < 6; ++k) p.A0d[k] = L->A0[k];
     p.a2d = c.a2;

@@ -328,31 +328,34 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
         p.Ys = tb + 2 * g.nx;
         p.Yc = tb + 2 * g.nx + g.ny;
     }
+    p.k0_one = c.k0 == 1.0 ? 1 : 0;
     p.first = first ? 1 : 0;
     p.flags = L->flags();
     // constants of the folded collision
     {
         const double k0 = c.k0, K1xx = L->K1[0], K1xy = L->K1[1], K1yy = L->K1[2];
-        const double kap = 4.5 * (L->k2 - k0);
-        const double w0 = 4.0 / 9.0, w1 = 1.0 / 9.0, w5 = 1.0 / 36.0;
+        const double dk = L->k2 - k0;
+        const double Px = K1xx * L->ux + K1xy * L->uy, Py = K1xy * L->ux + K1yy * L->uy;
+        const double gx = L->ux - 0.5 * Px, gy = L->uy - 0.5 * Py;
         FoldConsts<Real> &q = p.lin;
-        q.ux = (Real)L->ux;
-        q.uy = (Real)L->uy;
-        q.ux3 = (Real)(3.0 * k0 * L->ux);
-        q.uy3 = (Real)(3.0 * k0 * L->uy);
-        q.Qxx = (Real)(3.0 * (K1xx - k0));
-        q.Qxy = (Real)(3.0 * K1xy);
-        q.Qyy = (Real)(3.0 * (K1yy - k0));
-        q.gx = (Real)(3.0 * ((1.0 - 0.5 * K1xx) * L->ux - 0.5 * K1xy * L->uy));
-        q.gy = (Real)(3.0 * (-0.5 * K1xy * L->ux + (1.0 - 0.5 * K1yy) * L->uy));
+        q.Px = (Real)Px;
+        q.Py = (Real)Py;
+        q.Qxx = (Real)(K1xx - k0);
+        q.Qxy = (Real)K1xy;
+        q.Qyy = (Real)(K1yy - k0);
+        q.gx = (Real)gx;
+        q.gy = (Real)gy;
+        q.Pgx = (Real)(Px + gx);
+        q.Pgy = (Real)(Py + gy);
         q.k0 = (Real)k0;
         q.om = (Real)(1.0 - k0);
         q.k0x15 = (Real)(1.5 * k0);
-        q.c0 = (Real)(w0 * kap / 3.0);
-        q.k6 = (Real)(-w1 * kap / 6.0);
-        q.k6x3 = (Real)(-w1 * kap / 2.0);
-        q.kd = (Real)(-2.0 * w5 * kap / 3.0);
-        q.kdx3 = (Real)(-2.0 * w5 * kap);
+        q.c0 = (Real)(2.0 * dk / 3.0);
+        q.k6 = (Real)(-dk / 12.0);
+        q.k6x3 = (Real)(-dk / 4.0);
+        q.c0k = (Real)(-2.0 * k0 / 3.0);
+        q.k6k = (Real)(k0 / 12.0);
+        q.k6x3k = (Real)(k0 / 4.0);
         q.a2x3 = (Real)(3.0 * c.a2);
     }
     // the reference value of kShiftRef storage (zero otherwise)

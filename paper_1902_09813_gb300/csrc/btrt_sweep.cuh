@@ -21,6 +21,8 @@
 #include <cuda_fp16.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "btrt_dw.cuh"
 
 namespace btrt {
@@ -76,14 +78,14 @@ __device__ __forceinline__ long long checked_index(int *flags, long long idx, lo
 // the host in FP64.  kap = (9/2)(k2 - k0).
 template <typename Real>
 struct FoldConsts {
-    Real ux, uy;           // u^ (lattice units)
-    Real ux3, uy3;         // 3 k0 u^
-    Real Qxx, Qxy, Qyy;    // 3 (K1 - k0 I)          (constant K1)
-    Real gx, gy;           // 3 (I - K1/2) u^        (constant K1)
+    Real Px, Py;           // K1 u^                  (constant K1)
+    Real Qxx, Qxy, Qyy;    // K1 - k0 I
+    Real gx, gy;           // (I - K1/2) u^
+    Real Pgx, Pgy;         // K1 u^ + (I - K1/2) u^
     Real k0, om, k0x15;    // k0, 1 - k0, 1.5 k0
-    Real c0;               // w0 kap / 3             (constant k2)
-    Real k6, k6x3;         // -w1 kap / 6, 3 k6
-    Real kd, kdx3;         // -(2/3) w5 kap, 3 kd
+    Real c0;               // w0 kap / 3 = (2/3)(k2 - k0)   (constant k2)
+    Real k6, k6x3;         // -w1 kap / 6 = -(k2 - k0) / 12, 3 k6
+    Real c0k, k6k, k6x3k;  // -(2/3) k0, k0 / 12, k0 / 4   (k2 built per node)
     Real a2x3;             // 3 a2                   (phi-dependent coefficients)
 };
 
@@ -113,6 +115,7 @@ struct SweepParams {
     int bq_n, bq_h;        // q = bq_n + bq_h / 2 (bq_n >= 0) -> products and a square root; bq_n < 0: pow
     Real A0xx, A0xy, A0yy, a2;
     Real k0;
+    int k0_one;            // 1: k0 == 1
     int nonlin_A;          // 1: A depends on phi -> K1, k2 built per node
     int k2_hbb;            // 1: k2 from Eq. 62 at k1_eff
     Real k2c;              // constant k2
@@ -217,6 +220,20 @@ __device__ __forceinline__ Real reaction(const SweepParams<Real> &p, Real phi) {
     return p.react_rate * phi * (Real(1) - pe);
 }
 
+// K1 = (3 A^ + I/2)^-1 (Eq. 30) for A^ = (1 + a2 phi^2) A0^, built and inverted
+// in FP64 and rounded to FP32: the FP32 sweep's path for ill-conditioned blocks.
+// Not inlined, so that the FP32 sweeps issue none of its FP64 instructions at
+// well-conditioned nodes.
+struct K1f {
+    float xx, xy, yy;
+};
+static __device__ __noinline__ K1f k1_fp64(double phi, double a2, double bxx, double bxy, double byy) {
+    const double s3d = 3.0 + 3.0 * a2 * phi * phi;
+    const double dxx = s3d * bxx + 0.5, dxy = s3d * bxy, dyy = s3d * byy + 0.5;
+    const double id = 1.0 / (dxx * dyy - dxy * dxy);
+    return K1f{(float)(dyy * id), (float)(-dxy * id), (float)(dxx * id)};
+}
+
 // Moment-space form of Eq. 6 (Eqs. 94, 95, 99 with K2 = k2 Ihat), expanded back
 // into populations and written for shifted values d_i = f_i - w_i rs: rs = 0
 // (kShiftNone), rs = phi_ref (kShiftRef) or rs = phi^{n-1} of this node
@@ -226,11 +243,15 @@ __device__ __forceinline__ Real reaction(const SweepParams<Real> &p, Real phi) {
 //
 // With sigma = nxx + nyy and delta = nxx - nyy of the non-equilibrium second
 // moments, kap = (9/2)(k2 - k0) and a = k0 (phi - rs) + source:
-//   d_i^+ = (1 - k0) d_i + w_i (a + cC_i) + w_i 3 e_i . V - w_i kap H_i
+//   d_i^+ = (1 - k0) d_i + w_i (a + cC_i) + 3 w_i e_i . V - w_i kap H_i
 //   w0 kap H_0 = -(w0 kap/3) sigma,  w1 kap H_x,y = (w1 kap/6)(sigma +- 3 delta),
-//   w5 kap H_d = (2/3) w5 kap (sigma +- 3 nxy),
-//   V = k0 B - (K1 - k0 I)(M1 - B) + (I - K1/2)(B^n - B^{n-1})    (Eq. 11),
+//   w5 kap H_d = (2/3) w5 kap (sigma +- 3 nxy)   (w1 kap / 6 = (2/3) w5 kap = (k2 - k0) / 12),
+//   V = k0 B - (K1 - k0 I)(M1 - B) + (I - K1/2)(B^n - B^{n-1})    (Eq. 11)
+//     = K1 (B - M1 - dB/2) + k0 M1 + dB,   dB = B^n - B^{n-1},
 //   cC_i = (3/2) k0 (C - phi)(|e_i|^2 - 2/3)   (zero when C = phi).
+// The second form of V takes ten operations where the first takes twenty-one;
+// for B = u phi it is K1 u phi - (K1 - k0 I) M1 + (I - K1/2) u dphi, three
+// per-lattice vectors and a matrix.
 // MODE selects per-lattice constants (B = u phi, C = phi, constant A: kLinear,
 // kLinearK0One) or per-node coefficient evaluation (kGeneral: nonlinear B, C and
 // A(x, phi) with the first-order block K1 = (3 A^ + I/2)^-1 of Eq. 30 and k2 from
@@ -258,25 +279,31 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
     // phi^n - phi^{n-1}; with the local shift rs = phi^{n-1}, so it is phid itself
     const Real dphi = first ? Real(0) : (SH == kShiftLocal ? phid : phi - phi_prev);
 
-    Real Vx, Vy, c0, k6, k6x3, kd, kdx3;
+    Real Vx, Vy, c0, k6, k6x3;
     Real cmid = phid;                                   // C - rs
     Real cc = Real(0);                                  // (3/2) k0 (C - phi)
     if constexpr (MODE != kGeneral) {
-        const Real mx = fma(-L.ux, phi, jx), my = fma(-L.uy, phi, jy);
-        Vx = fma(L.gx, dphi, fma(L.ux3, phi, -fma(L.Qxy, my, L.Qxx * mx)));
-        Vy = fma(L.gy, dphi, fma(L.uy3, phi, -fma(L.Qyy, my, L.Qxy * mx)));
+        const Real qx = fma(L.Qxy, jy, L.Qxx * jx), qy = fma(L.Qyy, jy, L.Qxy * jx);   // (K1 - k0 I) M1
+        if constexpr (SH == kShiftLocal) {
+            Vx = fma(L.gx, dphi, fma(L.Px, phi, -qx));
+            Vy = fma(L.gy, dphi, fma(L.Py, phi, -qy));
+        } else {
+            // g dphi = g phi - g phi^{n-1}: the first term joins the coefficient of phi
+            const Real cx = first ? L.Px : L.Pgx, cy = first ? L.Py : L.Pgy;
+            const Real gx = first ? Real(0) : L.gx, gy = first ? Real(0) : L.gy;
+            Vx = fma(-gx, phi_prev, fma(cx, phi, -qx));
+            Vy = fma(-gy, phi_prev, fma(cy, phi, -qy));
+        }
         c0 = L.c0;
         k6 = L.k6;
         k6x3 = L.k6x3;
-        kd = L.kd;
-        kdx3 = L.kdx3;
     } else {
         // coefficients at phi (Eq. 1 families): B = u phi + bg phi^q and
         // dB = B(phi) - B(phi_prev) = u dphi + bg (phi^q - phi_prev^q), for q = 2
         // factored as bg (phi + phi_prev) dphi
+        const Real p2 = phi * phi;
         Real Bx, By, dBx, dBy;
         if (p.bq2) {
-            const Real p2 = phi * phi;
             Bx = fma(p.ux, phi, p.bgx * p2);
             By = fma(p.uy, phi, p.bgy * p2);
             const Real sp = phi + phi_prev;
@@ -290,11 +317,11 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
             dBx = fma(p.ux, dphi, p.bgx * dg);
             dBy = fma(p.uy, dphi, p.bgy * dg);
         }
-        const Real Cm = p.c3 * phi * phi * phi;          // C(phi) - phi
+        const Real Cm = p.c3 * p2 * phi;                 // C(phi) - phi
         cmid = phid + Cm;
         cc = L.k0x15 * Cm;
         // first-order block K1 = (3 A^ + I/2)^-1 (Eq. 30), A^ = (1 + a2 phi^2) A0^
-        const Real s3 = fma(L.a2x3, phi * phi, Real(3));
+        const Real s3 = fma(L.a2x3, p2, Real(3));
         Real a0xx = p.A0xx, a0xy = p.A0xy, a0yy = p.A0yy;
         if (p.Af) {   // spatially varying tensor A(x)
             a0xx = p.Af[BTRT_IX(p.flags, node, p.plane)];
@@ -313,19 +340,11 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
             // ill-conditioned FP32 block: build it again from FP64 coefficients (the
             // FP32-rounded entries would carry errors the condition number amplifies)
             // and invert it in FP64
-            const double ph = static_cast<double>(phi);
-            const double s3d = 3.0 + 3.0 * p.a2d * ph * ph;
-            double bxx = p.A0d[0], bxy = p.A0d[1], byy = p.A0d[2];
-            if (p.Af) {
-                bxx = (double)a0xx;
-                bxy = (double)a0xy;
-                byy = (double)a0yy;
-            }
-            const double dxx = s3d * bxx + 0.5, dxy = s3d * bxy, dyy = s3d * byy + 0.5;
-            const double id = 1.0 / (dxx * dyy - dxy * dxy);
-            K1xx = (Real)(dyy * id);
-            K1xy = (Real)(-dxy * id);
-            K1yy = (Real)(dxx * id);
+            const K1f k = p.Af ? k1_fp64(static_cast<double>(phi), p.a2d, (double)a0xx, (double)a0xy, (double)a0yy)
+                               : k1_fp64(static_cast<double>(phi), p.a2d, p.A0d[0], p.A0d[1], p.A0d[2]);
+            K1xx = (Real)k.xx;
+            K1xy = (Real)k.xy;
+            K1yy = (Real)k.yy;
         } else {
             const Real id = quot(Real(1), det);
             K1xx = myy * id;
@@ -334,20 +353,12 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
         }
         // Eq. 62 at k1_eff = 2/tr:  k2 = 8 (k1 - 2) / (3 (k1 - 4)) = (8/3)(tr - 1) / (2 tr - 1)
         const Real k2 = p.k2_hbb ? quot(cst<Real>(8, 3) * (tr - Real(1)), fma(Real(2), tr, Real(-1))) : p.k2c;
-        const Real kap = cst<Real>(9, 2) * (k2 - L.k0);
-        const Real mx = jx - Bx, my = jy - By;
-        const Real qx = fma(K1xx - L.k0, mx, K1xy * my);
-        const Real qy = fma(K1yy - L.k0, my, K1xy * mx);
-        const Real hx = Real(0.5) * K1xy;
-        const Real gx = fma(Real(1) - Real(0.5) * K1xx, dBx, -(hx * dBy));
-        const Real gy = fma(Real(1) - Real(0.5) * K1yy, dBy, -(hx * dBx));
-        Vx = Real(3) * (fma(L.k0, Bx, gx) - qx);
-        Vy = Real(3) * (fma(L.k0, By, gy) - qy);
-        c0 = cst<Real>(4, 27) * kap;                     // w0 kap / 3
-        k6 = cst<Real>(-1, 54) * kap;                    // -w1 kap / 6
-        k6x3 = cst<Real>(-1, 18) * kap;
-        kd = cst<Real>(-1, 54) * kap;                    // -(2/3) w5 kap
-        kdx3 = cst<Real>(-1, 18) * kap;
+        c0 = fma(cst<Real>(2, 3), k2, L.c0k);            // (2/3)(k2 - k0) = w0 kap / 3
+        k6 = fma(cst<Real>(-1, 12), k2, L.k6k);          // -(k2 - k0) / 12
+        k6x3 = fma(cst<Real>(-1, 4), k2, L.k6x3k);       // 3 k6
+        const Real ex = fma(Real(-0.5), dBx, Bx - jx), ey = fma(Real(-0.5), dBy, By - jy);
+        Vx = fma(K1xx, ex, fma(K1xy, ey, fma(L.k0, jx, dBx)));
+        Vy = fma(K1xy, ex, fma(K1yy, ey, fma(L.k0, jy, dBy)));
     }
     const Real sig = fma(cst<Real>(-2, 3), cmid, fma(Real(2), sd, a1324));
     Real a = K0ONE ? phid : L.k0 * phid;
@@ -361,30 +372,35 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
     }
     if constexpr (SRC != 0) a = fma(p.src_val, srcv, a);
     const Real w0 = cst<Real>(4, 9), w1 = cst<Real>(1, 9), w5 = cst<Real>(1, 36);
+    const Real v1 = cst<Real>(1, 3), v5 = cst<Real>(1, 12);   // 3 w1, 3 w5
     Real r[9];
     if constexpr (MODE == kGeneral) {
         r[0] = fma(c0, sig, w0 * fma(cst<Real>(-2, 3), cc, a));
     } else {
         r[0] = fma(c0, sig, w0 * a);
     }
-    const Real k6s = k6 * sig;
-    const Real hxp = fma(k6x3, del, k6s), hyp = fma(-k6x3, del, k6s);
     const Real wa1 = MODE == kGeneral ? w1 * fma(cst<Real>(1, 3), cc, a) : w1 * a;
-    const Real A1 = wa1 + hxp, A2 = wa1 + hyp;
-    r[1] = fma(w1, Vx, A1);
-    r[3] = fma(-w1, Vx, A1);
-    r[2] = fma(w1, Vy, A2);
-    r[4] = fma(-w1, Vy, A2);
-    const Real kds = kd * sig;
-    const Real hp = fma(kdx3, pxy, kds), hm = fma(-kdx3, pxy, kds);
+    const Real T1 = fma(k6, sig, wa1);
+    const Real A1 = fma(k6x3, del, T1), A2 = fma(-k6x3, del, T1);
+    r[1] = fma(v1, Vx, A1);
+    r[3] = fma(-v1, Vx, A1);
+    r[2] = fma(v1, Vy, A2);
+    r[4] = fma(-v1, Vy, A2);
     const Real wa5 = MODE == kGeneral ? w5 * fma(cst<Real>(4, 3), cc, a) : w5 * a;
-    const Real P = wa5 + hp, M = wa5 + hm;
+    const Real T5 = fma(k6, sig, wa5);
+    const Real P = fma(k6x3, pxy, T5), M = fma(-k6x3, pxy, T5);
     const Real Vp = Vx + Vy, Vm = Vx - Vy;
-    r[5] = fma(w5, Vp, P);
-    r[7] = fma(-w5, Vp, P);
-    r[6] = fma(-w5, Vm, M);
-    r[8] = fma(w5, Vm, M);
-    if constexpr (K0ONE) {
+    r[5] = fma(v5, Vp, P);
+    r[7] = fma(-v5, Vp, P);
+    r[6] = fma(-v5, Vm, M);
+    r[8] = fma(v5, Vm, M);
+    // k0 = 1: nothing of d_i is kept (bitwise the same as (1 - k0) d_i + r_i).  A
+    // run-time test where it saves more than it costs: the per-node coefficient
+    // path and the double-word sweep (an FMA is a dozen instructions there); the
+    // FP64 sweep has its own variant for k0 = 1, and the FP32 constant-coefficient
+    // sweep is bound by memory, where the test's extra registers cost occupancy.
+    constexpr bool K0RT = MODE == kGeneral || std::is_same<Real, dw>::value;
+    if (K0ONE || (K0RT && p.k0_one)) {
 #pragma unroll
         for (int i = 0; i < 9; ++i) d[i] = r[i];
     } else {

@@ -80,6 +80,11 @@ struct Sweep3Params {
     Real k2c;
     Real K1[6];            // constant K1 (symmetric) and k2 when A is constant
     Real k2;
+    Real Q[3];             // diagonal of K1 - k0 I (constant K1)
+    Real ka[3];            // w_i kap, kap = (9/2)(k2 - k0), for |c|^2 = 0, 1, 2 (constant k2)
+    Real kak[3];           // -(3/2) k0, -k0/4, -k0/8: w_i kap = (3/2, 1/4, 1/8) k2 + kak (k2 per node)
+    Real a2x3, k0x15;      // 3 a2, (3/2) k0
+    int k0_one;            // 1: k0 == 1
     Real Ku[3];            // constant-coefficient fold: K1 u (B = u phi)
     Real gu[3];            //   and (I - K1/2) u
     Real cond_limit;       // FP32: tr^3 > cond_limit det -> build and invert the block in FP64
@@ -123,6 +128,24 @@ __device__ __forceinline__ void equilibrium3(const Sweep3Params<Real> &p, Real p
     }
 }
 
+// K1 = (3 A^ + I/2)^-1 (Eq. 30) for A^ = (1 + a2 phi^2) A0^ (xx, xy, xz, yy, yz,
+// zz), built and inverted in FP64 by cofactors and rounded to FP32: the FP32
+// sweep's path for ill-conditioned blocks, not inlined so that well-conditioned
+// nodes issue none of its FP64 instructions.
+struct K1f3 {
+    float v[6];
+};
+static __device__ __noinline__ K1f3 k1_fp64_3(double phi, double a2, const double *A0) {
+    const double s3d = 3.0 + 3.0 * a2 * phi * phi;
+    const double dxx = s3d * A0[0] + 0.5, dxy = s3d * A0[1], dxz = s3d * A0[2];
+    const double dyy = s3d * A0[3] + 0.5, dyz = s3d * A0[4], dzz = s3d * A0[5] + 0.5;
+    const double ex = dyy * dzz - dyz * dyz, exy = dxz * dyz - dxy * dzz, exz = dxy * dyz - dxz * dyy;
+    const double ey = dxx * dzz - dxz * dxz, eyz = dxy * dxz - dxx * dyz, ez = dxx * dyy - dxy * dxy;
+    const double id = 1.0 / (dxx * ex + dxy * exy + dxz * exz);
+    return K1f3{{(float)(ex * id), (float)(exy * id), (float)(exz * id), (float)(ey * id), (float)(eyz * id),
+                 (float)(ez * id)}};
+}
+
 // Moment-space collision of one node in shifted form d_i = f_i - w_i rs
 // (rs = 0, phi_ref or phi^{n-1} of the node):
 //   d_i^+ = (1 - k0) d_i + w_i [a + cC_i + 3 c_i.V - kap H_i],
@@ -153,32 +176,30 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
 
     // coefficients
     Real Bx, By, Bz, dBx, dBy, dBz, Cm = Real(0);
-    if constexpr (MODE != kGeneral) {
-        Bx = By = Bz = dBx = dBy = dBz = Real(0);   // folded into Ku, gu below
-    } else if (p.bq2) {
-        const Real p2 = phi * phi;
-        Bx = fma(p.ux, phi, p.bgx * p2);
-        By = fma(p.uy, phi, p.bgy * p2);
-        Bz = fma(p.uz, phi, p.bgz * p2);
-        const Real sp = phi + phi_prev;
-        dBx = fma(p.bgx, sp, p.ux) * dphi;
-        dBy = fma(p.bgy, sp, p.uy) * dphi;
-        dBz = fma(p.bgz, sp, p.uz) * dphi;
-    } else {
-        const Real gq = pow_half(phi, p.bq, p.bq_n, p.bq_h);
-        const Real dg = first ? Real(0) : gq - pow_half(phi_prev, p.bq, p.bq_n, p.bq_h);
-        Bx = fma(p.ux, phi, p.bgx * gq);
-        By = fma(p.uy, phi, p.bgy * gq);
-        Bz = fma(p.uz, phi, p.bgz * gq);
-        dBx = fma(p.ux, dphi, p.bgx * dg);
-        dBy = fma(p.uy, dphi, p.bgy * dg);
-        dBz = fma(p.uz, dphi, p.bgz * dg);
-    }
-    Real Kxx, Kxy, Kxz, Kyy, Kyz, Kzz, k2;
+    Real Kxx, Kxy, Kxz, Kyy, Kyz, Kzz, k2 = Real(0);
     if constexpr (MODE == kGeneral) {
-        Cm = p.c3 * phi * phi * phi;
+        const Real p2 = phi * phi;
+        if (p.bq2) {
+            Bx = fma(p.ux, phi, p.bgx * p2);
+            By = fma(p.uy, phi, p.bgy * p2);
+            Bz = fma(p.uz, phi, p.bgz * p2);
+            const Real sp = phi + phi_prev;
+            dBx = fma(p.bgx, sp, p.ux) * dphi;
+            dBy = fma(p.bgy, sp, p.uy) * dphi;
+            dBz = fma(p.bgz, sp, p.uz) * dphi;
+        } else {
+            const Real gq = pow_half(phi, p.bq, p.bq_n, p.bq_h);
+            const Real dg = first ? Real(0) : gq - pow_half(phi_prev, p.bq, p.bq_n, p.bq_h);
+            Bx = fma(p.ux, phi, p.bgx * gq);
+            By = fma(p.uy, phi, p.bgy * gq);
+            Bz = fma(p.uz, phi, p.bgz * gq);
+            dBx = fma(p.ux, dphi, p.bgx * dg);
+            dBy = fma(p.uy, dphi, p.bgy * dg);
+            dBz = fma(p.uz, dphi, p.bgz * dg);
+        }
+        Cm = p.c3 * p2 * phi;
         // K1 = (3 A^ + I/2)^-1, A^ = (1 + a2 phi^2) A0^ (Eq. 30), symmetric 3x3 by cofactors
-        const Real s3 = fma(Real(3) * p.a2, phi * phi, Real(3));
+        const Real s3 = fma(p.a2x3, p2, Real(3));
         const Real mxx = fma(s3, p.A0[0], Real(0.5)), mxy = s3 * p.A0[1], mxz = s3 * p.A0[2];
         const Real myy = fma(s3, p.A0[3], Real(0.5)), myz = s3 * p.A0[4];
         const Real mzz = fma(s3, p.A0[5], Real(0.5));
@@ -195,15 +216,9 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
         if (ill) {
             // ill-conditioned FP32 block: rebuilt from FP64 coefficients (FP32-rounded
             // entries carry errors the condition number amplifies), inverted in FP64
-            const double ph = static_cast<double>(phi);
-            const double s3d = 3.0 + 3.0 * p.a2d * ph * ph;
-            const double dxx = s3d * p.A0d[0] + 0.5, dxy = s3d * p.A0d[1], dxz = s3d * p.A0d[2];
-            const double dyy = s3d * p.A0d[3] + 0.5, dyz = s3d * p.A0d[4], dzz = s3d * p.A0d[5] + 0.5;
-            const double ex = dyy * dzz - dyz * dyz, exy = dxz * dyz - dxy * dzz, exz = dxy * dyz - dxz * dyy;
-            const double ey = dxx * dzz - dxz * dxz, eyz = dxy * dxz - dxx * dyz, ez = dxx * dyy - dxy * dxy;
-            const double id = 1.0 / (dxx * ex + dxy * exy + dxz * exz);
-            Kxx = (Real)(ex * id); Kxy = (Real)(exy * id); Kxz = (Real)(exz * id);
-            Kyy = (Real)(ey * id); Kyz = (Real)(eyz * id); Kzz = (Real)(ez * id);
+            const K1f3 k = k1_fp64_3(static_cast<double>(phi), p.a2d, p.A0d);
+            Kxx = (Real)k.v[0]; Kxy = (Real)k.v[1]; Kxz = (Real)k.v[2];
+            Kyy = (Real)k.v[3]; Kyz = (Real)k.v[4]; Kzz = (Real)k.v[5];
         } else {
             const Real id = quot(Real(1), det);
             Kxx = cxx * id; Kxy = cxy * id; Kxz = cxz * id;
@@ -212,43 +227,52 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
         // Eq. 62 at k1_eff = 3/tr:  k2 = (8/3)(2 tr - 3) / (4 tr - 3)
         k2 = p.k2_hbb ? quot(cst<Real>(8, 3) * fma(Real(2), tr, Real(-3)), fma(Real(4), tr, Real(-3))) : p.k2c;
     } else {
+        Bx = By = Bz = dBx = dBy = dBz = Real(0);   // folded into Ku, gu below
         Kxx = p.K1[0]; Kxy = p.K1[1]; Kxz = p.K1[2]; Kyy = p.K1[3]; Kyz = p.K1[4]; Kzz = p.K1[5];
-        k2 = p.k2;
     }
-    // V = k0 B - (K1 - k0 I) M1 + (I - K1/2) dB (times 3 below)
-    const Real k0 = p.k0;
+    // V = k0 B - (K1 - k0 I)(j - B) + (I - K1/2) dB = K1 (B - j - dB/2) + k0 j + dB,
+    // dB = B^n - B^{n-1} (its first form takes 36 operations, the second 18); for
+    // B = u phi it is K1 u phi - (K1 - k0 I) j + (I - K1/2) u dphi
     Real Vx, Vy, Vz;
     if constexpr (MODE == kGeneral) {
-        const Real mx = jx - Bx, my = jy - By, mz = jz - Bz;
-        const Real qx = fma(Kxx - k0, mx, fma(Kxy, my, Kxz * mz));
-        const Real qy = fma(Kxy, mx, fma(Kyy - k0, my, Kyz * mz));
-        const Real qz = fma(Kxz, mx, fma(Kyz, my, (Kzz - k0) * mz));
-        const Real hx = fma(Real(-0.5), fma(Kxx, dBx, fma(Kxy, dBy, Kxz * dBz)), dBx);
-        const Real hy = fma(Real(-0.5), fma(Kxy, dBx, fma(Kyy, dBy, Kyz * dBz)), dBy);
-        const Real hz = fma(Real(-0.5), fma(Kxz, dBx, fma(Kyz, dBy, Kzz * dBz)), dBz);
-        Vx = Real(3) * (fma(k0, Bx, hx) - qx);
-        Vy = Real(3) * (fma(k0, By, hy) - qy);
-        Vz = Real(3) * (fma(k0, Bz, hz) - qz);
+        const Real ex = fma(Real(-0.5), dBx, Bx - jx);
+        const Real ey = fma(Real(-0.5), dBy, By - jy);
+        const Real ez = fma(Real(-0.5), dBz, Bz - jz);
+        Vx = fma(Kxx, ex, fma(Kxy, ey, fma(Kxz, ez, fma(p.k0, jx, dBx))));
+        Vy = fma(Kxy, ex, fma(Kyy, ey, fma(Kyz, ez, fma(p.k0, jy, dBy))));
+        Vz = fma(Kxz, ex, fma(Kyz, ey, fma(Kzz, ez, fma(p.k0, jz, dBz))));
     } else {
-        // constant K1, B = u phi: V = K1 u phi - (K1 - k0 I) j + (I - K1/2) u dphi
         (void)Bx; (void)By; (void)Bz; (void)dBx; (void)dBy; (void)dBz;
-        const Real qx = fma(Kxx - k0, jx, fma(Kxy, jy, Kxz * jz));
-        const Real qy = fma(Kxy, jx, fma(Kyy - k0, jy, Kyz * jz));
-        const Real qz = fma(Kxz, jx, fma(Kyz, jy, (Kzz - k0) * jz));
-        Vx = Real(3) * (fma(p.gu[0], dphi, fma(p.Ku[0], phi, -qx)));
-        Vy = Real(3) * (fma(p.gu[1], dphi, fma(p.Ku[1], phi, -qy)));
-        Vz = Real(3) * (fma(p.gu[2], dphi, fma(p.Ku[2], phi, -qz)));
+        const Real qx = fma(p.Q[0], jx, fma(Kxy, jy, Kxz * jz));
+        const Real qy = fma(Kxy, jx, fma(p.Q[1], jy, Kyz * jz));
+        const Real qz = fma(Kxz, jx, fma(Kyz, jy, p.Q[2] * jz));
+        Vx = fma(p.gu[0], dphi, fma(p.Ku[0], phi, -qx));
+        Vy = fma(p.gu[1], dphi, fma(p.Ku[1], phi, -qy));
+        Vz = fma(p.gu[2], dphi, fma(p.Ku[2], phi, -qz));
     }
 
-    // second-order non-equilibrium moments, H_i pieces
-    const Real cmid = phid + Cm;                                  // C - rs
+    // second-order non-equilibrium moments M2 = Pi - (C - rs)/3 I: the deviatoric
+    // parts h_a = Pi_aa - tr(Pi)/3 (C and the shift cancel from them) and
+    // t3 = tr(M2)/3; H_i = c_i c_i : M2 - t3 is then h_a (axis a), t3 - h_c (the
+    // face diagonals normal to axis c, from h_x + h_y + h_z = 0) +- 2 M_ab
     const Real third = cst<Real>(1, 3);
-    const Real Mxx = fma(-third, cmid, Pxx), Myy = fma(-third, cmid, Pyy), Mzz = fma(-third, cmid, Pzz);
-    const Real trM = (Mxx + Myy) + Mzz;
-    const Real t3 = third * trM;
-    const Real kap = cst<Real>(9, 2) * (k2 - k0);
+    const Real tP3 = third * ((Pxx + Pyy) + Pzz);
+    const Real hx = Pxx - tP3, hy = Pyy - tP3, hz = Pzz - tP3;
+    const Real cmid = MODE == kGeneral ? phid + Cm : phid;       // C - rs
+    const Real t3 = fma(-third, cmid, tP3);
+    // w_i kap for the three speeds, kap = (9/2)(k2 - k0)
+    Real ka0, ka1, ka2;
+    if constexpr (MODE == kGeneral) {
+        ka0 = fma(Real(1.5), k2, p.kak[0]);
+        ka1 = fma(Real(0.25), k2, p.kak[1]);
+        ka2 = fma(Real(0.125), k2, p.kak[2]);
+    } else {
+        ka0 = p.ka[0];
+        ka1 = p.ka[1];
+        ka2 = p.ka[2];
+    }
 
-    Real a = MODE == kLinearK0One ? phid : k0 * phid;
+    Real a = MODE == kLinearK0One ? phid : p.k0 * phid;
     if constexpr (SRC == kSrcReaction || SRC == kSrcRuntime) {
         if (SRC == kSrcReaction || p.src_kind == kSrcReaction) {
             const Real Sn =
@@ -261,33 +285,35 @@ __device__ __forceinline__ Real collide3(const Sweep3Params<Real> &p, Real (&d)[
         }
     }
     if constexpr (SRC != kSrcNone) a = fma(p.src_val, srcv, a);
-    const Real cC = Real(1.5) * k0 * Cm;                          // (3/2) k0 (C - phi)
+    const Real cC = MODE == kGeneral ? p.k0x15 * Cm : Real(0);   // (3/2) k0 (C - phi)
 
     const Real w0 = cst<Real>(1, 3), w1 = cst<Real>(1, 18), w2 = cst<Real>(1, 36);
+    const Real v1 = cst<Real>(1, 6), v2 = cst<Real>(1, 12);      // 3 w1, 3 w2
     Real r[19];
-    r[0] = w0 * (a - cC + kap * t3);
-    // axis directions: H = M_aa - tr/3
-    const Real bx = w1 * fma(-kap, Mxx - t3, a), by = w1 * fma(-kap, Myy - t3, a), bz = w1 * fma(-kap, Mzz - t3, a);
-    const Real v1x = w1 * Vx, v1y = w1 * Vy, v1z = w1 * Vz;
-    r[1] = bx + v1x; r[2] = bx - v1x;
-    r[3] = by + v1y; r[4] = by - v1y;
-    r[5] = bz + v1z; r[6] = bz - v1z;
-    // face diagonals: H = M_aa + M_bb +- 2 M_ab - tr/3
-    const Real ac = a + cC;
-    const Real bxy = w2 * fma(-kap, (Mxx + Myy) - t3, ac);
-    const Real bxz = w2 * fma(-kap, (Mxx + Mzz) - t3, ac);
-    const Real byz = w2 * fma(-kap, (Myy + Mzz) - t3, ac);
-    const Real pxy = w2 * Real(2) * kap * Pxy, pxz = w2 * Real(2) * kap * Pxz, pyz = w2 * Real(2) * kap * Pyz;
-    const Real vxpy = w2 * (Vx + Vy), vxmy = w2 * (Vx - Vy);
-    const Real vxpz = w2 * (Vx + Vz), vxmz = w2 * (Vx - Vz);
-    const Real vypz = w2 * (Vy + Vz), vymz = w2 * (Vy - Vz);
-    r[7] = (bxy - pxy) + vxpy;  r[10] = (bxy - pxy) - vxpy;
-    r[8] = (bxy + pxy) - vxmy;  r[9] = (bxy + pxy) + vxmy;
-    r[11] = (bxz - pxz) + vxpz; r[14] = (bxz - pxz) - vxpz;
-    r[12] = (bxz + pxz) - vxmz; r[13] = (bxz + pxz) + vxmz;
-    r[15] = (byz - pyz) + vypz; r[18] = (byz - pyz) - vypz;
-    r[16] = (byz + pyz) - vymz; r[17] = (byz + pyz) + vymz;
-    if constexpr (MODE == kLinearK0One) {
+    r[0] = fma(ka0, t3, w0 * (MODE == kGeneral ? a - cC : a));
+    // axis directions: w1 (a - kap h_a) +- 3 w1 V_a
+    const Real w1a = w1 * a;
+    const Real bx = fma(-ka1, hx, w1a), by = fma(-ka1, hy, w1a), bz = fma(-ka1, hz, w1a);
+    r[1] = fma(v1, Vx, bx); r[2] = fma(-v1, Vx, bx);
+    r[3] = fma(v1, Vy, by); r[4] = fma(-v1, Vy, by);
+    r[5] = fma(v1, Vz, bz); r[6] = fma(-v1, Vz, bz);
+    // face diagonals: w2 (a + cC - kap (t3 - h_c)) -+ 2 w2 kap M_ab (2 w2 = w1) + 3 w2 c_i . V
+    const Real G = fma(-ka2, t3, w2 * (MODE == kGeneral ? a + cC : a));
+    const Real bxy = fma(ka2, hz, G), bxz = fma(ka2, hy, G), byz = fma(ka2, hx, G);
+    const Real bxym = fma(-ka1, Pxy, bxy), bxyp = fma(ka1, Pxy, bxy);
+    const Real bxzm = fma(-ka1, Pxz, bxz), bxzp = fma(ka1, Pxz, bxz);
+    const Real byzm = fma(-ka1, Pyz, byz), byzp = fma(ka1, Pyz, byz);
+    const Real sxyp = Vx + Vy, sxym = Vx - Vy;
+    const Real sxzp = Vx + Vz, sxzm = Vx - Vz;
+    const Real syzp = Vy + Vz, syzm = Vy - Vz;
+    r[7] = fma(v2, sxyp, bxym);  r[10] = fma(-v2, sxyp, bxym);
+    r[8] = fma(-v2, sxym, bxyp); r[9] = fma(v2, sxym, bxyp);
+    r[11] = fma(v2, sxzp, bxzm); r[14] = fma(-v2, sxzp, bxzm);
+    r[12] = fma(-v2, sxzm, bxzp); r[13] = fma(v2, sxzm, bxzp);
+    r[15] = fma(v2, syzp, byzm); r[18] = fma(-v2, syzp, byzm);
+    r[16] = fma(-v2, syzm, byzp); r[17] = fma(v2, syzm, byzp);
+    // k0 = 1 (bitwise the same as (1 - k0) d_i + r_i); constant coefficients have their own variant
+    if (MODE == kLinearK0One || (MODE == kGeneral && p.k0_one)) {
 #pragma unroll
         for (int i = 0; i < 19; ++i) d[i] = r[i];
     } else {
