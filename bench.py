@@ -45,8 +45,8 @@ def _peaks():
 
 # FP64 operations (add, mul or fma, one each) per node of the FP64 sweep, counted
 # from the kernel source (collide_fold in the k0 = 1 constant-coefficient form
-# plus the trig source term): 20 adds (moments 18, V +- 2), 25 FMAs, 6 multiplies.
-FP64_OPS_PER_UPDATE_LINEAR = 51
+# plus the trig source term): 20 adds (moments 18, V +- 2), 25 FMAs, 5 multiplies.
+FP64_OPS_PER_UPDATE_LINEAR = 50
 # GB300 FP64 peak: 1.25 TFLOP/s nominal = 0.625 T FMA/s, i.e.
 # 0.625 T FP64 operations/s when every add, mul or fma takes one lane slot.
 FP64_PEAK_TOPS = 0.625
@@ -535,14 +535,27 @@ def run_serving(args, rates=(100.0, 500.0, 2000.0), count=96, seed=1):
     import workloads as w
     from paper_1902_09813_gb300.serve import Server, depth_series, poisson_trace, serve_sequential, summarize
 
+    import torch
+
+    from paper_1902_09813_gb300 import Batch, Lattice
+
     probs = w.batched_instances(count=count, seed=seed, nsteps=0)
     for p in probs:
         p.phi_ref = float(p.phi0().mean())
+    # tile shape of the server's batches: the autotuner on a throw-away batch of all
+    # the requests (its trial steps advance only these copies), before any trace runs
+    lats = [Lattice.from_problem(p, compute="f32", storage="f16").init(p.phi0(), t0=p.t0) for p in probs]
+    b = Batch(lats)
+    shape = b.autotune(steps_per_trial=3)
+    b.close()
+    del lats, b
+    torch.cuda.empty_cache()
     out = {"requests_per_rate": count, "slice_steps": 100, "max_steps": 20000, "tol": 1e-8,
-           "budget_gb": 150, "dtype": "f32 compute, f16 storage (local shift)", "rates": {}}
+           "budget_gb": 150, "dtype": "f32 compute, f16 storage (local shift)", "tile": list(shape),
+           "rates": {}}
     for lam in rates:
         trace = poisson_trace(probs, rate=lam, seed=seed)
-        srv = Server(budget_bytes=150e9, slice_steps=100, max_steps=20000, tol=1e-8)
+        srv = Server(budget_bytes=150e9, slice_steps=100, max_steps=20000, tol=1e-8, tiles=shape)
         res = srv.run(trace)
         out["rates"][str(int(lam))] = dict(summarize(res), peak_active=srv.stats["peak_active"],
                                            slices=srv.stats["slices"],

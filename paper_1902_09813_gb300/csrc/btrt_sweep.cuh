@@ -379,15 +379,14 @@ __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&
     } else {
         r[0] = fma(c0, sig, w0 * a);
     }
-    const Real wa1 = MODE == kGeneral ? w1 * fma(cst<Real>(1, 3), cc, a) : w1 * a;
-    const Real T1 = fma(k6, sig, wa1);
+    const Real ks = k6 * sig;   // the sigma term of the axis and diagonal directions (equal weights)
+    const Real T1 = MODE == kGeneral ? fma(w1, fma(cst<Real>(1, 3), cc, a), ks) : fma(w1, a, ks);
     const Real A1 = fma(k6x3, del, T1), A2 = fma(-k6x3, del, T1);
     r[1] = fma(v1, Vx, A1);
     r[3] = fma(-v1, Vx, A1);
     r[2] = fma(v1, Vy, A2);
     r[4] = fma(-v1, Vy, A2);
-    const Real wa5 = MODE == kGeneral ? w5 * fma(cst<Real>(4, 3), cc, a) : w5 * a;
-    const Real T5 = fma(k6, sig, wa5);
+    const Real T5 = MODE == kGeneral ? fma(w5, fma(cst<Real>(4, 3), cc, a), ks) : fma(w5, a, ks);
     const Real P = fma(k6x3, pxy, T5), M = fma(-k6x3, pxy, T5);
     const Real Vp = Vx + Vy, Vm = Vx - Vy;
     r[5] = fma(v5, Vp, P);
