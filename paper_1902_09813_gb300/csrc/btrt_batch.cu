@@ -39,6 +39,14 @@ struct BatchMember {
     int mode;                  // kGeneral or kLinear
 };
 
+// Resident blocks per SM the FP32 constant-coefficient step-per-launch form is
+// compiled for (0: the compiler's choice).  Five (48 registers, a few spilled
+// words) measured 73.7 GLUPS on the 512-instance FP16 batch against 68.6 with
+// the compiler's 58-61 registers and four blocks.
+#ifndef BTRT_BATCH_LIN_MINBLOCKS
+#define BTRT_BATCH_LIN_MINBLOCKS 5
+#endif
+
 constexpr int kMaxSliceSteps = 4096;   // steps per launch (the step table holds this many)
 
 template <typename Real>
@@ -86,8 +94,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int t
 
 // One tile of one step: load the member's parameters into shared memory, patch
 // the step-dependent ones (buffer parity, source and wall time factors from the
-// host-computed step table) and sweep the tile's nodes.
-template <typename Real, typename S, int SH, bool L2ONLY>
+// host-computed step table) and sweep the tile's nodes.  LIN: every member of
+// the batch takes the constant-coefficient collision and a source other than
+// the reaction term, so only that collision and those sources are compiled
+// (fewer registers than the form that can take any member).
+template <typename Real, typename S, int SH, bool L2ONLY, bool LIN>
 __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int k, bool resid,
                                            SweepParams<Real> &sp, double *red) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -122,12 +133,13 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int 
     double r = 0.0;
     if (x < sp.nx) {
         const int y0 = tile.z + threadIdx.y;
-        if (M.mode == kGeneral) {
+        if (!LIN && M.mode == kGeneral) {
             if (resid) r = sweep_rows<Real, S, SH, kGeneral, kSrcRuntime, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
             else sweep_rows<Real, S, SH, kGeneral, kSrcRuntime, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
         } else {
-            if (resid) r = sweep_rows<Real, S, SH, kLinear, kSrcRuntime, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
-            else sweep_rows<Real, S, SH, kLinear, kSrcRuntime, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+            constexpr int SRC = LIN ? kSrcRuntimeNR : kSrcRuntime;
+            if (resid) r = sweep_rows<Real, S, SH, kLinear, SRC, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, SH, kLinear, SRC, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
         }
     }
     if (resid) {
@@ -144,13 +156,13 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int 
 // Persistent form: every resident block walks the tile table each step; a
 // bounded grid barrier separates the steps.  Population and phi loads go
 // through L2 only, since other SMs rewrote them in the previous step.
-template <typename Real, typename S, int SH>
+template <typename Real, typename S, int SH, bool LIN>
 __global__ void __launch_bounds__(256) batch_kernel(const __grid_constant__ BatchArgs<Real> a) {
     __shared__ SweepParams<Real> sp;
     __shared__ double red[256];
     for (int k = 0; k < a.nsteps; ++k) {
         const bool resid = a.want_resid && (k == a.nsteps - 1);
-        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, SH, true>(a, t, k, resid, sp, red);
+        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, SH, true, LIN>(a, t, k, resid, sp, red);
         if (!grid_barrier(a.barrier, (unsigned)(k + 1) * gridDim.x + a.barrier_extra, a.err, a.wait_limit))
             return;
     }
@@ -158,12 +170,13 @@ __global__ void __launch_bounds__(256) batch_kernel(const __grid_constant__ Batc
 
 // Step-per-launch form: one launch per step (all of them in one CUDA graph);
 // kernel boundaries order the steps, so no barrier and ordinary cached loads.
-template <typename Real, typename S, int SH>
-__global__ void __launch_bounds__(256) batch_step_kernel(const __grid_constant__ BatchArgs<Real> a, int k) {
+template <typename Real, typename S, int SH, bool LIN>
+__global__ void __launch_bounds__(256, (LIN && sizeof(Real) == 4) ? BTRT_BATCH_LIN_MINBLOCKS : 0)
+    batch_step_kernel(const __grid_constant__ BatchArgs<Real> a, int k) {
     __shared__ SweepParams<Real> sp;
     __shared__ double red[256];
     const bool resid = a.want_resid && (k == a.nsteps - 1);
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, SH, false>(a, t, k, resid, sp, red);
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, SH, false, LIN>(a, t, k, resid, sp, red);
 }
 
 // Each member's device flags (bit 0: non-finite phi) gathered into one array.
@@ -295,7 +308,9 @@ struct btrt_batch_s {
     BatchLayout lay{};
     Shape shape{32, 8, 1, 0};
     int ntiles = 0;
-    int grid = 0;              // persistent grid (co-resident blocks)
+    int grid = 0;              // persistent grid (co-resident blocks), form that takes either collision
+    int grid_lin = 0;          // the same for the constant-coefficient-only form
+    bool all_linear = false;   // every member takes the constant-coefficient collision and no reaction term (set per slice)
     unsigned long long wait_limit = 1ull << 24;
     unsigned int barrier_extra = 0;
     bool use_graph = true;
@@ -314,19 +329,21 @@ struct btrt_batch_s {
 
 namespace {
 
-template <int SH>
+template <int SH, bool LIN>
 void *persistent_kernel_sh(int storage) {
     switch (storage) {
-    case BTRT_F32: return reinterpret_cast<void *>(&batch_kernel<float, float, SH>);
-    case BTRT_F16: return reinterpret_cast<void *>(&batch_kernel<float, __half, SH>);
-    case BTRT_BF16: return reinterpret_cast<void *>(&batch_kernel<float, __nv_bfloat16, SH>);
+    case BTRT_F32: return reinterpret_cast<void *>(&batch_kernel<float, float, SH, LIN>);
+    case BTRT_F16: return reinterpret_cast<void *>(&batch_kernel<float, __half, SH, LIN>);
+    case BTRT_BF16: return reinterpret_cast<void *>(&batch_kernel<float, __nv_bfloat16, SH, LIN>);
     }
     return nullptr;
 }
 
+template <bool LIN>
 void *persistent_kernel_for(int compute, int storage, int shift) {
-    if (compute == BTRT_F64) return reinterpret_cast<void *>(&batch_kernel<double, double, kShiftNone>);
-    return shift == kShiftLocal ? persistent_kernel_sh<kShiftLocal>(storage) : persistent_kernel_sh<kShiftRef>(storage);
+    if (compute == BTRT_F64) return reinterpret_cast<void *>(&batch_kernel<double, double, kShiftNone, LIN>);
+    return shift == kShiftLocal ? persistent_kernel_sh<kShiftLocal, LIN>(storage)
+                                : persistent_kernel_sh<kShiftRef, LIN>(storage);
 }
 
 // Tile table for the current shape; also sizes the persistent grid.
@@ -350,13 +367,16 @@ btrt_status build_tiles(btrt_batch B) {
     BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tcnt, cnt.data(), cnt.size() * sizeof(int),
                           cudaMemcpyHostToDevice, B->stream));
     BCUDA(cudaStreamSynchronize(B->stream));
-    int dev = 0, sms = 0, per_sm = 0;
+    int dev = 0, sms = 0, per_sm = 0, per_sm_lin = 0;
     BCUDA(cudaGetDevice(&dev));
     BCUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, persistent_kernel_for(B->compute, B->storage, B->shift),
-                                                        s.bx * s.by, 0));
-    if (per_sm < 1) return bfail(BTRT_ECUDA, "batch kernel cannot be resident");
+    BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm, persistent_kernel_for<false>(B->compute, B->storage, B->shift), s.bx * s.by, 0));
+    BCUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &per_sm_lin, persistent_kernel_for<true>(B->compute, B->storage, B->shift), s.bx * s.by, 0));
+    if (per_sm < 1 || per_sm_lin < 1) return bfail(BTRT_ECUDA, "batch kernel cannot be resident");
     B->grid = per_sm * sms;
+    B->grid_lin = per_sm_lin * sms;
     B->drop_graphs();
     return BTRT_OK;
 }
@@ -370,6 +390,7 @@ btrt_status upload_members(btrt_batch B, int nsteps) {
     B->host_vals.resize(n * (size_t)nsteps * 2 * sizeof(Real));
     BatchMember<Real> *hm = reinterpret_cast<BatchMember<Real> *>(B->host_members.data());
     Real *hv = reinterpret_cast<Real *>(B->host_vals.data());
+    B->all_linear = true;
     for (size_t m = 0; m < n; ++m) {
         btrt_lattice L = B->members[m];
         BatchMember<Real> d;
@@ -382,6 +403,7 @@ btrt_status upload_members(btrt_batch B, int nsteps) {
         d.step = L->step;
         d.cur = L->cur;
         d.mode = sweep_mode(L) == kGeneral ? kGeneral : kLinear;
+        B->all_linear = B->all_linear && d.mode == kLinear && d.p.src_kind != kSrcReaction;
         hm[m] = d;
         for (int k = 0; k < nsteps; ++k) {
             double sv = 0.0, wf = 1.0;
@@ -417,21 +439,27 @@ BatchArgs<Real> make_args(btrt_batch B, int nsteps, int want_resid) {
     return a;
 }
 
-template <typename Real, typename S, int SH>
-btrt_status enqueue_typed(btrt_batch B, int nsteps, int want_resid) {
+template <typename Real, typename S, int SH, bool LIN>
+btrt_status enqueue_form(btrt_batch B, int nsteps, int want_resid) {
     BatchArgs<Real> a = make_args<Real>(B, nsteps, want_resid);
     const dim3 block(B->shape.bx, B->shape.by);
     if (B->shape.per_step) {
         const unsigned grid = (unsigned)B->ntiles;
-        for (int k = 0; k < nsteps; ++k) batch_step_kernel<Real, S, SH><<<grid, block, 0, B->stream>>>(a, k);
+        for (int k = 0; k < nsteps; ++k) batch_step_kernel<Real, S, SH, LIN><<<grid, block, 0, B->stream>>>(a, k);
         BCUDA(cudaGetLastError());
         return BTRT_OK;
     }
     void *args[] = {&a};
     BCUDA(cudaMemsetAsync(B->barrier(), 0, sizeof(unsigned int), B->stream));
-    BCUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(&batch_kernel<Real, S, SH>), dim3(B->grid), block,
-                                      args, 0, B->stream));
+    BCUDA(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(&batch_kernel<Real, S, SH, LIN>),
+                                      dim3(LIN ? B->grid_lin : B->grid), block, args, 0, B->stream));
     return BTRT_OK;
+}
+
+template <typename Real, typename S, int SH>
+btrt_status enqueue_typed(btrt_batch B, int nsteps, int want_resid) {
+    return B->all_linear ? enqueue_form<Real, S, SH, true>(B, nsteps, want_resid)
+                         : enqueue_form<Real, S, SH, false>(B, nsteps, want_resid);
 }
 
 template <int SH>
@@ -454,7 +482,7 @@ btrt_status enqueue(btrt_batch B, int nsteps, int want_resid) {
 // launches if the launch cannot be captured.
 btrt_status run_slice(btrt_batch B, int nsteps, int want_resid) {
     if (B->use_graph) {
-        auto key = std::make_pair((long long)nsteps, want_resid);
+        auto key = std::make_pair((long long)nsteps, want_resid | (B->all_linear ? 2 : 0));
         auto it = B->graphs.find(key);
         if (it == B->graphs.end()) {
             cudaGraph_t g = nullptr;

@@ -176,8 +176,10 @@ __device__ __forceinline__ dw quot(dw a, dw b) { return a / b; }
 enum { kGeneral = 0, kLinear = 1, kLinearK0One = 2 };
 // Stored form of the populations (see the top of this file).
 enum { kShiftNone = 0, kShiftRef = 1, kShiftLocal = 2 };
-// Source kinds (compile-time SRC); kSrcRuntime decides per lattice at run time.
-enum { kSrcNone = 0, kSrcConst = 1, kSrcTrig = 2, kSrcField = 3, kSrcReaction = 4, kSrcRuntime = 5 };
+// Source kinds (compile-time SRC); kSrcRuntime decides per lattice at run time,
+// kSrcRuntimeNR the same among the kinds other than the reaction term (whose
+// power-law code then stays out of the kernel).
+enum { kSrcNone = 0, kSrcConst = 1, kSrcTrig = 2, kSrcField = 3, kSrcReaction = 4, kSrcRuntime = 5, kSrcRuntimeNR = 6 };
 
 // max(x, 0)^q for the power-law flux (q != 2) and the reaction term: those
 // terms are defined for phi >= 0, and an undershoot next to a steep front must
@@ -553,7 +555,7 @@ __device__ __forceinline__ Real source_at(const SweepParams<Real> &p, Real xs, R
     if constexpr (SRC == kSrcConst) return Real(1);
     else if constexpr (SRC == kSrcTrig) return fma(xs, p.Ys[BTRT_IX(p.flags, y, p.ny)], xc * p.Yc[BTRT_IX(p.flags, y, p.ny)]);
     else if constexpr (SRC == kSrcField) return p.srcF[BTRT_IX(p.flags, node, p.plane)];
-    else if constexpr (SRC == kSrcRuntime) {
+    else if constexpr (SRC == kSrcRuntime || SRC == kSrcRuntimeNR) {
         if (p.src_kind == kSrcConst) return Real(1);
         if (p.src_kind == kSrcTrig) return fma(xs, p.Ys[BTRT_IX(p.flags, y, p.ny)], xc * p.Yc[BTRT_IX(p.flags, y, p.ny)]);
         if (p.src_kind == kSrcField) return p.srcF[BTRT_IX(p.flags, node, p.plane)];
@@ -628,7 +630,7 @@ template <typename Real, typename S, int SH, int MODE, int SRC, bool L2ONLY, boo
 __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, int ybase, int ystride,
                                              int nrows) {
     Real xs = Real(0), xc = Real(0);
-    if (SRC == kSrcTrig || (SRC == kSrcRuntime && p.src_kind == kSrcTrig)) {
+    if (SRC == kSrcTrig || ((SRC == kSrcRuntime || SRC == kSrcRuntimeNR) && p.src_kind == kSrcTrig)) {
         xs = p.Xs[BTRT_IX(p.flags, x, p.nx)];
         xc = p.Xc[BTRT_IX(p.flags, x, p.nx)];
     }
