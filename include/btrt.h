@@ -180,14 +180,15 @@ btrt_status btrt_mass(btrt_lattice L, double *out);
 btrt_status btrt_check(btrt_lattice L, int32_t *flags);
 
 /* Kernel form of the ordinary FP32-compute sweep: BTRT_SWEEP_AUTO (default: the
- * faster form as measured on GB300, currently the plain one), BTRT_SWEEP_PLAIN
- * (two nodes per thread, direct global loads served by L1/L2), BTRT_SWEEP_TMA
+ * faster form as measured on GB300, currently BTRT_SWEEP_TB2), BTRT_SWEEP_PLAIN
+ * (one step per launch, direct global loads served by L1/L2), BTRT_SWEEP_TMA
  * (persistent tiles staged in shared memory by TMA with mbarrier pipelining) or
  * BTRT_SWEEP_TB2 (two time steps per launch: the first step's populations stay
- * in shared memory, halving the DRAM bytes per step; FP32 storage with
- * BTRT_SHIFT_REF only, otherwise BTRT_EINVAL; btrt_step runs pairs of steps this
- * way and an odd last step in the plain form).  All forms give bitwise identical
- * results.  FP64 and double-word lattices always use the plain form. */
+ * in shared memory, halving the DRAM bytes per step; btrt_step runs pairs of
+ * steps this way and an odd last step, and btrt_step_residual its last step, in
+ * the plain form).  Every storage format and shift of an FP32-compute lattice.
+ * All forms give bitwise identical results.  FP64 and double-word lattices
+ * always use the plain form (BTRT_SWEEP_TMA and BTRT_SWEEP_TB2: BTRT_EINVAL). */
 enum { BTRT_SWEEP_AUTO = 0, BTRT_SWEEP_PLAIN = 1, BTRT_SWEEP_TMA = 2, BTRT_SWEEP_TB2 = 3 };
 btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant);
 

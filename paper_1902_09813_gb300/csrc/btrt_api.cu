@@ -719,13 +719,17 @@ btrt_status btrt_step(btrt_lattice L, int64_t nsteps) {
     if (!L) return fail(BTRT_EINVAL, "null lattice");
     if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
     if (nsteps < 0) return fail(BTRT_EINVAL, "negative step count");
-    if (L->sweep_variant == BTRT_SWEEP_TB2) {
+    // the two-step form serves every FP32-compute lattice; AUTO takes it (it is the
+    // faster form on GB300 for every storage format and shift)
+    const bool tb2 = L->g.compute == BTRT_F32 &&
+                     (L->sweep_variant == BTRT_SWEEP_TB2 || L->sweep_variant == BTRT_SWEEP_AUTO);
+    if (tb2) {
         // pairs of steps in one launch: inputs from buffer cur, outputs to the other
         for (; nsteps >= 2; nsteps -= 2) {
             SweepParams<float> pa, pb;
             fill_params(L, pa, L->step + 1, false);
             fill_params(L, pb, L->step + 2, false);
-            CUDA_TRY(launch_sweep_tb2(pa, pb, sweep_mode(L), L->stream));
+            CUDA_TRY(launch_sweep_tb2(pa, pb, L->g.storage, shift_of(L->g), sweep_mode(L), L->stream));
             L->cur = 1 - L->cur;
             L->step += 2;
         }
@@ -841,9 +845,8 @@ btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant) {
     if (variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN && variant != BTRT_SWEEP_TMA &&
         variant != BTRT_SWEEP_TB2)
         return fail(BTRT_EINVAL, "unknown sweep variant %d", variant);
-    if (variant == BTRT_SWEEP_TB2 &&
-        (L->g.compute != BTRT_F32 || L->g.storage != BTRT_F32 || L->g.shift != BTRT_SHIFT_REF))
-        return fail(BTRT_EINVAL, "the two-step sweep serves FP32 compute with FP32 storage and the reference shift");
+    if (variant == BTRT_SWEEP_TB2 && L->g.compute != BTRT_F32)
+        return fail(BTRT_EINVAL, "the two-step sweep serves FP32-compute lattices");
     if (variant == BTRT_SWEEP_TMA && !L->have_tma)
         return fail(BTRT_EINVAL, "the TMA sweep serves FP32-compute lattices whose tensor maps could be encoded");
     L->sweep_variant = variant;

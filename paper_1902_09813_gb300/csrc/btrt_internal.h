@@ -118,9 +118,17 @@ cudaError_t launch_sweep_tma(const SweepParams<float> &p, int storage, int shift
                              const CUtensorMap *in_map, const CUtensorMap *out_map, cudaStream_t s);
 void tma_box(int storage, int *box_in_x, int *box_in_y, int *box_out_x, int *box_out_y);
 
-// Two steps in one launch (FP32 compute, FP32 storage, reference shift): pa holds
-// the parameters of the first step (its inputs), pb those of the second (its outputs).
-cudaError_t launch_sweep_tb2(const SweepParams<float> &pa, const SweepParams<float> &pb, int mode, cudaStream_t s);
+// Two steps in one launch (FP32 compute; storage BTRT_F32, F16 or BF16; shift
+// kShiftRef or kShiftLocal): pa holds the parameters of the first step (its
+// inputs), pb those of the second (its outputs).
+cudaError_t launch_sweep_tb2(const SweepParams<float> &pa, const SweepParams<float> &pb, int storage, int shift,
+                             int mode, cudaStream_t s);
+cudaError_t launch_sweep_tb2_f32(const SweepParams<float> &pa, const SweepParams<float> &pb, int shift, int mode,
+                                 cudaStream_t s);
+cudaError_t launch_sweep_tb2_f16(const SweepParams<float> &pa, const SweepParams<float> &pb, int shift, int mode,
+                                 cudaStream_t s);
+cudaError_t launch_sweep_tb2_bf16(const SweepParams<float> &pa, const SweepParams<float> &pb, int shift, int mode,
+                                  cudaStream_t s);
 
 // Blocks of one single-lattice sweep (32 x 8 threads, RowsPerThread nodes each).
 long long sweep_blocks(int nx, int ny, int compute, int storage);

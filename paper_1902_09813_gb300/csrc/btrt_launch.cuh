@@ -92,36 +92,34 @@ cudaError_t launch_tma_storage(const SweepParams<float> &p, int shift, int mode,
                : launch_tma_mode<S, kShiftRef, kGeneral>(p, in_map, out_map, s);
 }
 
-// Two steps per launch: one block per output tile, ~52 KB of shared memory.
-template <typename S, int MODE, int SRC>
+// Two steps per launch: one block per output tile, 24 KB of shared memory.
+template <typename S, int SH, int MODE, int SRC>
 cudaError_t launch_tb2_src(const SweepParams<float> &pa, const SweepParams<float> &pb, cudaStream_t s) {
-    static bool configured = false;   // one attribute call per instantiation
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_tb2_kernel<S, MODE, SRC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, TbGeom::SMEM);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
     const int ntx = (pa.nx + TbGeom::TX - 1) / TbGeom::TX;
     const int nty = (pa.ny + TbGeom::TY - 1) / TbGeom::TY;
-    sweep_tb2_kernel<S, MODE, SRC><<<ntx * nty, TbGeom::THREADS, TbGeom::SMEM, s>>>(pa, pb, ntx);
+    sweep_tb2_kernel<S, SH, MODE, SRC><<<ntx * nty, TbGeom::THREADS, TbGeom::SMEM, s>>>(pa, pb, ntx);
     return cudaGetLastError();
 }
 
-template <typename S, int MODE>
+template <typename S, int SH, int MODE>
 cudaError_t launch_tb2_mode(const SweepParams<float> &pa, const SweepParams<float> &pb, cudaStream_t s) {
     switch (pa.src_kind) {
-    case kSrcNone: return launch_tb2_src<S, MODE, kSrcNone>(pa, pb, s);
-    case kSrcConst: return launch_tb2_src<S, MODE, kSrcConst>(pa, pb, s);
-    case kSrcTrig: return launch_tb2_src<S, MODE, kSrcTrig>(pa, pb, s);
-    case kSrcField: return launch_tb2_src<S, MODE, kSrcField>(pa, pb, s);
-    default: return launch_tb2_src<S, MODE, kSrcReaction>(pa, pb, s);
+    case kSrcNone: return launch_tb2_src<S, SH, MODE, kSrcNone>(pa, pb, s);
+    case kSrcConst: return launch_tb2_src<S, SH, MODE, kSrcConst>(pa, pb, s);
+    case kSrcTrig: return launch_tb2_src<S, SH, MODE, kSrcTrig>(pa, pb, s);
+    case kSrcField: return launch_tb2_src<S, SH, MODE, kSrcField>(pa, pb, s);
+    default: return launch_tb2_src<S, SH, MODE, kSrcReaction>(pa, pb, s);
     }
 }
 
 template <typename S>
-cudaError_t launch_tb2_storage(const SweepParams<float> &pa, const SweepParams<float> &pb, int mode, cudaStream_t s) {
-    return mode == kGeneral ? launch_tb2_mode<S, kGeneral>(pa, pb, s) : launch_tb2_mode<S, kLinear>(pa, pb, s);
+cudaError_t launch_tb2_storage(const SweepParams<float> &pa, const SweepParams<float> &pb, int shift, int mode,
+                               cudaStream_t s) {
+    if (shift == kShiftLocal)
+        return mode == kGeneral ? launch_tb2_mode<S, kShiftLocal, kGeneral>(pa, pb, s)
+                                : launch_tb2_mode<S, kShiftLocal, kLinear>(pa, pb, s);
+    return mode == kGeneral ? launch_tb2_mode<S, kShiftRef, kGeneral>(pa, pb, s)
+                            : launch_tb2_mode<S, kShiftRef, kLinear>(pa, pb, s);
 }
 
 }  // namespace btrt

@@ -50,6 +50,38 @@ def test_alone_equals_in_mix_bitwise(compute, storage, shift):
     b.close()
 
 
+@pytest.mark.parametrize("compute,storage,shift,shape", [("f32", "f16", "local", (32, 8, 4, 1)),
+                                                        ("f32", "f32", "ref", (32, 8, 2, 0)),
+                                                        ("f64", "f64", "ref", (32, 8, 4, 1))])
+def test_constant_coefficient_batch_form_bitwise(compute, storage, shift, shape):
+    """A batch whose members all take the constant-coefficient collision and no
+    reaction source runs the form compiled for that case; a member switched to
+    nonlinear coefficients between slices makes the next slice run the form that
+    takes any member.  Both stay bitwise equal to the members stepped alone."""
+    from paper_1902_09813_gb300 import Batch
+    probs = w.batched_instances(count=8, seed=21, nmin=20, nmax=150, nsteps=30)
+    for p in probs:
+        p.phi_ref = float(p.phi0().mean()) if storage != "f64" else 0.0
+    alone = [_make(p, compute, storage, shift).step(10) for p in probs]
+    mixed = [_make(p, compute, storage, shift) for p in probs]
+    b = Batch(mixed).set_tiles(*shape)
+    b.step(10)
+    for a, m in zip(alone, mixed):
+        assert np.array_equal(a.phi_host(), m.phi_host())
+    for lat in (alone[3], mixed[3]):
+        c = lat.coef
+        c.a2 = 0.5
+        c.b2 = 0.01
+        lat.set_coeffs(c)
+    b.step(7)
+    alone = [a.step(7) for a in alone]
+    for a, m in zip(alone, mixed):
+        assert np.array_equal(a.phi_host(), m.phi_host())
+        assert np.array_equal(a.read_f(), m.read_f())
+    assert b.check() == 0
+    b.close()
+
+
 @pytest.mark.parametrize("shape", [(32, 8, 1, 0), (32, 8, 4, 0), (64, 4, 2, 0), (32, 4, 2, 0),
                                    (32, 8, 1, 1), (64, 4, 2, 1)])
 def test_tile_shapes_bitwise(shape):

@@ -411,11 +411,37 @@ def test_tb2_sweep_bitwise_equals_plain(case, steps):
     """Two steps per launch (first step kept in shared memory) and one step per
     launch do the same arithmetic node by node: results are bitwise identical,
     for odd step counts too (the last step runs in the plain form)."""
+    _tb2_against_plain(case, steps, "f32")
+
+
+@pytest.mark.parametrize("storage,shift", [("f16", "ref"), ("bf16", "ref"), ("f32", "local"), ("f16", "local"),
+                                           ("bf16", "local")])
+@pytest.mark.parametrize("case", TB_CASES[::2], ids=lambda c: f"{c[0]}x{c[1]}-bc{''.join(map(str, c[2]))}-{c[4]}")
+def test_tb2_sweep_other_storage_bitwise_equals_plain(case, storage, shift):
+    """The same with FP16 and BF16 storage (the first step's populations are kept
+    in shared memory rounded to the storage format, as a stored step would be)
+    and with the local shift (shared-memory values moved to the reading node's
+    phi as the one-step pull does)."""
+    _tb2_against_plain(case, 9, storage, shift)
+
+
+def test_default_form_bitwise_equals_plain():
+    """AUTO (the default; the two-step form for FP32 compute) and the plain form
+    give the same bits on a walled nonlinear lattice with FP16 storage."""
+    p = w.random_state_problem(64, 40, seed=31, bc=(1, 1, 0, 0), nonlinear=True, source="const")
+    a = _lattice(p, "f32", "f16", shift="local")
+    b = _lattice(p, "f32", "f16", shift="local").set_sweep_variant("plain")
+    a.init(p.phi0(), t0=p.t0).step(8)
+    b.init(p.phi0(), t0=p.t0).step(8)
+    assert np.array_equal(a.read_f(), b.read_f())
+
+
+def _tb2_against_plain(case, steps, storage, shift="ref"):
     nx, ny, bc, nonlin, src = case
     p = w.random_state_problem(nx, ny, seed=3 * nx + ny, bc=bc, nonlinear=nonlin, source=src,
                                flux_q=2.5 if src == "reaction" else 2.0)
-    a = _lattice(p, "f32", "f32", shift="ref").set_sweep_variant("tb2")
-    b = _lattice(p, "f32", "f32", shift="ref").set_sweep_variant("plain")
+    a = _lattice(p, "f32", storage, shift=shift).set_sweep_variant("tb2")
+    b = _lattice(p, "f32", storage, shift=shift).set_sweep_variant("plain")
     a.init(p.phi0(), t0=p.t0).step(steps)
     b.init(p.phi0(), t0=p.t0).step(steps)
     assert np.array_equal(a.phi_host(), b.phi_host())
@@ -446,12 +472,11 @@ def test_tb2_fields_and_large_ragged_grid():
     assert np.array_equal(pa, b.phi_host())
 
 
-def test_tb2_rejects_other_storage():
+def test_tb2_rejects_other_compute():
+    """The two-step form serves FP32-compute lattices only."""
     from paper_1902_09813_gb300 import _capi as C
     p = w.random_state_problem(20, 20, seed=2)
     with pytest.raises(C.BtrtError):
-        _lattice(p, "f32", "f16").set_sweep_variant("tb2")
-    with pytest.raises(C.BtrtError):
-        _lattice(p, "f32", "f32", shift="local").set_sweep_variant("tb2")
+        _lattice(p, "df64").set_sweep_variant("tb2")
     with pytest.raises(C.BtrtError):
         _lattice(p, "f64").set_sweep_variant("tb2")
