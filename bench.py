@@ -55,6 +55,14 @@ FP64_PEAK_TOPS = 0.625
 # (profiles/sweep_f64_mms2048_full.md), scaled to the benchmark by node count;
 # None when the kernel changed after the capture.
 FP64_TRAFFIC_PER_NODE = 149.3
+# DRAM bytes per node and step of the two-step FP32-compute kernel measured by ncu
+# (profiles/sweep_tb2_*_full.md), keyed by (storage, shift).
+TB2_DRAM_BYTES_PER_UPDATE = {("f32", "ref"): 38.6, ("f16", "local"): 20.9}
+
+
+def two_step_form(args) -> bool:
+    """FP32-compute lattices run pairs of steps in one launch unless asked otherwise."""
+    return args.compute == "f32" and args.sweep in ("auto", "tb2")
 
 
 def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
@@ -62,6 +70,15 @@ def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
            "frac": round(achieved_gbs / peak_hbm, 4), "peak_kind": peak_kind,
            "frac_of_nominal_8tbs": round(achieved_gbs / 8000.0, 4),
            "bytes_per_update": BYTES_PER_UPDATE[args.storage]}
+    if two_step_form(args):
+        # algorithmic bytes count one read and one write of the state per step; the
+        # two-step kernel moves about half of that through DRAM, so this fraction
+        # can exceed 1 (the DRAM bytes it measured are in `dram_bytes_per_update`)
+        shift = args.shift if args.shift != "auto" else ("local" if args.storage in ("f16", "bf16") else "ref")
+        key = (args.storage, shift)
+        return dict(hbm, traffic=None, kernel=f"sweep_tb2_kernel<f32,{args.storage}>",
+                    dram_bytes_per_update=TB2_DRAM_BYTES_PER_UPDATE.get(key),
+                    note="two steps per launch; achieved = algorithmic bytes of the steps / time")
     kernel = f"sweep_kernel<{args.compute},{args.storage}>"
     if args.compute != "f64" or args.workload != "mms":
         return dict(hbm, traffic=None, kernel=kernel)
@@ -267,7 +284,7 @@ def run_gpu(args):
                 "h2d_bytes_per_step": int(8 * nodes / args.steps),
                 "d2h_bytes_per_step": int(8 * nodes / args.steps),
                 "note": "one solve per K steps: phi0 in, phi out, amortised per step"},
-            "gpu_launches": args.steps,
+            "gpu_launches": (args.steps // 2 + args.steps % 2) if two_step_form(args) else args.steps,
             "clocks": clk,
         }
         line.update(extra)
@@ -307,27 +324,25 @@ def _time_single(p, phi0, compute, storage, steps, warmup, variant="plain", shif
 def run_variants(args, steps=200, warmup=5):
     """The other compute/storage paths at 8192^2: double-word (FP32-pair) arithmetic
     on the manufactured-solution workload, FP32 compute with FP32/FP16/BF16 shifted
-    storage (reference shift: plain and TMA-staged; local shift: plain) on the
-    manufactured-solution and nonlinear workloads."""
+    storage (both shifts: one and two steps per launch; reference shift: TMA-staged
+    too) on the manufactured-solution and nonlinear workloads."""
     import workloads as w
     out = {}
     p = w.mms_sinsin(n=args.n, nsteps=steps)
     phi0 = p.phi0()
     out["mms_df64"] = _time_single(p, phi0, "df64", "df64", steps, warmup)
-    for st in ("f32", "f16", "bf16"):
-        out[f"mms_f32_{st}"] = _time_single(p, phi0, "f32", st, steps, warmup)
-        out[f"mms_f32_{st}_tma"] = _time_single(p, phi0, "f32", st, steps, warmup, variant="tma")
-        out[f"mms_f32_{st}_local"] = _time_single(p, phi0, "f32", st, steps, warmup, shift="local")
-    out["mms_f32_f32_tb2"] = _time_single(p, phi0, "f32", "f32", steps, warmup, variant="tb2")
     q = w.nonlinear_modes(n=args.n, nsteps=steps)
-    phi0 = q.phi0()
-    q.phi_ref = float(phi0.mean())
-    for st in ("f32", "f16", "bf16"):
-        out[f"nonlinear_f32_{st}"] = _time_single(q, phi0, "f32", st, steps, warmup)
-        out[f"nonlinear_f32_{st}_tma"] = _time_single(q, phi0, "f32", st, steps, warmup, variant="tma")
-        out[f"nonlinear_f32_{st}_local"] = _time_single(q, phi0, "f32", st, steps, warmup, shift="local")
-    out["nonlinear_f32_f32_tb2"] = _time_single(q, phi0, "f32", "f32", steps, warmup, variant="tb2")
-    out["nonlinear_f64"] = _time_single(q, phi0, "f64", "f64", 50, 3)
+    q_phi0 = q.phi0()
+    q.phi_ref = float(q_phi0.mean())
+    for name, prob, a in (("mms", p, phi0), ("nonlinear", q, q_phi0)):
+        for st in ("f32", "f16", "bf16"):
+            for sh, tag in (("ref", ""), ("local", "_local")):
+                # one step per launch, and two (the default form of FP32 compute)
+                out[f"{name}_f32_{st}{tag}"] = _time_single(prob, a, "f32", st, steps, warmup, shift=sh)
+                out[f"{name}_f32_{st}{tag}_tb2"] = _time_single(prob, a, "f32", st, steps, warmup, variant="tb2",
+                                                               shift=sh)
+            out[f"{name}_f32_{st}_tma"] = _time_single(prob, a, "f32", st, steps, warmup, variant="tma")
+    out["nonlinear_f64"] = _time_single(q, q_phi0, "f64", "f64", 50, 3)
     out.update(run_d3q19(args))
     out.update(run_extended(args))
     return out
