@@ -228,7 +228,11 @@ btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_
 
 /* Tile shape: block_x x block_y threads, each sweeping `rows` nodes of its
  * column.  Candidates: 32x8x1, 32x8x2, 32x8x4, 64x4x1, 64x4x2, 32x4x2.
- * per_step_launch = 0: persistent launch per call; 1: one launch per step. */
+ * per_step_launch = 0: persistent launch per call; 1: one launch per step;
+ * 2 (FP32-compute batches only, else BTRT_EINVAL): two steps per launch on
+ * 32 x 16 output tiles (the form of BTRT_SWEEP_TB2), an odd last step and the
+ * residual step of btrt_batch_step in the form of 1 with the given shape.
+ * Results are bitwise the same in every form and shape. */
 btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y, int32_t rows,
                                  int32_t per_step_launch);
 

@@ -7,7 +7,10 @@
 //    tile table for one time step, meet at a grid barrier (bounded wait) and go
 //    on with the next step;
 //  - step-per-launch: one launch per step over all tiles.
-// Either form is captured in a CUDA graph per (steps, residual) pair and
+//  - two-step: FP32 compute only; one launch per pair of steps over a table of
+//    the two-step kernel's output tiles (btrt_tb.cuh), the last step of a slice
+//    that wants the residual (or an odd one) in the step-per-launch form.
+// Each form is captured in a CUDA graph per (steps, residual) pair and
 // replayed.  Members keep their own workspaces; the batch workspace holds only
 // the descriptors, tables and reduction scratch.  btrt_batch_autotune times the
 // candidate tile shapes in both forms on real steps and keeps the fastest.
@@ -26,6 +29,7 @@
 
 #include "../../include/btrt.h"
 #include "btrt_internal.h"
+#include "btrt_tb.cuh"
 
 using namespace btrt;
 
@@ -54,6 +58,8 @@ struct BatchArgs {
     const BatchMember<Real> *members;
     const int4 *tiles;         // {member, x0, y0, 0}
     int ntiles;
+    const int4 *tiles2;        // the two-step kernel's output tiles {member, x0, y0, 0}
+    int ntiles2;
     int rows;                  // nodes per thread along y
     int nsteps;
     int want_resid;
@@ -99,7 +105,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int t
 // the reaction term, so only that collision and those sources are compiled
 // (fewer registers than the form that can take any member).
 template <typename Real, typename S, int SH, bool L2ONLY, bool LIN>
-__device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int k, bool resid,
+__device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int k, int flip, bool resid,
                                            SweepParams<Real> &sp, double *red) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthr = blockDim.x * blockDim.y;
@@ -113,7 +119,7 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int 
     }
     __syncthreads();
     if (tid == 0) {
-        const int cur = (M.cur + k) & 1;
+        const int cur = (M.cur + flip) & 1;  // buffer flips since the slice began
         const void *b0 = M.p.fin;            // buffer 0
         void *b1 = M.p.fout;                 // buffer 1
         sp.fin = cur ? b1 : b0;
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(256) batch_kernel(const __grid_constant__ Batc
     __shared__ double red[256];
     for (int k = 0; k < a.nsteps; ++k) {
         const bool resid = a.want_resid && (k == a.nsteps - 1);
-        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, SH, true, LIN>(a, t, k, resid, sp, red);
+        for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, SH, true, LIN>(a, t, k, k, resid, sp, red);
         if (!grid_barrier(a.barrier, (unsigned)(k + 1) * gridDim.x + a.barrier_extra, a.err, a.wait_limit))
             return;
     }
@@ -172,11 +178,73 @@ __global__ void __launch_bounds__(256) batch_kernel(const __grid_constant__ Batc
 // kernel boundaries order the steps, so no barrier and ordinary cached loads.
 template <typename Real, typename S, int SH, bool LIN>
 __global__ void __launch_bounds__(256, (LIN && sizeof(Real) == 4) ? BTRT_BATCH_LIN_MINBLOCKS : 0)
-    batch_step_kernel(const __grid_constant__ BatchArgs<Real> a, int k) {
+    batch_step_kernel(const __grid_constant__ BatchArgs<Real> a, int k, int flip) {
     __shared__ SweepParams<Real> sp;
     __shared__ double red[256];
     const bool resid = a.want_resid && (k == a.nsteps - 1);
-    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x) batch_tile<Real, S, SH, false, LIN>(a, t, k, resid, sp, red);
+    for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x)
+        batch_tile<Real, S, SH, false, LIN>(a, t, k, flip, resid, sp, red);
+}
+
+// Two-step form (FP32 compute): steps k and k + 1 of the slice in one launch, one
+// block per two-step output tile; flip = buffer flips since the slice began.
+// Resident blocks per SM the two-step batch form is compiled for: four (64
+// registers) for the constant-coefficient collision, three for the per-node one.
+// On the 512-instance FP16 batch four blocks measured 73.3 GLUPS, five (48
+// registers, 200 spilled bytes) 58.5 and the compiler's 80-128 registers 63.2.
+#ifndef BTRT_BATCH_TB2_MINBLOCKS_LIN
+#define BTRT_BATCH_TB2_MINBLOCKS_LIN 4
+#endif
+#ifndef BTRT_BATCH_TB2_MINBLOCKS_GEN
+#define BTRT_BATCH_TB2_MINBLOCKS_GEN 3
+#endif
+template <typename S, int SH, bool LIN>
+__global__ void __launch_bounds__(256, LIN ? BTRT_BATCH_TB2_MINBLOCKS_LIN : BTRT_BATCH_TB2_MINBLOCKS_GEN)
+    batch_tb2_kernel(const __grid_constant__ BatchArgs<float> a, int k, int flip) {
+    __shared__ SweepParams<float> spa, spb;
+    extern __shared__ float tb_smem[];
+    const int tid = threadIdx.x;
+    const int4 tile = a.tiles2[blockIdx.x];
+    const BatchMember<float> &M = a.members[tile.x];
+    {
+        const int *src = reinterpret_cast<const int *>(&M.p);
+        int *da = reinterpret_cast<int *>(&spa), *db = reinterpret_cast<int *>(&spb);
+        for (int w = tid; w < (int)(sizeof(SweepParams<float>) / 4); w += blockDim.x) {
+            const int v = src[w];
+            da[w] = v;
+            db[w] = v;
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // both steps read buffer cur and write the other one (the first step's
+        // output stays in shared memory)
+        const int cur = (M.cur + flip) & 1;
+        const void *b0 = M.p.fin;
+        void *b1 = M.p.fout;
+        const float *q0 = M.p.phi_in;
+        float *q1 = M.p.phi_out;
+        spa.fin = spb.fin = cur ? b1 : b0;
+        spa.fout = spb.fout = cur ? const_cast<void *>(b0) : b1;
+        spa.phi_in = spb.phi_in = cur ? q1 : q0;
+        spa.phi_out = spb.phi_out = cur ? const_cast<float *>(q0) : q1;
+        const float *v = a.step_vals + ((size_t)tile.x * a.table_steps + k) * 2;
+        spa.src_val = v[0];
+        spa.wall_fac = v[1];
+        spa.first = 0;
+    } else if (tid == 32) {
+        const float *v = a.step_vals + ((size_t)tile.x * a.table_steps + k + 1) * 2;
+        spb.src_val = v[0];
+        spb.wall_fac = v[1];
+        spb.first = 0;
+    }
+    __syncthreads();
+    bool bad;
+    if (LIN || M.mode != kGeneral)
+        bad = tb2_tile<S, SH, kLinear, LIN ? kSrcRuntimeNR : kSrcRuntime>(spa, spb, tile.y, tile.z, tb_smem);
+    else
+        bad = tb2_tile<S, SH, kGeneral, kSrcRuntime>(spa, spb, tile.y, tile.z, tb_smem);
+    if (bad) atomicOr(spb.flags, 1);
 }
 
 // Each member's device flags (bit 0: non-finite phi) gathered into one array.
@@ -226,7 +294,8 @@ size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
 struct Shape {
     int bx, by, rows;
-    int per_step;   // 0: persistent launch per call; 1: one launch per step (in a graph)
+    int per_step;   // 0: persistent launch per call; 1: one launch per step; 2: two steps per launch
+                    // (FP32 compute; its odd or residual last step in the form of 1)
 };
 const Shape kShapes[] = {{32, 8, 1, 0}, {32, 8, 2, 0}, {32, 8, 4, 0}, {64, 4, 1, 0}, {64, 4, 2, 0}, {32, 4, 2, 0}};
 
@@ -247,7 +316,8 @@ size_t member_bytes(int compute) {
 }
 
 struct BatchLayout {
-    size_t off_members, off_tiles, off_partials, off_resid, off_tbeg, off_tcnt, off_vals, off_mflags, off_sync, total;
+    size_t off_members, off_tiles, off_tiles2, off_partials, off_resid, off_tbeg, off_tcnt, off_vals, off_mflags,
+        off_sync, total;
 };
 
 BatchLayout batch_layout(const std::vector<btrt_lattice> &m) {
@@ -259,6 +329,8 @@ BatchLayout batch_layout(const std::vector<btrt_lattice> &m) {
     off += up256(n * member_bytes(m[0]->g.compute));
     b.off_tiles = off;
     off += up256(T * sizeof(int4));
+    b.off_tiles2 = off;
+    off += up256((size_t)tiles_for(m, TbGeom::TX, TbGeom::TY, 1) * sizeof(int4));
     b.off_partials = off;
     off += up256(T * sizeof(double));
     b.off_resid = off;
@@ -308,6 +380,7 @@ struct btrt_batch_s {
     BatchLayout lay{};
     Shape shape{32, 8, 1, 0};
     int ntiles = 0;
+    int ntiles2 = 0;           // output tiles of the two-step form
     int grid = 0;              // persistent grid (co-resident blocks), form that takes either collision
     int grid_lin = 0;          // the same for the constant-coefficient-only form
     bool all_linear = false;   // every member takes the constant-coefficient collision and no reaction term (set per slice)
@@ -346,6 +419,12 @@ void *persistent_kernel_for(int compute, int storage, int shift) {
                                 : persistent_kernel_sh<kShiftRef, LIN>(storage);
 }
 
+// Two-step launches of a slice of nsteps steps in the two-step form (0 in the
+// others): every pair but the residual step, which runs alone.
+int pairs_in_slice(btrt_batch B, int nsteps, int want_resid) {
+    return B->shape.per_step == 2 ? (nsteps - (want_resid ? 1 : 0)) / 2 : 0;
+}
+
 // Tile table for the current shape; also sizes the persistent grid.
 btrt_status build_tiles(btrt_batch B) {
     const Shape s = B->shape;
@@ -361,6 +440,16 @@ btrt_status build_tiles(btrt_batch B) {
     }
     B->ntiles = (int)tiles.size();
     BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tiles, tiles.data(), tiles.size() * sizeof(int4),
+                          cudaMemcpyHostToDevice, B->stream));
+    // output tiles of the two-step form
+    std::vector<int4> tiles2;
+    for (size_t m = 0; m < B->members.size(); ++m) {
+        btrt_lattice L = B->members[m];
+        for (int y0 = 0; y0 < L->g.ny; y0 += TbGeom::TY)
+            for (int x0 = 0; x0 < L->g.nx; x0 += TbGeom::TX) tiles2.push_back(make_int4((int)m, x0, y0, 0));
+    }
+    B->ntiles2 = (int)tiles2.size();
+    BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tiles2, tiles2.data(), tiles2.size() * sizeof(int4),
                           cudaMemcpyHostToDevice, B->stream));
     BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tbeg, beg.data(), beg.size() * sizeof(int),
                           cudaMemcpyHostToDevice, B->stream));
@@ -426,6 +515,8 @@ BatchArgs<Real> make_args(btrt_batch B, int nsteps, int want_resid) {
     a.members = reinterpret_cast<const BatchMember<Real> *>(B->ws + B->lay.off_members);
     a.tiles = reinterpret_cast<const int4 *>(B->ws + B->lay.off_tiles);
     a.ntiles = B->ntiles;
+    a.tiles2 = reinterpret_cast<const int4 *>(B->ws + B->lay.off_tiles2);
+    a.ntiles2 = B->ntiles2;
     a.rows = B->shape.rows;
     a.nsteps = nsteps;
     a.want_resid = want_resid;
@@ -444,8 +535,15 @@ btrt_status enqueue_form(btrt_batch B, int nsteps, int want_resid) {
     BatchArgs<Real> a = make_args<Real>(B, nsteps, want_resid);
     const dim3 block(B->shape.bx, B->shape.by);
     if (B->shape.per_step) {
-        const unsigned grid = (unsigned)B->ntiles;
-        for (int k = 0; k < nsteps; ++k) batch_step_kernel<Real, S, SH, LIN><<<grid, block, 0, B->stream>>>(a, k);
+        int k = 0, flip = 0;
+        if constexpr (std::is_same<Real, float>::value) {
+            if (B->shape.per_step == 2)
+                for (int j = 0; j < pairs_in_slice(B, nsteps, want_resid); ++j, k += 2, ++flip)
+                    batch_tb2_kernel<S, SH, LIN><<<(unsigned)B->ntiles2, TbGeom::THREADS, TbGeom::SMEM, B->stream>>>(
+                        a, k, flip);
+        }
+        for (; k < nsteps; ++k, ++flip)
+            batch_step_kernel<Real, S, SH, LIN><<<(unsigned)B->ntiles, block, 0, B->stream>>>(a, k, flip);
         BCUDA(cudaGetLastError());
         return BTRT_OK;
     }
@@ -571,7 +669,11 @@ btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y,
     for (const Shape &s : kShapes) known |= (s.bx == block_x && s.by == block_y && s.rows == rows);
     if (!known) return bfail(BTRT_EINVAL, "tile shape %dx%dx%d is not one of the compiled candidates",
                              block_x, block_y, rows);
-    B->shape = Shape{block_x, block_y, rows, per_step_launch ? 1 : 0};
+    if (per_step_launch < 0 || per_step_launch > 2)
+        return bfail(BTRT_EINVAL, "per_step_launch must be 0, 1 or 2");
+    if (per_step_launch == 2 && B->compute != BTRT_F32)
+        return bfail(BTRT_EINVAL, "the two-step form serves FP32-compute batches");
+    B->shape = Shape{block_x, block_y, rows, per_step_launch};
     return build_tiles(B);
 }
 
@@ -586,6 +688,8 @@ btrt_status btrt_batch_step(btrt_batch B, int64_t nsteps, int32_t want_residual)
         if (st != BTRT_OK) return st;
         st = run_slice(B, chunk, resid);
         if (st != BTRT_OK) return st;
+        // buffer flips: one per launch (a two-step launch flips once for two steps)
+        const int flips = chunk - pairs_in_slice(B, chunk, resid);
         if (resid) {
             member_residual<<<(unsigned)B->members.size(), 256, 0, B->stream>>>(
                 reinterpret_cast<const double *>(B->ws + B->lay.off_partials),
@@ -597,7 +701,7 @@ btrt_status btrt_batch_step(btrt_batch B, int64_t nsteps, int32_t want_residual)
         }
         for (auto L : B->members) {
             L->step += chunk;
-            L->cur = (L->cur + chunk) & 1;
+            L->cur = (L->cur + flips) & 1;
         }
         nsteps -= chunk;
     }
@@ -677,7 +781,7 @@ btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *
         BCUDA(cudaEventCreate(&e0));
         BCUDA(cudaEventCreate(&e1));
         float best_ms = 1e30f;
-        for (int mode = 0; mode < 2; ++mode) {
+        for (int mode = 0; mode < (B->compute == BTRT_F32 ? 3 : 2); ++mode) {
             for (const Shape &s : kShapes) {
                 btrt_status st = btrt_batch_set_tiles(B, s.bx, s.by, s.rows, mode);
                 if (st != BTRT_OK) return st;

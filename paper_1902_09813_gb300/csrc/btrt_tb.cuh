@@ -113,16 +113,19 @@ __device__ __forceinline__ void tb_pull(const SweepParams<float> &p, const float
 #define BTRT_TB2_MINBLOCKS_GEN 5
 #endif
 
+// The two steps of one output tile with origin (x0, y0), by the whole block
+// (TbGeom::THREADS threads, TbGeom::SMEM bytes of shared memory at `smem`).  pa:
+// parameters of the first step, pb: of the second (the same buffers: inputs of
+// the first, outputs of the second).  Returns true when a non-finite phi appeared
+// in this thread's nodes.  Other threads may still read `smem` when one returns:
+// the caller places a barrier before reusing it.
 template <typename S, int SH, int MODE, int SRC>
-__global__ void __launch_bounds__(256, MODE == kGeneral ? BTRT_TB2_MINBLOCKS_GEN : BTRT_TB2_MINBLOCKS_LIN)
-    sweep_tb2_kernel(const __grid_constant__ SweepParams<float> pa,
-                                                        const __grid_constant__ SweepParams<float> pb, int ntx) {
+__device__ __forceinline__ bool tb2_tile(const SweepParams<float> &pa, const SweepParams<float> &pb, int x0, int y0,
+                                         float *smem) {
     using G = TbGeom;
-    extern __shared__ float tb_smem[];
-    float *mid = tb_smem;                    // [9][MY][MX]: after the first step (stored form)
+    float *mid = smem;                       // [9][MY][MX]: after the first step (stored form)
     float *phi_m = mid + G::MID_VALS;        // [MY][MX]: phi^{n+1}
     S *__restrict__ fout = static_cast<S *>(pb.fout);
-    const int x0 = (blockIdx.x % ntx) * G::TX, y0 = (blockIdx.x / ntx) * G::TY;
     const int tid = threadIdx.x;
     bool bad = false;
 
@@ -135,7 +138,7 @@ __global__ void __launch_bounds__(256, MODE == kGeneral ? BTRT_TB2_MINBLOCKS_GEN
         pull_node<float, S, SH, false>(pa, gx, gy, gx > 0 && gx < pa.nx - 1, d, phi_prev);
         const int node = gy * pa.pitch + gx;
         float xs = 0.f, xc = 0.f;
-        if (SRC == kSrcTrig) {
+        if (SRC == kSrcTrig || ((SRC == kSrcRuntime || SRC == kSrcRuntimeNR) && pa.src_kind == kSrcTrig)) {
             xs = pa.Xs[BTRT_IX(pa.flags, gx, pa.nx)];
             xc = pa.Xc[BTRT_IX(pa.flags, gx, pa.nx)];
         }
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(256, MODE == kGeneral ? BTRT_TB2_MINBLOCKS_GEN
         tb_pull<SH>(pb, mid, phi_m, G::MX, G::MY, ox + 1, oy + 1, gx, gy, phi_prev, d);
         const int node = gy * pb.pitch + gx;
         float xs = 0.f, xc = 0.f;
-        if (SRC == kSrcTrig) {
+        if (SRC == kSrcTrig || ((SRC == kSrcRuntime || SRC == kSrcRuntimeNR) && pb.src_kind == kSrcTrig)) {
             xs = pb.Xs[BTRT_IX(pb.flags, gx, pb.nx)];
             xc = pb.Xc[BTRT_IX(pb.flags, gx, pb.nx)];
         }
@@ -175,7 +178,16 @@ __global__ void __launch_bounds__(256, MODE == kGeneral ? BTRT_TB2_MINBLOCKS_GEN
         pb.phi_out[BTRT_IX(pb.flags, node, pb.plane)] = phi;
         bad |= not_finite(phi);
     }
-    if (bad) atomicOr(pb.flags, 1);
+    return bad;
+}
+
+template <typename S, int SH, int MODE, int SRC>
+__global__ void __launch_bounds__(256, MODE == kGeneral ? BTRT_TB2_MINBLOCKS_GEN : BTRT_TB2_MINBLOCKS_LIN)
+    sweep_tb2_kernel(const __grid_constant__ SweepParams<float> pa, const __grid_constant__ SweepParams<float> pb,
+                     int ntx) {
+    extern __shared__ float tb_smem[];
+    const int x0 = (blockIdx.x % ntx) * TbGeom::TX, y0 = (blockIdx.x / ntx) * TbGeom::TY;
+    if (tb2_tile<S, SH, MODE, SRC>(pa, pb, x0, y0, tb_smem)) atomicOr(pb.flags, 1);
 }
 
 }  // namespace btrt
