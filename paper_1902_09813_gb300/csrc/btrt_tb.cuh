@@ -25,8 +25,16 @@
 
 namespace btrt {
 
+// Output tile height.  Swept on GB300 at 8192^2 (GLUPS, FP32 storage MMS /
+// nonlinear, FP16 local-shift MMS / nonlinear): 8 rows 116.7 / 95.8 / 107.7 / 87.8,
+// 16 rows 125.3 / 111.1 / 120.6 / 97.8, 24 rows 85.5 / 114.1 / 104.2 / 103.4 (six
+// blocks then leave little L1 for the first step's halo), 32 rows 115.7 / 108.9 /
+// 117.4 / 101.1.
+#ifndef BTRT_TB2_TY
+#define BTRT_TB2_TY 16
+#endif
 struct TbGeom {
-    static constexpr int TX = 32, TY = 16;        // output tile
+    static constexpr int TX = 32, TY = BTRT_TB2_TY;  // output tile
     static constexpr int MX = TX + 2, MY = TY + 2; // first-step region
     static constexpr int THREADS = 256;
     static constexpr int MID_VALS = 9 * MY * MX;
