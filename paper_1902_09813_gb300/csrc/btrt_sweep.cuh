@@ -486,9 +486,12 @@ template <> struct RowsPerThread<float, float> {
 #ifndef BTRT_MINBLOCKS_F64
 #define BTRT_MINBLOCKS_F64 0
 #endif
+#ifndef BTRT_UNROLL_F64
+#define BTRT_UNROLL_F64 0
+#endif
 template <> struct RowsPerThread<double, double> {
     static constexpr int value = BTRT_ROWS_F64;
-    static constexpr bool unroll = false;
+    static constexpr bool unroll = BTRT_UNROLL_F64 != 0;
 };
 #ifndef BTRT_MINBLOCKS_F32
 #define BTRT_MINBLOCKS_F32 0
