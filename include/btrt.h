@@ -236,9 +236,10 @@ btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_
 btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y, int32_t rows,
                                  int32_t per_step_launch);
 
-/* Pick the fastest candidate (6 tile shapes x 2 launch forms) by timing
- * steps_per_trial steps of each after one warm-up step.  These are real steps:
- * on a first tuning every member advances by 12 x (steps_per_trial + 1) steps.
+/* Pick the fastest candidate (6 tile shapes x 2 launch forms, x 3 for FP32
+ * compute with the two-step form) by timing steps_per_trial steps of each after
+ * one warm-up step.  These are real steps: on a first tuning every member
+ * advances by 12 (FP32: 18) x (steps_per_trial + 1) steps.
  * The choice is cached per (members, total nodes, formats) in the process and
  * reused without timing.  Writes the choice (any pointer may be NULL). */
 btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *block_x, int32_t *block_y,

@@ -319,6 +319,8 @@ class Batch:
         return out
 
     def set_tiles(self, block_x: int, block_y: int, rows: int, per_step: int = 0):
+        """Tile shape and launch form: per_step 0 = persistent launch per call, 1 = one
+        launch per step, 2 = two steps per launch (FP32 compute)."""
         C.check(self.lib.btrt_batch_set_tiles(self.handle, block_x, block_y, rows, per_step))
         return self
 
