@@ -76,8 +76,11 @@ def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
         # can exceed 1 (the DRAM bytes it measured are in `dram_bytes_per_update`)
         shift = args.shift if args.shift != "auto" else ("local" if args.storage in ("f16", "bf16") else "ref")
         key = (args.storage, shift)
-        return dict(hbm, traffic=None, kernel=f"sweep_tb2_kernel<f32,{args.storage}>",
-                    dram_bytes_per_update=TB2_DRAM_BYTES_PER_UPDATE.get(key),
+        per_update = TB2_DRAM_BYTES_PER_UPDATE.get(key)
+        # DRAM bytes of one launch (two steps), from the capture scaled by node count
+        traffic = None if per_update is None else round(per_update * 2 * nodes)
+        return dict(hbm, traffic=traffic, kernel=f"sweep_tb2_kernel<f32,{args.storage}>",
+                    dram_bytes_per_update=per_update,
                     note="two steps per launch; achieved = algorithmic bytes of the steps / time")
     kernel = f"sweep_kernel<{args.compute},{args.storage}>"
     if args.compute != "f64" or args.workload != "mms":

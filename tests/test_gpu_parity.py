@@ -452,7 +452,8 @@ def _tb2_against_plain(case, steps, storage, shift="ref"):
 
 def test_tb2_fields_and_large_ragged_grid():
     """Per-node tensor and source fields, and a 4099 x 4093 grid (ragged tiles at
-    both far edges): bitwise equal to the one-step sweep; the residual step
+    both far edges; FP32 storage with the reference shift and FP16 storage with
+    the local shift): bitwise equal to the one-step sweep; the residual step
     after two-step launches also matches."""
     p = w.variable_tensor(n=70, alpha=1e-2, walls=True, t_end=0.2)
     p = p.replace(dt=20.0 * p.dx ** 2, nsteps=11, phi_ref=0.0)
@@ -463,13 +464,15 @@ def test_tb2_fields_and_large_ragged_grid():
     assert np.array_equal(a.phi_host(), b.phi_host())
     assert a.step_residual(5) == b.step_residual(5)
     q = w.nonlinear_modes(n=4096, nsteps=4).replace(nx=4099, ny=4093)
-    a = _lattice(q, "f32", "f32", shift="ref").set_sweep_variant("tb2")
-    a.init(q.phi0()).step(4)
-    pa = a.phi_host()
-    del a
-    b = _lattice(q, "f32", "f32", shift="ref").set_sweep_variant("plain")
-    b.init(q.phi0()).step(4)
-    assert np.array_equal(pa, b.phi_host())
+    for storage, shift in (("f32", "ref"), ("f16", "local")):
+        a = _lattice(q, "f32", storage, shift=shift).set_sweep_variant("tb2")
+        a.init(q.phi0()).step(4)
+        pa = a.phi_host()
+        del a
+        b = _lattice(q, "f32", storage, shift=shift).set_sweep_variant("plain")
+        b.init(q.phi0()).step(4)
+        assert np.array_equal(pa, b.phi_host())
+        del b
 
 
 def test_tb2_rejects_other_compute():
