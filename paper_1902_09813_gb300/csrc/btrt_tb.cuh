@@ -138,12 +138,15 @@ __device__ __forceinline__ bool tb2_tile(const SweepParams<float> &pa, const Swe
     bool bad = false;
 
     // first step on the grown tile, pulled from global memory
-    for (int k = tid; k < G::MX * G::MY; k += G::THREADS) {
+    auto pull_a = [&](int k, int &gx, int &gy, float (&d)[9], float &phi_prev) -> bool {
         const int mx = k % G::MX, my = k / G::MX;
-        int gx = x0 - 1 + mx, gy = y0 - 1 + my;
-        if (!tb_coord(gx, pa.nx, pa.hbb_x) || !tb_coord(gy, pa.ny, pa.hbb_y)) continue;
-        float d[9], phi_prev;
+        gx = x0 - 1 + mx;
+        gy = y0 - 1 + my;
+        if (!tb_coord(gx, pa.nx, pa.hbb_x) || !tb_coord(gy, pa.ny, pa.hbb_y)) return false;
         pull_node<float, S, SH, false>(pa, gx, gy, gx > 0 && gx < pa.nx - 1, d, phi_prev);
+        return true;
+    };
+    auto finish_a = [&](int k, int gx, int gy, float (&d)[9], float phi_prev) {
         const int node = gy * pa.pitch + gx;
         float xs = 0.f, xc = 0.f;
         if (SRC == kSrcTrig || ((SRC == kSrcRuntime || SRC == kSrcRuntimeNR) && pa.src_kind == kSrcTrig)) {
@@ -159,6 +162,11 @@ __device__ __forceinline__ bool tb2_tile(const SweepParams<float> &pa, const Swe
             mid[i * G::MX * G::MY + k] = Storage<S>::load(store_value<float, S, SH>(i, d[i], phid));
         phi_m[k] = phi;
         bad |= not_finite(phi);
+    };
+    for (int k = tid; k < G::MX * G::MY; k += G::THREADS) {
+        int gx, gy;
+        float d[9], phi_prev;
+        if (pull_a(k, gx, gy, d, phi_prev)) finish_a(k, gx, gy, d, phi_prev);
     }
     __syncthreads();
 
