@@ -241,9 +241,10 @@ __global__ void __launch_bounds__(256, LIN ? BTRT_BATCH_TB2_MINBLOCKS_LIN : BTRT
     __syncthreads();
     bool bad;
     if (LIN || M.mode != kGeneral)
-        bad = tb2_tile<S, SH, kLinear, LIN ? kSrcRuntimeNR : kSrcRuntime>(spa, spb, tile.y, tile.z, tb_smem);
+        bad = tb2_tile<S, SH, kLinear, LIN ? kSrcRuntimeNR : kSrcRuntime, TbGeom::TY>(spa, spb, tile.y, tile.z,
+                                                                                       tb_smem);
     else
-        bad = tb2_tile<S, SH, kGeneral, kSrcRuntime>(spa, spb, tile.y, tile.z, tb_smem);
+        bad = tb2_tile<S, SH, kGeneral, kSrcRuntime, TbGeom::TY>(spa, spb, tile.y, tile.z, tb_smem);
     if (bad) atomicOr(spb.flags, 1);
 }
 

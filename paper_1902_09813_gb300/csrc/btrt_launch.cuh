@@ -92,12 +92,13 @@ cudaError_t launch_tma_storage(const SweepParams<float> &p, int shift, int mode,
                : launch_tma_mode<S, kShiftRef, kGeneral>(p, in_map, out_map, s);
 }
 
-// Two steps per launch: one block per output tile, 24 KB of shared memory.
+// Two steps per launch: one block per output tile, 24-35 KB of shared memory.
 template <typename S, int SH, int MODE, int SRC>
 cudaError_t launch_tb2_src(const SweepParams<float> &pa, const SweepParams<float> &pb, cudaStream_t s) {
-    const int ntx = (pa.nx + TbGeom::TX - 1) / TbGeom::TX;
-    const int nty = (pa.ny + TbGeom::TY - 1) / TbGeom::TY;
-    sweep_tb2_kernel<S, SH, MODE, SRC><<<ntx * nty, TbGeom::THREADS, TbGeom::SMEM, s>>>(pa, pb, ntx);
+    using G = TbGeomFor<MODE>;
+    const int ntx = (pa.nx + G::TX - 1) / G::TX;
+    const int nty = (pa.ny + G::TY - 1) / G::TY;
+    sweep_tb2_kernel<S, SH, MODE, SRC><<<ntx * nty, G::THREADS, G::SMEM, s>>>(pa, pb, ntx);
     return cudaGetLastError();
 }
 

@@ -27,20 +27,27 @@ namespace btrt {
 
 // Output tile height.  Swept on GB300 at 8192^2 (GLUPS, FP32 storage MMS /
 // nonlinear, FP16 local-shift MMS / nonlinear): 8 rows 116.7 / 95.8 / 107.7 / 87.8,
-// 16 rows 125.3 / 111.1 / 120.6 / 97.8, 24 rows 85.5 / 114.1 / 104.2 / 103.4 (six
-// blocks then leave little L1 for the first step's halo), 32 rows 115.7 / 108.9 /
-// 117.4 / 101.1.
+// 16 rows 125.3 / 111.1 / 120.6 / 97.8, 24 rows 85.5 / 114.1 / 104.2 / 103.4 (the
+// constant-coefficient collision runs six blocks per SM, which then leave little L1
+// for the first step's halo), 32 rows 115.7 / 108.9 / 117.4 / 101.1.  So 16 rows
+// for the constant-coefficient collision and 24 for the per-node one.
 #ifndef BTRT_TB2_TY
 #define BTRT_TB2_TY 16
 #endif
-struct TbGeom {
-    static constexpr int TX = 32, TY = BTRT_TB2_TY;  // output tile
+#ifndef BTRT_TB2_TY_GEN
+#define BTRT_TB2_TY_GEN 24
+#endif
+template <int TYV>
+struct TbGeomT {
+    static constexpr int TX = 32, TY = TYV;        // output tile
     static constexpr int MX = TX + 2, MY = TY + 2; // first-step region
     static constexpr int THREADS = 256;
     static constexpr int MID_VALS = 9 * MY * MX;
     static constexpr int SMEM = (MID_VALS + MY * MX) * (int)sizeof(float);
+    static_assert(SMEM <= 48 * 1024, "the two-step kernel's shared memory fits the default per-block limit");
 };
-static_assert(TbGeom::SMEM <= 48 * 1024, "the two-step kernel's shared memory fits the default per-block limit");
+using TbGeom = TbGeomT<BTRT_TB2_TY>;   // the batch form's tiles
+template <int MODE> using TbGeomFor = TbGeomT<MODE == kGeneral ? BTRT_TB2_TY_GEN : BTRT_TB2_TY>;
 
 // Global coordinate -> wrapped coordinate on a periodic axis; false beyond a wall.
 __device__ __forceinline__ bool tb_coord(int &g, int n, int wall) {
@@ -122,15 +129,15 @@ __device__ __forceinline__ void tb_pull(const SweepParams<float> &p, const float
 #endif
 
 // The two steps of one output tile with origin (x0, y0), by the whole block
-// (TbGeom::THREADS threads, TbGeom::SMEM bytes of shared memory at `smem`).  pa:
+// (G::THREADS threads, G::SMEM bytes of shared memory at `smem`, G = TbGeomT<TYV>).  pa:
 // parameters of the first step, pb: of the second (the same buffers: inputs of
 // the first, outputs of the second).  Returns true when a non-finite phi appeared
 // in this thread's nodes.  Other threads may still read `smem` when one returns:
 // the caller places a barrier before reusing it.
-template <typename S, int SH, int MODE, int SRC>
+template <typename S, int SH, int MODE, int SRC, int TYV>
 __device__ __forceinline__ bool tb2_tile(const SweepParams<float> &pa, const SweepParams<float> &pb, int x0, int y0,
                                          float *smem) {
-    using G = TbGeom;
+    using G = TbGeomT<TYV>;
     float *mid = smem;                       // [9][MY][MX]: after the first step (stored form)
     float *phi_m = mid + G::MID_VALS;        // [MY][MX]: phi^{n+1}
     S *__restrict__ fout = static_cast<S *>(pb.fout);
@@ -202,8 +209,9 @@ __global__ void __launch_bounds__(256, MODE == kGeneral ? BTRT_TB2_MINBLOCKS_GEN
     sweep_tb2_kernel(const __grid_constant__ SweepParams<float> pa, const __grid_constant__ SweepParams<float> pb,
                      int ntx) {
     extern __shared__ float tb_smem[];
-    const int x0 = (blockIdx.x % ntx) * TbGeom::TX, y0 = (blockIdx.x / ntx) * TbGeom::TY;
-    if (tb2_tile<S, SH, MODE, SRC>(pa, pb, x0, y0, tb_smem)) atomicOr(pb.flags, 1);
+    using G = TbGeomFor<MODE>;
+    const int x0 = (blockIdx.x % ntx) * G::TX, y0 = (blockIdx.x / ntx) * G::TY;
+    if (tb2_tile<S, SH, MODE, SRC, G::TY>(pa, pb, x0, y0, tb_smem)) atomicOr(pb.flags, 1);
 }
 
 }  // namespace btrt
