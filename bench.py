@@ -352,17 +352,18 @@ def run_variants(args, steps=200, warmup=5):
 
 
 def run_extended(args, n=4096, steps=100):
-    """The extended coefficient paths at n^2: per-node diffusion tensor and source
-    fields (the variable-tensor problem, Eqs. 73-76; 4 field planes read per
-    update), and the Burgers-Fisher power-law flux with the reaction source
-    (Eq. 67, periodic copy of the problem; pow() per node)."""
+    """The extended coefficient paths at n^2 in the default kernel form (two steps
+    per launch for FP32 compute): per-node diffusion tensor and source fields (the
+    variable-tensor problem, Eqs. 73-76; 4 field planes read per update), and the
+    Burgers-Fisher power-law flux with the reaction source (Eq. 67, periodic copy
+    of the problem; products and a square root per node)."""
     import workloads as w
     out = {}
     vt = w.variable_tensor(n=n, alpha=1e-2, walls=True, t_end=0.0)
     vt = vt.replace(dt=20.0 * vt.dx ** 2)
     phi0 = vt.phi0()
     for comp, st in (("f64", "f64"), ("f32", "f32")):
-        r = _time_single(vt, phi0, comp, st, steps, 3)
+        r = _time_single(vt, phi0, comp, st, steps, 3, variant="auto")
         field_b = 4 * (8 if comp == "f64" else 4)
         gbs = (BYTES_PER_UPDATE[st] + field_b) * r["mlups"] * 1e6 / 1e9
         peak, _ = _peaks()
@@ -375,7 +376,7 @@ def run_extended(args, n=4096, steps=100):
         phi0_fn=lambda X, Y: 0.5 + 0.4 * np.sin(2 * np.pi * X / 3.0) * np.sin(2 * np.pi * Y / 3.0))
     phi0 = bf.phi0()
     for comp, st in (("f64", "f64"), ("f32", "f32"), ("f32", "f16")):
-        out[f"burgers_fisher_{n}_{comp}_{st}"] = _time_single(bf, phi0, comp, st, steps, 3,
+        out[f"burgers_fisher_{n}_{comp}_{st}"] = _time_single(bf, phi0, comp, st, steps, 3, variant="auto",
                                                              shift="local" if st == "f16" else "ref")
     return out
 
