@@ -91,7 +91,7 @@ def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
     return {"bound": "alu", "achieved": round(tops, 4), "peak": FP64_PEAK_TOPS,
             "unit": "T FP64 op/s", "frac": round(tops / FP64_PEAK_TOPS, 4), "traffic": traffic,
             "ops_per_update": FP64_OPS_PER_UPDATE_LINEAR,
-            "peak_kind": "recipe nominal FP64 1.25 TFLOP/s = 0.625 T op/s (one-off probe measured 1.20)",
+            "peak_kind": "GB300 nominal FP64 1.25 TFLOP/s = 0.625 T op/s (an FMA-chain probe measured 1.20)",
             "kernel": kernel, "hbm_view": hbm}
 
 
