@@ -1,5 +1,6 @@
-"""Tiny-grid runs shared by the index-check test: every kernel form on grids of
-3 to 7 nodes per side (every node is a boundary node or next to one).  Run as a
+"""Tiny-grid runs shared by the index-check test: every kernel form (one step,
+TMA-staged and two steps per launch; the batch forms; D3Q19) on grids of 3 to 7
+nodes per side (every node is a boundary node or next to one).  Run as a
 script it writes the results to an .npz file, with whatever libbtrt the
 BTRT_LIBRARY environment variable selects."""
 import sys
@@ -11,7 +12,8 @@ import workloads as w
 GRIDS_2D = [(4, 4, (0, 0, 0, 0)), (5, 5, (1, 1, 1, 1)), (7, 3, (0, 0, 1, 1)), (3, 3, (1, 1, 0, 0)),
             (3, 7, (1, 1, 1, 1))]
 FORMS_2D = [("f64", "f64", "ref", "plain"), ("df64", "df64", "ref", "plain"), ("f32", "f32", "ref", "plain"),
-            ("f32", "f16", "local", "plain"), ("f32", "bf16", "ref", "tma"), ("f32", "f16", "local", "tma")]
+            ("f32", "f16", "local", "plain"), ("f32", "bf16", "ref", "tma"), ("f32", "f16", "local", "tma"),
+            ("f32", "f32", "ref", "tb2"), ("f32", "f16", "local", "tb2"), ("f32", "bf16", "ref", "tb2")]
 GRIDS_3D = [(3, 3, 3, (0,) * 6), (4, 5, 6, (1,) * 6), (5, 3, 4, (1, 1, 0, 0, 1, 1))]
 FORMS_3D = [("f64", "f64", "ref"), ("f32", "f32", "ref"), ("f32", "f16", "local")]
 
@@ -43,6 +45,7 @@ def run_all():
             .init(q.phi0()) for q in probs]
     b = Batch(lats)
     b.step(6, residual=True)
+    b.set_tiles(32, 8, 1, 2).step(5, residual=True)   # the two-step batch form, an odd slice
     for k, lt in enumerate(lats):
         out[f"batch_{k}"] = lt.phi_host()
         flags[f"batch_{k}"] = int(b.member_flags()[k])
