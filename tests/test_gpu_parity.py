@@ -475,6 +475,54 @@ def test_tb2_fields_and_large_ragged_grid():
         del b
 
 
+@pytest.mark.parametrize("which", ["mms", "nonlinear"])
+def test_tb2_full_size_matches_oracle_two_steps(which):
+    """The default FP32 form (two steps per launch) at the benchmark's 8192^2
+    against the oracle at sampled nodes (corners, edges, tile seams, interior):
+    the oracle takes the nine neighbours one single-node step from the GPU's state,
+    then the node itself a second step from those (FP32 tolerance)."""
+    import torch
+    n = 8192
+    p = (w.mms_sinsin(n=n, nsteps=4) if which == "mms" else w.nonlinear_modes(n=n, nsteps=4))
+    if which != "mms":
+        p.phi_ref = float(p.phi0().mean())
+    lat = _lattice(p, "f32", "f32", shift="ref")
+    lat.init(p.phi0(), t0=p.t0).step(3)
+    pts = [(0, 0), (n - 1, n - 1), (0, n - 1), (31, 15), (32, 16), (5000, 6001), (4095, 0), (17, 8191)]
+    win5, phin = {}, {}
+    phi_dev = lat.phi()
+    for (x, y) in pts:
+        w5 = np.zeros((5, 5, 9))
+        ph = np.zeros((5, 5))
+        for dy in range(-2, 3):
+            for dx in range(-2, 3):
+                qx, qy = (x + dx) % n, (y + dy) % n
+                w5[dy + 2, dx + 2] = lat.read_f(qx, qy, 1, 1)[:, 0, 0]
+                ph[dy + 2, dx + 2] = float(phi_dev[qy, qx].item())
+        win5[(x, y)], phin[(x, y)] = w5, ph
+    _, t_now = lat.time()
+    lat.step(2)   # one two-step launch
+    torch.cuda.synchronize()
+    walled = which == "mms"
+    for (x, y) in pts:
+        w5, ph = win5[(x, y)], phin[(x, y)]
+        mid = np.zeros((3, 3, 9))
+        phi1 = 0.0
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                qx, qy = x + dx, y + dy
+                if walled and not (0 <= qx < n and 0 <= qy < n):
+                    continue   # beyond a wall: never pulled
+                f1, p1 = oracle.node_step(p, w5[dy + 1:dy + 4, dx + 1:dx + 4], qx % n, qy % n, ph[dy + 2, dx + 2],
+                                          t_now + p.dt)
+                mid[dy + 1, dx + 1] = f1
+                if dx == 0 and dy == 0:
+                    phi1 = p1
+        f2, _ = oracle.node_step(p, mid, x, y, phi1, t_now + 2 * p.dt)
+        got = lat.read_f(x, y, 1, 1)[:, 0, 0]
+        assert np.allclose(got, f2, rtol=2e-5, atol=2e-5 * np.abs(f2).max()), (x, y)
+
+
 def test_tb2_rejects_other_compute():
     """The two-step form serves FP32-compute lattices only."""
     from paper_1902_09813_gb300 import _capi as C
