@@ -504,6 +504,12 @@ template <> struct RowsPerThread<double, double> {
 #endif
 // Minimum resident blocks per SM requested from the compiler (register budget);
 // 0 leaves the choice to the compiler.
+// FP64 per-node coefficient sweeps: the compiler's 96 registers (two blocks);
+// four blocks (64 registers) measured 5.14 GLUPS against 5.57 on the nonlinear
+// workload.
+#ifndef BTRT_MINBLOCKS_F64_GEN
+#define BTRT_MINBLOCKS_F64_GEN 0
+#endif
 // Double-word constant-coefficient sweeps: five blocks (48 registers, 12 spilled
 // bytes) measured 36.9 GLUPS against 33.5 with the compiler's 64 registers; the
 // per-node coefficient form would spill hundreds of bytes there.
@@ -511,7 +517,9 @@ template <> struct RowsPerThread<double, double> {
 #define BTRT_MINBLOCKS_DW 5
 #endif
 template <typename Real, typename S, int MODE> struct MinBlocks { static constexpr int value = 0; };
-template <int MODE> struct MinBlocks<double, double, MODE> { static constexpr int value = BTRT_MINBLOCKS_F64; };
+template <int MODE> struct MinBlocks<double, double, MODE> {
+    static constexpr int value = MODE == kGeneral ? BTRT_MINBLOCKS_F64_GEN : BTRT_MINBLOCKS_F64;
+};
 template <int MODE> struct MinBlocks<float, float, MODE> { static constexpr int value = BTRT_MINBLOCKS_F32; };
 template <int MODE> struct MinBlocks<float, __half, MODE> { static constexpr int value = BTRT_MINBLOCKS_S16; };
 template <int MODE> struct MinBlocks<float, __nv_bfloat16, MODE> { static constexpr int value = BTRT_MINBLOCKS_S16; };
