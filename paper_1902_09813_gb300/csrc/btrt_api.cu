@@ -1,10 +1,12 @@
 // btrt_api.cu -- host runtime and C ABI of the B-TriRT D2Q9 solver (see include/btrt.h).
 //
 // A lattice lives entirely in a caller-owned device workspace:
-//   [F buffer 0: 9 planes][F buffer 1: 9 planes][phi plane][trig tables][wall arrays][reduction scratch]
+//   [F buffer 0: 9 planes][F buffer 1: 9 planes][phi plane 0][phi plane 1][trig tables]
+//   [wall arrays][reduction scratch][residual partials][optional field planes]
 // Planes are row major with a row pitch of nx rounded up to 64 elements; every
-// region starts on a 256-byte boundary.  Populations are double buffered: a
-// sweep reads buffer `cur` and writes buffer 1 - cur.
+// region starts on a 256-byte boundary.  Populations and phi are double
+// buffered: a launch reads buffer `cur` and writes buffer 1 - cur (one step per
+// launch, or two in the two-step form of FP32 compute).
 #include <cuda_runtime.h>
 
 #include <algorithm>
