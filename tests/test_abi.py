@@ -133,3 +133,23 @@ def test_d3q19_rejects_unknown_shift_and_fields(lib):
     d = _desc3()
     d.fields = 2      # no diffusion-field planes in 3-D
     assert lib.btrt3_workspace_bytes(ctypes.byref(d)) == 0
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: with the library missing, the first call that needs it
+    raises instead of computing anything."""
+    import subprocess
+    import sys
+    code = ("import numpy as np, workloads as w\n"
+            "from paper_1902_09813_gb300 import Lattice\n"
+            "p = w.random_state_problem(8, 8, seed=1)\n"
+            "try:\n"
+            "    Lattice.from_problem(p, compute='f64')\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', 'missing' in str(e))\n"
+            "else:\n"
+            "    print('no error')\n")
+    env = dict(os.environ, BTRT_LIBRARY=str(tmp_path / "absent" / "libbtrt.so"), PYTHONPATH=ROOT)
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT,
+                       timeout=300)
+    assert "raised: True" in r.stdout, (r.stdout, r.stderr[-2000:])
