@@ -1,0 +1,108 @@
+"""Host logic of the continuous-batching server without a GPU: admission by the
+memory budget, retirement at the residual tolerance or the step cap, a member
+with a non-finite flag retired alone, results in request order, the queue-depth
+series.  The lattice and batch classes are replaced by fakes that keep only a step
+count; the workspace sizes come from the real library (no device needed)."""
+import numpy as np
+import pytest
+
+import workloads as w
+from paper_1902_09813_gb300 import serve
+
+
+class _FakeLattice:
+    def __init__(self, p):
+        self.p = p
+        self.steps = 0
+
+    @classmethod
+    def from_problem(cls, p, compute="f32", storage="f16", stream=None, shift="auto"):
+        return cls(p)
+
+    def init(self, phi0, t0=0.0):
+        return self
+
+    def phi_host(self):
+        return np.full((self.p.ny, self.p.nx), float(self.steps))
+
+
+class _FakeBatch:
+    """Residual of a member after s steps: rate ** s (rate in the problem's meta);
+    a member whose meta has `bad_at` raises flag bit 0 once it passes that step."""
+    created = 0
+
+    def __init__(self, lats, stream=None):
+        self.lats = lats
+        _FakeBatch.created += 1
+
+    def set_tiles(self, *shape):
+        return self
+
+    def step(self, n, residual=False):
+        for lat in self.lats:
+            lat.steps += n
+        return self
+
+    def residuals(self):
+        return np.array([lat.p.meta["rate"] ** lat.steps for lat in self.lats])
+
+    def member_flags(self):
+        return np.array([1 if lat.steps >= lat.p.meta.get("bad_at", 1 << 30) else 0 for lat in self.lats])
+
+    def close(self):
+        pass
+
+
+@pytest.fixture
+def fakes(monkeypatch):
+    monkeypatch.setattr(serve, "Lattice", _FakeLattice)
+    monkeypatch.setattr(serve, "Batch", _FakeBatch)
+    _FakeBatch.created = 0
+
+
+def _problems(rates, n=32):
+    out = []
+    for k, r in enumerate(rates):
+        p = w.random_state_problem(n, n, seed=k)
+        p.meta = dict(p.meta, rate=r)
+        out.append(p)
+    return out
+
+
+def test_budget_admission_and_retirement(fakes):
+    probs = _problems([0.5, 0.9, 0.99, 0.5])
+    need = serve._bytes_needed(probs[0], "f32", "f16")
+    srv = serve.Server(budget_bytes=2.5 * need, slice_steps=10, max_steps=200, tol=1e-6, stream=object())
+    res = srv.run([(0.0, p) for p in probs])
+    assert [r.rid for r in res] == [0, 1, 2, 3]
+    assert srv.stats["peak_active"] == 2
+    # first slice whose end passes the tolerance, else the cap
+    expect = []
+    for r in (0.5, 0.9, 0.99, 0.5):
+        s = 10
+        while r ** s >= 1e-6 and s < 200:
+            s += 10
+        expect.append(s)
+    assert [r.steps for r in res] == expect
+    assert all(r.status == "done" for r in res)
+    assert all(np.all(r.phi == r.steps) for r in res)
+    assert res[2].residual > 1e-6 and res[2].steps == 200   # the cap, not the tolerance
+    # waiting requests are admitted as members retire: every request ran, never more than two at once
+    assert max(d[1] for d in srv.depth) == 2 and srv.depth[0][2] == 2
+
+
+def test_unstable_member_retired_alone(fakes):
+    probs = _problems([0.9, 0.9, 0.9])
+    probs[1].meta["bad_at"] = 30
+    srv = serve.Server(budget_bytes=1e12, slice_steps=10, max_steps=100, tol=1e-30, stream=object())
+    res = srv.run([(0.0, p) for p in probs])
+    assert [r.status for r in res] == ["done", "unstable", "done"]
+    assert res[1].steps == 30 and res[0].steps == 100 and res[2].steps == 100
+
+
+def test_depth_series_thinning():
+    depth = [(0.1 * k, k % 5, 10 - k % 10) for k in range(100)]
+    out = serve.depth_series(depth, points=16)
+    assert out[0] == list(depth[0]) and out[-1] == list(depth[-1])
+    assert 16 <= len(out) <= 18
+    assert serve.depth_series([]) == []
