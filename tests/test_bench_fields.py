@@ -1,0 +1,48 @@
+"""Host-side pieces of bench.py's JSON line: the roofline object for each kind of
+headline (FP64 sweep against the FP64 pipe; the two-step FP32 form with its
+measured DRAM bytes and per-launch traffic; one step per launch against HBM) and
+the launch count of the two-step form."""
+import argparse
+
+import bench
+
+
+def _args(**kw):
+    a = dict(compute="f64", storage="f64", workload="mms", shift="auto", sweep="auto", steps=1000)
+    a.update(kw)
+    return argparse.Namespace(**a)
+
+
+def test_fp64_roofline_is_the_fp64_pipe():
+    nodes, t = 8192 * 8192, 6.46e-3
+    r = bench.roofline(_args(), nodes, t, 160 * nodes / t / 1e9, 6800.0, "measured")
+    assert r["bound"] == "alu" and r["unit"] == "T FP64 op/s"
+    assert r["ops_per_update"] == bench.FP64_OPS_PER_UPDATE_LINEAR
+    assert abs(r["achieved"] - bench.FP64_OPS_PER_UPDATE_LINEAR * nodes / t / 1e12) < 1e-3
+    assert abs(r["frac"] - r["achieved"] / bench.FP64_PEAK_TOPS) < 1e-3
+    assert r["traffic"] == round(bench.FP64_TRAFFIC_PER_NODE * nodes)
+    assert r["hbm_view"]["bytes_per_update"] == 160
+
+
+def test_two_step_roofline_reports_measured_dram_bytes():
+    nodes, t = 8192 * 8192, 0.536e-3
+    args = _args(compute="f32", storage="f32", shift="ref")
+    assert bench.two_step_form(args)
+    r = bench.roofline(args, nodes, t, 80 * nodes / t / 1e9, 6800.0, "measured")
+    assert r["bound"] == "hbm" and r["kernel"].startswith("sweep_tb2_kernel")
+    assert r["dram_bytes_per_update"] == bench.TB2_DRAM_BYTES_PER_UPDATE[("f32", "ref")]
+    assert r["traffic"] == round(r["dram_bytes_per_update"] * 2 * nodes)   # one launch = two steps
+    assert r["frac"] > 1.0   # algorithmic one-step bytes over the copy peak
+    # the local shift is the default for 16-bit storage
+    r16 = bench.roofline(_args(compute="f32", storage="f16"), nodes, t, 1.0, 6800.0, "measured")
+    assert r16["dram_bytes_per_update"] == bench.TB2_DRAM_BYTES_PER_UPDATE[("f16", "local")]
+
+
+def test_one_step_forms_and_launch_counts():
+    nodes = 4096 * 4096
+    args = _args(compute="f32", storage="f32", shift="ref", sweep="plain")
+    assert not bench.two_step_form(args)
+    r = bench.roofline(args, nodes, 1e-3, 6000.0, 6800.0, "measured")
+    assert r["kernel"].startswith("sweep_kernel") and r["traffic"] is None
+    assert not bench.two_step_form(_args())                       # FP64: one launch per step
+    assert not bench.two_step_form(_args(compute="df64", storage="df64"))
