@@ -43,21 +43,81 @@ def _peaks():
         return 6800.0, "fallback"
 
 
-# FP64 operations (add, mul or fma, one each) per node of the FP64 sweep, counted
-# from the kernel source (collide_fold in the k0 = 1 constant-coefficient form
-# plus the trig source term): 20 adds (moments 18, V +- 2), 25 FMAs, 5 multiplies.
-FP64_OPS_PER_UPDATE_LINEAR = 50
-# GB300 FP64 peak: 1.25 TFLOP/s nominal = 0.625 T FMA/s, i.e.
-# 0.625 T FP64 operations/s when every add, mul or fma takes one lane slot.
-FP64_PEAK_TOPS = 0.625
+CSRC = os.path.join(ROOT, "paper_1902_09813_gb300", "csrc")
+
+
+def source_digest(names) -> str:
+    """sha256 (first 16 hex digits) of kernel source files, in the given order."""
+    import hashlib
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(CSRC, n), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _header_count(name: str) -> int:
+    """An integer constant kept next to the kernel code it describes."""
+    import re
+    with open(os.path.join(CSRC, "btrt_sweep.cuh")) as fh:
+        m = re.search(rf"constexpr int {name} = (\d+);", fh.read())
+    return int(m.group(1))
+
+
+# FP64 operations (add, mul or fma, one each) per node of the FP64 headline sweep,
+# counted from the kernel source next to collide_fold, in total and by kind.
+FP64_OPS_PER_UPDATE_LINEAR = _header_count("kFp64OpsPerNodeLinearTrig")
+FP64_MIX_PER_UPDATE = {"add": _header_count("kFp64AddsPerNodeLinearTrig"),
+                       "fma": _header_count("kFp64FmasPerNodeLinearTrig"),
+                       "mul": _header_count("kFp64MulsPerNodeLinearTrig")}
+# GB300's nominal FP64 rate, 1.25 TFLOP/s = 0.625 T FMA/s = 0.625 T FP64
+# operations/s when every add, mul or fma takes one lane slot; reported beside the
+# rate measured in the run (btrt_probe_fp64_rate), which is the roofline's peak.
+FP64_NOMINAL_TOPS = 0.625
 # DRAM bytes per node of one FP64 sweep launch measured by ncu
-# (dram__bytes_read.sum + dram__bytes_write.sum) on the same kernel at 2048^2
-# (profiles/sweep_f64_mms2048_full.md), scaled to the benchmark by node count;
-# None when the kernel changed after the capture.
+# (dram__bytes_read.sum + dram__bytes_write.sum) on the same kernel at 2048^2,
+# scaled to the benchmark by node count.  The operation count and this capture
+# hold for the kernel sources whose digest is FP64_SWEEP_DIGEST; after an edit
+# to them both are re-taken and the digest updated (a CPU test checks it), and
+# until then the traffic is reported as null.
+FP64_SWEEP_SOURCES = ("btrt_sweep.cuh", "btrt_kernels.cu", "btrt_dw.cuh")
+FP64_SWEEP_DIGEST = "a79ce8707e427c39"
 FP64_TRAFFIC_PER_NODE = 149.3
-# DRAM bytes per node and step of the two-step FP32-compute kernel measured by ncu
-# (profiles/sweep_tb2_*_full.md), keyed by (storage, shift).
+# DRAM bytes per node and step of the two-step FP32-compute kernel measured by ncu,
+# keyed by (storage, shift), for the sources with digest TB2_DIGEST.
+TB2_SOURCES = ("btrt_sweep.cuh", "btrt_tb.cuh", "btrt_launch.cuh")
+TB2_DIGEST = "9f8c00e5fe1e01a4"
 TB2_DRAM_BYTES_PER_UPDATE = {("f32", "ref"): 38.6, ("f16", "local"): 20.9}
+
+
+def measure_fp64_peak(iters: int = 2000):
+    """FP64 operation rates of the probe kernel on the current device: for each kind
+    (FMA, add, multiply) the best of 4, 8 and 16 independent chains per thread,
+    and the peak of the FP64 sweep's own mix of kinds, FP64_MIX_PER_UPDATE:
+    sum(n_k) / sum(n_k / rate_k) operations per second."""
+    import ctypes
+
+    import torch
+    from paper_1902_09813_gb300 import _capi as C
+    lib = C.load()
+    sink = torch.zeros(8, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    rates = {}
+    for name, kind in (("fma", C.PROBE_FMA), ("add", C.PROBE_ADD), ("mul", C.PROBE_MUL)):
+        best = 0.0
+        for chains in (4, 8, 16):
+            rate, ms = ctypes.c_double(), ctypes.c_double()
+            C.check(lib.btrt_probe_fp64_rate(ctypes.c_void_p(stream.cuda_stream), kind, chains, iters,
+                                             ctypes.c_void_p(sink.data_ptr()), ctypes.byref(rate),
+                                             ctypes.byref(ms)))
+            best = max(best, rate.value)
+        rates[name] = best
+    n = sum(FP64_MIX_PER_UPDATE.values())
+    mix = n / sum(FP64_MIX_PER_UPDATE[k] / rates[k] for k in FP64_MIX_PER_UPDATE)
+    return {"tops": round(mix / 1e12, 4),
+            "by_kind_tops": {k: round(v / 1e12, 4) for k, v in rates.items()},
+            "mix": dict(FP64_MIX_PER_UPDATE),
+            "kernel": "fp64_chains (4/8/16 independent chains per thread, whole waves, best per kind)"}
 
 
 def two_step_form(args) -> bool:
@@ -65,7 +125,7 @@ def two_step_form(args) -> bool:
     return args.compute == "f32" and args.sweep in ("auto", "tb2")
 
 
-def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
+def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind, fp64_peak=None):
     hbm = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peak_hbm, "unit": "GB/s",
            "frac": round(achieved_gbs / peak_hbm, 4), "peak_kind": peak_kind,
            "frac_of_nominal_8tbs": round(achieved_gbs / 8000.0, 4),
@@ -76,7 +136,8 @@ def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
         # can exceed 1 (the DRAM bytes it measured are in `dram_bytes_per_update`)
         shift = args.shift if args.shift != "auto" else ("local" if args.storage in ("f16", "bf16") else "ref")
         key = (args.storage, shift)
-        per_update = TB2_DRAM_BYTES_PER_UPDATE.get(key)
+        fresh = source_digest(TB2_SOURCES) == TB2_DIGEST
+        per_update = TB2_DRAM_BYTES_PER_UPDATE.get(key) if fresh else None
         # DRAM bytes of one launch (two steps), from the capture scaled by node count
         traffic = None if per_update is None else round(per_update * 2 * nodes)
         return dict(hbm, traffic=traffic, kernel=f"sweep_tb2_kernel<f32,{args.storage}>",
@@ -87,11 +148,18 @@ def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind):
         return dict(hbm, traffic=None, kernel=kernel)
     # the FP64 sweep is bound by GB300's FP64 pipe, not by HBM
     tops = FP64_OPS_PER_UPDATE_LINEAR * nodes / t_launch / 1e12
-    traffic = None if FP64_TRAFFIC_PER_NODE is None else round(FP64_TRAFFIC_PER_NODE * nodes)
-    return {"bound": "alu", "achieved": round(tops, 4), "peak": FP64_PEAK_TOPS,
-            "unit": "T FP64 op/s", "frac": round(tops / FP64_PEAK_TOPS, 4), "traffic": traffic,
-            "ops_per_update": FP64_OPS_PER_UPDATE_LINEAR,
-            "peak_kind": "GB300 nominal FP64 1.25 TFLOP/s = 0.625 T op/s (an FMA-chain probe measured 1.20)",
+    fresh = source_digest(FP64_SWEEP_SOURCES) == FP64_SWEEP_DIGEST
+    traffic = round(FP64_TRAFFIC_PER_NODE * nodes) if fresh else None
+    if fp64_peak:
+        peak, kind = fp64_peak["tops"], (f"measured in this run: probe rates by kind {fp64_peak['by_kind_tops']} "
+                                         f"T op/s combined over the sweep's mix {fp64_peak['mix']} "
+                                         f"(GB300 nominal FP64 1.25 TFLOP/s = {FP64_NOMINAL_TOPS} T op/s)")
+    else:
+        peak, kind = FP64_NOMINAL_TOPS, "GB300 nominal FP64 1.25 TFLOP/s = 0.625 T op/s (not measured)"
+    return {"bound": "alu", "achieved": round(tops, 4), "peak": peak,
+            "unit": "T FP64 op/s", "frac": round(tops / peak, 4), "traffic": traffic,
+            "ops_per_update": FP64_OPS_PER_UPDATE_LINEAR, "peak_kind": kind,
+            "frac_of_nominal": round(tops / FP64_NOMINAL_TOPS, 4),
             "kernel": kernel, "hbm_view": hbm}
 
 
@@ -256,6 +324,8 @@ def run_gpu(args):
     extra = {}
     del lat
     torch.cuda.empty_cache()
+    # the FP64 pipe's rate on this GPU, the FP64 sweep's roofline peak
+    fp64_peak = measure_fp64_peak() if args.compute == "f64" else None
     if ws > 1:
         # the per-GPU characterisations (variants, accuracy, batching, serving, CPU oracle)
         # are reported at N = 1; replicas only time the headline sweep
@@ -281,7 +351,7 @@ def run_gpu(args):
             "config": {"workload": desc, "nx": p.nx, "ny": p.ny,
                        "parallelism": "replicas" if ws > 1 else "single",
                        "l2": f"inputs {alg_bytes / 2 / 1e9:.2f} GB read per step >> L2, no flush"},
-            "roofline": roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind),
+            "roofline": roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind, fp64_peak),
             "e2e": None if e2e_mlups is None else {
                 "value": round(e2e_mlups, 2), "unit": "MLUPS",
                 "h2d_bytes_per_step": int(8 * nodes / args.steps),
@@ -440,24 +510,72 @@ REDUCED = [("df64", "df64", "ref"), ("f32", "f32", "ref"), ("f32", "f32", "local
            ("f32", "f16", "local"), ("f32", "bf16", "ref"), ("f32", "bf16", "local")]
 
 
+def _fmt_key(c, s, sh):
+    return c if c in ("f64", "df64") else f"{c}_{s}_{sh}"
+
+
+# The reduced-precision bar: a format's GRE against the closed form may differ
+# from the FP64 sweep's by at most this fraction of it.
+GRE_BAR = 0.01
+CONV_SIDES = (64, 128, 256, 512, 1024, 2048)
+
+
+def run_convergence(sides=CONV_SIDES, formats=None):
+    """Config-2 convergence sweep under diffusive scaling (dt = 4 dx^2, T_end = 0.1,
+    HBB walls, manufactured solution): the GRE against the closed form per grid
+    and format, the observed order log2(GRE(N/2) / GRE(N)), each format's GRE
+    relative to the FP64 sweep's, and the finest N at which a format stays within
+    GRE_BAR of it (all coarser grids too)."""
+    import workloads as w
+    formats = formats or [("f64", "f64", "ref")] + REDUCED
+    out = {"sides": list(sides), "kappa": 4.0, "t_end": 0.1, "bar": GRE_BAR, "formats": {}}
+    gre = {}
+    t_fmt = {}
+    for n in sides:
+        p = w.mms_sinsin(n=n)
+        phi0 = p.phi0()
+        ex = w.mms_sinsin_exact(p, p.t0 + p.nsteps * p.dt)
+        for c, s, sh in formats:
+            t0 = time.perf_counter()
+            g = w.gre(_final_phi(p, phi0, c, s, p.nsteps, sh), ex)
+            k = _fmt_key(c, s, sh)
+            gre.setdefault(k, []).append(g)
+            t_fmt[k] = t_fmt.get(k, 0.0) + time.perf_counter() - t0
+    out["steps"] = [int(w.mms_sinsin(n=n).nsteps) for n in sides]
+    base = gre["f64"]
+    for k, g in gre.items():
+        order = [None] + [round(math.log2(g[i - 1] / g[i]), 3) for i in range(1, len(g))]
+        rel = [round(g[i] / base[i] - 1.0, 5) for i in range(len(g))]
+        finest = None
+        for i, r in enumerate(rel):
+            if abs(r) > GRE_BAR:
+                break
+            finest = sides[i]
+        out["formats"][k] = {"gre": [float(f"{v:.5e}") for v in g], "order": order,
+                             "rel_to_f64": rel, "finest_n_within_bar": finest,
+                             "seconds": round(t_fmt[k], 2)}
+    return out
+
+
 def run_accuracy(args):
     """Error of each reduced-precision path: relative L2 against the FP64 sweep on
-    the nonlinear 16-mode workload (2048^2, 1000 steps; the FP64 sweep matches the
-    FP64 oracle to 1e-11 in the parity tests), and the discretisation error (GRE)
-    against the closed forms of the Gaussian hill (64^2, 500 steps) and the
-    manufactured solution (128^2) next to the FP64 sweep's."""
+    the nonlinear 16-mode workload (2048^2 and 8192^2, 1000 steps; the FP64 sweep
+    matches the FP64 oracle to 1e-11 in the parity tests, at 8192^2 on sampled
+    nodes), the discretisation error (GRE) against the closed forms of the
+    Gaussian hill (64^2, 500 steps) and the manufactured solution (128^2) next to
+    the FP64 sweep's, and the config-2 convergence sweep (run_convergence)."""
     import workloads as w
 
-    def key(c, s, sh):
-        return c if c == "df64" else f"{c}_{s}_{sh}"
-
     out = {"reference": "FP64 sweep (= FP64 oracle to 1e-11)"}
-    q = w.nonlinear_modes(n=2048, nsteps=1000)
-    phi0 = q.phi0()
-    q.phi_ref = float(phi0.mean())
-    ref = _final_phi(q, phi0, "f64", "f64", 1000)
-    out["nonlinear_2048_1000_rel_l2"] = {key(c, s, sh): float(f"{w.rel_l2(_final_phi(q, phi0, c, s, 1000, sh), ref):.3e}")
-                                         for c, s, sh in REDUCED}
+    for n in (2048, 8192):
+        q = w.nonlinear_modes(n=n, nsteps=1000)
+        phi0 = q.phi0()
+        q.phi_ref = float(phi0.mean())
+        ref = _final_phi(q, phi0, "f64", "f64", 1000)
+        out[f"nonlinear_{n}_1000_rel_l2"] = {
+            _fmt_key(c, s, sh): float(f"{w.rel_l2(_final_phi(q, phi0, c, s, 1000, sh), ref):.3e}")
+            for c, s, sh in REDUCED}
+        del ref
     closed = {"hill_64": (w.gaussian_hill(), lambda p: w.gaussian_hill_exact(p, p.nsteps * p.dt)),
               "mms_128": (w.mms_sinsin(n=128), lambda p: w.mms_sinsin_exact(p, p.t0 + p.nsteps * p.dt))}
     for name, (p, exact) in closed.items():
@@ -466,8 +584,9 @@ def run_accuracy(args):
         ex = exact(p)
         g = {"f64": float(f"{w.gre(_final_phi(p, phi0, 'f64', 'f64', p.nsteps), ex):.4e}")}
         for c, s, sh in REDUCED:
-            g[key(c, s, sh)] = float(f"{w.gre(_final_phi(p, phi0, c, s, p.nsteps, sh), ex):.4e}")
+            g[_fmt_key(c, s, sh)] = float(f"{w.gre(_final_phi(p, phi0, c, s, p.nsteps, sh), ex):.4e}")
         out[f"{name}_gre"] = g
+    out["mms_convergence"] = run_convergence()
     return out
 
 
@@ -672,6 +791,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--serve-seq", type=int, default=48)
+    ap.add_argument("--accuracy-only", action="store_true",
+                    help="only the accuracy study (reduced formats, closed forms, convergence sweep)")
     ap.add_argument("--batched-only", action="store_true",
                     help="only the batched persistent launch (for profiling small batches)")
     ap.add_argument("--d3q19-only", action="store_true",
@@ -693,6 +814,12 @@ def main():
         args.storage = args.compute
     if args.impl == "reference":
         run_reference(args)
+    elif args.accuracy_only:
+        import torch
+        torch.cuda.set_device(0)
+        t0 = time.perf_counter()
+        acc = run_accuracy(args)
+        print(json.dumps({"accuracy": acc, "seconds": round(time.perf_counter() - t0, 1)}), flush=True)
     elif args.batched_only:
         run_batched_only(args)
     elif args.d3q19_only:

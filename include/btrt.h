@@ -186,10 +186,14 @@ btrt_status btrt_check(btrt_lattice L, int32_t *flags);
  * BTRT_SWEEP_TB2 (two time steps per launch: the first step's populations stay
  * in shared memory, halving the DRAM bytes per step; btrt_step runs pairs of
  * steps this way and an odd last step, and btrt_step_residual its last step, in
- * the plain form).  Every storage format and shift of an FP32-compute lattice.
+ * the plain form), or BTRT_SWEEP_VEC (one step per launch; each thread owns four
+ * x-consecutive nodes and moves each population plane with one vector load and
+ * one vector store, 64 bits for F16/BF16 storage and 128 for F32; the
+ * initialising collision and btrt_step_residual's last step run in the plain
+ * form).  Every storage format and shift of an FP32-compute lattice.
  * All forms give bitwise identical results.  FP64 and double-word lattices
- * always use the plain form (BTRT_SWEEP_TMA and BTRT_SWEEP_TB2: BTRT_EINVAL). */
-enum { BTRT_SWEEP_AUTO = 0, BTRT_SWEEP_PLAIN = 1, BTRT_SWEEP_TMA = 2, BTRT_SWEEP_TB2 = 3 };
+ * always use the plain form (BTRT_SWEEP_TMA, _TB2 and _VEC: BTRT_EINVAL). */
+enum { BTRT_SWEEP_AUTO = 0, BTRT_SWEEP_PLAIN = 1, BTRT_SWEEP_TMA = 2, BTRT_SWEEP_TB2 = 3, BTRT_SWEEP_VEC = 4 };
 btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant);
 
 /* Number of completed steps and the current time t0 + n dt. */
@@ -227,19 +231,21 @@ btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_
                               void *cuda_stream, btrt_batch *out);
 
 /* Tile shape: block_x x block_y threads, each sweeping `rows` nodes of its
- * column.  Candidates: 32x8x1, 32x8x2, 32x8x4, 64x4x1, 64x4x2, 32x4x2.
- * per_step_launch = 0: persistent launch per call; 1: one launch per step;
- * 2 (FP32-compute batches only, else BTRT_EINVAL): two steps per launch on
+ * column.  Candidates: 32x8x1, 32x8x2, 32x8x4, 64x4x1, 64x4x2, 32x4x2, 16x16x1,
+ * 8x32x1.  per_step_launch = 0: persistent launch per call; 1: one launch per
+ * step; 2 (FP32-compute batches only, else BTRT_EINVAL): two steps per launch on
  * 32 x 16 output tiles (the form of BTRT_SWEEP_TB2), an odd last step and the
- * residual step of btrt_batch_step in the form of 1 with the given shape.
- * Results are bitwise the same in every form and shape. */
+ * residual step of btrt_batch_step in the form of 1 with the given shape;
+ * 3 (FP32-compute batches only): one launch per step in the vector form of
+ * BTRT_SWEEP_VEC on tiles of (4 block_x) x (block_y rows) nodes, the residual
+ * step in the form of 1.  Results are bitwise the same in every form and shape. */
 btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y, int32_t rows,
                                  int32_t per_step_launch);
 
-/* Pick the fastest candidate (6 tile shapes x 2 launch forms, x 3 for FP32
- * compute with the two-step form) by timing steps_per_trial steps of each after
- * one warm-up step.  These are real steps: on a first tuning every member
- * advances by 12 (FP32: 18) x (steps_per_trial + 1) steps.
+/* Pick the fastest candidate (8 tile shapes x 2 launch forms, x 4 for FP32
+ * compute with the two-step and vector forms) by timing steps_per_trial steps of
+ * each after one warm-up step.  These are real steps: on a first tuning every
+ * member advances by 16 (FP32: 32) x (steps_per_trial + 1) steps.
  * The choice is cached per (members, total nodes, formats) in the process and
  * reused without timing.  Writes the choice (any pointer may be NULL). */
 btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *block_x, int32_t *block_y,
@@ -275,8 +281,8 @@ btrt_status btrt_batch_destroy(btrt_batch B);
  * cannot call cudaMalloc or lend a workspace: a serving process that reserves
  * its whole device-memory budget at start-up and forbids later allocations, or a
  * plug-in inside a host framework that owns the device allocator.  The paper has
- * no counterpart; it is the btrt_mass reduction (same fixed order, same result)
- * applied to any device plane.
+ * no counterpart; it runs btrt_mass's own reduction kernels (same fixed order,
+ * bitwise the same result for the same values) on any device plane.
  *   phi_dev: device array of dtype BTRT_F64 or BTRT_F32, ny rows of `pitch`
  *   elements, the first nx of each row summed; 1 <= nx, ny <= 65536, pitch >= nx;
  *   larger planes are rejected with BTRT_EINVAL.  out_host: host double.

@@ -1,4 +1,4 @@
-"""ctypes declarations of the C ABI in include/btrt.h (argument marshalling only)."""
+"""ctypes declarations of the C ABI in include/*.h (argument marshalling only)."""
 from __future__ import annotations
 
 import ctypes
@@ -13,8 +13,9 @@ F64, F32, F16, BF16, DF64 = 0, 1, 2, 3, 4
 K2_HBB, K2_CONST = 0, 1
 SRC_NONE, SRC_CONST, SRC_TRIG, SRC_FIELD, SRC_REACTION = 0, 1, 2, 3, 4
 FIELD_SOURCE, FIELD_DIFFUSION = 1, 2
-SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA, SWEEP_TB2 = 0, 1, 2, 3
+SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA, SWEEP_TB2, SWEEP_VEC = 0, 1, 2, 3, 4
 SHIFT_REF, SHIFT_LOCAL = 0, 1
+PROBE_FMA, PROBE_ADD, PROBE_MUL = 0, 1, 2
 SHIFTS = {"ref": SHIFT_REF, "local": SHIFT_LOCAL}
 
 FORMATS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "df64": DF64}
@@ -110,6 +111,7 @@ SIGNATURES = [
     ("btrt_batch_set_wait_limit", ctypes.c_int, [_vp, ctypes.c_uint64, _i32]),
     ("btrt_batch_destroy", ctypes.c_int, [_vp]),
     ("btrt_phi_sum_static", ctypes.c_int, [_vp, _i32, _i32, _i32, _i64, _vp, _dp]),
+    ("btrt_probe_fp64_rate", ctypes.c_int, [_vp, _i32, _i32, _i64, _vp, _dp, _dp]),
     ("btrt3_workspace_bytes", _sz, [ctypes.POINTER(GridDesc3)]),
     ("btrt3_create", ctypes.c_int, [ctypes.POINTER(GridDesc3), _vp, _sz, _vp, ctypes.POINTER(_vp)]),
     ("btrt3_set_coeffs", ctypes.c_int, [_vp, ctypes.POINTER(Coeffs3)]),

@@ -18,8 +18,6 @@ using namespace btrt;
 namespace {
 
 constexpr size_t kAlign3 = 256;
-constexpr int kRed3Blocks = 1024;
-constexpr int kRed3Threads = 256;
 
 size_t up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -89,7 +87,7 @@ Layout3 layout3(const btrt3_grid_desc *g) {
         off += up((size_t)L.plane * sr, kAlign3);
     }
     L.off_red = off;
-    off += up((kRed3Blocks + 2) * sizeof(double) + 16, kAlign3);
+    off += up((kRedBlocks + 2) * sizeof(double) + 16, kAlign3);
     if (g->fields & BTRT_FIELD_SOURCE) {
         L.off_srcf = off;
         off += up((size_t)L.plane * sr, kAlign3);
@@ -115,36 +113,6 @@ __global__ void planes_to_dense3(const Real *__restrict__ src, Out *__restrict__
         if (x < nx) dst[r * nx + x] = (Out)(double)src[r * pitch + x];
 }
 
-// FP64 sum of a pitched 3-D field in a fixed order (rows y + ny z dealt to blocks).
-template <typename Real>
-__global__ void __launch_bounds__(kRed3Threads)
-sum_rows3(const Real *__restrict__ a, int nx, long long rows, long long pitch, double *partials) {
-    __shared__ double sh[kRed3Threads];
-    double acc = 0.0;
-    for (long long r = blockIdx.x; r < rows; r += gridDim.x)
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) acc += (double)a[r * pitch + x];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = kRed3Threads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
-}
-
-__global__ void __launch_bounds__(kRed3Threads) sum_partials3(const double *partials, int n, double *out) {
-    __shared__ double sh[kRed3Threads];
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = kRed3Threads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = sh[0];
-}
-
 }  // namespace
 
 struct btrt3_lattice_s {
@@ -165,8 +133,8 @@ struct btrt3_lattice_s {
     void *fbuf(int k) { return ws + lay.off_f[k]; }
     template <typename Real> Real *phi(int k) { return reinterpret_cast<Real *>(ws + lay.off_phi[k]); }
     double *partials() { return reinterpret_cast<double *>(ws + lay.off_red); }
-    double *red_out() { return partials() + kRed3Blocks; }
-    int *flags() { return reinterpret_cast<int *>(partials() + kRed3Blocks + 2); }
+    double *red_out() { return partials() + kRedBlocks; }
+    int *flags() { return reinterpret_cast<int *>(partials() + kRedBlocks + 2); }
     template <typename Real> Real *srcf() {
         return lay.off_srcf ? reinterpret_cast<Real *>(ws + lay.off_srcf) : nullptr;
     }
@@ -346,11 +314,8 @@ btrt_status read3(btrt3_lattice L, void *dst, int dtype, int on_device) {
 
 template <typename Real>
 btrt_status mass3(btrt3_lattice L, double *out) {
-    sum_rows3<Real><<<kRed3Blocks, kRed3Threads, 0, L->stream>>>(L->phi<Real>(L->cur), L->g.nx, L->rows(),
-                                                                   L->lay.pitch, L->partials());
-    CUDA3_TRY(cudaGetLastError());
-    sum_partials3<<<1, kRed3Threads, 0, L->stream>>>(L->partials(), kRed3Blocks, L->red_out());
-    CUDA3_TRY(cudaGetLastError());
+    CUDA3_TRY(enqueue_rows_sum<Real>(L->phi<Real>(L->cur), L->g.nx, L->rows(), L->lay.pitch, L->partials(),
+                                     L->red_out(), L->stream));
     CUDA3_TRY(cudaMemcpyAsync(out, L->red_out(), sizeof(double), cudaMemcpyDeviceToHost, L->stream));
     CUDA3_TRY(cudaStreamSynchronize(L->stream));
     return BTRT_OK;

@@ -174,38 +174,6 @@ __global__ void plane_to_dense(const Real *__restrict__ src, Out *__restrict__ d
     if (x < nx && y < ny) dst[(long long)y * nx + x] = (Out) static_cast<double>(src[(long long)y * pitch + x]);
 }
 
-// FP64 sum of a plane: every block owns the rows y = b, b + gridDim.x, ...;
-// threads stride over x; fixed tree inside the block.  Deterministic for a
-// fixed grid size.
-template <typename Real>
-__global__ void __launch_bounds__(kRedThreads)
-plane_sum_partials(const Real *__restrict__ a, int nx, int ny, long long pitch, double *partials) {
-    __shared__ double sh[kRedThreads];
-    double acc = 0.0;
-    for (int y = blockIdx.x; y < ny; y += gridDim.x)
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) acc += static_cast<double>(a[(long long)y * pitch + x]);
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
-}
-
-__global__ void __launch_bounds__(kRedThreads) sum_partials(const double *partials, int n, double *out) {
-    __shared__ double sh[kRedThreads];
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = kRedThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = sh[0];
-}
-
 }  // namespace
 
 void btrt::set_last_error(const char *fmt, ...) {
@@ -398,6 +366,8 @@ btrt_status launch(btrt_lattice L, int64_t n, bool first, bool resid = false) {
         if (!first && !resid && L->have_tma && L->sweep_variant == BTRT_SWEEP_TMA)
             CUDA_TRY(launch_sweep_tma(p, L->g.storage, sh, sweep_mode(L), &L->tma_in[L->cur],
                                       &L->tma_out[1 - L->cur], L->stream));
+        else if (!first && !resid && L->sweep_variant == BTRT_SWEEP_VEC)
+            CUDA_TRY(launch_sweep_vec(p, L->g.storage, sh, sweep_mode(L), L->stream));
         else
             CUDA_TRY(launch_sweep_f32(p, L->g.storage, sh, sweep_mode(L), L->stream));
     }
@@ -512,11 +482,8 @@ btrt_status copy_phi_out(btrt_lattice L, void *dst, int dtype, int on_device) {
 template <typename Real>
 btrt_status reduce_phi(btrt_lattice L, double *out) {
     const btrt_grid_desc &g = L->g;
-    plane_sum_partials<Real><<<kRedBlocks, kRedThreads, 0, L->stream>>>(L->phi<Real>(), g.nx, g.ny,
-                                                                          L->lay.pitch, L->partials());
-    CUDA_TRY(cudaGetLastError());
-    sum_partials<<<1, kRedThreads, 0, L->stream>>>(L->partials(), kRedBlocks, L->red_out());
-    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(enqueue_rows_sum<Real>(L->phi<Real>(), g.nx, g.ny, L->lay.pitch, L->partials(), L->red_out(),
+                                    L->stream));
     CUDA_TRY(cudaMemcpyAsync(out, L->red_out(), sizeof(double), cudaMemcpyDeviceToHost, L->stream));
     CUDA_TRY(cudaStreamSynchronize(L->stream));
     return BTRT_OK;
@@ -758,11 +725,8 @@ btrt_status btrt_step_residual(btrt_lattice L, int64_t nsteps, double *residual)
     L->step += 1;
     // fixed-order FP64 reduction of the per-block partials, then sqrt on the host
     const long long nb = L->lay.resid_blocks;
-    plane_sum_partials<double><<<kRedBlocks, kRedThreads, 0, L->stream>>>(
-        L->resid_partials(), (int)std::min<long long>(nb, 1 << 30), 1, nb, L->partials());
-    CUDA_TRY(cudaGetLastError());
-    sum_partials<<<1, kRedThreads, 0, L->stream>>>(L->partials(), kRedBlocks, L->red_out());
-    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(enqueue_rows_sum<double>(L->resid_partials(), (int)std::min<long long>(nb, 1 << 30), 1, nb,
+                                      L->partials(), L->red_out(), L->stream));
     double s2 = 0.0;
     CUDA_TRY(cudaMemcpyAsync(&s2, L->red_out(), sizeof(double), cudaMemcpyDeviceToHost, L->stream));
     CUDA_TRY(cudaStreamSynchronize(L->stream));
@@ -845,10 +809,12 @@ btrt_status btrt_check(btrt_lattice L, int32_t *flags) {
 btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant) {
     if (!L) return fail(BTRT_EINVAL, "null lattice");
     if (variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN && variant != BTRT_SWEEP_TMA &&
-        variant != BTRT_SWEEP_TB2)
+        variant != BTRT_SWEEP_TB2 && variant != BTRT_SWEEP_VEC)
         return fail(BTRT_EINVAL, "unknown sweep variant %d", variant);
     if (variant == BTRT_SWEEP_TB2 && L->g.compute != BTRT_F32)
         return fail(BTRT_EINVAL, "the two-step sweep serves FP32-compute lattices");
+    if (variant == BTRT_SWEEP_VEC && L->g.compute != BTRT_F32)
+        return fail(BTRT_EINVAL, "the vector-access sweep serves FP32-compute lattices");
     if (variant == BTRT_SWEEP_TMA && !L->have_tma)
         return fail(BTRT_EINVAL, "the TMA sweep serves FP32-compute lattices whose tensor maps could be encoded");
     L->sweep_variant = variant;

@@ -30,6 +30,7 @@
 #include "../../include/btrt.h"
 #include "btrt_internal.h"
 #include "btrt_tb.cuh"
+#include "btrt_vec.cuh"
 
 using namespace btrt;
 
@@ -60,6 +61,8 @@ struct BatchArgs {
     int ntiles;
     const int4 *tiles2;        // the two-step kernel's output tiles {member, x0, y0, 0}
     int ntiles2;
+    const int4 *tilesv;        // the vector form's tiles {member, x0, y0, 0}: (4 bx) x (by rows) nodes
+    int ntilesv;
     int rows;                  // nodes per thread along y
     int nsteps;
     int want_resid;
@@ -104,13 +107,16 @@ __device__ __forceinline__ bool grid_barrier(unsigned int *count, unsigned int t
 // the batch takes the constant-coefficient collision and a source other than
 // the reaction term, so only that collision and those sources are compiled
 // (fewer registers than the form that can take any member).
-template <typename Real, typename S, int SH, bool L2ONLY, bool LIN>
-__device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int k, int flip, bool resid,
-                                           SweepParams<Real> &sp, double *red) {
+// Copy member M's parameters into shared memory and patch the step-dependent
+// ones: buffer parity (flips since the slice began) and the source and wall time
+// factors of step k of the slice from the host-computed step table.  The caller
+// places no barrier before reading sp; this function ends with one.
+template <typename Real>
+__device__ __forceinline__ void stage_member(const BatchArgs<Real> &a, int member, int k, int flip,
+                                             SweepParams<Real> &sp) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     const int nthr = blockDim.x * blockDim.y;
-    const int4 tile = a.tiles[t];
-    const BatchMember<Real> &M = a.members[tile.x];
+    const BatchMember<Real> &M = a.members[member];
     __syncthreads();   // the previous tile is done with sp
     {
         const int *src = reinterpret_cast<const int *>(&M.p);
@@ -129,12 +135,26 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int 
         sp.phi_in = cur ? q1 : q0;
         sp.phi_out = cur ? const_cast<Real *>(q0) : q1;
     } else if (tid == 32) {
-        const Real *v = a.step_vals + ((size_t)tile.x * a.table_steps + k) * 2;
+        const Real *v = a.step_vals + ((size_t)member * a.table_steps + k) * 2;
         sp.src_val = v[0];
         sp.wall_fac = v[1];
         sp.first = 0;
     }
     __syncthreads();
+}
+
+// One tile of one step: stage the member's parameters (stage_member) and sweep
+// the tile's nodes.  LIN: every member of the batch takes the constant-coefficient
+// collision and a source other than the reaction term, so only that collision and
+// those sources are compiled (fewer registers than the form that can take any member).
+template <typename Real, typename S, int SH, bool L2ONLY, bool LIN>
+__device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int k, int flip, bool resid,
+                                           SweepParams<Real> &sp, double *red) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    const int4 tile = a.tiles[t];
+    const BatchMember<Real> &M = a.members[tile.x];
+    stage_member(a, tile.x, k, flip, sp);
     const int x = tile.y + threadIdx.x;
     double r = 0.0;
     if (x < sp.nx) {
@@ -184,6 +204,36 @@ __global__ void __launch_bounds__(256, (LIN && sizeof(Real) == 4) ? BTRT_BATCH_L
     const bool resid = a.want_resid && (k == a.nsteps - 1);
     for (int t = blockIdx.x; t < a.ntiles; t += gridDim.x)
         batch_tile<Real, S, SH, false, LIN>(a, t, k, flip, resid, sp, red);
+}
+
+// Vector form (FP32 compute): one launch per step (all of them in one CUDA
+// graph), one block per tile of (4 bx) x (by rows) nodes; each thread owns four
+// x-consecutive nodes of `rows` rows and sweeps them with the single-lattice
+// vector sweep's code (btrt_vec.cuh), so every node's arithmetic is that of the
+// plain form.  Resident blocks per SM it is compiled for:
+#ifndef BTRT_BATCH_VEC_MINBLOCKS
+#define BTRT_BATCH_VEC_MINBLOCKS 2
+#endif
+template <typename S, int SH, bool LIN>
+__global__ void __launch_bounds__(256, BTRT_BATCH_VEC_MINBLOCKS)
+    batch_vec_kernel(const __grid_constant__ BatchArgs<float> a, int k, int flip) {
+    __shared__ SweepParams<float> sp;
+    const int4 tile = a.tilesv[blockIdx.x];
+    const int mode = a.members[tile.x].mode;
+    stage_member(a, tile.x, k, flip, sp);
+    const int x0 = tile.y + threadIdx.x * kVec;
+    bool bad = false;
+    if (x0 < sp.nx) {
+        for (int r = 0; r < a.rows; ++r) {
+            const int y = tile.z + threadIdx.y + r * blockDim.y;
+            if (y >= sp.ny) break;
+            if (LIN || mode != kGeneral)
+                bad |= vec_group<S, SH, kLinear, LIN ? kSrcRuntimeNR : kSrcRuntime>(sp, x0, y);
+            else
+                bad |= vec_group<S, SH, kGeneral, kSrcRuntime>(sp, x0, y);
+        }
+    }
+    if (bad) atomicOr(sp.flags, 1);
 }
 
 // Two-step form (FP32 compute): steps k and k + 1 of the slice in one launch, one
@@ -296,9 +346,12 @@ size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 struct Shape {
     int bx, by, rows;
     int per_step;   // 0: persistent launch per call; 1: one launch per step; 2: two steps per launch
-                    // (FP32 compute; its odd or residual last step in the form of 1)
+                    // (FP32 compute; its odd or residual last step in the form of 1); 3: one launch
+                    // per step in the vector form (FP32 compute; its residual step in the form of 1)
 };
-const Shape kShapes[] = {{32, 8, 1, 0}, {32, 8, 2, 0}, {32, 8, 4, 0}, {64, 4, 1, 0}, {64, 4, 2, 0}, {32, 4, 2, 0}};
+const Shape kShapes[] = {{32, 8, 1, 0}, {32, 8, 2, 0}, {32, 8, 4, 0}, {64, 4, 1, 0},
+                         {64, 4, 2, 0}, {32, 4, 2, 0}, {16, 16, 1, 0}, {8, 32, 1, 0}};
+constexpr int kForms = 4;   // launch forms 0 .. 3 (FP64 batches: 0 and 1)
 
 long long tiles_for(const std::vector<btrt_lattice> &m, int bx, int by, int rows) {
     long long t = 0;
@@ -317,8 +370,8 @@ size_t member_bytes(int compute) {
 }
 
 struct BatchLayout {
-    size_t off_members, off_tiles, off_tiles2, off_partials, off_resid, off_tbeg, off_tcnt, off_vals, off_mflags,
-        off_sync, total;
+    size_t off_members, off_tiles, off_tiles2, off_tilesv, off_partials, off_resid, off_tbeg, off_tcnt, off_vals,
+        off_mflags, off_sync, total;
 };
 
 BatchLayout batch_layout(const std::vector<btrt_lattice> &m) {
@@ -332,6 +385,8 @@ BatchLayout batch_layout(const std::vector<btrt_lattice> &m) {
     off += up256(T * sizeof(int4));
     b.off_tiles2 = off;
     off += up256((size_t)tiles_for(m, TbGeom::TX, TbGeom::TY, 1) * sizeof(int4));
+    b.off_tilesv = off;   // vector-form tiles are four times wider: never more than T
+    off += up256(T * sizeof(int4));
     b.off_partials = off;
     off += up256(T * sizeof(double));
     b.off_resid = off;
@@ -382,6 +437,7 @@ struct btrt_batch_s {
     Shape shape{32, 8, 1, 0};
     int ntiles = 0;
     int ntiles2 = 0;           // output tiles of the two-step form
+    int ntilesv = 0;           // tiles of the vector form
     int grid = 0;              // persistent grid (co-resident blocks), form that takes either collision
     int grid_lin = 0;          // the same for the constant-coefficient-only form
     bool all_linear = false;   // every member takes the constant-coefficient collision and no reaction term (set per slice)
@@ -452,6 +508,16 @@ btrt_status build_tiles(btrt_batch B) {
     B->ntiles2 = (int)tiles2.size();
     BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tiles2, tiles2.data(), tiles2.size() * sizeof(int4),
                           cudaMemcpyHostToDevice, B->stream));
+    // tiles of the vector form: (4 bx) x (by rows) nodes
+    std::vector<int4> tilesv;
+    for (size_t m = 0; m < B->members.size(); ++m) {
+        btrt_lattice L = B->members[m];
+        for (int y0 = 0; y0 < L->g.ny; y0 += s.by * s.rows)
+            for (int x0 = 0; x0 < L->g.nx; x0 += kVec * s.bx) tilesv.push_back(make_int4((int)m, x0, y0, 0));
+    }
+    B->ntilesv = (int)tilesv.size();
+    BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tilesv, tilesv.data(), tilesv.size() * sizeof(int4),
+                          cudaMemcpyHostToDevice, B->stream));
     BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tbeg, beg.data(), beg.size() * sizeof(int),
                           cudaMemcpyHostToDevice, B->stream));
     BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tcnt, cnt.data(), cnt.size() * sizeof(int),
@@ -518,6 +584,8 @@ BatchArgs<Real> make_args(btrt_batch B, int nsteps, int want_resid) {
     a.ntiles = B->ntiles;
     a.tiles2 = reinterpret_cast<const int4 *>(B->ws + B->lay.off_tiles2);
     a.ntiles2 = B->ntiles2;
+    a.tilesv = reinterpret_cast<const int4 *>(B->ws + B->lay.off_tilesv);
+    a.ntilesv = B->ntilesv;
     a.rows = B->shape.rows;
     a.nsteps = nsteps;
     a.want_resid = want_resid;
@@ -542,6 +610,9 @@ btrt_status enqueue_form(btrt_batch B, int nsteps, int want_resid) {
                 for (int j = 0; j < pairs_in_slice(B, nsteps, want_resid); ++j, k += 2, ++flip)
                     batch_tb2_kernel<S, SH, LIN><<<(unsigned)B->ntiles2, TbGeom::THREADS, TbGeom::SMEM, B->stream>>>(
                         a, k, flip);
+            if (B->shape.per_step == 3)
+                for (; k < nsteps - (want_resid ? 1 : 0); ++k, ++flip)
+                    batch_vec_kernel<S, SH, LIN><<<(unsigned)B->ntilesv, block, 0, B->stream>>>(a, k, flip);
         }
         for (; k < nsteps; ++k, ++flip)
             batch_step_kernel<Real, S, SH, LIN><<<(unsigned)B->ntiles, block, 0, B->stream>>>(a, k, flip);
@@ -670,10 +741,10 @@ btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y,
     for (const Shape &s : kShapes) known |= (s.bx == block_x && s.by == block_y && s.rows == rows);
     if (!known) return bfail(BTRT_EINVAL, "tile shape %dx%dx%d is not one of the compiled candidates",
                              block_x, block_y, rows);
-    if (per_step_launch < 0 || per_step_launch > 2)
-        return bfail(BTRT_EINVAL, "per_step_launch must be 0, 1 or 2");
-    if (per_step_launch == 2 && B->compute != BTRT_F32)
-        return bfail(BTRT_EINVAL, "the two-step form serves FP32-compute batches");
+    if (per_step_launch < 0 || per_step_launch > 3)
+        return bfail(BTRT_EINVAL, "per_step_launch must be 0, 1, 2 or 3");
+    if (per_step_launch >= 2 && B->compute != BTRT_F32)
+        return bfail(BTRT_EINVAL, "the two-step and vector forms serve FP32-compute batches");
     B->shape = Shape{block_x, block_y, rows, per_step_launch};
     return build_tiles(B);
 }
@@ -782,7 +853,7 @@ btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *
         BCUDA(cudaEventCreate(&e0));
         BCUDA(cudaEventCreate(&e1));
         float best_ms = 1e30f;
-        for (int mode = 0; mode < (B->compute == BTRT_F32 ? 3 : 2); ++mode) {
+        for (int mode = 0; mode < (B->compute == BTRT_F32 ? kForms : 2); ++mode) {
             for (const Shape &s : kShapes) {
                 btrt_status st = btrt_batch_set_tiles(B, s.bx, s.by, s.rows, mode);
                 if (st != BTRT_OK) return st;

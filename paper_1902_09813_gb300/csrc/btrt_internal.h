@@ -8,12 +8,10 @@
 #include <stdint.h>
 
 #include "../../include/btrt.h"
+#include "btrt_reduce.cuh"
 #include "btrt_sweep.cuh"
 
 namespace btrt {
-
-constexpr int kRedBlocks = 1024;     // fixed grid of the FP64 reductions (deterministic order)
-constexpr int kRedThreads = 256;
 
 size_t elem_size(int fmt);
 // A stored FP16 (IEEE binary16, by its definition) or BF16 value as a double.
@@ -129,6 +127,14 @@ cudaError_t launch_sweep_tb2_f16(const SweepParams<float> &pa, const SweepParams
                                  cudaStream_t s);
 cudaError_t launch_sweep_tb2_bf16(const SweepParams<float> &pa, const SweepParams<float> &pb, int shift, int mode,
                                   cudaStream_t s);
+
+// One step per launch with vector memory access (FP32 compute; storage BTRT_F32,
+// F16 or BF16; shift kShiftRef or kShiftLocal); never the initialising collision
+// or a residual step.
+cudaError_t launch_sweep_vec(const SweepParams<float> &p, int storage, int shift, int mode, cudaStream_t s);
+cudaError_t launch_sweep_vec_f32(const SweepParams<float> &p, int shift, int mode, cudaStream_t s);
+cudaError_t launch_sweep_vec_f16(const SweepParams<float> &p, int shift, int mode, cudaStream_t s);
+cudaError_t launch_sweep_vec_bf16(const SweepParams<float> &p, int shift, int mode, cudaStream_t s);
 
 // Blocks of one single-lattice sweep (32 x 8 threads, RowsPerThread nodes each).
 long long sweep_blocks(int nx, int ny, int compute, int storage);

@@ -65,6 +65,15 @@ cudaError_t launch_sweep_f32(const SweepParams<float> &p, int storage, int shift
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_sweep_vec(const SweepParams<float> &p, int storage, int shift, int mode, cudaStream_t s) {
+    switch (storage) {
+    case BTRT_F32: return launch_sweep_vec_f32(p, shift, mode, s);
+    case BTRT_F16: return launch_sweep_vec_f16(p, shift, mode, s);
+    case BTRT_BF16: return launch_sweep_vec_bf16(p, shift, mode, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_sweep_tma(const SweepParams<float> &p, int storage, int shift, int mode,
                              const CUtensorMap *in_map, const CUtensorMap *out_map, cudaStream_t s) {
     switch (storage) {

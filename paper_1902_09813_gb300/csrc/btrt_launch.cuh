@@ -4,10 +4,12 @@
 #pragma once
 
 #include <algorithm>
+#include <mutex>
 
 #include "btrt_internal.h"
 #include "btrt_tb.cuh"
 #include "btrt_tma.cuh"
+#include "btrt_vec.cuh"
 
 namespace btrt {
 
@@ -44,21 +46,32 @@ template <typename S, int SH, int MODE, int SRC>
 cudaError_t launch_tma_src(const SweepParams<float> &p, const CUtensorMap *in_map, const CUtensorMap *out_map,
                            cudaStream_t s) {
     using G = TmaGeom<S>;
-    static bool configured = false;   // one attribute call per instantiation
-    static int per_sm = 0, sms = 0;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(sweep_tma_kernel<S, SH, MODE, SRC>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, G::SMEM);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        e = cudaGetDevice(&dev);
-        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_tma_kernel<S, SH, MODE, SRC>,
-                                                              G::THREADS, G::SMEM);
-        if (e != cudaSuccess) return e;
-        if (per_sm < 1) return cudaErrorInvalidConfiguration;
-        configured = true;
+    // The shared-memory attribute belongs to the current device's context, so it
+    // is set, and the grid measured, once per instantiation and device, under a lock.
+    constexpr int kMaxDev = 64;
+    static std::mutex mu;
+    static int per_sm_of[kMaxDev] = {}, sms_of[kMaxDev] = {};   // 0: not configured yet
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    int per_sm = 0, sms = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        if (!per_sm_of[dev]) {
+            e = cudaFuncSetAttribute(sweep_tma_kernel<S, SH, MODE, SRC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     G::SMEM);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess)
+                e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_tma_kernel<S, SH, MODE, SRC>,
+                                                                  G::THREADS, G::SMEM);
+            if (e != cudaSuccess) return e;
+            if (per_sm < 1) return cudaErrorInvalidConfiguration;
+            sms_of[dev] = sms;
+            per_sm_of[dev] = per_sm;
+        }
+        per_sm = per_sm_of[dev];
+        sms = sms_of[dev];
     }
     const int ntx = (p.nx + G::TX - 1) / G::TX;
     const int nty = (p.ny + G::TY - 1) / G::TY;
@@ -121,6 +134,32 @@ cudaError_t launch_tb2_storage(const SweepParams<float> &pa, const SweepParams<f
                                 : launch_tb2_mode<S, kShiftLocal, kLinear>(pa, pb, s);
     return mode == kGeneral ? launch_tb2_mode<S, kShiftRef, kGeneral>(pa, pb, s)
                             : launch_tb2_mode<S, kShiftRef, kLinear>(pa, pb, s);
+}
+
+// One step per launch with vector memory access (btrt_vec.cuh).
+template <typename S, int SH, int MODE>
+inline void launch_vec_src(const SweepParams<float> &p, cudaStream_t s) {
+    const dim3 g = sweep_vec_grid(p.nx, p.ny), b = sweep_block();
+    switch (p.src_kind) {
+    case kSrcNone: sweep_vec_kernel<S, SH, MODE, kSrcNone><<<g, b, 0, s>>>(p); break;
+    case kSrcConst: sweep_vec_kernel<S, SH, MODE, kSrcConst><<<g, b, 0, s>>>(p); break;
+    case kSrcTrig: sweep_vec_kernel<S, SH, MODE, kSrcTrig><<<g, b, 0, s>>>(p); break;
+    case kSrcField: sweep_vec_kernel<S, SH, MODE, kSrcField><<<g, b, 0, s>>>(p); break;
+    default: sweep_vec_kernel<S, SH, MODE, kSrcReaction><<<g, b, 0, s>>>(p); break;
+    }
+}
+
+template <typename S>
+cudaError_t launch_vec_storage(const SweepParams<float> &p, int shift, int mode, cudaStream_t s) {
+    const bool lin = mode != kGeneral;
+    if (shift == kShiftLocal) {
+        if (lin) launch_vec_src<S, kShiftLocal, kLinear>(p, s);
+        else launch_vec_src<S, kShiftLocal, kGeneral>(p, s);
+    } else {
+        if (lin) launch_vec_src<S, kShiftRef, kLinear>(p, s);
+        else launch_vec_src<S, kShiftRef, kGeneral>(p, s);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace btrt

@@ -14,45 +14,15 @@
 
 namespace {
 
-constexpr int kSumBlocks = 1024;   // same fixed grid and tree as btrt_mass
-constexpr int kSumThreads = 256;
 constexpr int kMaxDevices = 64;
 
-// 1024 partial sums + the result: 8200 bytes, held by every GPU that loads the
-// library until the process exits.  Shared by all calls on a device.
-__device__ __align__(256) double g_sum_scratch[kSumBlocks + 1];
+// 1024 partial sums (the fixed grid of the library's FP64 sum) + the result:
+// 8200 bytes, held by every GPU that loads the library until the process exits.
+// Shared by all calls on a device.
+__device__ __align__(256) double g_sum_scratch[btrt::kRedBlocks + 1];
 
 std::mutex g_setup_mu;
 double *g_scratch_addr[kMaxDevices] = {};
-
-template <typename Real>
-__global__ void __launch_bounds__(kSumThreads)
-static_sum_partials(const Real *__restrict__ a, int nx, int ny, long long pitch, double *partials) {
-    __shared__ double sh[kSumThreads];
-    double acc = 0.0;
-    for (int y = blockIdx.x; y < ny; y += gridDim.x)
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) acc += (double)a[(long long)y * pitch + x];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = kSumThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
-}
-
-__global__ void __launch_bounds__(kSumThreads) static_sum_final(const double *partials, int n, double *out) {
-    __shared__ double sh[kSumThreads];
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < n; k += blockDim.x) acc += partials[k];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int s = kSumThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *out = sh[0];
-}
 
 // Device address of the scratch array for the current device, looked up once per
 // device.  In host code the array's name is only a host-side stand-in.
@@ -107,16 +77,14 @@ extern "C" btrt_status btrt_phi_sum_static(const void *phi_dev, int32_t dtype, i
     btrt_status st = scratch_for_current_device(&scratch);
     if (st != BTRT_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    // every partial slot is overwritten by its block, so nothing needs clearing
-    if (dtype == BTRT_F64)
-        static_sum_partials<double><<<kSumBlocks, kSumThreads, 0, s>>>(static_cast<const double *>(phi_dev),
-                                                                      nx, ny, pitch, scratch);
-    else
-        static_sum_partials<float><<<kSumBlocks, kSumThreads, 0, s>>>(static_cast<const float *>(phi_dev),
-                                                                     nx, ny, pitch, scratch);
-    static_sum_final<<<1, kSumThreads, 0, s>>>(scratch, kSumBlocks, scratch + kSumBlocks);
-    cudaError_t e = cudaGetLastError();
-    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, scratch + kSumBlocks, sizeof(double),
+    // every partial slot is overwritten by its block, so nothing needs clearing; the
+    // kernels are btrt_mass's own (btrt_reduce.cuh), so the sums agree bitwise
+    cudaError_t e = dtype == BTRT_F64
+                        ? btrt::enqueue_rows_sum<double>(static_cast<const double *>(phi_dev), nx, ny, pitch,
+                                                         scratch, scratch + btrt::kRedBlocks, s)
+                        : btrt::enqueue_rows_sum<float>(static_cast<const float *>(phi_dev), nx, ny, pitch,
+                                                        scratch, scratch + btrt::kRedBlocks, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, scratch + btrt::kRedBlocks, sizeof(double),
                                               cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {

@@ -236,6 +236,20 @@ static __device__ __noinline__ K1f k1_fp64(double phi, double a2, double bxx, do
     return K1f{(float)(dyy * id), (float)(-dxy * id), (float)(dxx * id)};
 }
 
+// FP64 operations (add, multiply or FMA: one each) per node of the FP64 sweep in
+// its k0 = 1 constant-coefficient form with the trig source
+// (sweep_kernel<double, double, kShiftNone, kLinearK0One, kSrcTrig>), counted
+// from collide_fold and source_at below: the moments 18 adds (a13, a24, s57,
+// s68, sd, a1324, phid, b13, b24, d57, d68, jx: 2, jy: 2, pxy, del), V 2 adds
+// (Vp, Vm); qx, qy 2 FMAs + 2 multiplies, Vx, Vy 4 FMAs, sig 2 FMAs, r0 1 FMA +
+// 1 multiply, ks 1 multiply, T1, T5 2 FMAs, A1, A2, P, M 4 FMAs, r1..r8 8 FMAs,
+// the trig source 1 FMA + 1 multiply and a = ... + src 1 FMA: 20 adds, 25 FMAs,
+// 5 multiplies.  ncu counts 50.6 per node (DADD 20.5, DFMA 25.0, DMUL 5.0).
+constexpr int kFp64AddsPerNodeLinearTrig = 20;
+constexpr int kFp64FmasPerNodeLinearTrig = 25;
+constexpr int kFp64MulsPerNodeLinearTrig = 5;
+constexpr int kFp64OpsPerNodeLinearTrig = 50;
+
 // Moment-space form of Eq. 6 (Eqs. 94, 95, 99 with K2 = k2 Ihat), expanded back
 // into populations and written for shifted values d_i = f_i - w_i rs: rs = 0
 // (kShiftNone), rs = phi_ref (kShiftRef) or rs = phi^{n-1} of this node

@@ -1,0 +1,194 @@
+// btrt_vec.cuh -- one step per launch of the FP32-compute sweep with vector
+// memory access (the BTRT_SWEEP_VEC form).
+//
+// Each thread owns kVec = 4 x-consecutive nodes x0 .. x0 + 3 of one row.  The pull
+// of Eq. 38 reads, for population i, the values at x - e_ix of row y - e_iy: one
+// aligned vector load of the four stored values at x0 .. x0 + 3 of that row
+// (64 bits for FP16/BF16 storage, 128 bits for FP32) gives them all for e_ix = 0
+// and three of four otherwise; the fourth (x0 - 1 for e_ix = +1, x0 + 4 for
+// e_ix = -1) is one scalar load, which L1 serves since the neighbouring thread
+// loads it in its own vector.  With the local shift the eight neighbours' phi
+// arrive the same way: per row y - 1, y, y + 1 one 128-bit load and two scalar
+// ones.  The results leave in nine vector stores and one 128-bit phi store.  So a
+// node costs about a quarter of the plain sweep's memory instructions and address
+// arithmetic, while every node's arithmetic, and its order, is that of pull_node,
+// collide_fold and store_value: the results equal the plain sweep's bitwise.
+//
+// Groups that touch the domain edge (x0 = 0, x0 + 4 > nx - 1, y = 0 or
+// y = ny - 1: periodic wrap or bounce-back links) take the plain per-node path.
+// Alignment: rows are padded to 64 elements and planes are whole rows, so
+// x0 * sizeof(S) is a multiple of the vector size in every plane.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "btrt_sweep.cuh"
+
+namespace btrt {
+
+constexpr int kVec = 4;
+
+// Four stored values in one machine word, and their conversion to and from FP32
+// (exact widening; RN narrowing, as Storage<S>::pack).
+template <typename S> struct Vec4;
+template <> struct Vec4<__half> {
+    using W = uint2;
+    static __device__ __forceinline__ float get(const W &w, int k) {
+        const unsigned int u = k < 2 ? w.x : w.y;
+        return __half2float(__ushort_as_half((unsigned short)((k & 1) ? (u >> 16) : (u & 0xffffu))));
+    }
+    static __device__ __forceinline__ W put(float a, float b, float c, float d) {
+        const __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+        W w;
+        w.x = *reinterpret_cast<const unsigned int *>(&lo);
+        w.y = *reinterpret_cast<const unsigned int *>(&hi);
+        return w;
+    }
+};
+template <> struct Vec4<__nv_bfloat16> {
+    using W = uint2;
+    static __device__ __forceinline__ float get(const W &w, int k) {
+        const unsigned int u = k < 2 ? w.x : w.y;
+        return __uint_as_float((k & 1) ? (u & 0xffff0000u) : (u << 16));
+    }
+    static __device__ __forceinline__ W put(float a, float b, float c, float d) {
+        const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+        W w;
+        w.x = *reinterpret_cast<const unsigned int *>(&lo);
+        w.y = *reinterpret_cast<const unsigned int *>(&hi);
+        return w;
+    }
+};
+template <> struct Vec4<float> {
+    using W = float4;
+    static __device__ __forceinline__ float get(const W &w, int k) {
+        return k == 0 ? w.x : (k == 1 ? w.y : (k == 2 ? w.z : w.w));
+    }
+    static __device__ __forceinline__ W put(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+};
+
+// Value k (-1 .. 4) of a row segment: k in [0, 4) from the vector, else the edge value.
+template <typename S>
+__device__ __forceinline__ float seg_value(const typename Vec4<S>::W &w, float edge, int k) {
+    return (k < 0 || k >= kVec) ? edge : Vec4<S>::get(w, k);
+}
+
+// Resident blocks per SM the vector sweep is compiled for (0: the compiler's choice).
+#ifndef BTRT_VEC_MINBLOCKS
+#define BTRT_VEC_MINBLOCKS 2
+#endif
+
+// One step of the four nodes x0 .. x0 + 3 (those below nx) of row y.  Returns true
+// when a non-finite phi appeared.  L2ONLY: loads of data other SMs rewrite during
+// a persistent launch go through L2 only (as in pull_node).
+template <typename S, int SH, int MODE, int SRC, bool L2ONLY = false>
+__device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, int y) {
+    using V = Vec4<S>;
+    using W = typename V::W;
+    constexpr bool TRIG = SRC == kSrcTrig || SRC == kSrcRuntime || SRC == kSrcRuntimeNR;
+    bool bad = false;
+    const bool interior = x0 >= 1 && x0 + kVec <= p.nx - 1 && y >= 1 && y <= p.ny - 2;
+    if (!interior) {
+        // the plain sweep's per-node path (periodic wrap, bounce-back links)
+#pragma unroll 1
+        for (int v = 0; v < kVec && x0 + v < p.nx; ++v) {
+            const int x = x0 + v;
+            float xs = 0.f, xc = 0.f;
+            if (SRC == kSrcTrig || (TRIG && SRC != kSrcTrig && p.src_kind == kSrcTrig)) {
+                xs = p.Xs[BTRT_IX(p.flags, x, p.nx)];
+                xc = p.Xc[BTRT_IX(p.flags, x, p.nx)];
+            }
+            float f[9], phi_prev;
+            pull_node<float, S, SH, L2ONLY>(p, x, y, x > 0 && x < p.nx - 1, f, phi_prev);
+            finish_node<float, S, SH, MODE, SRC, false>(p, x, y, xs, xc, f, phi_prev, bad);
+        }
+        return bad;
+    }
+    const S *__restrict__ fin = static_cast<const S *>(p.fin);
+    S *__restrict__ fout = static_cast<S *>(p.fout);
+    const int node = y * p.pitch + x0;
+
+    // populations: per plane the vector of the source row and, for e_x != 0, the edge value
+    W raw[9];
+    float edge[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const int at = i * p.plane + node - ey_of(i) * p.pitch;
+        raw[i] = ldg<L2ONLY>(reinterpret_cast<const W *>(fin + BTRT_IX(p.flags, at, 9 * p.plane)));
+        edge[i] = 0.f;
+        if (ex_of(i) == 1) edge[i] = Storage<S>::load(ldg<L2ONLY>(fin + BTRT_IX(p.flags, at - 1, 9 * p.plane)));
+        if (ex_of(i) == -1) edge[i] = Storage<S>::load(ldg<L2ONLY>(fin + BTRT_IX(p.flags, at + kVec, 9 * p.plane)));
+    }
+    // phi^{n-1}: own row always; rows y - 1, y + 1 and the row edges for the local shift
+    float ph[3][kVec + 2];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        if (SH != kShiftLocal && r != 1) continue;
+        const int at = node + (r - 1) * p.pitch;
+        const float4 m = ldg<L2ONLY>(reinterpret_cast<const float4 *>(p.phi_in + BTRT_IX(p.flags, at, p.plane)));
+        ph[r][1] = m.x;
+        ph[r][2] = m.y;
+        ph[r][3] = m.z;
+        ph[r][4] = m.w;
+        if constexpr (SH == kShiftLocal) {
+            ph[r][0] = ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, at - 1, p.plane));
+            ph[r][kVec + 1] = ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, at + kVec, p.plane));
+        }
+    }
+
+    float outv[9][kVec];
+    float phi_o[kVec];
+#pragma unroll
+    for (int v = 0; v < kVec; ++v) {
+        const int x = x0 + v;
+        const float phi_prev = ph[1][v + 1];
+        float f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = seg_value<S>(raw[i], edge[i], v - ex_of(i));
+        if constexpr (SH == kShiftLocal) {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) f[i] = fma(wgt<float>(i), ph[1 - ey_of(i)][v - ex_of(i) + 1] - phi_prev, f[i]);
+        }
+        float xs = 0.f, xc = 0.f;
+        if (SRC == kSrcTrig || (TRIG && SRC != kSrcTrig && p.src_kind == kSrcTrig)) {
+            xs = p.Xs[BTRT_IX(p.flags, x, p.nx)];
+            xc = p.Xc[BTRT_IX(p.flags, x, p.nx)];
+        }
+        const float src = source_at<float, SRC>(p, xs, xc, y, node + v);
+        const float rs = SH == kShiftLocal ? phi_prev : p.phi_ref;
+        float phid;
+        const float phi = collide_fold<float, MODE, SRC, SH>(p, f, rs, phi_prev, src, false, node + v, phid);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            outv[i][v] = SH == kShiftLocal ? fma(-wgt<float>(i), phid, f[i]) : f[i];
+        phi_o[v] = phi;
+        bad |= not_finite(phi);
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i)
+        *reinterpret_cast<W *>(fout + BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)) =
+            V::put(outv[i][0], outv[i][1], outv[i][2], outv[i][3]);
+    *reinterpret_cast<float4 *>(p.phi_out + BTRT_IX(p.flags, node, p.plane)) =
+        make_float4(phi_o[0], phi_o[1], phi_o[2], phi_o[3]);
+    return bad;
+}
+
+// One step of one lattice, 32 x 8 threads per block: thread (tx, ty) owns nodes
+// x0 = 4 (32 bx + tx) .. x0 + 3 of row y = 8 by + ty.  Never the initialising
+// collision and never a residual step (the host runs those in the plain form).
+template <typename S, int SH, int MODE, int SRC>
+__global__ void __launch_bounds__(256, BTRT_VEC_MINBLOCKS) sweep_vec_kernel(const __grid_constant__ SweepParams<float> p) {
+    const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * kVec;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x0 >= p.nx || y >= p.ny) return;
+    if (vec_group<S, SH, MODE, SRC>(p, x0, y)) atomicOr(p.flags, 1);
+}
+
+// 32 x 8 threads, 128 x 8 nodes per block.
+inline dim3 sweep_vec_grid(int nx, int ny) {
+    const int groups = (nx + kVec - 1) / kVec;
+    return dim3((unsigned)((groups + 31) / 32), (unsigned)((ny + 7) / 8), 1);
+}
+
+}  // namespace btrt

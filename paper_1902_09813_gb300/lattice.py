@@ -165,9 +165,11 @@ class Lattice:
         return self
 
     def set_sweep_variant(self, variant: str):
-        """'auto', 'plain', 'tma' or 'tb2' (two steps per launch; FP32 storage,
-        reference shift) for FP32-compute lattices."""
-        code = {"auto": C.SWEEP_AUTO, "plain": C.SWEEP_PLAIN, "tma": C.SWEEP_TMA, "tb2": C.SWEEP_TB2}[variant]
+        """Kernel form of an FP32-compute lattice: 'auto', 'plain', 'tma' (TMA-staged
+        tiles), 'tb2' (two steps per launch) or 'vec' (one step per launch with
+        vector loads and stores of four x-consecutive nodes per thread)."""
+        code = {"auto": C.SWEEP_AUTO, "plain": C.SWEEP_PLAIN, "tma": C.SWEEP_TMA, "tb2": C.SWEEP_TB2,
+                "vec": C.SWEEP_VEC}[variant]
         C.check(self.lib.btrt_set_sweep_variant(self.handle, code))
         return self
 
@@ -320,7 +322,8 @@ class Batch:
 
     def set_tiles(self, block_x: int, block_y: int, rows: int, per_step: int = 0):
         """Tile shape and launch form: per_step 0 = persistent launch per call, 1 = one
-        launch per step, 2 = two steps per launch (FP32 compute)."""
+        launch per step, 2 = two steps per launch (FP32 compute), 3 = one launch per
+        step in the vector form (FP32 compute)."""
         C.check(self.lib.btrt_batch_set_tiles(self.handle, block_x, block_y, rows, per_step))
         return self
 

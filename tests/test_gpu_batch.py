@@ -52,6 +52,8 @@ def test_alone_equals_in_mix_bitwise(compute, storage, shift):
 
 @pytest.mark.parametrize("compute,storage,shift,shape", [("f32", "f16", "local", (32, 8, 4, 1)),
                                                         ("f32", "f16", "local", (32, 8, 4, 2)),
+                                                        ("f32", "f16", "local", (16, 16, 1, 3)),
+                                                        ("f32", "f32", "ref", (32, 8, 2, 3)),
                                                         ("f32", "bf16", "ref", (32, 8, 1, 2)),
                                                         ("f32", "f32", "ref", (32, 8, 2, 0)),
                                                         ("f64", "f64", "ref", (32, 8, 4, 1))])
@@ -85,7 +87,9 @@ def test_constant_coefficient_batch_form_bitwise(compute, storage, shift, shape)
 
 
 @pytest.mark.parametrize("shape", [(32, 8, 1, 0), (32, 8, 4, 0), (64, 4, 2, 0), (32, 4, 2, 0),
-                                   (32, 8, 1, 1), (64, 4, 2, 1), (32, 8, 4, 2), (64, 4, 1, 2)])
+                                   (32, 8, 1, 1), (64, 4, 2, 1), (32, 8, 4, 2), (64, 4, 1, 2),
+                                   (16, 16, 1, 1), (8, 32, 1, 0), (32, 8, 1, 3), (32, 8, 4, 3),
+                                   (64, 4, 2, 3), (16, 16, 1, 3), (8, 32, 1, 3)])
 def test_tile_shapes_bitwise(shape):
     from paper_1902_09813_gb300 import Batch
     probs = _mix("f32", "f16", count=6, seed=5)
@@ -157,16 +161,42 @@ def test_two_step_form_residual_and_odd_steps():
     b.close()
 
 
+def test_vector_form_residual_slice():
+    """The vector batch form with a residual slice (its last step in the
+    step-per-launch form): results bitwise equal to the members alone, residuals
+    equal to the definition."""
+    from paper_1902_09813_gb300 import Batch
+    probs = _mix("f32", "f16", count=5, seed=23)
+    alone = [_make(p, "f32", "f16", "local") for p in probs]
+    mixed = [_make(p, "f32", "f16", "local") for p in probs]
+    b = Batch(mixed).set_tiles(16, 16, 1, 3)
+    b.step(7)
+    b.step(6, residual=True)
+    r = b.residuals()
+    for a in alone:
+        a.step(12)
+    before = [a.phi_host() for a in alone]
+    for a in alone:
+        a.step(1)
+    for k, (a, m) in enumerate(zip(alone, mixed)):
+        assert np.array_equal(a.phi_host(), m.phi_host())
+        assert np.array_equal(a.read_f(), m.read_f())
+        expect = np.linalg.norm(a.phi_host() - before[k])
+        assert r[k] == pytest.approx(expect, rel=1e-5, abs=1e-30)
+    b.close()
+
+
 def test_autotune_keeps_results():
     from paper_1902_09813_gb300 import Batch
     probs = _mix("f32", "f16", count=6, seed=13)
     mixed = [_make(p, "f32", "f16") for p in probs]
     b = Batch(mixed)
     shape = b.autotune(steps_per_trial=2)
-    assert shape[:3] in [(32, 8, 1), (32, 8, 2), (32, 8, 4), (64, 4, 1), (64, 4, 2), (32, 4, 2)]
-    assert shape[3] in (0, 1, 2)
+    assert shape[:3] in [(32, 8, 1), (32, 8, 2), (32, 8, 4), (64, 4, 1), (64, 4, 2), (32, 4, 2), (16, 16, 1),
+                         (8, 32, 1)]
+    assert shape[3] in (0, 1, 2, 3)
     n_done = mixed[0].time()[0]
-    assert n_done == 6 * 3 * 3   # six shapes, three forms (FP32), 1 + 2 steps each
+    assert n_done == 8 * 4 * 3   # eight shapes, four forms (FP32), 1 + 2 steps each
     ref = [_make(p, "f32", "f16").step(n_done + 5) for p in probs]
     b.step(5)
     for a, m in zip(ref, mixed):

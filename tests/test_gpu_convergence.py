@@ -1,0 +1,105 @@
+"""Config-2 convergence sweep on the GPU: the manufactured solution
+phi* = exp(-t) sin(pi x) sin(pi y) with bounce-back walls on the unit square,
+anisotropic A = R(pi/6) diag(0.05, 0.01) R(pi/6)^T, u = (0.05, 0.02), under
+diffusive scaling dt = 4 dx^2 up to T_end = 0.1, at N = 64 ... 512.
+
+Checked here:
+- the FP64 sweep equals the FP64 oracle element-wise (rel L2 <= 1e-11) at every N;
+- the FP64 sweep is second order in dx (the paper's claim for its anisotropic
+  tests, Sec. 4.2.2 and Table 6), observed order within [1.9, 2.1];
+- the reduced-precision bar: a format's GRE against the closed form (Eq. 63)
+  within 1 % of the FP64 sweep's, at every (N, format) this design claims;
+- where a format misses the bar, a regression test pins the measured relative
+  GRE change, so that the miss is reported as it is and any change to it shows.
+
+Under diffusive scaling a step changes phi by O(dx^2) relative, a few FP32 ulps
+at N = 512, so every FP32-compute path drifts from the FP64 result as N grows,
+whatever the storage format; FP64 and double-word compute do not."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+from conftest import cpu_threads
+
+pytestmark = pytest.mark.gpu
+
+SIDES = (64, 128, 256, 512)
+BAR = 0.01
+TOL64 = 1e-11
+
+# (compute, storage, shift) -> the N at which the design claims the 1 % bar
+CLAIMED = {
+    ("df64", "df64", "ref"): (64, 128, 256, 512),
+    ("f32", "f32", "ref"): (64,),
+    ("f32", "f32", "local"): (64, 128),
+    ("f32", "f16", "local"): (64, 128),
+    ("f32", "bf16", "local"): (64,),
+}
+# measured misses: (compute, storage, shift, N) -> (low, high) bounds of the
+# relative GRE change against the FP64 sweep (measured value in the comment)
+MISSES = {
+    ("f32", "f32", "ref", 128): (-0.030, -0.018),     # -0.0241
+    ("f32", "f32", "ref", 512): (9.0, 14.5),          # 11.65
+    ("f32", "f32", "local", 256): (-0.080, -0.045),   # -0.0624
+    ("f32", "f32", "local", 512): (2.0, 3.2),         # 2.562
+    ("f32", "f16", "local", 256): (0.080, 0.130),     # 0.1043
+    ("f32", "f16", "local", 512): (1.8, 2.8),         # 2.260
+    ("f32", "bf16", "local", 128): (0.180, 0.280),    # 0.2273
+    ("f32", "bf16", "local", 256): (4.8, 7.4),        # 6.077
+}
+
+
+def _problem(n):
+    return w.mms_sinsin(n=n)
+
+
+_CACHE = {}
+
+
+def _gre_gpu(n, compute, storage, shift):
+    key = (n, compute, storage, shift)
+    if key not in _CACHE:
+        from paper_1902_09813_gb300 import Lattice
+        p = _problem(n)
+        lat = Lattice.from_problem(p, compute=compute, storage=storage, shift=shift)
+        lat.init(p.phi0(), t0=p.t0).step(p.nsteps)
+        phi = lat.phi_host()
+        assert lat.check() == 0
+        _CACHE[key] = (phi, w.gre(phi, w.mms_sinsin_exact(p, p.t0 + p.nsteps * p.dt)))
+    return _CACHE[key]
+
+
+@pytest.mark.parametrize("n", SIDES)
+def test_fp64_sweep_equals_oracle_across_the_sweep(n):
+    p = _problem(n)
+    phi, _ = _gre_gpu(n, "f64", "f64", "ref")
+    ref = oracle.OracleLattice(p, nthreads=cpu_threads()).init().step(p.nsteps).phi()
+    err = np.linalg.norm(phi - ref) / np.linalg.norm(ref)
+    assert err <= TOL64, (n, err)
+
+
+def test_fp64_sweep_is_second_order():
+    g = [_gre_gpu(n, "f64", "f64", "ref")[1] for n in SIDES]
+    orders = [math.log2(g[i - 1] / g[i]) for i in range(1, len(g))]
+    assert all(1.9 <= o <= 2.1 for o in orders), (g, orders)
+
+
+@pytest.mark.parametrize("fmt,n", [(f, n) for f, ns in CLAIMED.items() for n in ns],
+                         ids=lambda v: "-".join(v) if isinstance(v, tuple) else str(v))
+def test_reduced_format_within_bar(fmt, n):
+    g64 = _gre_gpu(n, "f64", "f64", "ref")[1]
+    g = _gre_gpu(n, *fmt)[1]
+    assert abs(g / g64 - 1.0) <= BAR, (fmt, n, g, g64)
+
+
+@pytest.mark.parametrize("case", list(MISSES), ids=lambda c: "-".join(map(str, c)))
+def test_reduced_format_misses_bar_regression(case):
+    """Not a bar: the measured miss, pinned so that it stays reported as it is."""
+    c, s, sh, n = case
+    lo, hi = MISSES[case]
+    rel = _gre_gpu(n, c, s, sh)[1] / _gre_gpu(n, "f64", "f64", "ref")[1] - 1.0
+    assert abs(rel) > BAR
+    assert lo <= rel <= hi, (case, rel)

@@ -1,7 +1,8 @@
 """Index-checked build (-DBTRT_DEBUG_BOUNDS): every global access of the sweeps
 checks its index and raises flag bit 3 instead of faulting.  Tiny grids in every
-kernel form (plain, TMA-staged, two steps per launch, batched, D3Q19) raise no
-flag, and the checked build computes the same results as the ordinary one."""
+kernel form (plain, vector access, TMA-staged, two steps per launch, batched,
+D3Q19) raise no flag, and the checked build computes the same results as the
+ordinary one."""
 import os
 import subprocess
 import sys

@@ -4,9 +4,10 @@ Two stored forms: deviations from w_i phi_ref (one reference per lattice) and
 deviations from w_i phi(x) of the node that wrote the population (local shift).
 Checked here: FP32 storage with the local shift against the FP64 oracle within
 the FP32 tolerance; the discretisation error against the closed-form solutions
-(Gaussian hill, manufactured solution) within 1 % of the oracle's own for the
-formats that reach it; the local shift never less accurate than the reference
-shift; TMA-staged and plain kernels, and checkpoint/resume, bitwise equal."""
+(Gaussian hill, manufactured solution) within 1 % of the oracle's own, except
+BF16 on the 128^2 manufactured solution, whose measured miss is pinned; the
+local shift never less accurate than the reference shift; TMA-staged and plain
+kernels, and checkpoint/resume, bitwise equal."""
 import numpy as np
 import pytest
 
@@ -55,15 +56,15 @@ CLOSED = {
     "mms64": (lambda: w.mms_sinsin(n=64), lambda p: w.mms_sinsin_exact(p, p.t0 + p.nsteps * p.dt)),
     "mms128": (lambda: w.mms_sinsin(n=128), lambda p: w.mms_sinsin_exact(p, p.t0 + p.nsteps * p.dt)),
 }
-# Relative change of the GRE against the closed form allowed for the local shift.
-# BF16 keeps 8 significant bits: on the 128^2 manufactured solution, whose
-# discretisation error is 7e-5, its rounding noise is a fifth of that error.
-GRE_BOUND = {("mms128", "bf16"): 0.3}
+# The reduced-precision bar: the local shift's GRE against the closed form within
+# 1 % of the oracle's.  BF16 (8 significant bits) misses it on the 128^2
+# manufactured solution (measured +22.7 %); that case is pinned separately below
+# as a regression of the measured miss, not as a bar.
+BAR = 0.01
+MISSED = {("mms128", "bf16")}
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
-@pytest.mark.parametrize("name", list(CLOSED))
-def test_storage_discretisation_error_vs_closed_form(name, storage):
+def _gre_pair(name, storage):
     make, exact = CLOSED[name]
     p = make()
     ex = exact(p)
@@ -76,10 +77,27 @@ def test_storage_discretisation_error_vs_closed_form(name, storage):
         lat.init(p.phi0(), t0=p.t0).step(p.nsteps)
         got = lat.phi_host()
         res[shift] = (w.gre(got, ex), _rel(got, phi_o))
+    return g0, res
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
+@pytest.mark.parametrize("name", list(CLOSED))
+def test_storage_discretisation_error_vs_closed_form(name, storage):
+    g0, res = _gre_pair(name, storage)
     g_loc, e_loc = res["local"]
-    assert abs(g_loc - g0) <= GRE_BOUND.get((name, storage), 0.01) * g0, (g0, res)
+    if (name, storage) not in MISSED:
+        assert abs(g_loc - g0) <= BAR * g0, (g0, res)
     # the local shift is never the less accurate form (up to FP32 arithmetic noise)
     assert e_loc <= res["ref"][1] * 1.05 + 1e-6, res
+
+
+def test_bf16_local_shift_misses_bar_on_mms128_regression():
+    """BF16 storage with the local shift on the 128^2 manufactured solution: the
+    GRE is 22.7 % above the oracle's, outside the 1 % bar.  Pinned as measured."""
+    g0, res = _gre_pair("mms128", "bf16")
+    rel = res["local"][0] / g0 - 1.0
+    assert rel > BAR
+    assert 0.18 <= rel <= 0.28, rel
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])

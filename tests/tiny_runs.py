@@ -1,6 +1,7 @@
 """Tiny-grid runs shared by the index-check test: every kernel form (one step,
-TMA-staged and two steps per launch; the batch forms; D3Q19) on grids of 3 to 7
-nodes per side (every node is a boundary node or next to one).  Run as a
+vector access, TMA-staged and two steps per launch; the batch forms; D3Q19) on
+grids of 3 to 14 nodes per side (every node is a boundary node or next to one,
+or, at 13 and 14 nodes, in the vector form's one interior group per row).  Run as a
 script it writes the results to an .npz file, with whatever libbtrt the
 BTRT_LIBRARY environment variable selects."""
 import sys
@@ -10,10 +11,11 @@ import numpy as np
 import workloads as w
 
 GRIDS_2D = [(4, 4, (0, 0, 0, 0)), (5, 5, (1, 1, 1, 1)), (7, 3, (0, 0, 1, 1)), (3, 3, (1, 1, 0, 0)),
-            (3, 7, (1, 1, 1, 1))]
+            (3, 7, (1, 1, 1, 1)), (13, 5, (0, 0, 0, 0)), (14, 6, (1, 1, 1, 1))]
 FORMS_2D = [("f64", "f64", "ref", "plain"), ("df64", "df64", "ref", "plain"), ("f32", "f32", "ref", "plain"),
             ("f32", "f16", "local", "plain"), ("f32", "bf16", "ref", "tma"), ("f32", "f16", "local", "tma"),
-            ("f32", "f32", "ref", "tb2"), ("f32", "f16", "local", "tb2"), ("f32", "bf16", "ref", "tb2")]
+            ("f32", "f32", "ref", "tb2"), ("f32", "f16", "local", "tb2"), ("f32", "bf16", "ref", "tb2"),
+            ("f32", "f32", "ref", "vec"), ("f32", "f16", "local", "vec"), ("f32", "bf16", "local", "vec")]
 GRIDS_3D = [(3, 3, 3, (0,) * 6), (4, 5, 6, (1,) * 6), (5, 3, 4, (1, 1, 0, 0, 1, 1))]
 FORMS_3D = [("f64", "f64", "ref"), ("f32", "f32", "ref"), ("f32", "f16", "local")]
 
