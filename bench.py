@@ -80,14 +80,19 @@ FP64_NOMINAL_TOPS = 0.625
 # hold for the kernel sources whose digest is FP64_SWEEP_DIGEST; after an edit
 # to them both are re-taken and the digest updated (a CPU test checks it), and
 # until then the traffic is reported as null.
-FP64_SWEEP_SOURCES = ("btrt_sweep.cuh", "btrt_kernels.cu", "btrt_dw.cuh")
-FP64_SWEEP_DIGEST = "a79ce8707e427c39"
+FP64_SWEEP_SOURCES = ("btrt_sweep.cuh", "btrt_dw.cuh")   # the FP64 sweep's device code
+FP64_SWEEP_DIGEST = "6164d767545f1816"
 FP64_TRAFFIC_PER_NODE = 149.3
 # DRAM bytes per node and step of the two-step FP32-compute kernel measured by ncu,
 # keyed by (storage, shift), for the sources with digest TB2_DIGEST.
 TB2_SOURCES = ("btrt_sweep.cuh", "btrt_tb.cuh", "btrt_launch.cuh")
 TB2_DIGEST = "9f8c00e5fe1e01a4"
 TB2_DRAM_BYTES_PER_UPDATE = {("f32", "ref"): 38.6, ("f16", "local"): 20.9}
+# DRAM bytes per node of one launch of the vector-access sweep measured by ncu,
+# keyed by (storage, shift), for the sources with digest VEC_DIGEST.
+VEC_SOURCES = ("btrt_sweep.cuh", "btrt_vec.cuh", "btrt_launch.cuh")
+VEC_DIGEST = "unset"
+VEC_DRAM_BYTES_PER_UPDATE = {}
 
 
 def measure_fp64_peak(iters: int = 2000):
@@ -120,9 +125,21 @@ def measure_fp64_peak(iters: int = 2000):
             "kernel": "fp64_chains (4/8/16 independent chains per thread, whole waves, best per kind)"}
 
 
+def kernel_form(args) -> str:
+    """The kernel form of the timed steps: what the library's AUTO resolves to for
+    FP32 compute (the vector form for FP16/BF16 storage, two steps per launch for
+    FP32 storage), the form asked for, or the plain sweep."""
+    if args.compute != "f32":
+        return "plain"
+    if args.sweep != "auto":
+        return args.sweep
+    return "vec" if args.storage in ("f16", "bf16") else "tb2"
+
+
 def two_step_form(args) -> bool:
-    """FP32-compute lattices run pairs of steps in one launch unless asked otherwise."""
-    return args.compute == "f32" and args.sweep in ("auto", "tb2")
+    """Pairs of steps in one launch (the scalar or the vector two-step kernel)."""
+    return kernel_form(args) in ("tb2", "tb2v")
+
 
 
 def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind, fp64_peak=None):
@@ -144,6 +161,12 @@ def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind, fp64_peak
                     dram_bytes_per_update=per_update,
                     note="two steps per launch; achieved = algorithmic bytes of the steps / time")
     kernel = f"sweep_kernel<{args.compute},{args.storage}>"
+    if kernel_form(args) == "vec":
+        shift = args.shift if args.shift != "auto" else ("local" if args.storage in ("f16", "bf16") else "ref")
+        fresh = source_digest(VEC_SOURCES) == VEC_DIGEST
+        per_update = VEC_DRAM_BYTES_PER_UPDATE.get((args.storage, shift)) if fresh else None
+        return dict(hbm, traffic=None if per_update is None else round(per_update * nodes),
+                    dram_bytes_per_update=per_update, kernel=f"sweep_vec_kernel<f32,{args.storage}>")
     if args.compute != "f64" or args.workload != "mms":
         return dict(hbm, traffic=None, kernel=kernel)
     # the FP64 sweep is bound by GB300's FP64 pipe, not by HBM
@@ -397,8 +420,9 @@ def _time_single(p, phi0, compute, storage, steps, warmup, variant="plain", shif
 def run_variants(args, steps=200, warmup=5):
     """The other compute/storage paths at 8192^2: double-word (FP32-pair) arithmetic
     on the manufactured-solution workload, FP32 compute with FP32/FP16/BF16 shifted
-    storage (both shifts: one and two steps per launch; reference shift: TMA-staged
-    too) on the manufactured-solution and nonlinear workloads."""
+    storage (both shifts: one step per launch plain and with vector access, two
+    steps per launch; reference shift: TMA-staged too) on the manufactured-solution
+    and nonlinear workloads."""
     import workloads as w
     out = {}
     p = w.mms_sinsin(n=args.n, nsteps=steps)
@@ -410,10 +434,14 @@ def run_variants(args, steps=200, warmup=5):
     for name, prob, a in (("mms", p, phi0), ("nonlinear", q, q_phi0)):
         for st in ("f32", "f16", "bf16"):
             for sh, tag in (("ref", ""), ("local", "_local")):
-                # one step per launch, and two (the default form of FP32 compute)
+                # one step per launch (plain and vector access), and two
                 out[f"{name}_f32_{st}{tag}"] = _time_single(prob, a, "f32", st, steps, warmup, shift=sh)
+                out[f"{name}_f32_{st}{tag}_vec"] = _time_single(prob, a, "f32", st, steps, warmup, variant="vec",
+                                                               shift=sh)
                 out[f"{name}_f32_{st}{tag}_tb2"] = _time_single(prob, a, "f32", st, steps, warmup, variant="tb2",
                                                                shift=sh)
+                out[f"{name}_f32_{st}{tag}_tb2v"] = _time_single(prob, a, "f32", st, steps, warmup,
+                                                                variant="tb2v", shift=sh)
             out[f"{name}_f32_{st}_tma"] = _time_single(prob, a, "f32", st, steps, warmup, variant="tma")
     out["nonlinear_f64"] = _time_single(q, q_phi0, "f64", "f64", 50, 3)
     out.update(run_d3q19(args))
@@ -669,7 +697,11 @@ def run_batched(args, count=512, nsteps=2000, seed=0, plain=True):
 def run_serving(args, rates=(100.0, 500.0, 2000.0), count=96, seed=1):
     """Config-5 style serving: Poisson arrivals of batched-config instances, each
     run to ||phi^{n+1} - phi^n||_2 < 1e-8 (checked every 100 steps) or 20000 steps,
-    150 GB admission budget; continuous batching vs sequential plain solves."""
+    150 GB admission budget; continuous batching vs sequential plain solves of the
+    same requests (the highest-rate trace), with each served phi compared to its
+    sequential counterpart.  Per rate: the device's idle share of the run (wall
+    time without a slice on the GPU), batch rebuilds, host time admitting and
+    rebuilding, and how many requests stopped at the tolerance or the cap."""
     import workloads as w
     from paper_1902_09813_gb300.serve import Server, depth_series, poisson_trace, serve_sequential, summarize
 
@@ -677,6 +709,7 @@ def run_serving(args, rates=(100.0, 500.0, 2000.0), count=96, seed=1):
 
     from paper_1902_09813_gb300 import Batch, Lattice
 
+    count = args.serve_count or count
     probs = w.batched_instances(count=count, seed=seed, nsteps=0)
     for p in probs:
         p.phi_ref = float(p.phi0().mean())
@@ -691,18 +724,32 @@ def run_serving(args, rates=(100.0, 500.0, 2000.0), count=96, seed=1):
     out = {"requests_per_rate": count, "slice_steps": 100, "max_steps": 20000, "tol": 1e-8,
            "budget_gb": 150, "dtype": "f32 compute, f16 storage (local shift)", "tile": list(shape),
            "rates": {}}
+    served = None
     for lam in rates:
         trace = poisson_trace(probs, rate=lam, seed=seed)
         srv = Server(budget_bytes=150e9, slice_steps=100, max_steps=20000, tol=1e-8, tiles=shape)
         res = srv.run(trace)
-        out["rates"][str(int(lam))] = dict(summarize(res), peak_active=srv.stats["peak_active"],
-                                           slices=srv.stats["slices"],
-                                           depth_t_active_waiting=depth_series(srv.depth))
-    # plain sequential baseline on the first requests of the highest-rate trace
-    nseq = min(count, args.serve_seq)
-    trace = poisson_trace(probs[:nseq], rate=max(rates), seed=seed)
+        st = srv.stats
+        out["rates"][str(int(lam))] = dict(
+            summarize(res), peak_active=st["peak_active"], slices=st["slices"], rebuilds=st["rebuilds"],
+            gpu_idle_fraction=round(srv.idle_fraction(), 4), gpu_busy_s=round(st["gpu_busy_s"], 3),
+            admit_s=round(st["admit_s"], 3), rebuild_s=round(st["rebuild_s"], 3),
+            stopped_at_tol=st["tol_hits"], stopped_at_cap=st["cap_hits"], rejected=st["rejected"],
+            unstable=st["unstable"], depth_t_active_waiting=depth_series(srv.depth))
+        served = res
+    # plain sequential baseline on the same requests as the highest-rate trace
+    trace = poisson_trace(probs, rate=max(rates), seed=seed)
     seq = serve_sequential(trace, slice_steps=100, max_steps=20000, tol=1e-8)
-    out["sequential_plain"] = summarize(seq)
+    out["sequential_plain"] = dict(summarize(seq), requests_same_as_served=True,
+                                   stopped_at_tol=sum(1 for r in seq if r.steps < 20000))
+    diffs = [float(np.max(np.abs(a.phi - b_.phi)) / max(np.max(np.abs(b_.phi)), 1e-300))
+             for a, b_ in zip(served, seq) if a.phi is not None and a.steps == b_.steps]
+    out["served_vs_sequential"] = {
+        "same_steps": sum(1 for a, b_ in zip(served, seq) if a.steps == b_.steps),
+        "bitwise_equal": sum(1 for a, b_ in zip(served, seq)
+                             if a.phi is not None and a.steps == b_.steps and np.array_equal(a.phi, b_.phi)),
+        "max_rel_diff": float(f"{max(diffs):.3e}") if diffs else None,
+        "requests": len(seq)}
     return out
 
 
@@ -790,7 +837,9 @@ def main():
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true")
-    ap.add_argument("--serve-seq", type=int, default=48)
+    ap.add_argument("--serve-count", type=int, default=0,
+                    help="requests per serving trace (0: the default 96)")
+    ap.add_argument("--serving-only", action="store_true", help="only the serving comparison")
     ap.add_argument("--accuracy-only", action="store_true",
                     help="only the accuracy study (reduced formats, closed forms, convergence sweep)")
     ap.add_argument("--batched-only", action="store_true",
@@ -805,7 +854,7 @@ def main():
     ap.add_argument("--storage", default=None, choices=["f64", "df64", "f32", "f16", "bf16"])
     ap.add_argument("--shift", default="auto", choices=["auto", "ref", "local"],
                     help="stored form of F32/F16/BF16 populations")
-    ap.add_argument("--sweep", default="auto", choices=["auto", "plain", "tma", "tb2"],
+    ap.add_argument("--sweep", default="auto", choices=["auto", "plain", "tma", "tb2", "vec", "tb2v"],
                     help="kernel form of FP32-compute sweeps")
     args = ap.parse_args()
     if args.warmup < 3:
@@ -822,6 +871,10 @@ def main():
         print(json.dumps({"accuracy": acc, "seconds": round(time.perf_counter() - t0, 1)}), flush=True)
     elif args.batched_only:
         run_batched_only(args)
+    elif args.serving_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"serving": run_serving(args)}), flush=True)
     elif args.d3q19_only:
         import workloads as w
         p = w.gaussian_hill3(n=args.n, sigma0=args.n / 16.0, u=(0.05, -0.03, 0.02),

@@ -180,7 +180,8 @@ btrt_status btrt_mass(btrt_lattice L, double *out);
 btrt_status btrt_check(btrt_lattice L, int32_t *flags);
 
 /* Kernel form of the ordinary FP32-compute sweep: BTRT_SWEEP_AUTO (default: the
- * faster form as measured on GB300, currently BTRT_SWEEP_TB2), BTRT_SWEEP_PLAIN
+ * faster form as measured on GB300: BTRT_SWEEP_VEC for F16/BF16 storage,
+ * BTRT_SWEEP_TB2 for F32 storage), BTRT_SWEEP_PLAIN
  * (one step per launch, direct global loads served by L1/L2), BTRT_SWEEP_TMA
  * (persistent tiles staged in shared memory by TMA with mbarrier pipelining) or
  * BTRT_SWEEP_TB2 (two time steps per launch: the first step's populations stay
@@ -190,10 +191,16 @@ btrt_status btrt_check(btrt_lattice L, int32_t *flags);
  * x-consecutive nodes and moves each population plane with one vector load and
  * one vector store, 64 bits for F16/BF16 storage and 128 for F32; the
  * initialising collision and btrt_step_residual's last step run in the plain
- * form).  Every storage format and shift of an FP32-compute lattice.
- * All forms give bitwise identical results.  FP64 and double-word lattices
- * always use the plain form (BTRT_SWEEP_TMA, _TB2 and _VEC: BTRT_EINVAL). */
-enum { BTRT_SWEEP_AUTO = 0, BTRT_SWEEP_PLAIN = 1, BTRT_SWEEP_TMA = 2, BTRT_SWEEP_TB2 = 3, BTRT_SWEEP_VEC = 4 };
+ * form), or BTRT_SWEEP_TB2V (two steps per launch as BTRT_SWEEP_TB2, with the
+ * vector access of BTRT_SWEEP_VEC in both steps and the intermediate step kept
+ * in shared memory in the storage format).  Every storage format and shift of
+ * an FP32-compute lattice.  All forms give bitwise identical results.  FP64 and
+ * double-word lattices always use the plain form (BTRT_SWEEP_TMA, _TB2, _VEC and
+ * _TB2V: BTRT_EINVAL). */
+enum {
+    BTRT_SWEEP_AUTO = 0, BTRT_SWEEP_PLAIN = 1, BTRT_SWEEP_TMA = 2, BTRT_SWEEP_TB2 = 3, BTRT_SWEEP_VEC = 4,
+    BTRT_SWEEP_TB2V = 5
+};
 btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant);
 
 /* Number of completed steps and the current time t0 + n dt. */
@@ -223,6 +230,12 @@ typedef struct btrt_batch_s *btrt_batch;
 /* Device workspace (descriptors, tile table, reduction scratch) for a batch of
  * these members; 0 if the member list is invalid. */
 size_t btrt_batch_workspace_bytes(const btrt_lattice *members, int32_t n);
+
+/* The same size for a batch of lattices with these n grid descriptions (no
+ * lattice needed): lets an admission policy count the batch tables of a
+ * membership before it creates the lattices.  0 if a description is invalid or
+ * they mix compute formats. */
+size_t btrt_batch_workspace_bytes_desc(const btrt_grid_desc *descs, int32_t n);
 
 /* Create a batch over n members in a caller-owned, 256-byte aligned device
  * workspace.  Synchronises the members' streams; the batch's own work goes to
@@ -255,6 +268,16 @@ btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *
  * steps).  want_residual != 0: also compute each member's ||phi^n - phi^{n-1}||_2
  * at the last step (fixed order). */
 btrt_status btrt_batch_step(btrt_batch B, int64_t nsteps, int32_t want_residual);
+
+/* Advance every member nsteps >= 1 steps (as btrt_batch_step with want_residual)
+ * and compare, on the device, each member's residual ||phi^n - phi^{n-1}||_2 of
+ * the last step with tol (the steady-state test of a serving loop, cf. Eq. 64):
+ * done[k] bit 0 = residual < tol, bit 1 = member k produced a non-finite phi.
+ * done: n int32 values in host memory (on_device = 0; pinned memory keeps the
+ * copy asynchronous) or device memory (on_device = 1).  Nothing synchronises:
+ * the flags are written in the batch stream's order, so read them after
+ * synchronising that stream (or an event recorded after this call). */
+btrt_status btrt_batch_step_tol(btrt_batch B, int64_t nsteps, double tol, int32_t *done, int32_t on_device);
 
 /* Residuals of the last step with want_residual, one per member (host, synchronises). */
 btrt_status btrt_batch_residuals(btrt_batch B, double *out_host);

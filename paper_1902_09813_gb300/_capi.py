@@ -13,7 +13,7 @@ F64, F32, F16, BF16, DF64 = 0, 1, 2, 3, 4
 K2_HBB, K2_CONST = 0, 1
 SRC_NONE, SRC_CONST, SRC_TRIG, SRC_FIELD, SRC_REACTION = 0, 1, 2, 3, 4
 FIELD_SOURCE, FIELD_DIFFUSION = 1, 2
-SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA, SWEEP_TB2, SWEEP_VEC = 0, 1, 2, 3, 4
+SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA, SWEEP_TB2, SWEEP_VEC, SWEEP_TB2V = 0, 1, 2, 3, 4, 5
 SHIFT_REF, SHIFT_LOCAL = 0, 1
 PROBE_FMA, PROBE_ADD, PROBE_MUL = 0, 1, 2
 SHIFTS = {"ref": SHIFT_REF, "local": SHIFT_LOCAL}
@@ -100,11 +100,13 @@ SIGNATURES = [
     ("btrt_load", ctypes.c_int, [_vp, _vp, _sz]),
     ("btrt_destroy", ctypes.c_int, [_vp]),
     ("btrt_batch_workspace_bytes", _sz, [ctypes.POINTER(_vp), _i32]),
+    ("btrt_batch_workspace_bytes_desc", _sz, [ctypes.POINTER(GridDesc), _i32]),
     ("btrt_batch_create", ctypes.c_int, [ctypes.POINTER(_vp), _i32, _vp, _sz, _vp, ctypes.POINTER(_vp)]),
     ("btrt_batch_set_tiles", ctypes.c_int, [_vp, _i32, _i32, _i32, _i32]),
     ("btrt_batch_autotune", ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                            ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     ("btrt_batch_step", ctypes.c_int, [_vp, _i64, _i32]),
+    ("btrt_batch_step_tol", ctypes.c_int, [_vp, _i64, ctypes.c_double, _vp, _i32]),
     ("btrt_batch_residuals", ctypes.c_int, [_vp, _dp]),
     ("btrt_batch_check", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     ("btrt_batch_member_flags", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),

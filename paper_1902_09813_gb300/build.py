@@ -1,8 +1,8 @@
 """Compile the CUDA library (sm_103a) in-tree: csrc/*.cu -> _lib/libbtrt.so.
 
 Translation units compile in parallel with nvcc; the shared object is linked
-with nvcc as well.  A build is skipped when the library is newer than every
-source and header.
+with nvcc as well.  A build is skipped when a stamp beside the library records
+the same digest of every source, header and flag, on the same architecture.
 """
 from __future__ import annotations
 
@@ -40,18 +40,36 @@ def _deps():
     return list(CSRC.glob("*")) + list((ROOT / "include").glob("*.h")) + [Path(__file__)]
 
 
-def up_to_date(lib: Path = LIB) -> bool:
-    if not lib.exists():
+def _stamp(extra) -> str:
+    """Digest of everything the library is built from (sources, headers, this
+    script, the extra flags) and of the machine: a copied tree whose file times
+    say nothing, or a library built on another architecture, is rebuilt."""
+    import hashlib
+    import platform
+    h = hashlib.sha256()
+    for p in sorted(_deps()):
+        h.update(p.name.encode())
+        h.update(p.read_bytes())
+    h.update(" ".join(list(extra or [])).encode())
+    h.update(platform.machine().encode())
+    return h.hexdigest()
+
+
+def _stamp_path(lib: Path) -> Path:
+    return Path(str(lib) + ".stamp")
+
+
+def up_to_date(lib: Path = LIB, extra=None) -> bool:
+    if not lib.exists() or not _stamp_path(lib).exists():
         return False
-    t = lib.stat().st_mtime
-    return all(p.stat().st_mtime <= t for p in _deps())
+    return _stamp_path(lib).read_text().strip() == _stamp(extra)
 
 
 def build(force: bool = False, verbose: bool = False, extra=None, lib: Path = LIB) -> Path:
     """Compile every csrc/*.cu and link `lib`.  `extra` adds nvcc flags (for example
     -DBTRT_DEBUG_BOUNDS for the index-checked build, linked to another path)."""
     lib = Path(lib)
-    if not force and up_to_date(lib):
+    if not force and up_to_date(lib, extra):
         return lib
     lib.parent.mkdir(parents=True, exist_ok=True)
     objdir = lib.parent / "obj"
@@ -77,6 +95,7 @@ def build(force: bool = False, verbose: bool = False, extra=None, lib: Path = LI
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, lib)
+    _stamp_path(lib).write_text(_stamp(extra) + "\n")
     return lib
 
 

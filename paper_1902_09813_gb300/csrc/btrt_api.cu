@@ -345,6 +345,19 @@ int btrt::sweep_mode(btrt_lattice L) {
     return kLinear;
 }
 
+// The kernel form BTRT_SWEEP_AUTO stands for, as measured on GB300 at 8192^2: the
+// one-step vector form for FP16/BF16 storage (manufactured solution 140-153
+// GLUPS against 119-141 for the two-step forms; nonlinear workload 117-130
+// against 77-116), the scalar two-step form for FP32 storage (116-124 and
+// 103-114 GLUPS against 110-117 and 69-79 with vector access, 80-86 for one step
+// per launch).
+int btrt::effective_sweep_variant(btrt_lattice L) {
+    if (L->g.compute != BTRT_F32) return BTRT_SWEEP_PLAIN;
+    if (L->sweep_variant != BTRT_SWEEP_AUTO) return L->sweep_variant;
+    const bool s16 = L->g.storage == BTRT_F16 || L->g.storage == BTRT_BF16;
+    return s16 ? BTRT_SWEEP_VEC : BTRT_SWEEP_TB2;
+}
+
 namespace {
 
 btrt_status launch(btrt_lattice L, int64_t n, bool first, bool resid = false) {
@@ -366,7 +379,7 @@ btrt_status launch(btrt_lattice L, int64_t n, bool first, bool resid = false) {
         if (!first && !resid && L->have_tma && L->sweep_variant == BTRT_SWEEP_TMA)
             CUDA_TRY(launch_sweep_tma(p, L->g.storage, sh, sweep_mode(L), &L->tma_in[L->cur],
                                       &L->tma_out[1 - L->cur], L->stream));
-        else if (!first && !resid && L->sweep_variant == BTRT_SWEEP_VEC)
+        else if (!first && !resid && effective_sweep_variant(L) == BTRT_SWEEP_VEC)
             CUDA_TRY(launch_sweep_vec(p, L->g.storage, sh, sweep_mode(L), L->stream));
         else
             CUDA_TRY(launch_sweep_f32(p, L->g.storage, sh, sweep_mode(L), L->stream));
@@ -688,17 +701,18 @@ btrt_status btrt_step(btrt_lattice L, int64_t nsteps) {
     if (!L) return fail(BTRT_EINVAL, "null lattice");
     if (!L->ready) return fail(BTRT_ESTATE, "lattice not initialised");
     if (nsteps < 0) return fail(BTRT_EINVAL, "negative step count");
-    // the two-step form serves every FP32-compute lattice; AUTO takes it (it is the
-    // faster form on GB300 for every storage format and shift)
-    const bool tb2 = L->g.compute == BTRT_F32 &&
-                     (L->sweep_variant == BTRT_SWEEP_TB2 || L->sweep_variant == BTRT_SWEEP_AUTO);
-    if (tb2) {
+    // the two-step forms serve every FP32-compute lattice (AUTO: see effective_sweep_variant)
+    const int form = effective_sweep_variant(L);
+    if (form == BTRT_SWEEP_TB2 || form == BTRT_SWEEP_TB2V) {
         // pairs of steps in one launch: inputs from buffer cur, outputs to the other
         for (; nsteps >= 2; nsteps -= 2) {
             SweepParams<float> pa, pb;
             fill_params(L, pa, L->step + 1, false);
             fill_params(L, pb, L->step + 2, false);
-            CUDA_TRY(launch_sweep_tb2(pa, pb, L->g.storage, shift_of(L->g), sweep_mode(L), L->stream));
+            if (form == BTRT_SWEEP_TB2V)
+                CUDA_TRY(launch_sweep_tb2v(pa, pb, L->g.storage, shift_of(L->g), sweep_mode(L), L->stream));
+            else
+                CUDA_TRY(launch_sweep_tb2(pa, pb, L->g.storage, shift_of(L->g), sweep_mode(L), L->stream));
             L->cur = 1 - L->cur;
             L->step += 2;
         }
@@ -809,10 +823,10 @@ btrt_status btrt_check(btrt_lattice L, int32_t *flags) {
 btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant) {
     if (!L) return fail(BTRT_EINVAL, "null lattice");
     if (variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN && variant != BTRT_SWEEP_TMA &&
-        variant != BTRT_SWEEP_TB2 && variant != BTRT_SWEEP_VEC)
+        variant != BTRT_SWEEP_TB2 && variant != BTRT_SWEEP_VEC && variant != BTRT_SWEEP_TB2V)
         return fail(BTRT_EINVAL, "unknown sweep variant %d", variant);
-    if (variant == BTRT_SWEEP_TB2 && L->g.compute != BTRT_F32)
-        return fail(BTRT_EINVAL, "the two-step sweep serves FP32-compute lattices");
+    if ((variant == BTRT_SWEEP_TB2 || variant == BTRT_SWEEP_TB2V) && L->g.compute != BTRT_F32)
+        return fail(BTRT_EINVAL, "the two-step sweeps serve FP32-compute lattices");
     if (variant == BTRT_SWEEP_VEC && L->g.compute != BTRT_F32)
         return fail(BTRT_EINVAL, "the vector-access sweep serves FP32-compute lattices");
     if (variant == BTRT_SWEEP_TMA && !L->have_tma)

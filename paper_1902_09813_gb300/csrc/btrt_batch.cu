@@ -155,17 +155,18 @@ __device__ __forceinline__ void batch_tile(const BatchArgs<Real> &a, int t, int 
     const int4 tile = a.tiles[t];
     const BatchMember<Real> &M = a.members[tile.x];
     stage_member(a, tile.x, k, flip, sp);
+    const SweepParams<Real> &lp = sp;
     const int x = tile.y + threadIdx.x;
     double r = 0.0;
-    if (x < sp.nx) {
+    if (x < lp.nx) {
         const int y0 = tile.z + threadIdx.y;
         if (!LIN && M.mode == kGeneral) {
-            if (resid) r = sweep_rows<Real, S, SH, kGeneral, kSrcRuntime, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
-            else sweep_rows<Real, S, SH, kGeneral, kSrcRuntime, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+            if (resid) r = sweep_rows<Real, S, SH, kGeneral, kSrcRuntime, L2ONLY, true>(lp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, SH, kGeneral, kSrcRuntime, L2ONLY, false>(lp, x, y0, blockDim.y, a.rows);
         } else {
             constexpr int SRC = LIN ? kSrcRuntimeNR : kSrcRuntime;
-            if (resid) r = sweep_rows<Real, S, SH, kLinear, SRC, L2ONLY, true>(sp, x, y0, blockDim.y, a.rows);
-            else sweep_rows<Real, S, SH, kLinear, SRC, L2ONLY, false>(sp, x, y0, blockDim.y, a.rows);
+            if (resid) r = sweep_rows<Real, S, SH, kLinear, SRC, L2ONLY, true>(lp, x, y0, blockDim.y, a.rows);
+            else sweep_rows<Real, S, SH, kLinear, SRC, L2ONLY, false>(lp, x, y0, blockDim.y, a.rows);
         }
     }
     if (resid) {
@@ -210,30 +211,31 @@ __global__ void __launch_bounds__(256, (LIN && sizeof(Real) == 4) ? BTRT_BATCH_L
 // graph), one block per tile of (4 bx) x (by rows) nodes; each thread owns four
 // x-consecutive nodes of `rows` rows and sweeps them with the single-lattice
 // vector sweep's code (btrt_vec.cuh), so every node's arithmetic is that of the
-// plain form.  Resident blocks per SM it is compiled for:
-#ifndef BTRT_BATCH_VEC_MINBLOCKS
-#define BTRT_BATCH_VEC_MINBLOCKS 2
-#endif
+// plain form.  Resident blocks per SM it is compiled for: as the single-lattice
+// vector sweep for the constant-coefficient form (VecMinBlocks: four for 16-bit
+// storage, two for FP32 storage); two for the form that takes any member, which
+// spills 700-900 bytes at four.
 template <typename S, int SH, bool LIN>
-__global__ void __launch_bounds__(256, BTRT_BATCH_VEC_MINBLOCKS)
+__global__ void __launch_bounds__(256, LIN ? VecMinBlocks<S>::value : 2)
     batch_vec_kernel(const __grid_constant__ BatchArgs<float> a, int k, int flip) {
     __shared__ SweepParams<float> sp;
     const int4 tile = a.tilesv[blockIdx.x];
     const int mode = a.members[tile.x].mode;
     stage_member(a, tile.x, k, flip, sp);
+    const SweepParams<float> &lp = sp;
     const int x0 = tile.y + threadIdx.x * kVec;
     bool bad = false;
-    if (x0 < sp.nx) {
+    if (x0 < lp.nx) {
         for (int r = 0; r < a.rows; ++r) {
             const int y = tile.z + threadIdx.y + r * blockDim.y;
-            if (y >= sp.ny) break;
+            if (y >= lp.ny) break;
             if (LIN || mode != kGeneral)
-                bad |= vec_group<S, SH, kLinear, LIN ? kSrcRuntimeNR : kSrcRuntime>(sp, x0, y);
+                bad |= vec_group<S, SH, kLinear, LIN ? kSrcRuntimeNR : kSrcRuntime>(lp, x0, y);
             else
-                bad |= vec_group<S, SH, kGeneral, kSrcRuntime>(sp, x0, y);
+                bad |= vec_group<S, SH, kGeneral, kSrcRuntime>(lp, x0, y);
         }
     }
-    if (bad) atomicOr(sp.flags, 1);
+    if (bad) atomicOr(lp.flags, 1);
 }
 
 // Two-step form (FP32 compute): steps k and k + 1 of the slice in one launch, one
@@ -305,6 +307,14 @@ __global__ void gather_member_flags(const BatchMember<Real> *members, int n, int
     if (k < n) out[k] = *members[k].p.flags;
 }
 
+// Per-member stop flags after a residual slice: bit 0 residual < tol, bit 1 a
+// non-finite phi in the member (its device flag bit 0).
+template <typename Real>
+__global__ void member_done(const BatchMember<Real> *members, const double *resid, int n, double tol, int *out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = (resid[k] < tol ? 1 : 0) | ((*members[k].p.flags & 1) ? 2 : 0);
+}
+
 // Per-member residual: fixed-order sum of its tiles' partials, then sqrt.
 __global__ void __launch_bounds__(256) member_residual(const double *tile_partials, const int *tile_begin,
                                                        const int *tile_count, double *out) {
@@ -353,13 +363,24 @@ const Shape kShapes[] = {{32, 8, 1, 0}, {32, 8, 2, 0}, {32, 8, 4, 0}, {64, 4, 1,
                          {64, 4, 2, 0}, {32, 4, 2, 0}, {16, 16, 1, 0}, {8, 32, 1, 0}};
 constexpr int kForms = 4;   // launch forms 0 .. 3 (FP64 batches: 0 and 1)
 
-long long tiles_for(const std::vector<btrt_lattice> &m, int bx, int by, int rows) {
+// Grid sizes of the members: all the batch tables depend on.
+struct MemberGeom {
+    int nx, ny;
+};
+
+std::vector<MemberGeom> geoms_of(const std::vector<btrt_lattice> &m) {
+    std::vector<MemberGeom> g;
+    for (auto L : m) g.push_back(MemberGeom{L->g.nx, L->g.ny});
+    return g;
+}
+
+long long tiles_for(const std::vector<MemberGeom> &m, int bx, int by, int rows) {
     long long t = 0;
-    for (auto L : m) t += (long long)((L->g.nx + bx - 1) / bx) * ((L->g.ny + by * rows - 1) / (by * rows));
+    for (const MemberGeom &g : m) t += (long long)((g.nx + bx - 1) / bx) * ((g.ny + by * rows - 1) / (by * rows));
     return t;
 }
 
-long long max_tiles(const std::vector<btrt_lattice> &m) {
+long long max_tiles(const std::vector<MemberGeom> &m) {
     long long t = 0;
     for (const Shape &s : kShapes) t = std::max(t, tiles_for(m, s.bx, s.by, s.rows));
     return t;
@@ -374,13 +395,13 @@ struct BatchLayout {
         off_mflags, off_sync, total;
 };
 
-BatchLayout batch_layout(const std::vector<btrt_lattice> &m) {
+BatchLayout batch_layout(const std::vector<MemberGeom> &m, int compute) {
     BatchLayout b;
     const size_t n = m.size();
     const size_t T = (size_t)max_tiles(m);
     size_t off = 0;
     b.off_members = off;
-    off += up256(n * member_bytes(m[0]->g.compute));
+    off += up256(n * member_bytes(compute));
     b.off_tiles = off;
     off += up256(T * sizeof(int4));
     b.off_tiles2 = off;
@@ -396,7 +417,7 @@ BatchLayout batch_layout(const std::vector<btrt_lattice> &m) {
     b.off_tcnt = off;
     off += up256(n * sizeof(int));
     b.off_vals = off;
-    off += up256(n * (size_t)kMaxSliceSteps * 2 * (m[0]->g.compute == BTRT_F64 ? 8 : 4));
+    off += up256(n * (size_t)kMaxSliceSteps * 2 * (compute == BTRT_F64 ? 8 : 4));
     b.off_mflags = off;
     off += up256(n * sizeof(int));
     b.off_sync = off;
@@ -684,7 +705,24 @@ extern "C" {
 size_t btrt_batch_workspace_bytes(const btrt_lattice *members, int32_t n) {
     std::vector<btrt_lattice> m;
     if (check_members(members, n, m) != BTRT_OK) return 0;
-    return batch_layout(m).total;
+    return batch_layout(geoms_of(m), m[0]->g.compute).total;
+}
+
+size_t btrt_batch_workspace_bytes_desc(const btrt_grid_desc *descs, int32_t n) {
+    if (!descs || n <= 0) {
+        bfail(BTRT_EINVAL, "a batch needs at least one member");
+        return 0;
+    }
+    std::vector<MemberGeom> g;
+    for (int k = 0; k < n; ++k) {
+        if (btrt_workspace_bytes(&descs[k]) == 0) return 0;   // the message says why
+        if (descs[k].compute != descs[0].compute || descs[k].compute == BTRT_DF64) {
+            bfail(BTRT_EINVAL, "member %d: batches take FP64 or FP32 members of one compute format", k);
+            return 0;
+        }
+        g.push_back(MemberGeom{descs[k].nx, descs[k].ny});
+    }
+    return batch_layout(g, descs[0].compute).total;
 }
 
 btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_workspace, size_t bytes,
@@ -696,7 +734,7 @@ btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_
     if (st != BTRT_OK) return st;
     if (!dev_workspace || ((uintptr_t)dev_workspace) % 256)
         return bfail(BTRT_EINVAL, "batch workspace must be a 256-byte aligned device pointer");
-    BatchLayout lay = batch_layout(m);
+    BatchLayout lay = batch_layout(geoms_of(m), m[0]->g.compute);
     if (bytes < lay.total) return bfail(BTRT_ENOMEM, "batch workspace of %zu bytes < required %zu", bytes, lay.total);
     int coop = 0, dev = 0;
     BCUDA(cudaGetDevice(&dev));
@@ -777,6 +815,27 @@ btrt_status btrt_batch_step(btrt_batch B, int64_t nsteps, int32_t want_residual)
         }
         nsteps -= chunk;
     }
+    return BTRT_OK;
+}
+
+btrt_status btrt_batch_step_tol(btrt_batch B, int64_t nsteps, double tol, int32_t *done, int32_t on_device) {
+    if (!B || !done) return bfail(BTRT_EINVAL, "null argument");
+    if (nsteps < 1) return bfail(BTRT_EINVAL, "btrt_batch_step_tol needs at least one step");
+    btrt_status st = btrt_batch_step(B, nsteps, 1);
+    if (st != BTRT_OK) return st;
+    const int n = (int)B->members.size();
+    int *dflags = on_device ? done : reinterpret_cast<int *>(B->ws + B->lay.off_mflags);
+    const double *resid = reinterpret_cast<const double *>(B->ws + B->lay.off_resid);
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (B->compute == BTRT_F64)
+        member_done<double><<<grid, 256, 0, B->stream>>>(
+            reinterpret_cast<const BatchMember<double> *>(B->ws + B->lay.off_members), resid, n, tol, dflags);
+    else
+        member_done<float><<<grid, 256, 0, B->stream>>>(
+            reinterpret_cast<const BatchMember<float> *>(B->ws + B->lay.off_members), resid, n, tol, dflags);
+    BCUDA(cudaGetLastError());
+    if (!on_device)
+        BCUDA(cudaMemcpyAsync(done, dflags, n * sizeof(int), cudaMemcpyDeviceToHost, B->stream));
     return BTRT_OK;
 }
 

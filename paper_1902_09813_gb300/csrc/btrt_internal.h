@@ -83,6 +83,9 @@ template <typename Real> void fill_params(btrt_lattice L, SweepParams<Real> &p, 
 void step_scalars(btrt_lattice L, int64_t n, bool first, double *src_val, double *wall_fac);
 // Compiled variant (kGeneral / kLinear / kLinearK0One) that serves L's coefficients.
 int sweep_mode(btrt_lattice L);
+// Kernel form of L's ordinary steps (BTRT_SWEEP_AUTO resolved; PLAIN for FP64 and
+// double-word lattices).
+int effective_sweep_variant(btrt_lattice L);
 
 // Threads of a single-lattice sweep block, and its grid: 32 x 8 threads, each
 // sweeping rows_per_thread nodes of its column.
@@ -127,6 +130,17 @@ cudaError_t launch_sweep_tb2_f16(const SweepParams<float> &pa, const SweepParams
                                  cudaStream_t s);
 cudaError_t launch_sweep_tb2_bf16(const SweepParams<float> &pa, const SweepParams<float> &pb, int shift, int mode,
                                   cudaStream_t s);
+
+// Two steps per launch with vector memory access (FP32 compute; arguments as
+// launch_sweep_tb2).
+cudaError_t launch_sweep_tb2v(const SweepParams<float> &pa, const SweepParams<float> &pb, int storage, int shift,
+                              int mode, cudaStream_t s);
+cudaError_t launch_sweep_tb2v_f32(const SweepParams<float> &pa, const SweepParams<float> &pb, int shift, int mode,
+                                  cudaStream_t s);
+cudaError_t launch_sweep_tb2v_f16(const SweepParams<float> &pa, const SweepParams<float> &pb, int shift, int mode,
+                                  cudaStream_t s);
+cudaError_t launch_sweep_tb2v_bf16(const SweepParams<float> &pa, const SweepParams<float> &pb, int shift, int mode,
+                                   cudaStream_t s);
 
 // One step per launch with vector memory access (FP32 compute; storage BTRT_F32,
 // F16 or BF16; shift kShiftRef or kShiftLocal); never the initialising collision

@@ -65,6 +65,16 @@ cudaError_t launch_sweep_f32(const SweepParams<float> &p, int storage, int shift
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_sweep_tb2v(const SweepParams<float> &pa, const SweepParams<float> &pb, int storage, int shift,
+                              int mode, cudaStream_t s) {
+    switch (storage) {
+    case BTRT_F32: return launch_sweep_tb2v_f32(pa, pb, shift, mode, s);
+    case BTRT_F16: return launch_sweep_tb2v_f16(pa, pb, shift, mode, s);
+    case BTRT_BF16: return launch_sweep_tb2v_bf16(pa, pb, shift, mode, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_sweep_vec(const SweepParams<float> &p, int storage, int shift, int mode, cudaStream_t s) {
     switch (storage) {
     case BTRT_F32: return launch_sweep_vec_f32(p, shift, mode, s);

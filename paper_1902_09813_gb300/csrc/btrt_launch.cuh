@@ -9,6 +9,7 @@
 #include "btrt_internal.h"
 #include "btrt_tb.cuh"
 #include "btrt_tma.cuh"
+#include "btrt_tb2v.cuh"
 #include "btrt_vec.cuh"
 
 namespace btrt {
@@ -134,6 +135,38 @@ cudaError_t launch_tb2_storage(const SweepParams<float> &pa, const SweepParams<f
                                 : launch_tb2_mode<S, kShiftLocal, kLinear>(pa, pb, s);
     return mode == kGeneral ? launch_tb2_mode<S, kShiftRef, kGeneral>(pa, pb, s)
                             : launch_tb2_mode<S, kShiftRef, kLinear>(pa, pb, s);
+}
+
+// Two steps per launch with vector memory access (btrt_tb2v.cuh): one block per
+// 32 x TY output tile.
+template <typename S, int SH, int MODE, int SRC>
+cudaError_t launch_tb2v_src(const SweepParams<float> &pa, const SweepParams<float> &pb, cudaStream_t s) {
+    using G = Tb2vGeom<S>;
+    const int ntx = (pa.nx + G::TX - 1) / G::TX;
+    const int nty = (pa.ny + G::TY - 1) / G::TY;
+    sweep_tb2v_kernel<S, SH, MODE, SRC><<<ntx * nty, G::THREADS, G::SMEM, s>>>(pa, pb, ntx);
+    return cudaGetLastError();
+}
+
+template <typename S, int SH, int MODE>
+cudaError_t launch_tb2v_mode(const SweepParams<float> &pa, const SweepParams<float> &pb, cudaStream_t s) {
+    switch (pa.src_kind) {
+    case kSrcNone: return launch_tb2v_src<S, SH, MODE, kSrcNone>(pa, pb, s);
+    case kSrcConst: return launch_tb2v_src<S, SH, MODE, kSrcConst>(pa, pb, s);
+    case kSrcTrig: return launch_tb2v_src<S, SH, MODE, kSrcTrig>(pa, pb, s);
+    case kSrcField: return launch_tb2v_src<S, SH, MODE, kSrcField>(pa, pb, s);
+    default: return launch_tb2v_src<S, SH, MODE, kSrcReaction>(pa, pb, s);
+    }
+}
+
+template <typename S>
+cudaError_t launch_tb2v_storage(const SweepParams<float> &pa, const SweepParams<float> &pb, int shift, int mode,
+                                cudaStream_t s) {
+    if (shift == kShiftLocal)
+        return mode == kGeneral ? launch_tb2v_mode<S, kShiftLocal, kGeneral>(pa, pb, s)
+                                : launch_tb2v_mode<S, kShiftLocal, kLinear>(pa, pb, s);
+    return mode == kGeneral ? launch_tb2v_mode<S, kShiftRef, kGeneral>(pa, pb, s)
+                            : launch_tb2v_mode<S, kShiftRef, kLinear>(pa, pb, s);
 }
 
 // One step per launch with vector memory access (btrt_vec.cuh).

@@ -58,14 +58,15 @@ __device__ __forceinline__ bool tb_coord(int &g, int n, int wall) {
 }
 
 // Pull of one node from a shared-memory region: `reg` holds 9 planes of
-// `rw` x `rh` stored-form values and `phr` the phi of the same region, the node
-// sits at (lx, ly) of the region; (gx, gy) are its global coordinates (inside the
-// domain) and phi_prev its own phi.  The same arithmetic as `pull_node` and
-// `pull_boundary`: links that cross a bounce-back wall take the node's own
-// opposite population and the wall term; with the local shift a value stored
-// relative to the writer's phi is moved to this node's (w_i (phi_writer - phi_prev)).
-template <int SH>
-__device__ __forceinline__ void tb_pull(const SweepParams<float> &p, const float *reg, const float *phr, int rw,
+// `rw` x `rh` stored-form values (FP32 copies of them, or the stored format T
+// itself) and `phr` the phi of the same region, the node sits at (lx, ly) of the
+// region; (gx, gy) are its global coordinates (inside the domain) and phi_prev
+// its own phi.  The same arithmetic as `pull_node` and `pull_boundary`: links
+// that cross a bounce-back wall take the node's own opposite population and the
+// wall term; with the local shift a value stored relative to the writer's phi is
+// moved to this node's (w_i (phi_writer - phi_prev)).
+template <int SH, typename T>
+__device__ __forceinline__ void tb_pull(const SweepParams<float> &p, const T *reg, const float *phr, int rw,
                                         int rh, int lx, int ly, int gx, int gy, float phi_prev, float (&d)[9]) {
     const int plane = rw * rh;
     // no link of a node one or more nodes away from every bounce-back wall crosses one
@@ -73,7 +74,7 @@ __device__ __forceinline__ void tb_pull(const SweepParams<float> &p, const float
     if (inner) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            d[i] = reg[BTRT_IX(p.flags, i * plane + (ly - ey_of(i)) * rw + (lx - ex_of(i)), 9 * plane)];
+            d[i] = Storage<T>::load(reg[BTRT_IX(p.flags, i * plane + (ly - ey_of(i)) * rw + (lx - ex_of(i)), 9 * plane)]);
         if constexpr (SH == kShiftLocal) {
 #pragma unroll
             for (int i = 1; i < 9; ++i)
@@ -96,7 +97,7 @@ __device__ __forceinline__ void tb_pull(const SweepParams<float> &p, const float
         }
         if (wx < 0 && wy < 0) {
             const int at = (ly - ey_of(i)) * rw + (lx - ex_of(i));
-            d[i] = reg[BTRT_IX(p.flags, i * plane + at, 9 * plane)];
+            d[i] = Storage<T>::load(reg[BTRT_IX(p.flags, i * plane + at, 9 * plane)]);
             if constexpr (SH == kShiftLocal)
                 if (i != 0) d[i] = fma(wgt<float>(i), phr[BTRT_IX(p.flags, at, plane)] - phi_prev, d[i]);
         } else {
@@ -108,7 +109,7 @@ __device__ __forceinline__ void tb_pull(const SweepParams<float> &p, const float
                 phi_w = wall_value(p, wy, gx);
             else
                 phi_w = wall_value(p, wx, gy);
-            const float dout = reg[BTRT_IX(p.flags, o * plane + ly * rw + lx, 9 * plane)];
+            const float dout = Storage<T>::load(reg[BTRT_IX(p.flags, o * plane + ly * rw + lx, 9 * plane)]);
             float wt = wall_term(p, o, phi_w);
             if constexpr (SH == kShiftRef) wt = wt - 2.0f * p.wref[i];
             if constexpr (SH == kShiftLocal) wt = fma(-2.0f * wgt<float>(i), phi_prev, wt);
@@ -184,7 +185,7 @@ __device__ __forceinline__ bool tb2_tile(const SweepParams<float> &pa, const Swe
         if (gx >= pb.nx || gy >= pb.ny) continue;
         const float phi_prev = phi_m[(oy + 1) * G::MX + ox + 1];
         float d[9];
-        tb_pull<SH>(pb, mid, phi_m, G::MX, G::MY, ox + 1, oy + 1, gx, gy, phi_prev, d);
+        tb_pull<SH, float>(pb, mid, phi_m, G::MX, G::MY, ox + 1, oy + 1, gx, gy, phi_prev, d);
         const int node = gy * pb.pitch + gx;
         float xs = 0.f, xc = 0.f;
         if (SRC == kSrcTrig || ((SRC == kSrcRuntime || SRC == kSrcRuntimeNR) && pb.src_kind == kSrcTrig)) {

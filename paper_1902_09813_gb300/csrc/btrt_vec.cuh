@@ -74,39 +74,32 @@ __device__ __forceinline__ float seg_value(const typename Vec4<S>::W &w, float e
     return (k < 0 || k >= kVec) ? edge : Vec4<S>::get(w, k);
 }
 
-// Resident blocks per SM the vector sweep is compiled for (0: the compiler's choice).
-#ifndef BTRT_VEC_MINBLOCKS
-#define BTRT_VEC_MINBLOCKS 2
+// Resident blocks per SM the vector sweep is compiled for.  FP16/BF16 storage:
+// four (64 registers, a few spilled words); measured at 8192^2 against the
+// compiler's 70-96 registers (two blocks) and three blocks: manufactured solution
+// 141 / 137 / 138 GLUPS with the local shift, 153 / 147 / 147 with the reference
+// shift; nonlinear workload 118 / 99 / 117 and 130 / 100 / 122.  FP32 storage
+// spills 160-240 bytes at 64 registers and keeps two blocks.
+#ifndef BTRT_VEC_MINBLOCKS_S16
+#define BTRT_VEC_MINBLOCKS_S16 4
 #endif
+#ifndef BTRT_VEC_MINBLOCKS_S32
+#define BTRT_VEC_MINBLOCKS_S32 2
+#endif
+template <typename S> struct VecMinBlocks { static constexpr int value = BTRT_VEC_MINBLOCKS_S16; };
+template <> struct VecMinBlocks<float> { static constexpr int value = BTRT_VEC_MINBLOCKS_S32; };
 
-// One step of the four nodes x0 .. x0 + 3 (those below nx) of row y.  Returns true
-// when a non-finite phi appeared.  L2ONLY: loads of data other SMs rewrite during
-// a persistent launch go through L2 only (as in pull_node).
-template <typename S, int SH, int MODE, int SRC, bool L2ONLY = false>
-__device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, int y) {
-    using V = Vec4<S>;
-    using W = typename V::W;
+// Pull and collide the four nodes x0 .. x0 + 3 of row y when all of them are
+// interior (x0 >= 1, x0 + 4 <= nx - 1, 1 <= y <= ny - 2: no pull wraps or crosses
+// a wall), and hand the stored-form outputs (FP32 values before the narrowing
+// to S) and the four phi to `put(outv, phi_o)`.  Returns true when a
+// non-finite phi appeared.  L2ONLY: loads of data other SMs rewrite during a
+// persistent launch go through L2 only (as in pull_node).
+template <typename S, int SH, int MODE, int SRC, bool L2ONLY, typename Put>
+__device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0, int y, Put &&put) {
+    using W = typename Vec4<S>::W;
     constexpr bool TRIG = SRC == kSrcTrig || SRC == kSrcRuntime || SRC == kSrcRuntimeNR;
-    bool bad = false;
-    const bool interior = x0 >= 1 && x0 + kVec <= p.nx - 1 && y >= 1 && y <= p.ny - 2;
-    if (!interior) {
-        // the plain sweep's per-node path (periodic wrap, bounce-back links)
-#pragma unroll 1
-        for (int v = 0; v < kVec && x0 + v < p.nx; ++v) {
-            const int x = x0 + v;
-            float xs = 0.f, xc = 0.f;
-            if (SRC == kSrcTrig || (TRIG && SRC != kSrcTrig && p.src_kind == kSrcTrig)) {
-                xs = p.Xs[BTRT_IX(p.flags, x, p.nx)];
-                xc = p.Xc[BTRT_IX(p.flags, x, p.nx)];
-            }
-            float f[9], phi_prev;
-            pull_node<float, S, SH, L2ONLY>(p, x, y, x > 0 && x < p.nx - 1, f, phi_prev);
-            finish_node<float, S, SH, MODE, SRC, false>(p, x, y, xs, xc, f, phi_prev, bad);
-        }
-        return bad;
-    }
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
-    S *__restrict__ fout = static_cast<S *>(p.fout);
     const int node = y * p.pitch + x0;
 
     // populations: per plane the vector of the source row and, for e_x != 0, the edge value
@@ -137,6 +130,7 @@ __device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, i
         }
     }
 
+    bool bad = false;
     float outv[9][kVec];
     float phi_o[kVec];
 #pragma unroll
@@ -165,20 +159,52 @@ __device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, i
         phi_o[v] = phi;
         bad |= not_finite(phi);
     }
-#pragma unroll
-    for (int i = 0; i < 9; ++i)
-        *reinterpret_cast<W *>(fout + BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)) =
-            V::put(outv[i][0], outv[i][1], outv[i][2], outv[i][3]);
-    *reinterpret_cast<float4 *>(p.phi_out + BTRT_IX(p.flags, node, p.plane)) =
-        make_float4(phi_o[0], phi_o[1], phi_o[2], phi_o[3]);
+    put(outv, phi_o);
     return bad;
+}
+
+// One step of the four nodes x0 .. x0 + 3 (those below nx) of row y, written to
+// the output buffer.  Returns true when a non-finite phi appeared.
+template <typename S, int SH, int MODE, int SRC, bool L2ONLY = false>
+__device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, int y) {
+    using V = Vec4<S>;
+    using W = typename V::W;
+    constexpr bool TRIG = SRC == kSrcTrig || SRC == kSrcRuntime || SRC == kSrcRuntimeNR;
+    const bool interior = x0 >= 1 && x0 + kVec <= p.nx - 1 && y >= 1 && y <= p.ny - 2;
+    if (!interior) {
+        // the plain sweep's per-node path (periodic wrap, bounce-back links)
+        bool bad = false;
+#pragma unroll 1
+        for (int v = 0; v < kVec && x0 + v < p.nx; ++v) {
+            const int x = x0 + v;
+            float xs = 0.f, xc = 0.f;
+            if (SRC == kSrcTrig || (TRIG && SRC != kSrcTrig && p.src_kind == kSrcTrig)) {
+                xs = p.Xs[BTRT_IX(p.flags, x, p.nx)];
+                xc = p.Xc[BTRT_IX(p.flags, x, p.nx)];
+            }
+            float f[9], phi_prev;
+            pull_node<float, S, SH, L2ONLY>(p, x, y, x > 0 && x < p.nx - 1, f, phi_prev);
+            finish_node<float, S, SH, MODE, SRC, false>(p, x, y, xs, xc, f, phi_prev, bad);
+        }
+        return bad;
+    }
+    S *__restrict__ fout = static_cast<S *>(p.fout);
+    const int node = y * p.pitch + x0;
+    return vec_interior<S, SH, MODE, SRC, L2ONLY>(p, x0, y, [&](const float (&outv)[9][kVec], const float (&phi_o)[kVec]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            *reinterpret_cast<W *>(fout + BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)) =
+                V::put(outv[i][0], outv[i][1], outv[i][2], outv[i][3]);
+        *reinterpret_cast<float4 *>(p.phi_out + BTRT_IX(p.flags, node, p.plane)) =
+            make_float4(phi_o[0], phi_o[1], phi_o[2], phi_o[3]);
+    });
 }
 
 // One step of one lattice, 32 x 8 threads per block: thread (tx, ty) owns nodes
 // x0 = 4 (32 bx + tx) .. x0 + 3 of row y = 8 by + ty.  Never the initialising
 // collision and never a residual step (the host runs those in the plain form).
 template <typename S, int SH, int MODE, int SRC>
-__global__ void __launch_bounds__(256, BTRT_VEC_MINBLOCKS) sweep_vec_kernel(const __grid_constant__ SweepParams<float> p) {
+__global__ void __launch_bounds__(256, VecMinBlocks<S>::value) sweep_vec_kernel(const __grid_constant__ SweepParams<float> p) {
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * kVec;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x0 >= p.nx || y >= p.ny) return;

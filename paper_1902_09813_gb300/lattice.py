@@ -60,6 +60,15 @@ def workspace_bytes(desc: C.GridDesc) -> int:
     return int(n)
 
 
+def batch_workspace_bytes(descs) -> int:
+    """Device bytes of the batch tables for lattices with these grid descriptions."""
+    arr = (C.GridDesc * len(descs))(*descs)
+    n = C.load().btrt_batch_workspace_bytes_desc(arr, len(descs))
+    if n == 0:
+        raise C.BtrtError(C.EINVAL, C.load().btrt_last_error().decode())
+    return int(n)
+
+
 class Lattice:
     """One B-TriRT D2Q9 lattice resident on the GPU.
 
@@ -166,10 +175,11 @@ class Lattice:
 
     def set_sweep_variant(self, variant: str):
         """Kernel form of an FP32-compute lattice: 'auto', 'plain', 'tma' (TMA-staged
-        tiles), 'tb2' (two steps per launch) or 'vec' (one step per launch with
-        vector loads and stores of four x-consecutive nodes per thread)."""
+        tiles), 'tb2' (two steps per launch), 'vec' (one step per launch with
+        vector loads and stores of four x-consecutive nodes per thread) or 'tb2v'
+        (two steps per launch with the vector access in both)."""
         code = {"auto": C.SWEEP_AUTO, "plain": C.SWEEP_PLAIN, "tma": C.SWEEP_TMA, "tb2": C.SWEEP_TB2,
-                "vec": C.SWEEP_VEC}[variant]
+                "vec": C.SWEEP_VEC, "tb2v": C.SWEEP_TB2V}[variant]
         C.check(self.lib.btrt_set_sweep_variant(self.handle, code))
         return self
 
@@ -308,6 +318,17 @@ class Batch:
     def step(self, nsteps: int, residual: bool = False):
         C.check(self.lib.btrt_batch_step(self.handle, int(nsteps), 1 if residual else 0))
         return self
+
+    def step_tol(self, nsteps: int, tol: float, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Advance nsteps steps and flag, on the device, each member whose residual
+        of the last step is below tol (bit 0) or whose phi went non-finite (bit 1).
+        The flags land in `out` (pinned host int32 by default) in stream order:
+        synchronise the batch stream before reading them."""
+        if out is None:
+            out = torch.empty(len(self.members), dtype=torch.int32, pin_memory=True)
+        C.check(self.lib.btrt_batch_step_tol(self.handle, int(nsteps), float(tol),
+                                             ctypes.c_void_p(out.data_ptr()), 1 if out.is_cuda else 0))
+        return out
 
     def member_flags(self) -> np.ndarray:
         """Each member's device flags (bit 0: non-finite phi)."""

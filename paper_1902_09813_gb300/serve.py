@@ -3,10 +3,11 @@
 Requests (lattice problems) arrive over time.  The server admits them while the
 device-memory budget allows, keeps every admitted lattice resident, and
 advances all active lattices together in slices of ``slice_steps`` steps with
-one persistent batched launch per slice (:class:`~.lattice.Batch`).  At every
-slice boundary it reads each member's steady-state residual
-||phi^{n+1} - phi^n||_2 (computed on the device in the last step of the slice),
-retires the members that converged (residual < tol) or reached ``max_steps``,
+one batched launch (a CUDA graph) per slice (:class:`~.lattice.Batch`).  The
+device computes each member's steady-state residual ||phi^{n+1} - phi^n||_2 in
+the slice's last step and compares it with the tolerance; at every slice
+boundary the server reads those flags, retires the members that converged
+(residual < tol), went non-finite or reached ``max_steps``,
 copies their phi to the host, frees their memory and admits waiting requests.
 Requests that arrive while others run therefore join at the next boundary and
 share the device with them.
@@ -25,7 +26,7 @@ from typing import List, Optional
 import numpy as np
 import torch
 
-from .lattice import Batch, Lattice, grid_desc, workspace_bytes
+from .lattice import Batch, Lattice, batch_workspace_bytes, grid_desc, workspace_bytes
 
 
 @dataclasses.dataclass
@@ -36,18 +37,28 @@ class Result:
     finished: float
     steps: int
     residual: float
-    phi: np.ndarray
-    status: str = "done"     # "unstable": a non-finite phi appeared; the request was retired alone
+    phi: Optional[np.ndarray]
+    status: str = "done"     # "unstable": a non-finite phi appeared; the request was retired alone;
+                             # "rejected": it needs more device memory than the whole budget (no phi)
 
     @property
     def latency(self) -> float:
         return self.finished - self.arrival
 
 
-def _bytes_needed(p, compute, storage) -> int:
+def _desc(p, compute, storage):
     # the workspace size does not depend on the stored form
-    d = grid_desc(p.nx, p.ny, p.dx, p.dt, p.bc, compute, storage, p.x0, p.y0, p.phi_ref)
-    return workspace_bytes(d)
+    return grid_desc(p.nx, p.ny, p.dx, p.dt, p.bc, compute, storage, p.x0, p.y0, p.phi_ref)
+
+
+def _bytes_needed(p, compute, storage) -> int:
+    return workspace_bytes(_desc(p, compute, storage))
+
+
+def _batch_bytes(problems, compute, storage) -> int:
+    """Device bytes of the batch tables (descriptors, tiles, step table, reduction
+    scratch) for a batch of these problems."""
+    return batch_workspace_bytes([_desc(p, compute, storage) for p in problems]) if problems else 0
 
 
 class Server:
@@ -62,67 +73,102 @@ class Server:
         self.max_active = max_active
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self.tiles = tiles
-        self.stats = dict(slices=0, rebuilds=0, peak_active=0, peak_bytes=0)
+        self.stats = dict(slices=0, rebuilds=0, peak_active=0, peak_bytes=0, rejected=0, tol_hits=0,
+                          cap_hits=0, unstable=0, gpu_busy_s=0.0, admit_s=0.0, rebuild_s=0.0, span_s=0.0)
         self.depth = []        # (t, active, waiting) at every slice
+        self._flags = None     # pinned stop flags, see _flag_buffer
 
     def run(self, trace) -> List[Result]:
         """trace: list of (arrival_seconds, problem), arrival-sorted.  Runs in real
-        time: a request becomes visible once the wall clock passes its arrival."""
+        time: a request becomes visible once the wall clock passes its arrival.
+
+        Admission counts every active lattice's workspace and the batch tables of
+        the membership it would join; a request that needs more than the whole
+        budget on its own is rejected (status "rejected").  The stats record the
+        device's busy time (CUDA events around every slice), the host time spent
+        admitting and rebuilding batches, and how many requests stopped at the
+        tolerance or at the step cap."""
         t0 = time.perf_counter()
         pending = deque((i, a, p) for i, (a, p) in enumerate(trace))
         waiting = deque()
-        active = []            # [rid, arrival, admitted, lattice, bytes, steps]
+        active = []            # [rid, arrival, admitted, lattice, bytes, steps, problem]
         used = 0.0
         results: List[Result] = []
         batch: Optional[Batch] = None
         dirty = True
+        st = self.stats
         while pending or waiting or active:
             now = time.perf_counter() - t0
             while pending and pending[0][1] <= now:
                 waiting.append(pending.popleft())
             # admission by memory budget (and a cap on members)
+            ta = time.perf_counter()
             while waiting and len(active) < self.max_active:
                 rid, arr, p = waiting[0]
                 need = _bytes_needed(p, self.compute, self.storage)
-                if used + need > self.budget and active:
+                if need + _batch_bytes([p], self.compute, self.storage) > self.budget:
+                    waiting.popleft()      # can never fit: reject rather than break the budget
+                    results.append(Result(rid, arr, now, time.perf_counter() - t0, 0, float("nan"), None,
+                                          "rejected"))
+                    st["rejected"] += 1
+                    continue
+                tables = _batch_bytes([a[6] for a in active] + [p], self.compute, self.storage)
+                if used + need + tables > self.budget:
                     break
                 waiting.popleft()
                 lat = Lattice.from_problem(p, compute=self.compute, storage=self.storage,
                                            stream=self.stream, shift=self.shift)
                 lat.init(p.phi0(), t0=p.t0)
                 used += need
-                active.append([rid, arr, time.perf_counter() - t0, lat, need, 0])
+                active.append([rid, arr, time.perf_counter() - t0, lat, need, 0, p])
                 dirty = True
-            self.stats["peak_active"] = max(self.stats["peak_active"], len(active))
-            self.stats["peak_bytes"] = max(self.stats["peak_bytes"], used)
+            st["admit_s"] += time.perf_counter() - ta
+            st["peak_active"] = max(st["peak_active"], len(active))
+            tables = _batch_bytes([a[6] for a in active], self.compute, self.storage)
+            st["peak_bytes"] = max(st["peak_bytes"], used + tables)
             if not active:
                 if pending:   # idle until the next arrival
                     time.sleep(max(0.0, min(0.002, pending[0][1] - (time.perf_counter() - t0))))
                 continue
             if dirty:
+                tr = time.perf_counter()
                 if batch is not None:
                     batch.close()
                 batch = Batch([a[3] for a in active], stream=self.stream)
                 if self.tiles:
                     batch.set_tiles(*self.tiles)
-                self.stats["rebuilds"] += 1
+                st["rebuilds"] += 1
+                st["rebuild_s"] += time.perf_counter() - tr
                 dirty = False
-            batch.step(self.slice_steps, residual=True)
-            res = batch.residuals()          # synchronises
-            bad = batch.member_flags() & 1   # non-finite phi in that member only
-            self.stats["slices"] += 1
+            ev0, ev1 = _event(), _event()
+            _record(ev0, self.stream)
+            # the slice, then the tolerance test and non-finite check on the device
+            ft = batch.step_tol(self.slice_steps, self.tol, out=self._flag_buffer(len(active)))
+            _record(ev1, self.stream)
+            res = batch.residuals()          # synchronises: the flags have landed too
+            flags = np.array(ft)
+            st["gpu_busy_s"] += _elapsed_s(ev0, ev1)
+            bad = flags & 2                  # non-finite phi in that member only
+            st["slices"] += 1
             self.depth.append((round(time.perf_counter() - t0, 4), len(active), len(waiting) + len(pending)))
             done_idx = []
             for k, a in enumerate(active):
                 a[5] += self.slice_steps
-                if bad[k] or res[k] < self.tol or a[5] >= self.max_steps:
+                if bad[k] or (flags[k] & 1) or a[5] >= self.max_steps:
                     done_idx.append(k)
             if done_idx:
                 for k in reversed(done_idx):
-                    rid, arr, adm, lat, need, steps = active[k]
+                    rid, arr, adm, lat, need, steps, _ = active[k]
                     phi = lat.phi_host()
+                    status = "unstable" if bad[k] else "done"
+                    if status == "unstable":
+                        st["unstable"] += 1
+                    elif flags[k] & 1:
+                        st["tol_hits"] += 1
+                    else:
+                        st["cap_hits"] += 1
                     results.append(Result(rid, arr, adm, time.perf_counter() - t0, steps,
-                                          float(res[k]), phi, "unstable" if bad[k] else "done"))
+                                          float(res[k]), phi, status))
                     used -= need
                     del active[k]
                 batch.close()
@@ -130,8 +176,35 @@ class Server:
                 dirty = True
         if batch is not None:
             batch.close()
+        st["span_s"] = time.perf_counter() - t0
         results.sort(key=lambda r: r.rid)
         return results
+
+    def _flag_buffer(self, n: int):
+        """Pinned host memory for the per-member stop flags of a slice (reused)."""
+        if not torch.cuda.is_available():
+            return None
+        if self._flags is None or self._flags.numel() < n:
+            self._flags = torch.empty(max(n, 256), dtype=torch.int32, pin_memory=True)
+        return self._flags[:n]
+
+    def idle_fraction(self) -> float:
+        """Share of the run's wall time in which no slice was running on the device."""
+        span = self.stats["span_s"]
+        return 0.0 if span <= 0 else max(0.0, 1.0 - self.stats["gpu_busy_s"] / span)
+
+
+def _event():
+    return torch.cuda.Event(enable_timing=True) if torch.cuda.is_available() else None
+
+
+def _record(ev, stream):
+    if ev is not None:
+        ev.record(stream)
+
+
+def _elapsed_s(e0, e1) -> float:
+    return 0.0 if e0 is None else e0.elapsed_time(e1) * 1e-3
 
 
 def serve_sequential(trace, slice_steps: int = 100, max_steps: int = 20000, tol: float = 1e-8,

@@ -52,7 +52,9 @@ def test_stale_captures_are_reported_as_null(monkeypatch):
     assert r["traffic"] is None and r["dram_bytes_per_update"] is None
 
 
-def test_two_step_roofline_reports_measured_dram_bytes():
+def test_two_step_roofline_reports_measured_dram_bytes(monkeypatch):
+    # as if the capture were of the current two-step sources
+    monkeypatch.setattr(bench, "TB2_DIGEST", bench.source_digest(bench.TB2_SOURCES))
     nodes, t = 8192 * 8192, 0.536e-3
     args = _args(compute="f32", storage="f32", shift="ref")
     assert bench.two_step_form(args)
@@ -61,9 +63,25 @@ def test_two_step_roofline_reports_measured_dram_bytes():
     assert r["dram_bytes_per_update"] == bench.TB2_DRAM_BYTES_PER_UPDATE[("f32", "ref")]
     assert r["traffic"] == round(r["dram_bytes_per_update"] * 2 * nodes)   # one launch = two steps
     assert r["frac"] > 1.0   # algorithmic one-step bytes over the copy peak
-    # the local shift is the default for 16-bit storage
-    r16 = bench.roofline(_args(compute="f32", storage="f16"), nodes, t, 1.0, 6800.0, "measured")
+    # the local shift is the default for 16-bit storage (two-step form asked for)
+    r16 = bench.roofline(_args(compute="f32", storage="f16", sweep="tb2"), nodes, t, 1.0, 6800.0, "measured")
     assert r16["dram_bytes_per_update"] == bench.TB2_DRAM_BYTES_PER_UPDATE[("f16", "local")]
+
+
+def test_auto_kernel_form_follows_the_library():
+    """AUTO resolves as the library does: the vector form for FP16/BF16 storage,
+    two steps per launch for FP32 storage, the plain sweep for FP64 and
+    double-word."""
+    assert bench.kernel_form(_args(compute="f32", storage="f16")) == "vec"
+    assert bench.kernel_form(_args(compute="f32", storage="bf16")) == "vec"
+    assert bench.kernel_form(_args(compute="f32", storage="f32")) == "tb2"
+    assert bench.kernel_form(_args(compute="f32", storage="f16", workload="nonlinear")) == "vec"
+    assert bench.two_step_form(_args(compute="f32", storage="f16", sweep="tb2v"))
+    assert bench.kernel_form(_args()) == "plain"
+    assert bench.kernel_form(_args(compute="df64", storage="df64")) == "plain"
+    assert bench.kernel_form(_args(compute="f32", storage="f16", sweep="plain")) == "plain"
+    r = bench.roofline(_args(compute="f32", storage="f16"), 4096 * 4096, 1e-3, 6000.0, 6800.0, "measured")
+    assert r["bound"] == "hbm" and r["kernel"].startswith("sweep_vec_kernel") and r["bytes_per_update"] == 44
 
 
 def test_one_step_forms_and_launch_counts():

@@ -204,6 +204,38 @@ def test_autotune_keeps_results():
     b.close()
 
 
+def test_step_tol_flags_match_residuals_and_nonfinite():
+    """btrt_batch_step_tol: bit 0 exactly where the member's residual of the last
+    step is below tol, bit 1 for the member whose initial field holds a NaN (a
+    failure made on the host); flags in pinned host memory and in device memory
+    agree, and the members advance as with btrt_batch_step."""
+    import torch
+    from paper_1902_09813_gb300 import Batch
+    probs = _mix("f32", "f16", count=6, seed=29)
+    mixed = [_make(p, "f32", "f16", "local") for p in probs]
+    bad = w.random_state_problem(24, 20, seed=4, bc=(1, 1, 0, 0))
+    arr = bad.phi0()
+    arr[3, 4] = float("nan")
+    lat_bad = _make(bad.replace(phi0_array=arr), "f32", "f16", "local")
+    b = Batch(mixed + [lat_bad])
+    flags = b.step_tol(10, tol=1e30)
+    torch.cuda.synchronize()
+    f = flags.numpy()
+    assert list(f[:-1] & 2) == [0] * len(mixed) and f[-1] & 2 == 2
+    r = b.residuals()
+    tol = float(np.median(r[:-1]))
+    flags = b.step_tol(4, tol=tol)
+    dev = torch.empty(len(mixed) + 1, dtype=torch.int32, device="cuda")
+    r = b.residuals()            # synchronises: the pinned flags are ready
+    f = flags.numpy().copy()
+    assert list(f[:-1] & 1) == [1 if v < tol else 0 for v in r[:-1]]
+    b.step_tol(1, tol=tol, out=dev)
+    r1 = b.residuals()
+    assert list(dev.cpu().numpy()[:-1] & 1) == [1 if v < tol else 0 for v in r1[:-1]]
+    assert mixed[0].time()[0] == 15
+    b.close()
+
+
 def test_barrier_timeout_reported():
     """A barrier that can never be released ends the launch after the wait limit
     with BTRT_ETIMEOUT (no hang, no device fault); the device stays usable."""

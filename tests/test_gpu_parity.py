@@ -425,10 +425,12 @@ def test_tb2_sweep_other_storage_bitwise_equals_plain(case, storage, shift):
     _tb2_against_plain(case, 9, storage, shift)
 
 
-def test_default_form_bitwise_equals_plain():
-    """AUTO (the default; the two-step form for FP32 compute) and the plain form
-    give the same bits on a walled nonlinear lattice with FP16 storage."""
-    p = w.random_state_problem(64, 40, seed=31, bc=(1, 1, 0, 0), nonlinear=True, source="const")
+@pytest.mark.parametrize("nonlinear", [True, False])
+def test_default_form_bitwise_equals_plain(nonlinear):
+    """AUTO (the default: the vector form for 16-bit storage) and the plain form
+    give the same bits on a walled lattice with FP16 storage, for constant and
+    per-node coefficients."""
+    p = w.random_state_problem(64, 40, seed=31, bc=(1, 1, 0, 0), nonlinear=nonlinear, source="const")
     a = _lattice(p, "f32", "f16", shift="local")
     b = _lattice(p, "f32", "f16", shift="local").set_sweep_variant("plain")
     a.init(p.phi0(), t0=p.t0).step(8)

@@ -46,6 +46,11 @@ class _FakeBatch:
     def residuals(self):
         return np.array([lat.p.meta["rate"] ** lat.steps for lat in self.lats])
 
+    def step_tol(self, n, tol, out=None):
+        self.step(n, residual=True)
+        conv = (self.residuals() < tol).astype(np.int32)
+        return conv | (2 * self.member_flags().astype(np.int32))
+
     def member_flags(self):
         return np.array([1 if lat.steps >= lat.p.meta.get("bad_at", 1 << 30) else 0 for lat in self.lats])
 
@@ -72,7 +77,8 @@ def _problems(rates, n=32):
 def test_budget_admission_and_retirement(fakes):
     probs = _problems([0.5, 0.9, 0.99, 0.5])
     need = serve._bytes_needed(probs[0], "f32", "f16")
-    srv = serve.Server(budget_bytes=2.5 * need, slice_steps=10, max_steps=200, tol=1e-6, stream=object())
+    budget = 2.5 * need + serve._batch_bytes(probs[:2], "f32", "f16")   # two lattices and their tables
+    srv = serve.Server(budget_bytes=budget, slice_steps=10, max_steps=200, tol=1e-6, stream=object())
     res = srv.run([(0.0, p) for p in probs])
     assert [r.rid for r in res] == [0, 1, 2, 3]
     assert srv.stats["peak_active"] == 2
@@ -89,6 +95,45 @@ def test_budget_admission_and_retirement(fakes):
     assert res[2].residual > 1e-6 and res[2].steps == 200   # the cap, not the tolerance
     # waiting requests are admitted as members retire: every request ran, never more than two at once
     assert max(d[1] for d in srv.depth) == 2 and srv.depth[0][2] == 2
+
+
+def test_oversized_request_rejected_and_budget_kept(fakes):
+    """A request whose workspace and batch tables alone exceed the budget is
+    rejected (status "rejected", no phi) instead of being admitted past the budget;
+    the others run, and the peak of lattice workspaces plus batch tables never
+    exceeds the budget."""
+    probs = _problems([0.5, 0.5, 0.5])
+    big = w.random_state_problem(400, 300, seed=5)
+    big.meta = dict(big.meta, rate=0.5)
+    small = serve._bytes_needed(probs[0], "f32", "f16")
+    budget = 2 * small + serve._batch_bytes(probs[:2], "f32", "f16")
+    assert serve._bytes_needed(big, "f32", "f16") > budget
+    srv = serve.Server(budget_bytes=budget, slice_steps=10, max_steps=100, tol=1e-6, stream=object())
+    res = srv.run([(0.0, probs[0]), (0.0, big), (0.0, probs[1]), (0.0, probs[2])])
+    assert [r.status for r in res] == ["done", "rejected", "done", "done"]
+    assert res[1].phi is None and srv.stats["rejected"] == 1
+    assert srv.stats["peak_bytes"] <= budget
+    assert srv.stats["peak_active"] == 2
+
+
+def test_batch_tables_counted_in_admission(fakes):
+    """Two lattices fit the budget only without their batch tables: the second
+    waits for the first to retire."""
+    probs = _problems([0.5, 0.5])
+    need = serve._bytes_needed(probs[0], "f32", "f16")
+    budget = 2 * need + serve._batch_bytes(probs[:1], "f32", "f16")   # less than the two-member tables
+    assert 2 * need + serve._batch_bytes(probs, "f32", "f16") > budget
+    srv = serve.Server(budget_bytes=budget, slice_steps=10, max_steps=100, tol=1e-6, stream=object())
+    res = srv.run([(0.0, p) for p in probs])
+    assert [r.status for r in res] == ["done", "done"]
+    assert srv.stats["peak_active"] == 1 and srv.stats["peak_bytes"] <= budget
+
+
+def test_stop_reasons_counted(fakes):
+    probs = _problems([0.5, 0.999])
+    srv = serve.Server(budget_bytes=1e12, slice_steps=10, max_steps=50, tol=1e-6, stream=object())
+    srv.run([(0.0, p) for p in probs])
+    assert srv.stats["tol_hits"] == 1 and srv.stats["cap_hits"] == 1
 
 
 def test_unstable_member_retired_alone(fakes):
