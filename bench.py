@@ -91,8 +91,8 @@ TB2_DRAM_BYTES_PER_UPDATE = {("f32", "ref"): 38.6, ("f16", "local"): 20.9}
 # DRAM bytes per node of one launch of the vector-access sweep measured by ncu,
 # keyed by (storage, shift), for the sources with digest VEC_DIGEST.
 VEC_SOURCES = ("btrt_sweep.cuh", "btrt_vec.cuh", "btrt_launch.cuh")
-VEC_DIGEST = "unset"
-VEC_DRAM_BYTES_PER_UPDATE = {}
+VEC_DIGEST = "0a77a67ce126cfd9"
+VEC_DRAM_BYTES_PER_UPDATE = {("f16", "local"): 41.3}
 
 
 def measure_fp64_peak(iters: int = 2000):
@@ -127,13 +127,14 @@ def measure_fp64_peak(iters: int = 2000):
 
 def kernel_form(args) -> str:
     """The kernel form of the timed steps: what the library's AUTO resolves to for
-    FP32 compute (the vector form for FP16/BF16 storage, two steps per launch for
-    FP32 storage), the form asked for, or the plain sweep."""
+    FP32 compute (the vector form for FP16/BF16 storage on lattices of 2^21 nodes
+    or more, two steps per launch otherwise), the form asked for, or the plain
+    sweep."""
     if args.compute != "f32":
         return "plain"
     if args.sweep != "auto":
         return args.sweep
-    return "vec" if args.storage in ("f16", "bf16") else "tb2"
+    return "vec" if args.storage in ("f16", "bf16") and args.n * args.n >= 1 << 21 else "tb2"
 
 
 def two_step_form(args) -> bool:

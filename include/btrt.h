@@ -180,8 +180,8 @@ btrt_status btrt_mass(btrt_lattice L, double *out);
 btrt_status btrt_check(btrt_lattice L, int32_t *flags);
 
 /* Kernel form of the ordinary FP32-compute sweep: BTRT_SWEEP_AUTO (default: the
- * faster form as measured on GB300: BTRT_SWEEP_VEC for F16/BF16 storage,
- * BTRT_SWEEP_TB2 for F32 storage), BTRT_SWEEP_PLAIN
+ * faster form as measured on GB300: BTRT_SWEEP_VEC for F16/BF16 storage on
+ * lattices of 2^21 nodes or more, BTRT_SWEEP_TB2 otherwise), BTRT_SWEEP_PLAIN
  * (one step per launch, direct global loads served by L1/L2), BTRT_SWEEP_TMA
  * (persistent tiles staged in shared memory by TMA with mbarrier pipelining) or
  * BTRT_SWEEP_TB2 (two time steps per launch: the first step's populations stay

@@ -350,12 +350,18 @@ int btrt::sweep_mode(btrt_lattice L) {
 // GLUPS against 119-141 for the two-step forms; nonlinear workload 117-130
 // against 77-116), the scalar two-step form for FP32 storage (116-124 and
 // 103-114 GLUPS against 110-117 and 69-79 with vector access, 80-86 for one step
-// per launch).
+// per launch).  Lattices below kVecAutoNodes nodes take the two-step form with
+// every storage: a step there lasts a few microseconds, launches dominate, and
+// two steps per launch halve them (512 instances of 32^2 to 1024^2 nodes, 2000
+// steps each, one after the other: 10.5 s with the vector form, 6.8 s with two
+// steps per launch).
+constexpr long long kVecAutoNodes = 1LL << 21;
 int btrt::effective_sweep_variant(btrt_lattice L) {
     if (L->g.compute != BTRT_F32) return BTRT_SWEEP_PLAIN;
     if (L->sweep_variant != BTRT_SWEEP_AUTO) return L->sweep_variant;
     const bool s16 = L->g.storage == BTRT_F16 || L->g.storage == BTRT_BF16;
-    return s16 ? BTRT_SWEEP_VEC : BTRT_SWEEP_TB2;
+    const bool large = (long long)L->g.nx * L->g.ny >= kVecAutoNodes;
+    return s16 && large ? BTRT_SWEEP_VEC : BTRT_SWEEP_TB2;
 }
 
 namespace {

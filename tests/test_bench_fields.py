@@ -8,7 +8,7 @@ import bench
 
 
 def _args(**kw):
-    a = dict(compute="f64", storage="f64", workload="mms", shift="auto", sweep="auto", steps=1000)
+    a = dict(compute="f64", storage="f64", workload="mms", shift="auto", sweep="auto", steps=1000, n=8192)
     a.update(kw)
     return argparse.Namespace(**a)
 
@@ -69,14 +69,15 @@ def test_two_step_roofline_reports_measured_dram_bytes(monkeypatch):
 
 
 def test_auto_kernel_form_follows_the_library():
-    """AUTO resolves as the library does: the vector form for FP16/BF16 storage,
-    two steps per launch for FP32 storage, the plain sweep for FP64 and
-    double-word."""
+    """AUTO resolves as the library does: the vector form for FP16/BF16 storage on
+    large lattices, two steps per launch for FP32 storage and small lattices, the
+    plain sweep for FP64 and double-word."""
     assert bench.kernel_form(_args(compute="f32", storage="f16")) == "vec"
     assert bench.kernel_form(_args(compute="f32", storage="bf16")) == "vec"
     assert bench.kernel_form(_args(compute="f32", storage="f32")) == "tb2"
     assert bench.kernel_form(_args(compute="f32", storage="f16", workload="nonlinear")) == "vec"
     assert bench.two_step_form(_args(compute="f32", storage="f16", sweep="tb2v"))
+    assert bench.kernel_form(_args(compute="f32", storage="f16", n=1024)) == "tb2"   # small: fewer launches
     assert bench.kernel_form(_args()) == "plain"
     assert bench.kernel_form(_args(compute="df64", storage="df64")) == "plain"
     assert bench.kernel_form(_args(compute="f32", storage="f16", sweep="plain")) == "plain"

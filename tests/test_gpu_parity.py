@@ -427,10 +427,17 @@ def test_tb2_sweep_other_storage_bitwise_equals_plain(case, storage, shift):
 
 @pytest.mark.parametrize("nonlinear", [True, False])
 def test_default_form_bitwise_equals_plain(nonlinear):
-    """AUTO (the default: the vector form for 16-bit storage) and the plain form
-    give the same bits on a walled lattice with FP16 storage, for constant and
-    per-node coefficients."""
+    """AUTO (the default: the vector form for 16-bit storage on lattices of 2^21
+    nodes or more, two steps per launch below) and the plain form give the same
+    bits on walled lattices with FP16 storage, for constant and per-node
+    coefficients."""
     p = w.random_state_problem(64, 40, seed=31, bc=(1, 1, 0, 0), nonlinear=nonlinear, source="const")
+    q = w.random_state_problem(2100, 1000, seed=32, bc=(1, 1, 0, 0), nonlinear=nonlinear, source="const")
+    a = _lattice(q, "f32", "f16", shift="local")
+    b = _lattice(q, "f32", "f16", shift="local").set_sweep_variant("plain")
+    a.init(q.phi0(), t0=q.t0).step(5)
+    b.init(q.phi0(), t0=q.t0).step(5)
+    assert np.array_equal(a.phi_host(), b.phi_host())
     a = _lattice(p, "f32", "f16", shift="local")
     b = _lattice(p, "f32", "f16", shift="local").set_sweep_variant("plain")
     a.init(p.phi0(), t0=p.t0).step(8)
