@@ -81,7 +81,7 @@ FP64_NOMINAL_TOPS = 0.625
 # to them both are re-taken and the digest updated (a CPU test checks it), and
 # until then the traffic is reported as null.
 FP64_SWEEP_SOURCES = ("btrt_sweep.cuh", "btrt_dw.cuh")   # the FP64 sweep's device code
-FP64_SWEEP_DIGEST = "6164d767545f1816"
+FP64_SWEEP_DIGEST = "2254efa133f17e57"
 FP64_TRAFFIC_PER_NODE = 149.3
 # DRAM bytes per node and step of the two-step FP32-compute kernel measured by ncu,
 # keyed by (storage, shift), for the sources with digest TB2_DIGEST.
@@ -130,7 +130,7 @@ def kernel_form(args) -> str:
     FP32 compute (the vector form for FP16/BF16 storage on lattices of 2^21 nodes
     or more, two steps per launch otherwise), the form asked for, or the plain
     sweep."""
-    if args.compute != "f32":
+    if args.compute != "f32" or args.shift == "local_dw":
         return "plain"
     if args.sweep != "auto":
         return args.sweep
@@ -444,6 +444,8 @@ def run_variants(args, steps=200, warmup=5):
                 out[f"{name}_f32_{st}{tag}_tb2v"] = _time_single(prob, a, "f32", st, steps, warmup,
                                                                 variant="tb2v", shift=sh)
             out[f"{name}_f32_{st}_tma"] = _time_single(prob, a, "f32", st, steps, warmup, variant="tma")
+            # phi as a double-word pair (plain form)
+            out[f"{name}_f32_{st}_local_dw"] = _time_single(prob, a, "f32", st, steps, warmup, shift="local_dw")
     out["nonlinear_f64"] = _time_single(q, q_phi0, "f64", "f64", 50, 3)
     out.update(run_d3q19(args))
     out.update(run_extended(args))
@@ -536,7 +538,8 @@ def _final_phi(p, phi0, compute, storage, steps, shift="ref"):
 
 
 REDUCED = [("df64", "df64", "ref"), ("f32", "f32", "ref"), ("f32", "f32", "local"), ("f32", "f16", "ref"),
-           ("f32", "f16", "local"), ("f32", "bf16", "ref"), ("f32", "bf16", "local")]
+           ("f32", "f16", "local"), ("f32", "bf16", "ref"), ("f32", "bf16", "local"),
+           ("f32", "f32", "local_dw"), ("f32", "f16", "local_dw"), ("f32", "bf16", "local_dw")]
 
 
 def _fmt_key(c, s, sh):
@@ -853,7 +856,7 @@ def main():
     ap.add_argument("--n", type=int, default=N_MAIN)
     ap.add_argument("--compute", default="f64", choices=["f64", "df64", "f32"])
     ap.add_argument("--storage", default=None, choices=["f64", "df64", "f32", "f16", "bf16"])
-    ap.add_argument("--shift", default="auto", choices=["auto", "ref", "local"],
+    ap.add_argument("--shift", default="auto", choices=["auto", "ref", "local", "local_dw"],
                     help="stored form of F32/F16/BF16 populations")
     ap.add_argument("--sweep", default="auto", choices=["auto", "plain", "tma", "tb2", "vec", "tb2v"],
                     help="kernel form of FP32-compute sweeps")

@@ -68,8 +68,14 @@ enum { BTRT_SIDE_XMIN = 0, BTRT_SIDE_XMAX = 1, BTRT_SIDE_YMIN = 2, BTRT_SIDE_YMA
  *                    from the previous phi plane.  What is rounded is then of the
  *                    size of the non-equilibrium part only, which keeps F16/BF16
  *                    storage far closer to the FP32-storage result.
+ *  BTRT_SHIFT_LOCAL_DW as BTRT_SHIFT_LOCAL, with phi kept as a double-word pair
+ *                    (two FP32 planes, high and low word; 8 more bytes per update):
+ *                    phi is never rounded to FP32, which under diffusive scaling on
+ *                    fine grids (a step changes phi by a few FP32 ulps) keeps FP32
+ *                    storage within the FP64 discretisation error.  Plain kernel
+ *                    form only (BTRT_SWEEP_AUTO / PLAIN); not in batches.
  * FP64 and double-word storage are never shifted. */
-enum { BTRT_SHIFT_REF = 0, BTRT_SHIFT_LOCAL = 1 };
+enum { BTRT_SHIFT_REF = 0, BTRT_SHIFT_LOCAL = 1, BTRT_SHIFT_LOCAL_DW = 2 };
 
 typedef struct btrt_lattice_s *btrt_lattice;
 
@@ -84,7 +90,7 @@ typedef struct {
     double x0, y0;         /* physical position of the lower-left domain corner         */
     double phi_ref;        /* BTRT_SHIFT_REF: F32/F16/BF16 storage holds f_i - w_i phi_ref  */
     int32_t fields;        /* BTRT_FIELD_* bits: reserve per-node source / diffusion planes */
-    int32_t shift;         /* BTRT_SHIFT_REF or BTRT_SHIFT_LOCAL (F32/F16/BF16 storage)   */
+    int32_t shift;         /* BTRT_SHIFT_REF, _LOCAL or _LOCAL_DW (F32/F16/BF16 storage)  */
 } btrt_grid_desc;
 
 /* Coefficients of Eq. 1 and the relaxation parameters (physical units). */

@@ -15,6 +15,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/btrt.h"
@@ -110,8 +111,10 @@ btrt_status check_desc(const btrt_grid_desc *g) {
         return fail(BTRT_EINVAL, "phi_ref, x0, y0 must be finite");
     if (g->fields & ~(BTRT_FIELD_SOURCE | BTRT_FIELD_DIFFUSION))
         return fail(BTRT_EINVAL, "unknown field bits 0x%x", g->fields);
-    if (g->shift != BTRT_SHIFT_REF && g->shift != BTRT_SHIFT_LOCAL)
+    if (g->shift != BTRT_SHIFT_REF && g->shift != BTRT_SHIFT_LOCAL && g->shift != BTRT_SHIFT_LOCAL_DW)
         return fail(BTRT_EINVAL, "unknown storage shift %d", g->shift);
+    if (g->shift == BTRT_SHIFT_LOCAL_DW && g->compute != BTRT_F32)
+        return fail(BTRT_EINVAL, "the double-word phi planes of BTRT_SHIFT_LOCAL_DW serve FP32 compute");
     const long long pitch = (long long)((g->nx + 63) / 64) * 64;
     if (9 * pitch * (long long)g->ny >= (1LL << 31))
         return fail(BTRT_EINVAL, "grid %d x %d: the nine padded planes must hold fewer than 2^31 values "
@@ -132,9 +135,11 @@ Layout make_layout(const btrt_grid_desc *g) {
     off += L.fbuf_bytes;
     L.off_f[1] = off;
     off += L.fbuf_bytes;
+    // a double-word phi (BTRT_SHIFT_LOCAL_DW) keeps its low words in a second plane
+    const size_t phi_planes = g->shift == BTRT_SHIFT_LOCAL_DW ? 2 : 1;
     for (int k = 0; k < 2; ++k) {
         L.off_phi[k] = off;
-        off += align_up((size_t)L.plane * sr, kAlign);
+        off += align_up(phi_planes * (size_t)L.plane * sr, kAlign);
     }
     L.off_tab = off;
     off += align_up(2 * ((size_t)g->nx + (size_t)g->ny) * sr, kAlign);
@@ -164,6 +169,28 @@ __global__ void dense_to_plane(const In *__restrict__ src, Real *__restrict__ ds
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y;
     if (x < nx && y < ny) dst[(long long)y * pitch + x] = Real((double)src[(long long)y * nx + x]);
+}
+
+// Low words of a double-word phi plane: v - (float)v, rounded to FP32.
+template <typename In>
+__global__ void dense_to_plane_lo(const In *__restrict__ src, float *__restrict__ lo, int nx, int ny,
+                                  long long pitch) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x < nx && y < ny) {
+        const double v = (double)src[(long long)y * nx + x];
+        lo[(long long)y * pitch + x] = (float)(v - (double)(float)v);
+    }
+}
+
+// A double-word phi plane (high and low words) as dense FP64 or FP32 values.
+template <typename Out>
+__global__ void dw_planes_to_dense(const float *__restrict__ hi, const float *__restrict__ lo, Out *__restrict__ dst,
+                                   int nx, int ny, long long pitch) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x < nx && y < ny)
+        dst[(long long)y * nx + x] = (Out)((double)hi[(long long)y * pitch + x] + (double)lo[(long long)y * pitch + x]);
 }
 
 template <typename Real, typename Out>
@@ -244,6 +271,10 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
     p.fout = L->fbuf(first ? L->cur : 1 - L->cur);
     p.phi_in = L->phi<Real>(L->cur);
     p.phi_out = L->phi<Real>(first ? L->cur : 1 - L->cur);
+    if constexpr (std::is_same<Real, float>::value) {
+        p.phi_in_lo = L->phi_lo(L->cur);
+        p.phi_out_lo = L->phi_lo(first ? L->cur : 1 - L->cur);
+    }
     p.nx = g.nx;
     p.ny = g.ny;
     p.pitch = (int)L->lay.pitch;
@@ -357,7 +388,7 @@ int btrt::sweep_mode(btrt_lattice L) {
 // steps per launch).
 constexpr long long kVecAutoNodes = 1LL << 21;
 int btrt::effective_sweep_variant(btrt_lattice L) {
-    if (L->g.compute != BTRT_F32) return BTRT_SWEEP_PLAIN;
+    if (L->g.compute != BTRT_F32 || L->g.shift == BTRT_SHIFT_LOCAL_DW) return BTRT_SWEEP_PLAIN;
     if (L->sweep_variant != BTRT_SWEEP_AUTO) return L->sweep_variant;
     const bool s16 = L->g.storage == BTRT_F16 || L->g.storage == BTRT_BF16;
     const bool large = (long long)L->g.nx * L->g.ny >= kVecAutoNodes;
@@ -462,6 +493,15 @@ btrt_status stage_phi0(btrt_lattice L, const void *phi0, int dtype, int on_devic
         dense_to_plane<Real, float><<<grd, blk, 0, L->stream>>>((const float *)dev_src, L->phi<Real>(0),
                                                                 g.nx, g.ny, L->lay.pitch);
     CUDA_TRY(cudaGetLastError());
+    if (L->phi_lo(0)) {
+        if (dtype == BTRT_F64)
+            dense_to_plane_lo<double><<<grd, blk, 0, L->stream>>>((const double *)dev_src, L->phi_lo(0), g.nx, g.ny,
+                                                                 L->lay.pitch);
+        else
+            dense_to_plane_lo<float><<<grd, blk, 0, L->stream>>>((const float *)dev_src, L->phi_lo(0), g.nx, g.ny,
+                                                                L->lay.pitch);
+        CUDA_TRY(cudaGetLastError());
+    }
     if (!on_device) CUDA_TRY(cudaStreamSynchronize(L->stream));  // host buffer may be reused
     return BTRT_OK;
 }
@@ -470,6 +510,27 @@ template <typename Real>
 btrt_status copy_phi_out(btrt_lattice L, void *dst, int dtype, int on_device) {
     const btrt_grid_desc &g = L->g;
     const size_t n = (size_t)g.nx * g.ny;
+    if (L->phi_lo(L->cur)) {
+        // double-word phi: high + low word, in FP64 (or rounded once to FP32)
+        const dim3 blk(256), grd((unsigned)((g.nx + 255) / 256), (unsigned)g.ny);
+        void *out = dst;
+        if (!on_device) {
+            if (n * elem_size(dtype) > L->lay.fbuf_bytes) return fail(BTRT_ENOMEM, "staging area too small");
+            out = L->fbuf(1 - L->cur);   // the other population buffer: rewritten by the next step anyway
+        }
+        if (dtype == BTRT_F64)
+            dw_planes_to_dense<double><<<grd, blk, 0, L->stream>>>(L->phi<float>(L->cur), L->phi_lo(L->cur),
+                                                                   (double *)out, g.nx, g.ny, L->lay.pitch);
+        else
+            dw_planes_to_dense<float><<<grd, blk, 0, L->stream>>>(L->phi<float>(L->cur), L->phi_lo(L->cur),
+                                                                  (float *)out, g.nx, g.ny, L->lay.pitch);
+        CUDA_TRY(cudaGetLastError());
+        if (!on_device) {
+            CUDA_TRY(cudaMemcpyAsync(dst, out, n * elem_size(dtype), cudaMemcpyDeviceToHost, L->stream));
+            CUDA_TRY(cudaStreamSynchronize(L->stream));
+        }
+        return BTRT_OK;
+    }
     if (on_device) {
         const dim3 blk(256), grd((unsigned)((g.nx + 255) / 256), (unsigned)g.ny);
         if (dtype == BTRT_F64)
@@ -505,6 +566,15 @@ btrt_status reduce_phi(btrt_lattice L, double *out) {
                                     L->stream));
     CUDA_TRY(cudaMemcpyAsync(out, L->red_out(), sizeof(double), cudaMemcpyDeviceToHost, L->stream));
     CUDA_TRY(cudaStreamSynchronize(L->stream));
+    if (L->phi_lo(L->cur)) {
+        // double-word phi: the low words' sum, same fixed order, added once
+        double lo = 0.0;
+        CUDA_TRY(enqueue_rows_sum<float>(L->phi_lo(L->cur), g.nx, g.ny, L->lay.pitch, L->partials(), L->red_out(),
+                                         L->stream));
+        CUDA_TRY(cudaMemcpyAsync(&lo, L->red_out(), sizeof(double), cudaMemcpyDeviceToHost, L->stream));
+        CUDA_TRY(cudaStreamSynchronize(L->stream));
+        *out += lo;
+    }
     return BTRT_OK;
 }
 
@@ -556,7 +626,7 @@ btrt_status btrt_create(const btrt_grid_desc *g, void *dev_workspace, size_t wor
         delete L;
         return fail(BTRT_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     }
-    if (g->compute == BTRT_F32) {
+    if (g->compute == BTRT_F32 && g->shift != BTRT_SHIFT_LOCAL_DW) {
         int bix, biy, box, boy;
         tma_box(g->storage, &bix, &biy, &box, &boy);
         bool ok = true;
@@ -773,12 +843,19 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
     std::vector<unsigned char> raw((size_t)w * h * sf);
     const double wts[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
     const int sh = shift_of(g);
-    std::vector<float> phiw;   // the nodes' phi, for the local shift (FP32 compute)
-    if (sh == kShiftLocal) {
+    std::vector<float> phiw, phiw_lo;   // the nodes' phi, for the local shifts (FP32 compute)
+    if (sh == kShiftLocal || sh == kShiftLocalDW) {
         phiw.resize((size_t)w * h);
         CUDA_TRY(cudaMemcpy2DAsync(phiw.data(), w * sizeof(float), L->phi<float>() + (size_t)y0 * L->lay.pitch + x0,
                                    L->lay.pitch * sizeof(float), w * sizeof(float), h, cudaMemcpyDeviceToHost,
                                    L->stream));
+        if (sh == kShiftLocalDW) {
+            phiw_lo.resize((size_t)w * h);
+            CUDA_TRY(cudaMemcpy2DAsync(phiw_lo.data(), w * sizeof(float),
+                                       L->phi_lo(L->cur) + (size_t)y0 * L->lay.pitch + x0,
+                                       L->lay.pitch * sizeof(float), w * sizeof(float), h, cudaMemcpyDeviceToHost,
+                                       L->stream));
+        }
         CUDA_TRY(cudaStreamSynchronize(L->stream));
     }
     for (int i = 0; i < 9; ++i) {
@@ -801,7 +878,9 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
             }
             else if (g.storage == BTRT_F32) { float fv; std::memcpy(&fv, &raw[k * 4], 4); v = fv; }
             else v = half_bits_to_double(g.storage, &raw[k * 2]);
-            const double loc = sh == kShiftLocal ? wts[i] * (double)phiw[k] : 0.0;
+            const double loc = sh == kShiftLocal     ? wts[i] * (double)phiw[k]
+                               : sh == kShiftLocalDW ? wts[i] * ((double)phiw[k] + (double)phiw_lo[k])
+                                                     : 0.0;
             dst[(size_t)i * w * h + k] = v + shift + loc;
         }
     }
@@ -835,6 +914,8 @@ btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant) {
         return fail(BTRT_EINVAL, "the two-step sweeps serve FP32-compute lattices");
     if (variant == BTRT_SWEEP_VEC && L->g.compute != BTRT_F32)
         return fail(BTRT_EINVAL, "the vector-access sweep serves FP32-compute lattices");
+    if (L->g.shift == BTRT_SHIFT_LOCAL_DW && variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN)
+        return fail(BTRT_EINVAL, "lattices with double-word phi planes (BTRT_SHIFT_LOCAL_DW) take the plain form");
     if (variant == BTRT_SWEEP_TMA && !L->have_tma)
         return fail(BTRT_EINVAL, "the TMA sweep serves FP32-compute lattices whose tensor maps could be encoded");
     L->sweep_variant = variant;
@@ -848,9 +929,14 @@ btrt_status btrt_get_time(btrt_lattice L, int64_t *step, double *t) {
     return BTRT_OK;
 }
 
+// Bytes of one phi buffer (both words of a double-word phi).
+static size_t phi_state_bytes(btrt_lattice L) {
+    return (L->g.shift == BTRT_SHIFT_LOCAL_DW ? 2 : 1) * (size_t)L->lay.plane * elem_size(L->g.compute);
+}
+
 size_t btrt_state_bytes(btrt_lattice L) {
     if (!L) return 0;
-    return sizeof(StateHeader) + L->lay.fbuf_bytes + (size_t)L->lay.plane * elem_size(L->g.compute);
+    return sizeof(StateHeader) + L->lay.fbuf_bytes + phi_state_bytes(L);
 }
 
 btrt_status btrt_save(btrt_lattice L, void *host_buf, size_t n) {
@@ -870,8 +956,8 @@ btrt_status btrt_save(btrt_lattice L, void *host_buf, size_t n) {
     std::memcpy(host_buf, &h, sizeof h);
     unsigned char *p = static_cast<unsigned char *>(host_buf) + sizeof h;
     CUDA_TRY(cudaMemcpyAsync(p, L->fbuf(L->cur), L->lay.fbuf_bytes, cudaMemcpyDeviceToHost, L->stream));
-    CUDA_TRY(cudaMemcpyAsync(p + L->lay.fbuf_bytes, L->ws + L->lay.off_phi[L->cur],
-                             (size_t)L->lay.plane * elem_size(L->g.compute), cudaMemcpyDeviceToHost, L->stream));
+    CUDA_TRY(cudaMemcpyAsync(p + L->lay.fbuf_bytes, L->ws + L->lay.off_phi[L->cur], phi_state_bytes(L),
+                             cudaMemcpyDeviceToHost, L->stream));
     CUDA_TRY(cudaStreamSynchronize(L->stream));
     return BTRT_OK;
 }
@@ -888,8 +974,8 @@ btrt_status btrt_load(btrt_lattice L, const void *host_buf, size_t n) {
     const unsigned char *p = static_cast<const unsigned char *>(host_buf) + sizeof h;
     L->cur = 0;
     CUDA_TRY(cudaMemcpyAsync(L->fbuf(0), p, L->lay.fbuf_bytes, cudaMemcpyHostToDevice, L->stream));
-    CUDA_TRY(cudaMemcpyAsync(L->ws + L->lay.off_phi[0], p + L->lay.fbuf_bytes,
-                             (size_t)L->lay.plane * elem_size(L->g.compute), cudaMemcpyHostToDevice, L->stream));
+    CUDA_TRY(cudaMemcpyAsync(L->ws + L->lay.off_phi[0], p + L->lay.fbuf_bytes, phi_state_bytes(L),
+                             cudaMemcpyHostToDevice, L->stream));
     CUDA_TRY(cudaMemsetAsync(L->flags(), 0, 16, L->stream));
     CUDA_TRY(cudaStreamSynchronize(L->stream));
     L->step = h.step;

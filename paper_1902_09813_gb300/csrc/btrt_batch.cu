@@ -434,6 +434,8 @@ btrt_status check_members(const btrt_lattice *members, int32_t n, std::vector<bt
         if (!out[k]->ready) return bfail(BTRT_ESTATE, "member %d is not initialised", k);
         if (out[k]->g.compute == BTRT_DF64)
             return bfail(BTRT_EINVAL, "member %d: batches take FP64 or FP32 members", k);
+        if (out[k]->g.shift == BTRT_SHIFT_LOCAL_DW)
+            return bfail(BTRT_EINVAL, "member %d: batches take no double-word phi planes (BTRT_SHIFT_LOCAL_DW)", k);
         if (out[k]->g.compute != out[0]->g.compute || out[k]->g.storage != out[0]->g.storage ||
             shift_of(out[k]->g) != shift_of(out[0]->g))
             return bfail(BTRT_EINVAL, "member %d: all members need the same compute and storage formats and shift", k);
@@ -716,6 +718,10 @@ size_t btrt_batch_workspace_bytes_desc(const btrt_grid_desc *descs, int32_t n) {
     std::vector<MemberGeom> g;
     for (int k = 0; k < n; ++k) {
         if (btrt_workspace_bytes(&descs[k]) == 0) return 0;   // the message says why
+        if (descs[k].shift == BTRT_SHIFT_LOCAL_DW && descs[k].storage != BTRT_F64 && descs[k].storage != BTRT_DF64) {
+            bfail(BTRT_EINVAL, "member %d: batches take no double-word phi planes (BTRT_SHIFT_LOCAL_DW)", k);
+            return 0;
+        }
         if (descs[k].compute != descs[0].compute || descs[k].compute == BTRT_DF64) {
             bfail(BTRT_EINVAL, "member %d: batches take FP64 or FP32 members of one compute format", k);
             return 0;

@@ -60,6 +60,10 @@ struct btrt_lattice_s {
     // phi plane k; phi<Real>() is the current one (written with the populations of buffer cur)
     template <typename Real> Real *phi(int k) { return reinterpret_cast<Real *>(ws + lay.off_phi[k]); }
     template <typename Real> Real *phi() { return phi<Real>(cur); }
+    // low words of phi plane k (BTRT_SHIFT_LOCAL_DW lattices: the plane after the high words)
+    float *phi_lo(int k) {
+        return g.shift == BTRT_SHIFT_LOCAL_DW ? reinterpret_cast<float *>(ws + lay.off_phi[k]) + lay.plane : nullptr;
+    }
     void *fbuf(int k) { return ws + lay.off_f[k]; }
     template <typename Real> Real *tab() { return reinterpret_cast<Real *>(ws + lay.off_tab); }
     template <typename Real> Real *wall(int side) {
@@ -111,7 +115,7 @@ inline void half_split(double q, int *n, int *h) {
 // Storage shift of a lattice (kShiftNone for FP64 / double-word storage).
 inline int shift_of(const btrt_grid_desc &g) {
     if (g.storage == BTRT_F64 || g.storage == BTRT_DF64) return kShiftNone;
-    return g.shift == BTRT_SHIFT_LOCAL ? kShiftLocal : kShiftRef;
+    return g.shift == BTRT_SHIFT_LOCAL ? kShiftLocal : (g.shift == BTRT_SHIFT_LOCAL_DW ? kShiftLocalDW : kShiftRef);
 }
 
 // TMA-staged sweep (FP32 compute) and the box sizes its tensor maps need.

@@ -27,7 +27,8 @@ inline void launch_src(const SweepParams<Real> &p, dim3 g, dim3 b, cudaStream_t 
     }
 }
 
-// Plain FP32-compute sweep for storage S: shift x {kGeneral, kLinear} x source.
+// Plain FP32-compute sweep for storage S: shift (reference, local, local with a
+// double-word phi) x {kGeneral, kLinear} x source.
 template <typename S>
 cudaError_t launch_f32_storage(const SweepParams<float> &p, int shift, int mode, cudaStream_t s) {
     const dim3 g = sweep_grid(p.nx, p.ny, RowsPerThread<float, S>::value), b = sweep_block();
@@ -35,6 +36,9 @@ cudaError_t launch_f32_storage(const SweepParams<float> &p, int shift, int mode,
     if (shift == kShiftLocal) {
         if (lin) launch_src<float, S, kShiftLocal, kLinear>(p, g, b, s);
         else launch_src<float, S, kShiftLocal, kGeneral>(p, g, b, s);
+    } else if (shift == kShiftLocalDW) {
+        if (lin) launch_src<float, S, kShiftLocalDW, kLinear>(p, g, b, s);
+        else launch_src<float, S, kShiftLocalDW, kGeneral>(p, g, b, s);
     } else {
         if (lin) launch_src<float, S, kShiftRef, kLinear>(p, g, b, s);
         else launch_src<float, S, kShiftRef, kGeneral>(p, g, b, s);

@@ -15,6 +15,12 @@
 //                from the previous phi plane.  What is rounded to the storage
 //                format is then of the size of the non-equilibrium and convective
 //                parts only, not of phi itself.
+//   kShiftLocalDW the same with phi kept as a double-word pair (hi + lo, FP32
+//                each): the planes are never rounded to FP32, so a step that
+//                changes phi by a few FP32 ulps (diffusive scaling on fine grids)
+//                is not lost.  The collision and the stored deviations are those
+//                of kShiftLocal; only the neighbour differences phi(x - e_i) -
+//                phi(x) and the new phi take the low words along.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -96,6 +102,8 @@ struct SweepParams {
     void *fout;            // post-collision populations at step n
     const Real *phi_in;    // phi^{n-1} (the phi of the nodes that wrote fin)
     Real *phi_out;         // phi^n (equal to phi_in for the initialising collision)
+    const Real *phi_in_lo; // kShiftLocalDW: low words of phi_in and phi_out (null otherwise)
+    Real *phi_out_lo;
     int nx, ny;
     int pitch;             // elements between rows
     int plane;             // elements between population planes; 9 * plane < 2^31
@@ -175,7 +183,9 @@ __device__ __forceinline__ dw quot(dw a, dw b) { return a / b; }
 // B = u phi, C = phi and constant A with any k0 (kLinear) or k0 = 1 (kLinearK0One).
 enum { kGeneral = 0, kLinear = 1, kLinearK0One = 2 };
 // Stored form of the populations (see the top of this file).
-enum { kShiftNone = 0, kShiftRef = 1, kShiftLocal = 2 };
+enum { kShiftNone = 0, kShiftRef = 1, kShiftLocal = 2, kShiftLocalDW = 3 };
+// The collision and the stored deviations of kShiftLocalDW are those of kShiftLocal.
+template <int SH> struct CollShift { static constexpr int value = SH == kShiftLocalDW ? kShiftLocal : SH; };
 // Source kinds (compile-time SRC); kSrcRuntime decides per lattice at run time,
 // kSrcRuntimeNR the same among the kinds other than the reaction term (whose
 // power-law code then stays out of the kernel).
@@ -556,7 +566,7 @@ __device__ __forceinline__ T ldg(const T *ptr) {
 // rs = phi_prev (the node's phi^{n-1}) for the local shift.
 template <typename Real, typename S, int SH, bool L2ONLY>
 __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const S *__restrict__ fin, int x,
-                                              int y, int node, Real phi_prev, Real (&d)[9]) {
+                                              int y, int node, Real phi_prev, Real (&d)[9], Real phi_lo = Real(0)) {
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         int sx = x - ex_of(i), sy = y - ey_of(i);
@@ -570,6 +580,12 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
             d[i] = Storage<S>::load(ldg<L2ONLY>(fin + BTRT_IX(p.flags, i * p.plane + src, 9 * p.plane)));
             if constexpr (SH == kShiftLocal)
                 if (i != 0) d[i] = fma(wgt<Real>(i), ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, src, p.plane)) - phi_prev, d[i]);
+            if constexpr (SH == kShiftLocalDW)
+                if (i != 0)
+                    d[i] = fma(wgt<Real>(i),
+                               (ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, src, p.plane)) - phi_prev) +
+                                   (ldg<L2ONLY>(p.phi_in_lo + BTRT_IX(p.flags, src, p.plane)) - phi_lo),
+                               d[i]);
         } else {
             const int o = opp_of(i);
             Real phi_w;
@@ -584,7 +600,8 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
             // (for the local shift f_o^+ was stored relative to this node's own phi^{n-1} = rs)
             Real wt = wall_term(p, o, phi_w);
             if constexpr (SH == kShiftRef) wt = wt - Real(2) * p.wref[i];
-            if constexpr (SH == kShiftLocal) wt = fma(Real(-2) * wgt<Real>(i), phi_prev, wt);
+            if constexpr (SH == kShiftLocal || SH == kShiftLocalDW) wt = fma(Real(-2) * wgt<Real>(i), phi_prev, wt);
+            if constexpr (SH == kShiftLocalDW) wt = fma(Real(-2) * wgt<Real>(i), phi_lo, wt);
             d[i] = wt - dout;
         }
     }
@@ -608,12 +625,17 @@ __device__ __forceinline__ Real source_at(const SweepParams<Real> &p, Real xs, R
 // Pull of one node's populations (shifted form, see collide_fold) and of phi^{n-1}.
 template <typename Real, typename S, int SH, bool L2ONLY>
 __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int y, bool x_inner, Real (&f)[9],
-                                          Real &phi_prev) {
+                                          Real &phi_prev, Real *phi_lo_out = nullptr) {
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
     const int node = y * p.pitch + x;
     phi_prev = ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, node, p.plane));
+    Real phi_lo = Real(0);
+    if constexpr (SH == kShiftLocalDW) {
+        phi_lo = ldg<L2ONLY>(p.phi_in_lo + BTRT_IX(p.flags, node, p.plane));
+        *phi_lo_out = phi_lo;
+    }
     if (p.first) {
-        equilibrium<Real, SH>(p, phi_prev, f);
+        equilibrium<Real, CollShift<SH>::value>(p, phi_prev, f);
     } else if (x_inner && y > 0 && y < p.ny - 1) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
@@ -627,8 +649,18 @@ __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int
                                phi_prev,
                            f[i]);
         }
+        if constexpr (SH == kShiftLocalDW) {
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const int nb = node - ey_of(i) * p.pitch - ex_of(i);
+                f[i] = fma(wgt<Real>(i),
+                           (ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, nb, p.plane)) - phi_prev) +
+                               (ldg<L2ONLY>(p.phi_in_lo + BTRT_IX(p.flags, nb, p.plane)) - phi_lo),
+                           f[i]);
+            }
+        }
     } else {
-        pull_boundary<Real, S, SH, L2ONLY>(p, fin, x, y, node, phi_prev, f);
+        pull_boundary<Real, S, SH, L2ONLY>(p, fin, x, y, node, phi_prev, f, phi_lo);
     }
 }
 
@@ -643,22 +675,43 @@ __device__ __forceinline__ S store_value(int i, Real d, Real phid) {
 // when RESID.  A non-finite phi sets `bad` (one atomic per thread at the end).
 template <typename Real, typename S, int SH, int MODE, int SRC, bool RESID>
 __device__ __forceinline__ double finish_node(const SweepParams<Real> &p, int x, int y, Real xs, Real xc,
-                                              Real (&f)[9], Real phi_prev, bool &bad) {
+                                              Real (&f)[9], Real phi_prev, bool &bad, Real phi_lo = Real(0)) {
+    constexpr int SC = CollShift<SH>::value;
     S *__restrict__ fout = static_cast<S *>(p.fout);
     const int node = y * p.pitch + x;
     const Real src = source_at<Real, SRC>(p, xs, xc, y, node);
-    const Real rs = SH == kShiftLocal ? phi_prev : p.phi_ref;
+    const Real rs = SC == kShiftLocal ? phi_prev : p.phi_ref;
     Real phid;
-    const Real phi = collide_fold<Real, MODE, SRC, SH>(p, f, rs, phi_prev, src, p.first != 0, node, phid);
+    const Real phi = collide_fold<Real, MODE, SRC, SC>(p, f, rs, phi_prev, src, p.first != 0, node, phid);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fout[BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)] = store_value<Real, S, SH>(i, f[i], phid);
-    p.phi_out[BTRT_IX(p.flags, node, p.plane)] = phi;
-    bad |= not_finite(phi);
-    if (RESID) {
-        const double dd = static_cast<double>(phi) - static_cast<double>(phi_prev);
-        return dd * dd;
+    for (int i = 0; i < 9; ++i) fout[BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)] = store_value<Real, S, SC>(i, f[i], phid);
+    if constexpr (SH == kShiftLocalDW) {
+        // phi^n = (phi_prev + phi_lo) + phid as a double-word pair: TwoSum of the high
+        // word and phid (its sum is the collision's phi), the error into the low word,
+        // then Fast2Sum to renormalise
+        const Real bb = phi - phi_prev;
+        const Real e = (phi_prev - (phi - bb)) + (phid - bb);
+        const Real lo = phi_lo + e;
+        const Real hi_n = phi + lo;
+        const Real lo_n = lo - (hi_n - phi);
+        p.phi_out[BTRT_IX(p.flags, node, p.plane)] = hi_n;
+        p.phi_out_lo[BTRT_IX(p.flags, node, p.plane)] = lo_n;
+        bad |= not_finite(hi_n);
+        if (RESID) {
+            const double dd = (static_cast<double>(hi_n) - static_cast<double>(phi_prev)) +
+                              (static_cast<double>(lo_n) - static_cast<double>(phi_lo));
+            return dd * dd;
+        }
+        return 0.0;
+    } else {
+        p.phi_out[BTRT_IX(p.flags, node, p.plane)] = phi;
+        bad |= not_finite(phi);
+        if (RESID) {
+            const double dd = static_cast<double>(phi) - static_cast<double>(phi_prev);
+            return dd * dd;
+        }
+        return 0.0;
     }
-    return 0.0;
 }
 
 // Sweep nodes of column x, rows ybase, ybase + ystride, ...: NR > 0 nodes, with
@@ -680,17 +733,18 @@ __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, 
     double resid = 0.0;
     bool bad = false;
     if constexpr (NR > 0 && UNROLL) {
-        Real f[NR][9], phi_prev[NR];
+        Real f[NR][9], phi_prev[NR], phi_lo[NR];
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const int y = ybase + r * ystride;
-            if (y < p.ny) pull_node<Real, S, SH, L2ONLY>(p, x, y, x_inner, f[r], phi_prev[r]);
+            if (y < p.ny) pull_node<Real, S, SH, L2ONLY>(p, x, y, x_inner, f[r], phi_prev[r], &phi_lo[r]);
         }
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
             const int y = ybase + r * ystride;
             if (y < p.ny)
-                resid += finish_node<Real, S, SH, MODE, SRC, RESID>(p, x, y, xs, xc, f[r], phi_prev[r], bad);
+                resid += finish_node<Real, S, SH, MODE, SRC, RESID>(p, x, y, xs, xc, f[r], phi_prev[r], bad,
+                                                                    phi_lo[r]);
         }
     } else {
         const int n = NR > 0 ? NR : nrows;
@@ -698,9 +752,9 @@ __device__ __forceinline__ double sweep_rows(const SweepParams<Real> &p, int x, 
         for (int r = 0; r < n; ++r) {
             const int y = ybase + r * ystride;
             if (y >= p.ny) break;
-            Real f[9], phi_prev;
-            pull_node<Real, S, SH, L2ONLY>(p, x, y, x_inner, f, phi_prev);
-            resid += finish_node<Real, S, SH, MODE, SRC, RESID>(p, x, y, xs, xc, f, phi_prev, bad);
+            Real f[9], phi_prev, phi_lo = Real(0);
+            pull_node<Real, S, SH, L2ONLY>(p, x, y, x_inner, f, phi_prev, &phi_lo);
+            resid += finish_node<Real, S, SH, MODE, SRC, RESID>(p, x, y, xs, xc, f, phi_prev, bad, phi_lo);
         }
     }
     if (bad) atomicOr(p.flags, 1);

@@ -101,9 +101,10 @@ class Lattice:
     def from_problem(cls, p, compute="f64", storage=None, device=None, stream=None,
                      phi_ref=None, shift="auto") -> "Lattice":
         """shift: stored form of F32/F16/BF16 populations -- "ref" (f - w_i phi_ref),
-        "local" (f^+ - w_i phi of the writing node) or "auto" (local for the 16-bit
-        formats, whose rounding it keeps well below the discretisation error; ref
-        for FP32 storage)."""
+        "local" (f^+ - w_i phi of the writing node), "local_dw" (local, with phi kept
+        as a double-word pair so that it is never rounded to FP32; plain kernel form)
+        or "auto" (local for the 16-bit formats, whose rounding it keeps well below the
+        discretisation error; ref for FP32 storage)."""
         storage = storage or compute
         if shift == "auto":
             shift = "local" if storage in ("f16", "bf16") else "ref"

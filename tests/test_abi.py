@@ -81,7 +81,7 @@ def test_invalid_descriptions_rejected(lib, kw):
 
 def test_unknown_storage_shift_rejected(lib):
     d = _desc(compute="f32", storage="f16")
-    d.shift = 2
+    d.shift = 3
     assert lib.btrt_workspace_bytes(ctypes.byref(d)) == 0
     assert b"shift" in lib.btrt_last_error()
     d.shift = 1
@@ -153,3 +153,15 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, cwd=ROOT,
                        timeout=300)
     assert "raised: True" in r.stdout, (r.stdout, r.stderr[-2000:])
+
+
+def test_double_word_phi_needs_fp32_compute(lib):
+    """BTRT_SHIFT_LOCAL_DW keeps phi as two FP32 planes: FP32 compute only, and the
+    workspace holds the low-word planes (one more plane per phi buffer)."""
+    from paper_1902_09813_gb300.lattice import workspace_bytes
+    from paper_1902_09813_gb300 import _capi as C
+    with pytest.raises(C.BtrtError):
+        workspace_bytes(_desc(compute="f64", storage="f64", shift="local_dw"))
+    dw = workspace_bytes(_desc(compute="f32", storage="f16", shift="local_dw"))
+    loc = workspace_bytes(_desc(compute="f32", storage="f16", shift="local"))
+    assert dw - loc >= 2 * 64 * 48 * 4
