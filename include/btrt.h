@@ -251,7 +251,7 @@ btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_
 
 /* Tile shape: block_x x block_y threads, each sweeping `rows` nodes of its
  * column.  Candidates: 32x8x1, 32x8x2, 32x8x4, 64x4x1, 64x4x2, 32x4x2, 16x16x1,
- * 8x32x1.  per_step_launch = 0: persistent launch per call; 1: one launch per
+ * 8x32x1, 32x4x4, 16x8x2.  per_step_launch = 0: persistent launch per call; 1: one launch per
  * step; 2 (FP32-compute batches only, else BTRT_EINVAL): two steps per launch on
  * 32 x 16 output tiles (the form of BTRT_SWEEP_TB2), an odd last step and the
  * residual step of btrt_batch_step in the form of 1 with the given shape;
@@ -261,10 +261,10 @@ btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_
 btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y, int32_t rows,
                                  int32_t per_step_launch);
 
-/* Pick the fastest candidate (8 tile shapes x 2 launch forms, x 4 for FP32
+/* Pick the fastest candidate (10 tile shapes x 2 launch forms, x 4 for FP32
  * compute with the two-step and vector forms) by timing steps_per_trial steps of
  * each after one warm-up step.  These are real steps: on a first tuning every
- * member advances by 16 (FP32: 32) x (steps_per_trial + 1) steps.
+ * member advances by 20 (FP32: 40) x (steps_per_trial + 1) steps.
  * The choice is cached per (members, total nodes, formats) in the process and
  * reused without timing.  Writes the choice (any pointer may be NULL). */
 btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *block_x, int32_t *block_y,

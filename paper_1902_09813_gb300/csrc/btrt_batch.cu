@@ -211,29 +211,59 @@ __global__ void __launch_bounds__(256, (LIN && sizeof(Real) == 4) ? BTRT_BATCH_L
 // graph), one block per tile of (4 bx) x (by rows) nodes; each thread owns four
 // x-consecutive nodes of `rows` rows and sweeps them with the single-lattice
 // vector sweep's code (btrt_vec.cuh), so every node's arithmetic is that of the
-// plain form.  Resident blocks per SM it is compiled for: as the single-lattice
-// vector sweep for the constant-coefficient form (VecMinBlocks: four for 16-bit
-// storage, two for FP32 storage); two for the form that takes any member, which
-// spills 700-900 bytes at four.
+// plain form.  Resident blocks per SM it is compiled for: BatchVecMinBlocks for the
+// constant-coefficient form (16-bit storage: BTRT_BATCH_VEC_MINBLOCKS_S16; FP32
+// storage two), two for the form that takes any member, which spills 700-900
+// bytes at four.
+#ifndef BTRT_BATCH_VEC_MINBLOCKS_S16
+#define BTRT_BATCH_VEC_MINBLOCKS_S16 4
+#endif
+template <typename S> struct BatchVecMinBlocks { static constexpr int value = BTRT_BATCH_VEC_MINBLOCKS_S16; };
+template <> struct BatchVecMinBlocks<float> { static constexpr int value = 2; };
+// The members' folded collision constants travel in the launch's parameter
+// block: the kernel reads them from the constant bank, as the single-lattice
+// kernels read theirs, instead of holding them in registers loaded from shared
+// memory.  One launch serves at most kParamMembers members (a contiguous range
+// of the vector form's tile table); larger batches take several launches a step.
+constexpr int kParamMembers = 256;
+struct BatchVecArgs {
+    BatchArgs<float> a;
+    int m0;                                   // first member of this launch
+    int t0;                                   // its first tile in the vector form's tile table
+    FoldConsts<float> lin[kParamMembers];     // constants of members m0, m0 + 1, ...
+};
+
 template <typename S, int SH, bool LIN>
-__global__ void __launch_bounds__(256, LIN ? VecMinBlocks<S>::value : 2)
-    batch_vec_kernel(const __grid_constant__ BatchArgs<float> a, int k, int flip) {
+__global__ void __launch_bounds__(256, LIN ? BatchVecMinBlocks<S>::value : 2)
+    batch_vec_kernel(const __grid_constant__ BatchVecArgs va, int k, int flip) {
     __shared__ SweepParams<float> sp;
-    const int4 tile = a.tilesv[blockIdx.x];
+    const BatchArgs<float> &a = va.a;
+    const int4 tile = a.tilesv[va.t0 + blockIdx.x];
     const int mode = a.members[tile.x].mode;
+    const FoldConsts<float> *Lc = &va.lin[tile.x - va.m0];
     stage_member(a, tile.x, k, flip, sp);
     const SweepParams<float> &lp = sp;
     const int x0 = tile.y + threadIdx.x * kVec;
     bool bad = false;
-    if (x0 < lp.nx) {
-        for (int r = 0; r < a.rows; ++r) {
-            const int y = tile.z + threadIdx.y + r * blockDim.y;
-            if (y >= lp.ny) break;
-            if (LIN || mode != kGeneral)
-                bad |= vec_group<S, SH, kLinear, LIN ? kSrcRuntimeNR : kSrcRuntime>(lp, x0, y);
-            else
-                bad |= vec_group<S, SH, kGeneral, kSrcRuntime>(lp, x0, y);
-        }
+    // interior groups on the vector path, then the tile's edge nodes spread over the block
+    const int tw = kVec * blockDim.x, th = blockDim.y * a.rows;
+    if (LIN || mode != kGeneral) {
+        constexpr int SRC = LIN ? kSrcRuntimeNR : kSrcRuntime;
+        if (x0 < lp.nx)
+            for (int r = 0; r < a.rows; ++r) {
+                const int y = tile.z + threadIdx.y + r * blockDim.y;
+                if (y >= lp.ny) break;
+                bad |= vec_group_inner<S, SH, kLinear, SRC>(lp, x0, y, Lc);
+            }
+        bad |= vec_tile_edges<S, SH, kLinear, SRC>(lp, tile.y, tile.z, tw, th, Lc);
+    } else {
+        if (x0 < lp.nx)
+            for (int r = 0; r < a.rows; ++r) {
+                const int y = tile.z + threadIdx.y + r * blockDim.y;
+                if (y >= lp.ny) break;
+                bad |= vec_group_inner<S, SH, kGeneral, kSrcRuntime>(lp, x0, y, Lc);
+            }
+        bad |= vec_tile_edges<S, SH, kGeneral, kSrcRuntime>(lp, tile.y, tile.z, tw, th, Lc);
     }
     if (bad) atomicOr(lp.flags, 1);
 }
@@ -359,8 +389,8 @@ struct Shape {
                     // (FP32 compute; its odd or residual last step in the form of 1); 3: one launch
                     // per step in the vector form (FP32 compute; its residual step in the form of 1)
 };
-const Shape kShapes[] = {{32, 8, 1, 0}, {32, 8, 2, 0}, {32, 8, 4, 0}, {64, 4, 1, 0},
-                         {64, 4, 2, 0}, {32, 4, 2, 0}, {16, 16, 1, 0}, {8, 32, 1, 0}};
+const Shape kShapes[] = {{32, 8, 1, 0}, {32, 8, 2, 0}, {32, 8, 4, 0}, {64, 4, 1, 0},  {64, 4, 2, 0},
+                         {32, 4, 2, 0}, {16, 16, 1, 0}, {8, 32, 1, 0}, {32, 4, 4, 0}, {16, 8, 2, 0}};
 constexpr int kForms = 4;   // launch forms 0 .. 3 (FP64 batches: 0 and 1)
 
 // Grid sizes of the members: all the batch tables depend on.
@@ -461,6 +491,8 @@ struct btrt_batch_s {
     int ntiles = 0;
     int ntiles2 = 0;           // output tiles of the two-step form
     int ntilesv = 0;           // tiles of the vector form
+    std::vector<int2> vchunks; // vector form: per launch {first member, first tile}; tiles run to the next entry
+    std::vector<FoldConsts<float>> graph_lin;   // members' constants inside the captured graphs
     int grid = 0;              // persistent grid (co-resident blocks), form that takes either collision
     int grid_lin = 0;          // the same for the constant-coefficient-only form
     bool all_linear = false;   // every member takes the constant-coefficient collision and no reaction term (set per slice)
@@ -531,9 +563,12 @@ btrt_status build_tiles(btrt_batch B) {
     B->ntiles2 = (int)tiles2.size();
     BCUDA(cudaMemcpyAsync(B->ws + B->lay.off_tiles2, tiles2.data(), tiles2.size() * sizeof(int4),
                           cudaMemcpyHostToDevice, B->stream));
-    // tiles of the vector form: (4 bx) x (by rows) nodes
+    // tiles of the vector form: (4 bx) x (by rows) nodes, in member order, split into
+    // launches of at most kParamMembers members
     std::vector<int4> tilesv;
+    B->vchunks.clear();
     for (size_t m = 0; m < B->members.size(); ++m) {
+        if (m % kParamMembers == 0) B->vchunks.push_back(make_int2((int)m, (int)tilesv.size()));
         btrt_lattice L = B->members[m];
         for (int y0 = 0; y0 < L->g.ny; y0 += s.by * s.rows)
             for (int x0 = 0; x0 < L->g.nx; x0 += kVec * s.bx) tilesv.push_back(make_int4((int)m, x0, y0, 0));
@@ -633,9 +668,25 @@ btrt_status enqueue_form(btrt_batch B, int nsteps, int want_resid) {
                 for (int j = 0; j < pairs_in_slice(B, nsteps, want_resid); ++j, k += 2, ++flip)
                     batch_tb2_kernel<S, SH, LIN><<<(unsigned)B->ntiles2, TbGeom::THREADS, TbGeom::SMEM, B->stream>>>(
                         a, k, flip);
-            if (B->shape.per_step == 3)
+            if (B->shape.per_step == 3) {
+                // one parameter block per member range, reused by every step
+                const BatchMember<float> *hm = reinterpret_cast<const BatchMember<float> *>(B->host_members.data());
+                std::vector<BatchVecArgs> va(B->vchunks.size());
+                for (size_t c = 0; c < B->vchunks.size(); ++c) {
+                    std::memset(&va[c], 0, sizeof(BatchVecArgs));
+                    va[c].a = a;
+                    va[c].m0 = B->vchunks[c].x;
+                    va[c].t0 = B->vchunks[c].y;
+                    const int m1 = c + 1 < B->vchunks.size() ? B->vchunks[c + 1].x : (int)B->members.size();
+                    for (int m = va[c].m0; m < m1; ++m) va[c].lin[m - va[c].m0] = hm[m].p.lin;
+                }
                 for (; k < nsteps - (want_resid ? 1 : 0); ++k, ++flip)
-                    batch_vec_kernel<S, SH, LIN><<<(unsigned)B->ntilesv, block, 0, B->stream>>>(a, k, flip);
+                    for (size_t c = 0; c < va.size(); ++c) {
+                        const int t1 = c + 1 < B->vchunks.size() ? B->vchunks[c + 1].y : B->ntilesv;
+                        batch_vec_kernel<S, SH, LIN><<<(unsigned)(t1 - va[c].t0), block, 0, B->stream>>>(va[c], k,
+                                                                                                      flip);
+                    }
+            }
         }
         for (; k < nsteps; ++k, ++flip)
             batch_step_kernel<Real, S, SH, LIN><<<(unsigned)B->ntiles, block, 0, B->stream>>>(a, k, flip);
@@ -674,6 +725,20 @@ btrt_status enqueue(btrt_batch B, int nsteps, int want_resid) {
 // Replay (or capture, then replay) the slice graph; falls back to direct
 // launches if the launch cannot be captured.
 btrt_status run_slice(btrt_batch B, int nsteps, int want_resid) {
+    if (B->compute == BTRT_F32) {
+        // the vector form's graphs hold the members' collision constants in their
+        // launch parameters: a change of coefficients invalidates them
+        const BatchMember<float> *hm = reinterpret_cast<const BatchMember<float> *>(B->host_members.data());
+        const size_t n = B->members.size();
+        bool same = B->graph_lin.size() == n;
+        for (size_t m = 0; same && m < n; ++m)
+            same = std::memcmp(&B->graph_lin[m], &hm[m].p.lin, sizeof(FoldConsts<float>)) == 0;
+        if (!same) {
+            B->drop_graphs();
+            B->graph_lin.resize(n);
+            for (size_t m = 0; m < n; ++m) B->graph_lin[m] = hm[m].p.lin;
+        }
+    }
     if (B->use_graph) {
         auto key = std::make_pair((long long)nsteps, want_resid | (B->all_linear ? 2 : 0));
         auto it = B->graphs.find(key);

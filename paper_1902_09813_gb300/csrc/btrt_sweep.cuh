@@ -285,8 +285,11 @@ constexpr int kFp64OpsPerNodeLinearTrig = 50;
 // 4 decided at run time.  Returns phi; phid_out = phi - rs as summed from the d_i.
 template <typename Real, int MODE, int SRC, int SH>
 __device__ __forceinline__ Real collide_fold(const SweepParams<Real> &p, Real (&d)[9], Real rs, Real phi_prev,
-                                             Real srcv, bool first, int node, Real &phid_out) {
-    const FoldConsts<Real> &L = p.lin;
+                                             Real srcv, bool first, int node, Real &phid_out,
+                                             const FoldConsts<Real> *Lc = nullptr) {
+    // the folded constants: p.lin, or the copy at Lc (a batch keeps its members'
+    // copies in the kernel's parameter space)
+    const FoldConsts<Real> &L = Lc ? *Lc : p.lin;
     constexpr bool K0ONE = MODE == kLinearK0One;
     const Real a13 = d[1] + d[3], a24 = d[2] + d[4];
     const Real s57 = d[5] + d[7], s68 = d[6] + d[8];
@@ -675,14 +678,15 @@ __device__ __forceinline__ S store_value(int i, Real d, Real phid) {
 // when RESID.  A non-finite phi sets `bad` (one atomic per thread at the end).
 template <typename Real, typename S, int SH, int MODE, int SRC, bool RESID>
 __device__ __forceinline__ double finish_node(const SweepParams<Real> &p, int x, int y, Real xs, Real xc,
-                                              Real (&f)[9], Real phi_prev, bool &bad, Real phi_lo = Real(0)) {
+                                              Real (&f)[9], Real phi_prev, bool &bad, Real phi_lo = Real(0),
+                                              const FoldConsts<Real> *Lc = nullptr) {
     constexpr int SC = CollShift<SH>::value;
     S *__restrict__ fout = static_cast<S *>(p.fout);
     const int node = y * p.pitch + x;
     const Real src = source_at<Real, SRC>(p, xs, xc, y, node);
     const Real rs = SC == kShiftLocal ? phi_prev : p.phi_ref;
     Real phid;
-    const Real phi = collide_fold<Real, MODE, SRC, SC>(p, f, rs, phi_prev, src, p.first != 0, node, phid);
+    const Real phi = collide_fold<Real, MODE, SRC, SC>(p, f, rs, phi_prev, src, p.first != 0, node, phid, Lc);
 #pragma unroll
     for (int i = 0; i < 9; ++i) fout[BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)] = store_value<Real, S, SC>(i, f[i], phid);
     if constexpr (SH == kShiftLocalDW) {

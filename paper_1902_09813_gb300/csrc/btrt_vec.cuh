@@ -96,7 +96,8 @@ template <> struct VecMinBlocks<float> { static constexpr int value = BTRT_VEC_M
 // non-finite phi appeared.  L2ONLY: loads of data other SMs rewrite during a
 // persistent launch go through L2 only (as in pull_node).
 template <typename S, int SH, int MODE, int SRC, bool L2ONLY, typename Put>
-__device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0, int y, Put &&put) {
+__device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0, int y, Put &&put,
+                                             const FoldConsts<float> *Lc = nullptr) {
     using W = typename Vec4<S>::W;
     constexpr bool TRIG = SRC == kSrcTrig || SRC == kSrcRuntime || SRC == kSrcRuntimeNR;
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
@@ -152,7 +153,7 @@ __device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0
         const float src = source_at<float, SRC>(p, xs, xc, y, node + v);
         const float rs = SH == kShiftLocal ? phi_prev : p.phi_ref;
         float phid;
-        const float phi = collide_fold<float, MODE, SRC, SH>(p, f, rs, phi_prev, src, false, node + v, phid);
+        const float phi = collide_fold<float, MODE, SRC, SH>(p, f, rs, phi_prev, src, false, node + v, phid, Lc);
 #pragma unroll
         for (int i = 0; i < 9; ++i)
             outv[i][v] = SH == kShiftLocal ? fma(-wgt<float>(i), phid, f[i]) : f[i];
@@ -164,9 +165,11 @@ __device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0
 }
 
 // One step of the four nodes x0 .. x0 + 3 (those below nx) of row y, written to
-// the output buffer.  Returns true when a non-finite phi appeared.
+// the output buffer.  Returns true when a non-finite phi appeared.  Lc: the folded
+// collision constants when not p.lin (see collide_fold).
 template <typename S, int SH, int MODE, int SRC, bool L2ONLY = false>
-__device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, int y) {
+__device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, int y,
+                                          const FoldConsts<float> *Lc = nullptr) {
     using V = Vec4<S>;
     using W = typename V::W;
     constexpr bool TRIG = SRC == kSrcTrig || SRC == kSrcRuntime || SRC == kSrcRuntimeNR;
@@ -184,7 +187,7 @@ __device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, i
             }
             float f[9], phi_prev;
             pull_node<float, S, SH, L2ONLY>(p, x, y, x > 0 && x < p.nx - 1, f, phi_prev);
-            finish_node<float, S, SH, MODE, SRC, false>(p, x, y, xs, xc, f, phi_prev, bad);
+            finish_node<float, S, SH, MODE, SRC, false>(p, x, y, xs, xc, f, phi_prev, bad, 0.f, Lc);
         }
         return bad;
     }
@@ -197,7 +200,79 @@ __device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, i
                 V::put(outv[i][0], outv[i][1], outv[i][2], outv[i][3]);
         *reinterpret_cast<float4 *>(p.phi_out + BTRT_IX(p.flags, node, p.plane)) =
             make_float4(phi_o[0], phi_o[1], phi_o[2], phi_o[3]);
-    });
+    }, Lc);
+}
+
+// True when the group x0 .. x0 + 3 of row y takes the vector path (no pull wraps
+// or crosses a wall).
+__device__ __forceinline__ bool vec_interior_group(const SweepParams<float> &p, int x0, int y) {
+    return x0 >= 1 && x0 + kVec <= p.nx - 1 && y >= 1 && y <= p.ny - 2;
+}
+
+// One step of the group x0 .. x0 + 3 of row y when it is interior (vector path,
+// written to the output buffer); nothing otherwise (vec_tile_edges takes those
+// nodes).  Returns true when a non-finite phi appeared.
+template <typename S, int SH, int MODE, int SRC, bool L2ONLY = false>
+__device__ __forceinline__ bool vec_group_inner(const SweepParams<float> &p, int x0, int y,
+                                                const FoldConsts<float> *Lc = nullptr) {
+    if (!vec_interior_group(p, x0, y)) return false;
+    return vec_group<S, SH, MODE, SRC, L2ONLY>(p, x0, y, Lc);
+}
+
+// The nodes of the tile [tx0, tx0 + tw) x [ty0, ty0 + th) (clipped to the grid;
+// tx0 a multiple of four) whose groups are not interior -- the columns 0 .. 3 and
+// from the last interior group's end to nx - 1, and the whole of rows 0 and
+// ny - 1 -- one node per thread of the block, by the plain sweep's per-node path.
+// Spreading them over the block keeps the slow path out of the warps that run the
+// vector path (a warp holding one edge group otherwise runs both paths).
+template <typename S, int SH, int MODE, int SRC, bool L2ONLY = false>
+__device__ __forceinline__ bool vec_tile_edges(const SweepParams<float> &p, int tx0, int ty0, int tw, int th,
+                                               const FoldConsts<float> *Lc = nullptr) {
+    constexpr bool TRIG = SRC == kSrcTrig || SRC == kSrcRuntime || SRC == kSrcRuntimeNR;
+    // first column of the right-hand non-interior groups: groups start at multiples
+    // of four, and x0 + 4 > nx - 1 leaves the vector path
+    const int xr = p.nx - kVec > 0 ? (p.nx - 1) & ~(kVec - 1) : 0;
+    const int xrs = max(xr, kVec);                 // [0, 4) is the left range
+    // most tiles have no such node: leave at once
+    if (tx0 >= kVec && tx0 + tw <= xrs && ty0 > 0 && ty0 + th < p.ny) return false;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthr = blockDim.x * blockDim.y;
+    const int tx1 = min(tx0 + tw, p.nx), ty1 = min(ty0 + th, p.ny);
+    if (tx0 >= tx1 || ty0 >= ty1) return false;
+    const int l0 = tx0, l1 = min(tx1, kVec);       // left columns in the tile (empty if l0 >= l1)
+    const int r0 = max(tx0, xrs), r1 = tx1;        // right columns in the tile
+    const int nl = max(0, l1 - l0), nr = max(0, r1 - r0);
+    const int width = tx1 - tx0;
+    bool bad = false;
+    auto node = [&](int x, int y) {
+        float xs = 0.f, xc = 0.f;
+        if (SRC == kSrcTrig || (TRIG && SRC != kSrcTrig && p.src_kind == kSrcTrig)) {
+            xs = p.Xs[BTRT_IX(p.flags, x, p.nx)];
+            xc = p.Xc[BTRT_IX(p.flags, x, p.nx)];
+        }
+        float f[9], phi_prev;
+        pull_node<float, S, SH, L2ONLY>(p, x, y, x > 0 && x < p.nx - 1, f, phi_prev);
+        finish_node<float, S, SH, MODE, SRC, false>(p, x, y, xs, xc, f, phi_prev, bad, 0.f, Lc);
+    };
+    // whole rows 0 and ny - 1, then the edge columns of the rows between
+    int nedge = 0;
+    const bool has_top = ty0 == 0, has_bot = ty1 == p.ny && p.ny - 1 > 0;
+    nedge = (has_top ? 1 : 0) + (has_bot ? 1 : 0);
+    for (int k = tid; k < nedge * width; k += nthr) {
+        const int row = k / width, x = tx0 + k % width;
+        const int y = (row == 0 && has_top) ? 0 : p.ny - 1;
+        node(x, y);
+    }
+    const int iy0 = max(ty0, 1), iy1 = min(ty1, p.ny - 1);   // rows with interior groups
+    const int per_row = nl + nr;
+    if (per_row > 0 && iy0 < iy1) {
+        const int items = (iy1 - iy0) * per_row;
+        for (int k = tid; k < items; k += nthr) {
+            const int y = iy0 + k / per_row, j = k % per_row;
+            node(j < nl ? l0 + j : r0 + (j - nl), y);
+        }
+    }
+    return bad;
 }
 
 // One step of one lattice, 32 x 8 threads per block: thread (tx, ty) owns nodes
@@ -207,8 +282,11 @@ template <typename S, int SH, int MODE, int SRC>
 __global__ void __launch_bounds__(256, VecMinBlocks<S>::value) sweep_vec_kernel(const __grid_constant__ SweepParams<float> p) {
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * kVec;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x0 >= p.nx || y >= p.ny) return;
-    if (vec_group<S, SH, MODE, SRC>(p, x0, y)) atomicOr(p.flags, 1);
+    bool bad = false;
+    if (x0 < p.nx && y < p.ny) bad = vec_group_inner<S, SH, MODE, SRC>(p, x0, y);
+    bad |= vec_tile_edges<S, SH, MODE, SRC>(p, blockIdx.x * blockDim.x * kVec, blockIdx.y * blockDim.y,
+                                            blockDim.x * kVec, blockDim.y);
+    if (bad) atomicOr(p.flags, 1);
 }
 
 // 32 x 8 threads, 128 x 8 nodes per block.

@@ -146,7 +146,7 @@ class Server:
             ft = batch.step_tol(self.slice_steps, self.tol, out=self._flag_buffer(len(active)))
             _record(ev1, self.stream)
             res = batch.residuals()          # synchronises: the flags have landed too
-            flags = np.array(ft)
+            flags = ft.numpy().copy() if isinstance(ft, torch.Tensor) else np.asarray(ft)
             st["gpu_busy_s"] += _elapsed_s(ev0, ev1)
             bad = flags & 2                  # non-finite phi in that member only
             st["slices"] += 1

@@ -89,7 +89,8 @@ def test_constant_coefficient_batch_form_bitwise(compute, storage, shift, shape)
 @pytest.mark.parametrize("shape", [(32, 8, 1, 0), (32, 8, 4, 0), (64, 4, 2, 0), (32, 4, 2, 0),
                                    (32, 8, 1, 1), (64, 4, 2, 1), (32, 8, 4, 2), (64, 4, 1, 2),
                                    (16, 16, 1, 1), (8, 32, 1, 0), (32, 8, 1, 3), (32, 8, 4, 3),
-                                   (64, 4, 2, 3), (16, 16, 1, 3), (8, 32, 1, 3)])
+                                   (64, 4, 2, 3), (16, 16, 1, 3), (8, 32, 1, 3), (32, 4, 4, 3), (16, 8, 2, 3),
+                                   (32, 4, 4, 1)])
 def test_tile_shapes_bitwise(shape):
     from paper_1902_09813_gb300 import Batch
     probs = _mix("f32", "f16", count=6, seed=5)
@@ -193,10 +194,10 @@ def test_autotune_keeps_results():
     b = Batch(mixed)
     shape = b.autotune(steps_per_trial=2)
     assert shape[:3] in [(32, 8, 1), (32, 8, 2), (32, 8, 4), (64, 4, 1), (64, 4, 2), (32, 4, 2), (16, 16, 1),
-                         (8, 32, 1)]
+                         (8, 32, 1), (32, 4, 4), (16, 8, 2)]
     assert shape[3] in (0, 1, 2, 3)
     n_done = mixed[0].time()[0]
-    assert n_done == 8 * 4 * 3   # eight shapes, four forms (FP32), 1 + 2 steps each
+    assert n_done == 10 * 4 * 3   # ten shapes, four forms (FP32), 1 + 2 steps each
     ref = [_make(p, "f32", "f16").step(n_done + 5) for p in probs]
     b.step(5)
     for a, m in zip(ref, mixed):
