@@ -81,18 +81,18 @@ FP64_NOMINAL_TOPS = 0.625
 # to them both are re-taken and the digest updated (a CPU test checks it), and
 # until then the traffic is reported as null.
 FP64_SWEEP_SOURCES = ("btrt_sweep.cuh", "btrt_dw.cuh")   # the FP64 sweep's device code
-FP64_SWEEP_DIGEST = "2254efa133f17e57"
+FP64_SWEEP_DIGEST = "310e6ddfe7f4a381"
 FP64_TRAFFIC_PER_NODE = 149.3
 # DRAM bytes per node and step of the two-step FP32-compute kernel measured by ncu,
 # keyed by (storage, shift), for the sources with digest TB2_DIGEST.
 TB2_SOURCES = ("btrt_sweep.cuh", "btrt_tb.cuh", "btrt_launch.cuh")
-TB2_DIGEST = "9f8c00e5fe1e01a4"
+TB2_DIGEST = "8c614ffa0c32392a"
 TB2_DRAM_BYTES_PER_UPDATE = {("f32", "ref"): 38.6, ("f16", "local"): 20.9}
 # DRAM bytes per node of one launch of the vector-access sweep measured by ncu,
 # keyed by (storage, shift), for the sources with digest VEC_DIGEST.
 VEC_SOURCES = ("btrt_sweep.cuh", "btrt_vec.cuh", "btrt_launch.cuh")
-VEC_DIGEST = "0a77a67ce126cfd9"
-VEC_DRAM_BYTES_PER_UPDATE = {("f16", "local"): 41.3}
+VEC_DIGEST = "7692bfccf9de4946"
+VEC_DRAM_BYTES_PER_UPDATE = {("f16", "local"): 41.4}
 
 
 def measure_fp64_peak(iters: int = 2000):
@@ -130,11 +130,14 @@ def kernel_form(args) -> str:
     FP32 compute (the vector form for FP16/BF16 storage on lattices of 2^21 nodes
     or more, two steps per launch otherwise), the form asked for, or the plain
     sweep."""
-    if args.compute != "f32" or args.shift == "local_dw":
+    if args.compute != "f32" or args.shift in ("local_dw", "local_dw_sr"):
         return "plain"
     if args.sweep != "auto":
         return args.sweep
-    return "vec" if args.storage in ("f16", "bf16") and args.n * args.n >= 1 << 21 else "tb2"
+    large = args.n * args.n >= 1 << 21
+    if args.shift == "local_sr":
+        return "vec" if large else "plain"
+    return "vec" if args.storage in ("f16", "bf16") and large else "tb2"
 
 
 def two_step_form(args) -> bool:
@@ -446,6 +449,12 @@ def run_variants(args, steps=200, warmup=5):
             out[f"{name}_f32_{st}_tma"] = _time_single(prob, a, "f32", st, steps, warmup, variant="tma")
             # phi as a double-word pair (plain form)
             out[f"{name}_f32_{st}_local_dw"] = _time_single(prob, a, "f32", st, steps, warmup, shift="local_dw")
+            if st != "f32":
+                # stochastically rounded 16-bit storage: vector form, and with a double-word phi
+                out[f"{name}_f32_{st}_local_sr_vec"] = _time_single(prob, a, "f32", st, steps, warmup,
+                                                                    variant="vec", shift="local_sr")
+                out[f"{name}_f32_{st}_local_dw_sr"] = _time_single(prob, a, "f32", st, steps, warmup,
+                                                                   shift="local_dw_sr")
     out["nonlinear_f64"] = _time_single(q, q_phi0, "f64", "f64", 50, 3)
     out.update(run_d3q19(args))
     out.update(run_extended(args))
@@ -539,7 +548,9 @@ def _final_phi(p, phi0, compute, storage, steps, shift="ref"):
 
 REDUCED = [("df64", "df64", "ref"), ("f32", "f32", "ref"), ("f32", "f32", "local"), ("f32", "f16", "ref"),
            ("f32", "f16", "local"), ("f32", "bf16", "ref"), ("f32", "bf16", "local"),
-           ("f32", "f32", "local_dw"), ("f32", "f16", "local_dw"), ("f32", "bf16", "local_dw")]
+           ("f32", "f32", "local_dw"), ("f32", "f16", "local_dw"), ("f32", "bf16", "local_dw"),
+           ("f32", "f16", "local_sr"), ("f32", "bf16", "local_sr"), ("f32", "f16", "local_dw_sr"),
+           ("f32", "bf16", "local_dw_sr")]
 
 
 def _fmt_key(c, s, sh):
@@ -626,8 +637,9 @@ def run_accuracy(args):
 def run_batched(args, count=512, nsteps=2000, seed=0, plain=True):
     """Config-4 style batch: `count` instances, side log-uniform in [32, 1024], half
     periodic Gaussian hills / half HBB manufactured solutions, FP32 compute + FP16
-    shifted storage, `nsteps` steps each: one persistent launch per call (CUDA
-    graph) with an autotuned tile shape, against plain per-instance launches."""
+    shifted storage, `nsteps` steps each: one batched launch form per call (CUDA
+    graph) with an autotuned tile shape (or the one `--batch-tile` names), against
+    plain per-instance launches."""
     import torch
 
     import workloads as w
@@ -649,15 +661,19 @@ def run_batched(args, count=512, nsteps=2000, seed=0, plain=True):
         return lats
 
     # batched: autotune on a throw-away copy (its steps are real steps), then time
-    lats = make()
-    b = Batch(lats, stream=stream)
-    shape = b.autotune(steps_per_trial=3)
-    b.close()
-    del lats, b
+    shape = tuple(getattr(args, "batch_tile", None) or ())
+    if not shape:
+        lats = make()
+        b = Batch(lats, stream=stream)
+        shape = b.autotune(steps_per_trial=3)
+        b.close()
+        del lats, b
     lats = make()
     b = Batch(lats, stream=stream)
     b.set_tiles(*shape)
-    b.step(2)                      # graph capture + warm-up, not timed
+    b.step(2)                      # warm-up, not timed
+    b.prepare(nsteps - 2, residual=False)   # capture the timed call's graph outside the timed region
+    graphs = b.graphs()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -693,7 +709,8 @@ def run_batched(args, count=512, nsteps=2000, seed=0, plain=True):
             "plain_mlups": round(nodes * nsteps / t_plain / 1e6, 1),
             "speedup": round(t_plain / t_batch, 3),
             "batched_equals_plain_bitwise_first8": same,
-            "launch": "step-per-launch graph" if shape[3] else "persistent cooperative",
+            "launch": ("one launch per step" if shape[3] in (1, 3) else "two steps per launch" if shape[3] == 2
+                       else "persistent cooperative") + (", CUDA graph" if graphs > 0 else ", direct launches"),
             "dtype": "f32 compute, f16 storage (local shift)"}
 
 
@@ -705,7 +722,9 @@ def run_serving(args, rates=(100.0, 500.0, 2000.0), count=96, seed=1):
     same requests (the highest-rate trace), with each served phi compared to its
     sequential counterpart.  Per rate: the device's idle share of the run (wall
     time without a slice on the GPU), batch rebuilds, host time admitting and
-    rebuilding, and how many requests stopped at the tolerance or the cap."""
+    rebuilding (with the graph capture; both while queued slices run) and waiting
+    for the oldest queued slice, and how many requests stopped at the tolerance or
+    the cap."""
     import workloads as w
     from paper_1902_09813_gb300.serve import Server, depth_series, poisson_trace, serve_sequential, summarize
 
@@ -738,7 +757,7 @@ def run_serving(args, rates=(100.0, 500.0, 2000.0), count=96, seed=1):
             summarize(res), peak_active=st["peak_active"], slices=st["slices"], rebuilds=st["rebuilds"],
             gpu_idle_fraction=round(srv.idle_fraction(), 4), gpu_busy_s=round(st["gpu_busy_s"], 3),
             admit_s=round(st["admit_s"], 3), rebuild_s=round(st["rebuild_s"], 3),
-            stopped_at_tol=st["tol_hits"], stopped_at_cap=st["cap_hits"], rejected=st["rejected"],
+            wait_s=round(st["wait_s"], 3), stopped_at_tol=st["tol_hits"], stopped_at_cap=st["cap_hits"], rejected=st["rejected"],
             unstable=st["unstable"], depth_t_active_waiting=depth_series(srv.depth))
         served = res
     # plain sequential baseline on the same requests as the highest-rate trace
@@ -852,11 +871,13 @@ def main():
                     help="only the D3Q19 sweep on an n^3 box (--n, --compute, --storage, --shift, --steps)")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--batch-tile", type=lambda v: tuple(int(x) for x in v.split(",")), default=None,
+                    help="block_x,block_y,rows,form of the batch instead of the autotuner's pick")
     ap.add_argument("--workload", default="mms", choices=["mms", "nonlinear"])
     ap.add_argument("--n", type=int, default=N_MAIN)
     ap.add_argument("--compute", default="f64", choices=["f64", "df64", "f32"])
     ap.add_argument("--storage", default=None, choices=["f64", "df64", "f32", "f16", "bf16"])
-    ap.add_argument("--shift", default="auto", choices=["auto", "ref", "local", "local_dw"],
+    ap.add_argument("--shift", default="auto", choices=["auto", "ref", "local", "local_dw", "local_sr", "local_dw_sr"],
                     help="stored form of F32/F16/BF16 populations")
     ap.add_argument("--sweep", default="auto", choices=["auto", "plain", "tma", "tb2", "vec", "tb2v"],
                     help="kernel form of FP32-compute sweeps")

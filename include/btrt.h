@@ -74,8 +74,21 @@ enum { BTRT_SIDE_XMIN = 0, BTRT_SIDE_XMAX = 1, BTRT_SIDE_YMIN = 2, BTRT_SIDE_YMA
  *                    fine grids (a step changes phi by a few FP32 ulps) keeps FP32
  *                    storage within the FP64 discretisation error.  Plain kernel
  *                    form only (BTRT_SWEEP_AUTO / PLAIN); not in batches.
+ *  BTRT_SHIFT_LOCAL_SR as BTRT_SHIFT_LOCAL, F16/BF16 storage only, with the stored
+ *                    deviations rounded stochastically: up with probability equal to
+ *                    the fraction of the last place cut off, from random bits that
+ *                    depend only on the node, the step index and the population.
+ *                    Under diffusive scaling a step changes the state by far less
+ *                    than a 16-bit last place, and round-to-nearest then repeats
+ *                    nearly the same error step after step; stochastic rounding
+ *                    makes each stored value right on average.  Plain and vector
+ *                    kernel forms (AUTO takes the vector form from 2^21 nodes on);
+ *                    not in batches.
+ *  BTRT_SHIFT_LOCAL_DW_SR both: double-word phi and stochastically rounded F16/BF16
+ *                    deviations.  Plain kernel form only; not in batches.
  * FP64 and double-word storage are never shifted. */
-enum { BTRT_SHIFT_REF = 0, BTRT_SHIFT_LOCAL = 1, BTRT_SHIFT_LOCAL_DW = 2 };
+enum { BTRT_SHIFT_REF = 0, BTRT_SHIFT_LOCAL = 1, BTRT_SHIFT_LOCAL_DW = 2, BTRT_SHIFT_LOCAL_SR = 3,
+       BTRT_SHIFT_LOCAL_DW_SR = 4 };
 
 typedef struct btrt_lattice_s *btrt_lattice;
 
@@ -90,7 +103,7 @@ typedef struct {
     double x0, y0;         /* physical position of the lower-left domain corner         */
     double phi_ref;        /* BTRT_SHIFT_REF: F32/F16/BF16 storage holds f_i - w_i phi_ref  */
     int32_t fields;        /* BTRT_FIELD_* bits: reserve per-node source / diffusion planes */
-    int32_t shift;         /* BTRT_SHIFT_REF, _LOCAL or _LOCAL_DW (F32/F16/BF16 storage)  */
+    int32_t shift;         /* BTRT_SHIFT_* (F32/F16/BF16 storage; _SR forms F16/BF16)     */
 } btrt_grid_desc;
 
 /* Coefficients of Eq. 1 and the relaxation parameters (physical units). */
@@ -275,15 +288,48 @@ btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *
  * at the last step (fixed order). */
 btrt_status btrt_batch_step(btrt_batch B, int64_t nsteps, int32_t want_residual);
 
+/* Capture and instantiate, without running anything, the CUDA graphs that
+ * btrt_batch_step(B, nsteps, want_residual) (and btrt_batch_step_tol with nsteps)
+ * will replay: lets a caller take the capture's host time while the device is busy
+ * elsewhere or outside a timed region.  Uploads the member tables on the batch
+ * stream (asynchronous); advances no member.  No-op for a batch that launches
+ * directly.  nsteps >= 1 (BTRT_EINVAL otherwise). */
+btrt_status btrt_batch_prepare(btrt_batch B, int64_t nsteps, int32_t want_residual);
+
+/* Number of slice graphs the batch holds (each (steps, residual) pair captured
+ * once and replayed), or -1 if capture failed and the batch launches directly. */
+btrt_status btrt_batch_graphs(btrt_batch B, int32_t *n_graphs);
+
 /* Advance every member nsteps >= 1 steps (as btrt_batch_step with want_residual)
  * and compare, on the device, each member's residual ||phi^n - phi^{n-1}||_2 of
  * the last step with tol (the steady-state test of a serving loop, cf. Eq. 64):
- * done[k] bit 0 = residual < tol, bit 1 = member k produced a non-finite phi.
- * done: n int32 values in host memory (on_device = 0; pinned memory keeps the
- * copy asynchronous) or device memory (on_device = 1).  Nothing synchronises:
- * the flags are written in the batch stream's order, so read them after
- * synchronising that stream (or an event recorded after this call). */
-btrt_status btrt_batch_step_tol(btrt_batch B, int64_t nsteps, double tol, int32_t *done, int32_t on_device);
+ * done[k] bit 0 = residual < tol, bit 1 = member k produced a non-finite phi,
+ * bit 2 = member k was frozen before this call (see btrt_batch_set_freeze; its
+ * residual is then NaN and bits 0-1 are clear).  done: n int32 values; resid
+ * (may be NULL): the n residuals.  Both in host memory (on_device = 0; pinned
+ * memory keeps the copies asynchronous) or device memory (on_device = 1).
+ * Nothing synchronises: the results are written in the batch stream's order, so
+ * read them after synchronising that stream or an event recorded after this
+ * call.  Table uploads use pinned staging, so the call does not wait for work
+ * already queued on the stream: a caller may queue the next call before reading
+ * this one's results. */
+btrt_status btrt_batch_step_tol(btrt_batch B, int64_t nsteps, double tol, int32_t *done, double *resid,
+                                int32_t on_device);
+
+/* enable != 0: btrt_batch_step_tol freezes every member it flags (done bit 0 or
+ * 1).  The mark lives in the member lattice's device flags, so launches of this
+ * and of any later batch leave a frozen member unchanged, while the host's step
+ * count of the member still advances with its batch; btrt_settle restores it.
+ * Lets a serving loop queue slice k + 1 before it has read slice k's flags and
+ * still take each retired member exactly as it was when flagged. */
+btrt_status btrt_batch_set_freeze(btrt_batch B, int32_t enable);
+
+/* Read lattice L's freeze mark (synchronises L's stream; call it once the batch
+ * launch that flagged L has completed).  If L is frozen: *frozen_step = the step
+ * count at which it froze, L's step count and buffer index are set back to that
+ * step, and clear != 0 also removes the mark (do that only when no queued batch
+ * launch still includes L, which would then step it).  Otherwise *frozen_step = -1. */
+btrt_status btrt_settle(btrt_lattice L, int32_t clear, int64_t *frozen_step);
 
 /* Residuals of the last step with want_residual, one per member (host, synchronises). */
 btrt_status btrt_batch_residuals(btrt_batch B, double *out_host);

@@ -16,8 +16,9 @@ FIELD_SOURCE, FIELD_DIFFUSION = 1, 2
 SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA, SWEEP_TB2, SWEEP_VEC, SWEEP_TB2V = 0, 1, 2, 3, 4, 5
 SHIFT_REF, SHIFT_LOCAL = 0, 1
 PROBE_FMA, PROBE_ADD, PROBE_MUL = 0, 1, 2
-SHIFT_LOCAL_DW = 2
-SHIFTS = {"ref": SHIFT_REF, "local": SHIFT_LOCAL, "local_dw": SHIFT_LOCAL_DW}
+SHIFT_LOCAL_DW, SHIFT_LOCAL_SR, SHIFT_LOCAL_DW_SR = 2, 3, 4
+SHIFTS = {"ref": SHIFT_REF, "local": SHIFT_LOCAL, "local_dw": SHIFT_LOCAL_DW, "local_sr": SHIFT_LOCAL_SR,
+          "local_dw_sr": SHIFT_LOCAL_DW_SR}
 
 FORMATS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "df64": DF64}
 
@@ -107,7 +108,11 @@ SIGNATURES = [
     ("btrt_batch_autotune", ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i32), ctypes.POINTER(_i32),
                                            ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
     ("btrt_batch_step", ctypes.c_int, [_vp, _i64, _i32]),
-    ("btrt_batch_step_tol", ctypes.c_int, [_vp, _i64, ctypes.c_double, _vp, _i32]),
+    ("btrt_batch_prepare", ctypes.c_int, [_vp, _i64, _i32]),
+    ("btrt_batch_graphs", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
+    ("btrt_batch_step_tol", ctypes.c_int, [_vp, _i64, ctypes.c_double, _vp, _vp, _i32]),
+    ("btrt_batch_set_freeze", ctypes.c_int, [_vp, _i32]),
+    ("btrt_settle", ctypes.c_int, [_vp, _i32, ctypes.POINTER(_i64)]),
     ("btrt_batch_residuals", ctypes.c_int, [_vp, _dp]),
     ("btrt_batch_check", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),
     ("btrt_batch_member_flags", ctypes.c_int, [_vp, ctypes.POINTER(_i32)]),

@@ -111,10 +111,12 @@ btrt_status check_desc(const btrt_grid_desc *g) {
         return fail(BTRT_EINVAL, "phi_ref, x0, y0 must be finite");
     if (g->fields & ~(BTRT_FIELD_SOURCE | BTRT_FIELD_DIFFUSION))
         return fail(BTRT_EINVAL, "unknown field bits 0x%x", g->fields);
-    if (g->shift != BTRT_SHIFT_REF && g->shift != BTRT_SHIFT_LOCAL && g->shift != BTRT_SHIFT_LOCAL_DW)
+    if (g->shift < BTRT_SHIFT_REF || g->shift > BTRT_SHIFT_LOCAL_DW_SR)
         return fail(BTRT_EINVAL, "unknown storage shift %d", g->shift);
-    if (g->shift == BTRT_SHIFT_LOCAL_DW && g->compute != BTRT_F32)
-        return fail(BTRT_EINVAL, "the double-word phi planes of BTRT_SHIFT_LOCAL_DW serve FP32 compute");
+    if (has_phi_lo(*g) && g->compute != BTRT_F32)
+        return fail(BTRT_EINVAL, "the double-word phi planes of BTRT_SHIFT_LOCAL_DW(_SR) serve FP32 compute");
+    if (stochastic_store(*g) && (g->compute != BTRT_F32 || (g->storage != BTRT_F16 && g->storage != BTRT_BF16)))
+        return fail(BTRT_EINVAL, "stochastic rounding (BTRT_SHIFT_LOCAL_SR, _DW_SR) serves F16/BF16 storage with FP32 compute");
     const long long pitch = (long long)((g->nx + 63) / 64) * 64;
     if (9 * pitch * (long long)g->ny >= (1LL << 31))
         return fail(BTRT_EINVAL, "grid %d x %d: the nine padded planes must hold fewer than 2^31 values "
@@ -135,8 +137,8 @@ Layout make_layout(const btrt_grid_desc *g) {
     off += L.fbuf_bytes;
     L.off_f[1] = off;
     off += L.fbuf_bytes;
-    // a double-word phi (BTRT_SHIFT_LOCAL_DW) keeps its low words in a second plane
-    const size_t phi_planes = g->shift == BTRT_SHIFT_LOCAL_DW ? 2 : 1;
+    // a double-word phi (BTRT_SHIFT_LOCAL_DW, _DW_SR) keeps its low words in a second plane
+    const size_t phi_planes = has_phi_lo(*g) ? 2 : 1;
     for (int k = 0; k < 2; ++k) {
         L.off_phi[k] = off;
         off += align_up(phi_planes * (size_t)L.plane * sr, kAlign);
@@ -361,6 +363,8 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
     }
     // the reference value of kShiftRef storage (zero otherwise)
     p.phi_ref = shift_of(g) == kShiftRef ? (Real)g.phi_ref : (Real)0.0;
+    // stochastic rounding: the seed of step index n (the same in every kernel form)
+    p.sr_seed = sr_step_seed(n);
 }
 
 template void btrt::fill_params<double>(btrt_lattice, SweepParams<double> &, int64_t, bool);
@@ -386,12 +390,15 @@ int btrt::sweep_mode(btrt_lattice L) {
 // two steps per launch halve them (512 instances of 32^2 to 1024^2 nodes, 2000
 // steps each, one after the other: 10.5 s with the vector form, 6.8 s with two
 // steps per launch).
+// Stochastically rounded storage has the plain and vector forms only: the vector
+// form from kVecAutoNodes on, the plain one below.
 constexpr long long kVecAutoNodes = 1LL << 21;
 int btrt::effective_sweep_variant(btrt_lattice L) {
-    if (L->g.compute != BTRT_F32 || L->g.shift == BTRT_SHIFT_LOCAL_DW) return BTRT_SWEEP_PLAIN;
+    if (L->g.compute != BTRT_F32 || has_phi_lo(L->g)) return BTRT_SWEEP_PLAIN;
     if (L->sweep_variant != BTRT_SWEEP_AUTO) return L->sweep_variant;
     const bool s16 = L->g.storage == BTRT_F16 || L->g.storage == BTRT_BF16;
     const bool large = (long long)L->g.nx * L->g.ny >= kVecAutoNodes;
+    if (stochastic_store(L->g)) return large ? BTRT_SWEEP_VEC : BTRT_SWEEP_PLAIN;
     return s16 && large ? BTRT_SWEEP_VEC : BTRT_SWEEP_TB2;
 }
 
@@ -626,7 +633,7 @@ btrt_status btrt_create(const btrt_grid_desc *g, void *dev_workspace, size_t wor
         delete L;
         return fail(BTRT_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
     }
-    if (g->compute == BTRT_F32 && g->shift != BTRT_SHIFT_LOCAL_DW) {
+    if (g->compute == BTRT_F32 && !has_phi_lo(*g) && !stochastic_store(*g)) {
         int bix, biy, box, boy;
         tma_box(g->storage, &bix, &biy, &box, &boy);
         bool ok = true;
@@ -842,7 +849,9 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
     const size_t sf = elem_size(g.storage);
     std::vector<unsigned char> raw((size_t)w * h * sf);
     const double wts[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-    const int sh = shift_of(g);
+    // the local forms: stored relative to the node's phi (both words of a double-word phi)
+    const int sh0 = shift_of(g);
+    const int sh = sh0 == kShiftLocalSR ? kShiftLocal : (sh0 == kShiftLocalDWSR ? kShiftLocalDW : sh0);
     std::vector<float> phiw, phiw_lo;   // the nodes' phi, for the local shifts (FP32 compute)
     if (sh == kShiftLocal || sh == kShiftLocalDW) {
         phiw.resize((size_t)w * h);
@@ -914,8 +923,11 @@ btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant) {
         return fail(BTRT_EINVAL, "the two-step sweeps serve FP32-compute lattices");
     if (variant == BTRT_SWEEP_VEC && L->g.compute != BTRT_F32)
         return fail(BTRT_EINVAL, "the vector-access sweep serves FP32-compute lattices");
-    if (L->g.shift == BTRT_SHIFT_LOCAL_DW && variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN)
-        return fail(BTRT_EINVAL, "lattices with double-word phi planes (BTRT_SHIFT_LOCAL_DW) take the plain form");
+    if (has_phi_lo(L->g) && variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN)
+        return fail(BTRT_EINVAL, "lattices with double-word phi planes (BTRT_SHIFT_LOCAL_DW, _DW_SR) take the plain form");
+    if (stochastic_store(L->g) && variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN &&
+        variant != BTRT_SWEEP_VEC)
+        return fail(BTRT_EINVAL, "stochastically rounded storage (BTRT_SHIFT_LOCAL_SR) takes the plain or vector form");
     if (variant == BTRT_SWEEP_TMA && !L->have_tma)
         return fail(BTRT_EINVAL, "the TMA sweep serves FP32-compute lattices whose tensor maps could be encoded");
     L->sweep_variant = variant;
@@ -931,7 +943,7 @@ btrt_status btrt_get_time(btrt_lattice L, int64_t *step, double *t) {
 
 // Bytes of one phi buffer (both words of a double-word phi).
 static size_t phi_state_bytes(btrt_lattice L) {
-    return (L->g.shift == BTRT_SHIFT_LOCAL_DW ? 2 : 1) * (size_t)L->lay.plane * elem_size(L->g.compute);
+    return (has_phi_lo(L->g) ? 2 : 1) * (size_t)L->lay.plane * elem_size(L->g.compute);
 }
 
 size_t btrt_state_bytes(btrt_lattice L) {

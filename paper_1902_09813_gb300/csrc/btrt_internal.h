@@ -30,6 +30,23 @@ struct Layout {
     long long resid_blocks = 0;   // partial slots of a residual sweep (one per block)
 };
 
+// Lattices whose phi is a double-word pair (a plane of low words after each phi plane).
+inline bool has_phi_lo(const btrt_grid_desc &g) {
+    return g.shift == BTRT_SHIFT_LOCAL_DW || g.shift == BTRT_SHIFT_LOCAL_DW_SR;
+}
+// Lattices whose 16-bit stored deviations are rounded stochastically.
+inline bool stochastic_store(const btrt_grid_desc &g) {
+    return g.shift == BTRT_SHIFT_LOCAL_SR || g.shift == BTRT_SHIFT_LOCAL_DW_SR;
+}
+// Stochastic-rounding seed of the step that produces step index n: the SplitMix64
+// output function (Steele, Lea and Flood, 2014) of the step index.
+inline unsigned int sr_step_seed(int64_t n) {
+    unsigned long long z = (unsigned long long)n * 0x9e3779b97f4a7c15ull + 0x632be59bd9b4e019ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return (unsigned int)(z ^ (z >> 31));
+}
+
 }  // namespace btrt
 
 // The host-side lattice object behind btrt_lattice.
@@ -62,7 +79,7 @@ struct btrt_lattice_s {
     template <typename Real> Real *phi() { return phi<Real>(cur); }
     // low words of phi plane k (BTRT_SHIFT_LOCAL_DW lattices: the plane after the high words)
     float *phi_lo(int k) {
-        return g.shift == BTRT_SHIFT_LOCAL_DW ? reinterpret_cast<float *>(ws + lay.off_phi[k]) + lay.plane : nullptr;
+        return btrt::has_phi_lo(g) ? reinterpret_cast<float *>(ws + lay.off_phi[k]) + lay.plane : nullptr;
     }
     void *fbuf(int k) { return ws + lay.off_f[k]; }
     template <typename Real> Real *tab() { return reinterpret_cast<Real *>(ws + lay.off_tab); }
@@ -115,7 +132,13 @@ inline void half_split(double q, int *n, int *h) {
 // Storage shift of a lattice (kShiftNone for FP64 / double-word storage).
 inline int shift_of(const btrt_grid_desc &g) {
     if (g.storage == BTRT_F64 || g.storage == BTRT_DF64) return kShiftNone;
-    return g.shift == BTRT_SHIFT_LOCAL ? kShiftLocal : (g.shift == BTRT_SHIFT_LOCAL_DW ? kShiftLocalDW : kShiftRef);
+    switch (g.shift) {
+    case BTRT_SHIFT_LOCAL: return kShiftLocal;
+    case BTRT_SHIFT_LOCAL_DW: return kShiftLocalDW;
+    case BTRT_SHIFT_LOCAL_SR: return kShiftLocalSR;
+    case BTRT_SHIFT_LOCAL_DW_SR: return kShiftLocalDWSR;
+    default: return kShiftRef;
+    }
 }
 
 // TMA-staged sweep (FP32 compute) and the box sizes its tensor maps need.

@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <mutex>
+#include <type_traits>
 
 #include "btrt_internal.h"
 #include "btrt_tb.cuh"
@@ -28,17 +29,31 @@ inline void launch_src(const SweepParams<Real> &p, dim3 g, dim3 b, cudaStream_t 
 }
 
 // Plain FP32-compute sweep for storage S: shift (reference, local, local with a
-// double-word phi) x {kGeneral, kLinear} x source.
+// double-word phi; for 16-bit storage also both local forms with stochastic
+// rounding) x {kGeneral, kLinear} x source.
 template <typename S>
 cudaError_t launch_f32_storage(const SweepParams<float> &p, int shift, int mode, cudaStream_t s) {
     const dim3 g = sweep_grid(p.nx, p.ny, RowsPerThread<float, S>::value), b = sweep_block();
     const bool lin = mode != kGeneral;
+    constexpr bool S16 = !std::is_same<S, float>::value;
     if (shift == kShiftLocal) {
         if (lin) launch_src<float, S, kShiftLocal, kLinear>(p, g, b, s);
         else launch_src<float, S, kShiftLocal, kGeneral>(p, g, b, s);
     } else if (shift == kShiftLocalDW) {
         if (lin) launch_src<float, S, kShiftLocalDW, kLinear>(p, g, b, s);
         else launch_src<float, S, kShiftLocalDW, kGeneral>(p, g, b, s);
+    } else if (shift == kShiftLocalSR || shift == kShiftLocalDWSR) {
+        if constexpr (S16) {
+            if (shift == kShiftLocalSR) {
+                if (lin) launch_src<float, S, kShiftLocalSR, kLinear>(p, g, b, s);
+                else launch_src<float, S, kShiftLocalSR, kGeneral>(p, g, b, s);
+            } else {
+                if (lin) launch_src<float, S, kShiftLocalDWSR, kLinear>(p, g, b, s);
+                else launch_src<float, S, kShiftLocalDWSR, kGeneral>(p, g, b, s);
+            }
+        } else {
+            return cudaErrorInvalidValue;   // stochastic rounding serves 16-bit storage
+        }
     } else {
         if (lin) launch_src<float, S, kShiftRef, kLinear>(p, g, b, s);
         else launch_src<float, S, kShiftRef, kGeneral>(p, g, b, s);
@@ -192,6 +207,13 @@ cudaError_t launch_vec_storage(const SweepParams<float> &p, int shift, int mode,
     if (shift == kShiftLocal) {
         if (lin) launch_vec_src<S, kShiftLocal, kLinear>(p, s);
         else launch_vec_src<S, kShiftLocal, kGeneral>(p, s);
+    } else if (shift == kShiftLocalSR) {
+        if constexpr (!std::is_same<S, float>::value) {
+            if (lin) launch_vec_src<S, kShiftLocalSR, kLinear>(p, s);
+            else launch_vec_src<S, kShiftLocalSR, kGeneral>(p, s);
+        } else {
+            return cudaErrorInvalidValue;
+        }
     } else {
         if (lin) launch_vec_src<S, kShiftRef, kLinear>(p, s);
         else launch_vec_src<S, kShiftRef, kGeneral>(p, s);

@@ -146,6 +146,7 @@ struct SweepParams {
     int *flags;            // bit 0: non-finite phi
     double *resid_partials;  // non-null: per-block sum of (phi^n - phi^{n-1})^2 (single-lattice sweep)
     Real phi_ref;          // kShiftRef: the reference value (0 otherwise)
+    unsigned int sr_seed;  // stochastic rounding: the step's seed (sr_step_seed of its step index)
     FoldConsts<Real> lin;
 };
 
@@ -183,9 +184,19 @@ __device__ __forceinline__ dw quot(dw a, dw b) { return a / b; }
 // B = u phi, C = phi and constant A with any k0 (kLinear) or k0 = 1 (kLinearK0One).
 enum { kGeneral = 0, kLinear = 1, kLinearK0One = 2 };
 // Stored form of the populations (see the top of this file).
-enum { kShiftNone = 0, kShiftRef = 1, kShiftLocal = 2, kShiftLocalDW = 3 };
-// The collision and the stored deviations of kShiftLocalDW are those of kShiftLocal.
-template <int SH> struct CollShift { static constexpr int value = SH == kShiftLocalDW ? kShiftLocal : SH; };
+// kShiftLocalSR and kShiftLocalDWSR are kShiftLocal and kShiftLocalDW with the
+// stored 16-bit deviations rounded stochastically (see pack_sr).
+enum { kShiftNone = 0, kShiftRef = 1, kShiftLocal = 2, kShiftLocalDW = 3, kShiftLocalSR = 4, kShiftLocalDWSR = 5 };
+// The collision and the stored deviations of the local variants are those of kShiftLocal.
+template <int SH> struct CollShift {
+    static constexpr int value = (SH == kShiftLocalDW || SH == kShiftLocalSR || SH == kShiftLocalDWSR) ? kShiftLocal : SH;
+};
+// The pull (neighbour phi, low words) of each stored form.
+template <int SH> struct PullShift {
+    static constexpr int value = SH == kShiftLocalSR ? kShiftLocal : (SH == kShiftLocalDWSR ? kShiftLocalDW : SH);
+};
+// Stochastic rounding of the stored values.
+template <int SH> struct StoreSR { static constexpr bool value = SH == kShiftLocalSR || SH == kShiftLocalDWSR; };
 // Source kinds (compile-time SRC); kSrcRuntime decides per lattice at run time,
 // kSrcRuntimeNR the same among the kinds other than the reaction term (whose
 // power-law code then stays out of the kernel).
@@ -570,6 +581,7 @@ __device__ __forceinline__ T ldg(const T *ptr) {
 template <typename Real, typename S, int SH, bool L2ONLY>
 __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const S *__restrict__ fin, int x,
                                               int y, int node, Real phi_prev, Real (&d)[9], Real phi_lo = Real(0)) {
+    constexpr int PS = PullShift<SH>::value;
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
         int sx = x - ex_of(i), sy = y - ey_of(i);
@@ -581,9 +593,9 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
         if (wx < 0 && wy < 0) {
             const int src = sy * p.pitch + sx;
             d[i] = Storage<S>::load(ldg<L2ONLY>(fin + BTRT_IX(p.flags, i * p.plane + src, 9 * p.plane)));
-            if constexpr (SH == kShiftLocal)
+            if constexpr (PS == kShiftLocal)
                 if (i != 0) d[i] = fma(wgt<Real>(i), ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, src, p.plane)) - phi_prev, d[i]);
-            if constexpr (SH == kShiftLocalDW)
+            if constexpr (PS == kShiftLocalDW)
                 if (i != 0)
                     d[i] = fma(wgt<Real>(i),
                                (ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, src, p.plane)) - phi_prev) +
@@ -602,9 +614,9 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
             // f_i = -f_o^+ + wall term; in shifted form the two shifts add up to -2 w_i rs
             // (for the local shift f_o^+ was stored relative to this node's own phi^{n-1} = rs)
             Real wt = wall_term(p, o, phi_w);
-            if constexpr (SH == kShiftRef) wt = wt - Real(2) * p.wref[i];
-            if constexpr (SH == kShiftLocal || SH == kShiftLocalDW) wt = fma(Real(-2) * wgt<Real>(i), phi_prev, wt);
-            if constexpr (SH == kShiftLocalDW) wt = fma(Real(-2) * wgt<Real>(i), phi_lo, wt);
+            if constexpr (PS == kShiftRef) wt = wt - Real(2) * p.wref[i];
+            if constexpr (PS == kShiftLocal || PS == kShiftLocalDW) wt = fma(Real(-2) * wgt<Real>(i), phi_prev, wt);
+            if constexpr (PS == kShiftLocalDW) wt = fma(Real(-2) * wgt<Real>(i), phi_lo, wt);
             d[i] = wt - dout;
         }
     }
@@ -629,11 +641,12 @@ __device__ __forceinline__ Real source_at(const SweepParams<Real> &p, Real xs, R
 template <typename Real, typename S, int SH, bool L2ONLY>
 __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int y, bool x_inner, Real (&f)[9],
                                           Real &phi_prev, Real *phi_lo_out = nullptr) {
+    constexpr int PS = PullShift<SH>::value;
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
     const int node = y * p.pitch + x;
     phi_prev = ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, node, p.plane));
     Real phi_lo = Real(0);
-    if constexpr (SH == kShiftLocalDW) {
+    if constexpr (PS == kShiftLocalDW) {
         phi_lo = ldg<L2ONLY>(p.phi_in_lo + BTRT_IX(p.flags, node, p.plane));
         *phi_lo_out = phi_lo;
     }
@@ -644,7 +657,7 @@ __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int
         for (int i = 0; i < 9; ++i)
             f[i] = Storage<S>::load(
                 ldg<L2ONLY>(fin + BTRT_IX(p.flags, i * p.plane + node - ey_of(i) * p.pitch - ex_of(i), 9 * p.plane)));
-        if constexpr (SH == kShiftLocal) {
+        if constexpr (PS == kShiftLocal) {
 #pragma unroll
             for (int i = 1; i < 9; ++i)
                 f[i] = fma(wgt<Real>(i),
@@ -652,7 +665,7 @@ __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int
                                phi_prev,
                            f[i]);
         }
-        if constexpr (SH == kShiftLocalDW) {
+        if constexpr (PS == kShiftLocalDW) {
 #pragma unroll
             for (int i = 1; i < 9; ++i) {
                 const int nb = node - ey_of(i) * p.pitch - ex_of(i);
@@ -665,6 +678,46 @@ __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int
     } else {
         pull_boundary<Real, S, SH, L2ONLY>(p, fin, x, y, node, phi_prev, f, phi_lo);
     }
+}
+
+// ---------------------------------------------------------------- stochastic rounding
+// Under diffusive scaling a step changes the state by much less than a 16-bit
+// last place, and round-to-nearest then makes nearly the same error in the same
+// direction step after step.  Stochastic rounding rounds up with probability
+// equal to the fraction of the last place that is cut off, so every stored
+// value is right on average and the errors of successive steps do not add up.
+// Random bits: the 32-bit finalizer of MurmurHash3 (Appleby) of the node index
+// mixed with the step's seed, then one multiply per population by a distinct
+// odd constant (the product's high bits are used).  They depend only on the
+// node, the step index and the population, so every kernel form stores the same
+// values.
+__device__ __forceinline__ unsigned int sr_node_bits(unsigned int seed, int node) {
+    unsigned int h = (unsigned int)node ^ seed;
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ unsigned int sr_bits(unsigned int h, int i) {
+    return h * (0x9e3779b1u + 0x3c6ef372u * (unsigned int)i);
+}
+// FP32 -> BF16: add 16 random bits below BF16's last place to the FP32 pattern and
+// truncate (BF16 has FP32's exponent range, so this holds for every finite value).
+// FP32 -> FP16: the same with the FP32 mantissa bits below FP16's last place: 13 in
+// FP16's normal range, 14 .. 23 in its subnormal range (values below 2^-24 are cut
+// to zero), then conversion toward zero.
+template <typename S> __device__ __forceinline__ S pack_sr(float v, unsigned int r);
+template <> __device__ __forceinline__ __nv_bfloat16 pack_sr<__nv_bfloat16>(float v, unsigned int r) {
+    const unsigned int b = __float_as_uint(v) + (r >> 16);
+    return __ushort_as_bfloat16((unsigned short)(b >> 16));
+}
+template <> __device__ __forceinline__ __half pack_sr<__half>(float v, unsigned int r) {
+    const unsigned int u = __float_as_uint(v);
+    const int e = (int)((u >> 23) & 0xffu);
+    const int k = e >= 113 ? 13 : min(23, 126 - e);
+    return __float2half_rz(__uint_as_float(u + ((r >> 9) & ((1u << k) - 1u))));
 }
 
 // Shifted post-collision value d_i^+ = f_i^+ - w_i rs -> the stored form.
@@ -687,9 +740,16 @@ __device__ __forceinline__ double finish_node(const SweepParams<Real> &p, int x,
     const Real rs = SC == kShiftLocal ? phi_prev : p.phi_ref;
     Real phid;
     const Real phi = collide_fold<Real, MODE, SRC, SC>(p, f, rs, phi_prev, src, p.first != 0, node, phid, Lc);
+    if constexpr (StoreSR<SH>::value) {
+        const unsigned int h = sr_node_bits(p.sr_seed, node);
 #pragma unroll
-    for (int i = 0; i < 9; ++i) fout[BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)] = store_value<Real, S, SC>(i, f[i], phid);
-    if constexpr (SH == kShiftLocalDW) {
+        for (int i = 0; i < 9; ++i)
+            fout[BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)] = pack_sr<S>(fma(-wgt<Real>(i), phid, f[i]), sr_bits(h, i));
+    } else {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fout[BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)] = store_value<Real, S, SC>(i, f[i], phid);
+    }
+    if constexpr (PullShift<SH>::value == kShiftLocalDW) {
         // phi^n = (phi_prev + phi_lo) + phid as a double-word pair: TwoSum of the high
         // word and phid (its sum is the collision's phi), the error into the low word,
         // then Fast2Sum to renormalise

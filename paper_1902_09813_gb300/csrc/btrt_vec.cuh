@@ -45,6 +45,16 @@ template <> struct Vec4<__half> {
         w.y = *reinterpret_cast<const unsigned int *>(&hi);
         return w;
     }
+    // stochastic rounding (pack_sr) with the random bits of each value
+    static __device__ __forceinline__ W put_sr(const float (&v)[kVec], unsigned int ra, unsigned int rb,
+                                               unsigned int rc, unsigned int rd) {
+        W w;
+        w.x = (unsigned int)__half_as_ushort(pack_sr<__half>(v[0], ra)) |
+              ((unsigned int)__half_as_ushort(pack_sr<__half>(v[1], rb)) << 16);
+        w.y = (unsigned int)__half_as_ushort(pack_sr<__half>(v[2], rc)) |
+              ((unsigned int)__half_as_ushort(pack_sr<__half>(v[3], rd)) << 16);
+        return w;
+    }
 };
 template <> struct Vec4<__nv_bfloat16> {
     using W = uint2;
@@ -57,6 +67,15 @@ template <> struct Vec4<__nv_bfloat16> {
         W w;
         w.x = *reinterpret_cast<const unsigned int *>(&lo);
         w.y = *reinterpret_cast<const unsigned int *>(&hi);
+        return w;
+    }
+    static __device__ __forceinline__ W put_sr(const float (&v)[kVec], unsigned int ra, unsigned int rb,
+                                               unsigned int rc, unsigned int rd) {
+        W w;
+        w.x = (unsigned int)__bfloat16_as_ushort(pack_sr<__nv_bfloat16>(v[0], ra)) |
+              ((unsigned int)__bfloat16_as_ushort(pack_sr<__nv_bfloat16>(v[1], rb)) << 16);
+        w.y = (unsigned int)__bfloat16_as_ushort(pack_sr<__nv_bfloat16>(v[2], rc)) |
+              ((unsigned int)__bfloat16_as_ushort(pack_sr<__nv_bfloat16>(v[3], rd)) << 16);
         return w;
     }
 };
@@ -100,6 +119,7 @@ __device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0
                                              const FoldConsts<float> *Lc = nullptr) {
     using W = typename Vec4<S>::W;
     constexpr bool TRIG = SRC == kSrcTrig || SRC == kSrcRuntime || SRC == kSrcRuntimeNR;
+    constexpr int SC = CollShift<SH>::value;   // kShiftLocalSR pulls and collides as kShiftLocal
     const S *__restrict__ fin = static_cast<const S *>(p.fin);
     const int node = y * p.pitch + x0;
 
@@ -118,14 +138,14 @@ __device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0
     float ph[3][kVec + 2];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        if (SH != kShiftLocal && r != 1) continue;
+        if (SC != kShiftLocal && r != 1) continue;
         const int at = node + (r - 1) * p.pitch;
         const float4 m = ldg<L2ONLY>(reinterpret_cast<const float4 *>(p.phi_in + BTRT_IX(p.flags, at, p.plane)));
         ph[r][1] = m.x;
         ph[r][2] = m.y;
         ph[r][3] = m.z;
         ph[r][4] = m.w;
-        if constexpr (SH == kShiftLocal) {
+        if constexpr (SC == kShiftLocal) {
             ph[r][0] = ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, at - 1, p.plane));
             ph[r][kVec + 1] = ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, at + kVec, p.plane));
         }
@@ -141,7 +161,7 @@ __device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0
         float f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = seg_value<S>(raw[i], edge[i], v - ex_of(i));
-        if constexpr (SH == kShiftLocal) {
+        if constexpr (SC == kShiftLocal) {
 #pragma unroll
             for (int i = 1; i < 9; ++i) f[i] = fma(wgt<float>(i), ph[1 - ey_of(i)][v - ex_of(i) + 1] - phi_prev, f[i]);
         }
@@ -151,12 +171,12 @@ __device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0
             xc = p.Xc[BTRT_IX(p.flags, x, p.nx)];
         }
         const float src = source_at<float, SRC>(p, xs, xc, y, node + v);
-        const float rs = SH == kShiftLocal ? phi_prev : p.phi_ref;
+        const float rs = SC == kShiftLocal ? phi_prev : p.phi_ref;
         float phid;
-        const float phi = collide_fold<float, MODE, SRC, SH>(p, f, rs, phi_prev, src, false, node + v, phid, Lc);
+        const float phi = collide_fold<float, MODE, SRC, SC>(p, f, rs, phi_prev, src, false, node + v, phid, Lc);
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            outv[i][v] = SH == kShiftLocal ? fma(-wgt<float>(i), phid, f[i]) : f[i];
+            outv[i][v] = SC == kShiftLocal ? fma(-wgt<float>(i), phid, f[i]) : f[i];
         phi_o[v] = phi;
         bad |= not_finite(phi);
     }
@@ -194,10 +214,20 @@ __device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, i
     S *__restrict__ fout = static_cast<S *>(p.fout);
     const int node = y * p.pitch + x0;
     return vec_interior<S, SH, MODE, SRC, L2ONLY>(p, x0, y, [&](const float (&outv)[9][kVec], const float (&phi_o)[kVec]) {
+        if constexpr (StoreSR<SH>::value) {
+            unsigned int h[kVec];
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            *reinterpret_cast<W *>(fout + BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)) =
-                V::put(outv[i][0], outv[i][1], outv[i][2], outv[i][3]);
+            for (int v = 0; v < kVec; ++v) h[v] = sr_node_bits(p.sr_seed, node + v);
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                *reinterpret_cast<W *>(fout + BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)) =
+                    V::put_sr(outv[i], sr_bits(h[0], i), sr_bits(h[1], i), sr_bits(h[2], i), sr_bits(h[3], i));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                *reinterpret_cast<W *>(fout + BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)) =
+                    V::put(outv[i][0], outv[i][1], outv[i][2], outv[i][3]);
+        }
         *reinterpret_cast<float4 *>(p.phi_out + BTRT_IX(p.flags, node, p.plane)) =
             make_float4(phi_o[0], phi_o[1], phi_o[2], phi_o[3]);
     }, Lc);

@@ -102,9 +102,11 @@ class Lattice:
                      phi_ref=None, shift="auto") -> "Lattice":
         """shift: stored form of F32/F16/BF16 populations -- "ref" (f - w_i phi_ref),
         "local" (f^+ - w_i phi of the writing node), "local_dw" (local, with phi kept
-        as a double-word pair so that it is never rounded to FP32; plain kernel form)
-        or "auto" (local for the 16-bit formats, whose rounding it keeps well below the
-        discretisation error; ref for FP32 storage)."""
+        as a double-word pair so that it is never rounded to FP32; plain kernel form),
+        "local_sr" (local, F16/BF16 storage rounded stochastically; plain and vector
+        forms), "local_dw_sr" (both; plain form) or "auto" (local for the 16-bit
+        formats, whose rounding it keeps well below the discretisation error; ref for
+        FP32 storage)."""
         storage = storage or compute
         if shift == "auto":
             shift = "local" if storage in ("f16", "bf16") else "ref"
@@ -251,6 +253,14 @@ class Lattice:
         C.check(self.lib.btrt_mass(self.handle, ctypes.byref(v)))
         return v.value
 
+    def settle(self, clear: bool = False) -> int:
+        """The step at which a batch froze this lattice (its step count is set back
+        to it), or -1 if it is not frozen.  clear: also remove the mark (only when
+        no queued batch launch still includes the lattice)."""
+        s = ctypes.c_int64()
+        C.check(self.lib.btrt_settle(self.handle, 1 if clear else 0, ctypes.byref(s)))
+        return s.value
+
     def check(self) -> int:
         """Raises BtrtError(EUNSTABLE) if the sweep has produced a non-finite phi."""
         flags = ctypes.c_int32()
@@ -320,16 +330,41 @@ class Batch:
         C.check(self.lib.btrt_batch_step(self.handle, int(nsteps), 1 if residual else 0))
         return self
 
-    def step_tol(self, nsteps: int, tol: float, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    def prepare(self, nsteps: int, residual: bool = True):
+        """Capture the CUDA graphs of an nsteps-step call (step with residual, or
+        step_tol) without running them; no member advances."""
+        C.check(self.lib.btrt_batch_prepare(self.handle, int(nsteps), 1 if residual else 0))
+        return self
+
+    def graphs(self) -> int:
+        """Slice graphs held (-1: capture failed, launches go directly)."""
+        n = ctypes.c_int32()
+        C.check(self.lib.btrt_batch_graphs(self.handle, ctypes.byref(n)))
+        return n.value
+
+    def step_tol(self, nsteps: int, tol: float, out: Optional[torch.Tensor] = None,
+                 resid_out: Optional[torch.Tensor] = None) -> torch.Tensor:
         """Advance nsteps steps and flag, on the device, each member whose residual
-        of the last step is below tol (bit 0) or whose phi went non-finite (bit 1).
-        The flags land in `out` (pinned host int32 by default) in stream order:
-        synchronise the batch stream before reading them."""
+        of the last step is below tol (bit 0), whose phi went non-finite (bit 1) or
+        that was frozen before the call (bit 2).  The flags land in `out` (pinned
+        host int32 by default) and, if given, the residuals in `resid_out` (float64,
+        same memory kind) in stream order: synchronise the batch stream, or an event
+        recorded after the call, before reading them."""
         if out is None:
             out = torch.empty(len(self.members), dtype=torch.int32, pin_memory=True)
+        if resid_out is not None and resid_out.is_cuda != out.is_cuda:
+            raise ValueError("out and resid_out must both be host or both be device tensors")
         C.check(self.lib.btrt_batch_step_tol(self.handle, int(nsteps), float(tol),
-                                             ctypes.c_void_p(out.data_ptr()), 1 if out.is_cuda else 0))
+                                             ctypes.c_void_p(out.data_ptr()),
+                                             ctypes.c_void_p(resid_out.data_ptr() if resid_out is not None else 0),
+                                             1 if out.is_cuda else 0))
         return out
+
+    def set_freeze(self, enable: bool = True):
+        """step_tol freezes the members it flags: later batch launches leave them
+        unchanged (Lattice.settle restores their step counts)."""
+        C.check(self.lib.btrt_batch_set_freeze(self.handle, 1 if enable else 0))
+        return self
 
     def member_flags(self) -> np.ndarray:
         """Each member's device flags (bit 0: non-finite phi)."""

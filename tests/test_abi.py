@@ -81,11 +81,29 @@ def test_invalid_descriptions_rejected(lib, kw):
 
 def test_unknown_storage_shift_rejected(lib):
     d = _desc(compute="f32", storage="f16")
-    d.shift = 3
-    assert lib.btrt_workspace_bytes(ctypes.byref(d)) == 0
-    assert b"shift" in lib.btrt_last_error()
-    d.shift = 1
-    assert lib.btrt_workspace_bytes(ctypes.byref(d)) > 0
+    for bad in (5, -1):
+        d.shift = bad
+        assert lib.btrt_workspace_bytes(ctypes.byref(d)) == 0
+        assert b"shift" in lib.btrt_last_error()
+    for good in (0, 1, 2, 3, 4):
+        d.shift = good
+        assert lib.btrt_workspace_bytes(ctypes.byref(d)) > 0
+
+
+def test_stochastic_rounding_needs_16bit_storage(lib):
+    """BTRT_SHIFT_LOCAL_SR / _DW_SR round F16/BF16 storage stochastically: FP32
+    compute with 16-bit storage only; the _DW_SR form holds the low-word planes."""
+    from paper_1902_09813_gb300.lattice import workspace_bytes
+    from paper_1902_09813_gb300 import _capi as C
+    for comp, st in (("f32", "f32"), ("f64", "f64"), ("df64", "df64")):
+        for sh in ("local_sr", "local_dw_sr"):
+            with pytest.raises(C.BtrtError):
+                workspace_bytes(_desc(compute=comp, storage=st, shift=sh))
+    for st in ("f16", "bf16"):
+        loc = workspace_bytes(_desc(compute="f32", storage=st, shift="local"))
+        assert workspace_bytes(_desc(compute="f32", storage=st, shift="local_sr")) == loc
+        assert workspace_bytes(_desc(compute="f32", storage=st, shift="local_dw_sr")) == \
+            workspace_bytes(_desc(compute="f32", storage=st, shift="local_dw"))
 
 
 def test_create_rejects_null_workspace(lib):

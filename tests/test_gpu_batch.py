@@ -237,6 +237,84 @@ def test_step_tol_flags_match_residuals_and_nonfinite():
     b.close()
 
 
+@pytest.mark.parametrize("own_stream", [False, True])
+def test_slice_graphs_captured_and_prepare_advances_nothing(own_stream):
+    """The slice graphs are captured on the default stream as on a stream of the
+    caller's; btrt_batch_prepare captures without running (no member moves), and
+    the replayed graphs give the members' plain results bitwise, in every form."""
+    import torch
+    from paper_1902_09813_gb300 import Batch
+    probs = _mix("f32", "f16", count=5, seed=31)
+    stream = torch.cuda.Stream() if own_stream else torch.cuda.current_stream()
+    with torch.cuda.stream(stream):
+        mixed = [_make(p, "f32", "f16", "local") for p in probs]
+        ref = [_make(p, "f32", "f16", "local") for p in probs]
+        b = Batch(mixed, stream=stream)
+        for form in (1, 2, 3, 0):
+            b.set_tiles(32, 4, 2, form)
+            assert b.graphs() == 0
+            b.prepare(6)
+            # the cooperative persistent form (0) may not be capturable: it then launches directly
+            captured = b.graphs()
+            assert captured == 1 or (form == 0 and captured == -1)
+            assert mixed[0].time()[0] == ref[0].time()[0]      # nothing ran
+            b.step_tol(6, tol=0.0)
+            b.step(6, residual=True)
+            assert b.graphs() == captured                      # replayed, not captured again
+            for a in ref:
+                a.step(12)
+        stream.synchronize()
+        for a, m in zip(ref, mixed):
+            assert np.array_equal(a.phi_host(), m.phi_host())
+        b.close()
+
+
+@pytest.mark.parametrize("form", [1, 2, 3, 0])
+def test_freeze_keeps_flagged_members_and_settle_rewinds(form):
+    """Freezing on: the members a step_tol call flags are left unchanged by later
+    launches of this batch and of a new one (bit 2 and a NaN residual from then
+    on), settle() sets their step counts back to the flagged step, and a cleared
+    member steps on alone as if never batched; the others stay bitwise equal to
+    their solves alone."""
+    import torch
+    from paper_1902_09813_gb300 import Batch
+    probs = _mix("f32", "f16", count=6, seed=41)
+    mixed = [_make(p, "f32", "f16", "local") for p in probs]
+    b = Batch(mixed).set_tiles(32, 4, 2, form).set_freeze(True)
+    n = len(mixed)
+    f = torch.empty(n, dtype=torch.int32, pin_memory=True)
+    r = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    b.step_tol(10, tol=0.0, out=f, resid_out=r)
+    torch.cuda.synchronize()
+    assert not f.numpy().any()
+    tol = float(np.median(r.numpy()))
+    b.step_tol(5, tol=tol, out=f, resid_out=r)
+    torch.cuda.synchronize()
+    frozen = (f.numpy() & 1).astype(bool)
+    assert 0 < frozen.sum() < n
+    b.step_tol(7, tol=0.0, out=f, resid_out=r)
+    torch.cuda.synchronize()
+    assert list(f.numpy() & 4) == [4 if z else 0 for z in frozen]
+    assert np.all(np.isnan(r.numpy()[frozen])) and not np.any(np.isnan(r.numpy()[~frozen]))
+    b.close()
+    b2 = Batch(mixed).set_tiles(32, 8, 1, 1)
+    b2.step(4)
+    torch.cuda.synchronize()
+    b2.close()
+    for k, (p, lat) in enumerate(zip(probs, mixed)):
+        s = lat.settle()
+        assert s == (15 if frozen[k] else -1)
+        steps = 15 if frozen[k] else 26
+        assert lat.time()[0] == steps
+        ref = _make(p, "f32", "f16", "local").step(steps)
+        assert np.array_equal(lat.phi_host(), ref.phi_host())
+        if frozen[k]:
+            assert lat.settle(clear=True) == 15
+            assert lat.settle() == -1
+            lat.step(3)
+            assert np.array_equal(lat.phi_host(), ref.step(3).phi_host())
+
+
 def test_barrier_timeout_reported():
     """A barrier that can never be released ends the launch after the wait limit
     with BTRT_ETIMEOUT (no hang, no device fault); the device stays usable."""

@@ -1,0 +1,118 @@
+"""Stochastically rounded FP16/BF16 storage (BTRT_SHIFT_LOCAL_SR and, with phi as
+a double-word pair, BTRT_SHIFT_LOCAL_DW_SR).
+
+Checked here: against the FP64 oracle about as close as round-to-nearest storage
+(stochastic rounding has twice the error variance of round-to-nearest per value,
+but no repeated bias); the plain and vector forms store the same values bitwise,
+since the random bits depend only on the node, the step index and the population;
+the stored values are not those of round-to-nearest; the steps are reproducible
+(same steps, same values) and survive checkpoint/resume bitwise; the kernel forms,
+storage formats and batches that do not take it refuse it."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as w
+from conftest import cpu_threads
+
+pytestmark = pytest.mark.gpu
+
+
+def _rel(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def _lattice(p, storage, shift, **kw):
+    from paper_1902_09813_gb300 import Lattice
+    return Lattice.from_problem(p, compute="f32", storage=storage, shift=shift, **kw)
+
+
+CASES = [(37, 29, (0, 0, 0, 0), True, "trig"), (37, 29, (1, 1, 1, 1), True, "trig"),
+         (70, 65, (0, 0, 1, 1), True, "const"), (96, 40, (1, 1, 1, 1), False, "trig"),
+         (3, 3, (1, 1, 1, 1), True, "const"), (5, 97, (1, 1, 0, 0), True, "reaction")]
+
+
+@pytest.mark.parametrize("shift", ["local_sr", "local_dw_sr"])
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}-bc{''.join(map(str, c[2]))}-{c[4]}")
+def test_sr_matches_oracle_like_round_to_nearest(case, storage, shift):
+    nx, ny, bc, nonlin, src = case
+    p = w.random_state_problem(nx, ny, seed=17 * nx + ny, bc=bc, nonlinear=nonlin, source=src,
+                               flux_q=2.5 if src == "reaction" else 2.0)
+    steps = 10
+    ref = oracle.OracleLattice(p, nthreads=cpu_threads()).init().step(steps).phi()
+    got = {}
+    for sh in (shift, shift.replace("_sr", "")):
+        lat = _lattice(p, storage, sh)
+        lat.init(p.phi0(), t0=p.t0).step(steps)
+        assert lat.check() == 0
+        got[sh] = _rel(lat.phi_host(), ref)
+    rn = got[shift.replace("_sr", "")]
+    assert got[shift] <= 2.0 * rn + 1e-6, got
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("workload", ["mms", "nonlinear"])
+def test_sr_plain_and_vector_forms_bitwise(storage, workload):
+    """Interior groups on the vector path, edges on the per-node path: every node
+    stores the same stochastically rounded values as in the plain form."""
+    if workload == "mms":
+        p = w.mms_sinsin(n=130)
+    else:
+        p = w.random_state_problem(134, 70, seed=5, bc=(0, 0, 1, 1), nonlinear=True)
+    out = {}
+    for form in ("plain", "vec"):
+        lat = _lattice(p, storage, "local_sr")
+        lat.set_sweep_variant(form)
+        lat.init(p.phi0(), t0=p.t0).step(9)
+        out[form] = (lat.phi_host(), lat.read_f())
+    assert np.array_equal(out["plain"][0], out["vec"][0])
+    assert np.array_equal(out["plain"][1], out["vec"][1])
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_sr_differs_from_round_to_nearest_and_repeats(storage):
+    p = w.random_state_problem(66, 41, seed=9, bc=(1, 1, 0, 0), nonlinear=True)
+    runs = []
+    for shift in ("local_sr", "local_sr", "local"):
+        lat = _lattice(p, storage, shift).init(p.phi0(), t0=p.t0).step(6)
+        runs.append(lat.read_f())
+    assert np.array_equal(runs[0], runs[1])          # same steps, same random bits
+    assert not np.array_equal(runs[0], runs[2])      # not the round-to-nearest values
+    # the two roundings differ by at most one last place of the stored deviation
+    assert _rel(runs[0], runs[2]) < 1e-2
+
+
+@pytest.mark.parametrize("shift", ["local_sr", "local_dw_sr"])
+def test_sr_checkpoint_resume_bitwise(shift):
+    p = w.random_state_problem(45, 33, seed=4, bc=(1, 1, 0, 0), nonlinear=True)
+    a = _lattice(p, "bf16", shift)
+    a.init(p.phi0()).step(7)
+    state = a.save()
+    a.step(6)
+    b = _lattice(p, "bf16", shift)
+    b.load(state)
+    b.step(6)
+    assert np.array_equal(a.phi_host(), b.phi_host())
+    assert np.array_equal(a.read_f(), b.read_f())
+
+
+def test_sr_refusals():
+    from paper_1902_09813_gb300 import Batch, Lattice, _capi as C
+    p = w.random_state_problem(40, 30, seed=6)
+    lat = _lattice(p, "f16", "local_sr").init(p.phi0())
+    for form in ("tb2", "tb2v", "tma"):
+        with pytest.raises(C.BtrtError):
+            lat.set_sweep_variant(form)
+    lat.set_sweep_variant("vec")
+    lat.set_sweep_variant("plain")
+    dw = _lattice(p, "f16", "local_dw_sr").init(p.phi0())
+    with pytest.raises(C.BtrtError):
+        dw.set_sweep_variant("vec")
+    for bad in (lat, dw):
+        with pytest.raises(C.BtrtError):
+            Batch([bad])
+    with pytest.raises(C.BtrtError):
+        Lattice.from_problem(p, compute="f32", storage="f32", shift="local_sr")
+    with pytest.raises(C.BtrtError):
+        Lattice.from_problem(p, compute="f64", storage="f64", shift="local_sr")

@@ -11,9 +11,16 @@ from paper_1902_09813_gb300 import serve
 
 
 class _FakeLattice:
+    """Keeps a step count.  A frozen lattice (flagged by a batch with freezing on)
+    no longer moves on the device, while its host count goes on with its batch;
+    settle() sets the count back, as the library does."""
+    closed = 0
+
     def __init__(self, p):
         self.p = p
-        self.steps = 0
+        self.steps = 0          # device state
+        self.host_steps = 0     # the step count the host believes
+        self.frozen_at = None
 
     @classmethod
     def from_problem(cls, p, compute="f32", storage="f16", stream=None, shift="auto"):
@@ -22,40 +29,64 @@ class _FakeLattice:
     def init(self, phi0, t0=0.0):
         return self
 
+    def settle(self, clear=False):
+        if self.frozen_at is None:
+            return -1
+        self.host_steps = self.frozen_at
+        return self.frozen_at
+
     def phi_host(self):
+        assert self.host_steps == self.steps
         return np.full((self.p.ny, self.p.nx), float(self.steps))
+
+    def close(self):
+        _FakeLattice.closed += 1
 
 
 class _FakeBatch:
     """Residual of a member after s steps: rate ** s (rate in the problem's meta);
-    a member whose meta has `bad_at` raises flag bit 0 once it passes that step."""
+    a member whose meta has `bad_at` raises flag bit 1 once it passes that step."""
     created = 0
+    open_ = 0
 
     def __init__(self, lats, stream=None):
         self.lats = lats
+        self.freeze = False
         _FakeBatch.created += 1
+        _FakeBatch.open_ += 1
 
     def set_tiles(self, *shape):
         return self
 
-    def step(self, n, residual=False):
-        for lat in self.lats:
-            lat.steps += n
+    def set_freeze(self, on=True):
+        self.freeze = on
         return self
 
-    def residuals(self):
-        return np.array([lat.p.meta["rate"] ** lat.steps for lat in self.lats])
+    def prepare(self, n, residual=True):
+        return self
 
-    def step_tol(self, n, tol, out=None):
+    def step(self, n, residual=False):
+        for lat in self.lats:
+            lat.host_steps += n
+            if lat.frozen_at is None:
+                lat.steps += n
+        return self
+
+    def step_tol(self, n, tol, out=None, resid_out=None):
         self.step(n, residual=True)
-        conv = (self.residuals() < tol).astype(np.int32)
-        return conv | (2 * self.member_flags().astype(np.int32))
-
-    def member_flags(self):
-        return np.array([1 if lat.steps >= lat.p.meta.get("bad_at", 1 << 30) else 0 for lat in self.lats])
+        for k, lat in enumerate(self.lats):
+            if lat.frozen_at is not None:
+                out[k], resid_out[k] = 4, float("nan")
+                continue
+            r = lat.p.meta["rate"] ** lat.steps
+            f = (1 if r < tol else 0) | (2 if lat.steps >= lat.p.meta.get("bad_at", 1 << 30) else 0)
+            out[k], resid_out[k] = f, r
+            if self.freeze and f:
+                lat.frozen_at = lat.steps
+        return out
 
     def close(self):
-        pass
+        _FakeBatch.open_ -= 1
 
 
 @pytest.fixture
@@ -63,6 +94,8 @@ def fakes(monkeypatch):
     monkeypatch.setattr(serve, "Lattice", _FakeLattice)
     monkeypatch.setattr(serve, "Batch", _FakeBatch)
     _FakeBatch.created = 0
+    _FakeBatch.open_ = 0
+    _FakeLattice.closed = 0
 
 
 def _problems(rates, n=32):
@@ -151,3 +184,31 @@ def test_depth_series_thinning():
     assert out[0] == list(depth[0]) and out[-1] == list(depth[-1])
     assert 16 <= len(out) <= 18
     assert serve.depth_series([]) == []
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_queued_slices_give_the_same_results(fakes, depth):
+    """With one, two or three slices queued ahead of the flags being read, every
+    request stops at the same step with the same phi (a flagged member stays
+    frozen in the slices queued after it: the fake checks that the host's step
+    count was set back before phi is read); every lattice and every batch is
+    closed at the end and the budget is returned."""
+    probs = _problems([0.5, 0.9, 0.99, 0.5, 0.7, 0.95])
+    probs[4].meta["bad_at"] = 20
+    srv = serve.Server(budget_bytes=1e12, slice_steps=10, max_steps=120, tol=1e-6, stream=object(),
+                       depth=depth)
+    res = srv.run([(0.0, p) for p in probs])
+    assert [r.status for r in res] == ["done", "done", "done", "done", "unstable", "done"]
+    expect = []
+    for r in (0.5, 0.9, 0.99, 0.5, None, 0.95):
+        s = 10
+        while r is not None and r ** s >= 1e-6 and s < 120:
+            s += 10
+        expect.append(s if r is not None else 20)
+    assert [r.steps for r in res] == expect
+    assert all(np.all(r.phi == r.steps) for r in res)
+    assert _FakeLattice.closed == len(probs) and _FakeBatch.open_ == 0
+    assert srv._used == 0
+    caps = sum(1 for r in res if r.status == "done" and r.steps == 120)
+    assert caps == 3 and srv.stats["cap_hits"] == caps
+    assert srv.stats["tol_hits"] == 2 and srv.stats["unstable"] == 1
