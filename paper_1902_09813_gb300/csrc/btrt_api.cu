@@ -849,6 +849,8 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
     const size_t sf = elem_size(g.storage);
     std::vector<unsigned char> raw((size_t)w * h * sf);
     const double wts[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+    // FP16 deviations of the stochastically rounded forms are stored scaled by 2^12
+    const bool sr_f16 = stochastic_store(g) && g.storage == BTRT_F16;
     // the local forms: stored relative to the node's phi (both words of a double-word phi)
     const int sh0 = shift_of(g);
     const int sh = sh0 == kShiftLocalSR ? kShiftLocal : (sh0 == kShiftLocalDWSR ? kShiftLocalDW : sh0);
@@ -886,7 +888,7 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
                 v = (double)hl[0] + (double)hl[1];
             }
             else if (g.storage == BTRT_F32) { float fv; std::memcpy(&fv, &raw[k * 4], 4); v = fv; }
-            else v = half_bits_to_double(g.storage, &raw[k * 2]);
+            else v = half_bits_to_double(g.storage, &raw[k * 2]) * (sr_f16 ? 1.0 / 4096.0 : 1.0);
             const double loc = sh == kShiftLocal     ? wts[i] * (double)phiw[k]
                                : sh == kShiftLocalDW ? wts[i] * ((double)phiw[k] + (double)phiw_lo[k])
                                                      : 0.0;

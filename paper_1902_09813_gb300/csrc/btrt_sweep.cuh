@@ -486,6 +486,57 @@ __device__ __forceinline__ bool not_finite(float v) {
     return (__float_as_int(v) & 0x7f800000) == 0x7f800000;
 }
 
+// ---------------------------------------------------------------- stochastic rounding
+// Under diffusive scaling a step changes the state by much less than a 16-bit
+// last place, and round-to-nearest then makes nearly the same error in the same
+// direction step after step.  Stochastic rounding rounds up with probability
+// equal to the fraction of the last place that is cut off, so every stored
+// value is right on average and the errors of successive steps do not add up.
+// Random bits: the 32-bit finalizer of MurmurHash3 (Appleby) of the node index
+// mixed with the step's seed, then one multiply per population by a distinct
+// odd constant (the product's high bits are used).  They depend only on the
+// node, the step index and the population, so every kernel form stores the same
+// values.
+__device__ __forceinline__ unsigned int sr_node_bits(unsigned int seed, int node) {
+    unsigned int h = (unsigned int)node ^ seed;
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+__device__ __forceinline__ unsigned int sr_bits(unsigned int h, int i) {
+    return h * (0x9e3779b1u + 0x3c6ef372u * (unsigned int)i);
+}
+// FP32 -> BF16: add 16 random bits below BF16's last place to the FP32 pattern and
+// truncate (BF16 has FP32's exponent range, so this holds for every finite value).
+// FP32 -> FP16: the deviations are stored scaled by kSrScaleF16 = 2^12, which keeps
+// them in FP16's normal range (on fine grids they are 1e-5 and below, where FP16's
+// subnormal spacing 2^-24 would be a large part of each value; FP16's largest
+// value, 65504, still allows deviations up to 16); then 13 random bits below FP16's
+// last place are added to the FP32 pattern and the value converted toward zero.
+// Both scalings are exact (powers of two).  Scaled values below FP16's normal range
+// (deviations below 1.5e-8) are cut toward zero.
+constexpr float kSrScaleF16 = 4096.f;
+template <typename S> __device__ __forceinline__ S pack_sr(float v, unsigned int r);
+template <> __device__ __forceinline__ __nv_bfloat16 pack_sr<__nv_bfloat16>(float v, unsigned int r) {
+    const unsigned int b = __float_as_uint(v) + (r >> 16);
+    return __ushort_as_bfloat16((unsigned short)(b >> 16));
+}
+template <> __device__ __forceinline__ __half pack_sr<__half>(float v, unsigned int r) {
+    return __float2half_rz(__uint_as_float(__float_as_uint(v * kSrScaleF16) + (r >> 19)));
+}
+// The stored deviation back in the compute type: FP16 values of the stochastically
+// rounded forms carry the 2^12 scale.
+template <typename S, int SH> struct DevScaled {
+    static constexpr bool value = StoreSR<SH>::value && std::is_same<S, __half>::value;
+};
+template <typename Real, typename S, int SH> __device__ __forceinline__ Real dev_load(S v) {
+    if constexpr (DevScaled<S, SH>::value) return Storage<S>::load(v) * (1.f / kSrScaleF16);
+    else return Storage<S>::load(v);
+}
+
 // FP64 and double-word storage are never shifted; the other formats take the
 // shift the lattice was created with.
 template <typename S, int SH> struct ShiftOf { static constexpr int value = SH; };
@@ -592,7 +643,7 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
         if (sy >= p.ny) { if (p.hbb_y) wy = 3; else sy -= p.ny; }
         if (wx < 0 && wy < 0) {
             const int src = sy * p.pitch + sx;
-            d[i] = Storage<S>::load(ldg<L2ONLY>(fin + BTRT_IX(p.flags, i * p.plane + src, 9 * p.plane)));
+            d[i] = dev_load<Real, S, SH>(ldg<L2ONLY>(fin + BTRT_IX(p.flags, i * p.plane + src, 9 * p.plane)));
             if constexpr (PS == kShiftLocal)
                 if (i != 0) d[i] = fma(wgt<Real>(i), ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, src, p.plane)) - phi_prev, d[i]);
             if constexpr (PS == kShiftLocalDW)
@@ -610,7 +661,7 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
                 phi_w = wall_value(p, wy, x);
             else
                 phi_w = wall_value(p, wx, y);
-            const Real dout = Storage<S>::load(ldg<L2ONLY>(fin + BTRT_IX(p.flags, o * p.plane + node, 9 * p.plane)));
+            const Real dout = dev_load<Real, S, SH>(ldg<L2ONLY>(fin + BTRT_IX(p.flags, o * p.plane + node, 9 * p.plane)));
             // f_i = -f_o^+ + wall term; in shifted form the two shifts add up to -2 w_i rs
             // (for the local shift f_o^+ was stored relative to this node's own phi^{n-1} = rs)
             Real wt = wall_term(p, o, phi_w);
@@ -655,7 +706,7 @@ __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int
     } else if (x_inner && y > 0 && y < p.ny - 1) {
 #pragma unroll
         for (int i = 0; i < 9; ++i)
-            f[i] = Storage<S>::load(
+            f[i] = dev_load<Real, S, SH>(
                 ldg<L2ONLY>(fin + BTRT_IX(p.flags, i * p.plane + node - ey_of(i) * p.pitch - ex_of(i), 9 * p.plane)));
         if constexpr (PS == kShiftLocal) {
 #pragma unroll
@@ -678,46 +729,6 @@ __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int
     } else {
         pull_boundary<Real, S, SH, L2ONLY>(p, fin, x, y, node, phi_prev, f, phi_lo);
     }
-}
-
-// ---------------------------------------------------------------- stochastic rounding
-// Under diffusive scaling a step changes the state by much less than a 16-bit
-// last place, and round-to-nearest then makes nearly the same error in the same
-// direction step after step.  Stochastic rounding rounds up with probability
-// equal to the fraction of the last place that is cut off, so every stored
-// value is right on average and the errors of successive steps do not add up.
-// Random bits: the 32-bit finalizer of MurmurHash3 (Appleby) of the node index
-// mixed with the step's seed, then one multiply per population by a distinct
-// odd constant (the product's high bits are used).  They depend only on the
-// node, the step index and the population, so every kernel form stores the same
-// values.
-__device__ __forceinline__ unsigned int sr_node_bits(unsigned int seed, int node) {
-    unsigned int h = (unsigned int)node ^ seed;
-    h ^= h >> 16;
-    h *= 0x85ebca6bu;
-    h ^= h >> 13;
-    h *= 0xc2b2ae35u;
-    h ^= h >> 16;
-    return h;
-}
-__device__ __forceinline__ unsigned int sr_bits(unsigned int h, int i) {
-    return h * (0x9e3779b1u + 0x3c6ef372u * (unsigned int)i);
-}
-// FP32 -> BF16: add 16 random bits below BF16's last place to the FP32 pattern and
-// truncate (BF16 has FP32's exponent range, so this holds for every finite value).
-// FP32 -> FP16: the same with the FP32 mantissa bits below FP16's last place: 13 in
-// FP16's normal range, 14 .. 23 in its subnormal range (values below 2^-24 are cut
-// to zero), then conversion toward zero.
-template <typename S> __device__ __forceinline__ S pack_sr(float v, unsigned int r);
-template <> __device__ __forceinline__ __nv_bfloat16 pack_sr<__nv_bfloat16>(float v, unsigned int r) {
-    const unsigned int b = __float_as_uint(v) + (r >> 16);
-    return __ushort_as_bfloat16((unsigned short)(b >> 16));
-}
-template <> __device__ __forceinline__ __half pack_sr<__half>(float v, unsigned int r) {
-    const unsigned int u = __float_as_uint(v);
-    const int e = (int)((u >> 23) & 0xffu);
-    const int k = e >= 113 ? 13 : min(23, 126 - e);
-    return __float2half_rz(__uint_as_float(u + ((r >> 9) & ((1u << k) - 1u))));
 }
 
 // Shifted post-collision value d_i^+ = f_i^+ - w_i rs -> the stored form.

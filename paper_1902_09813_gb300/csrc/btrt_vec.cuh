@@ -161,6 +161,10 @@ __device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0
         float f[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) f[i] = seg_value<S>(raw[i], edge[i], v - ex_of(i));
+        if constexpr (DevScaled<S, SH>::value) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] *= 1.f / kSrScaleF16;
+        }
         if constexpr (SC == kShiftLocal) {
 #pragma unroll
             for (int i = 1; i < 9; ++i) f[i] = fma(wgt<float>(i), ph[1 - ey_of(i)][v - ex_of(i) + 1] - phi_prev, f[i]);
