@@ -81,18 +81,18 @@ FP64_NOMINAL_TOPS = 0.625
 # to them both are re-taken and the digest updated (a CPU test checks it), and
 # until then the traffic is reported as null.
 FP64_SWEEP_SOURCES = ("btrt_sweep.cuh", "btrt_dw.cuh")   # the FP64 sweep's device code
-FP64_SWEEP_DIGEST = "310e6ddfe7f4a381"
+FP64_SWEEP_DIGEST = "868baab5f6c8f892"
 FP64_TRAFFIC_PER_NODE = 149.3
 # DRAM bytes per node and step of the two-step FP32-compute kernel measured by ncu,
 # keyed by (storage, shift), for the sources with digest TB2_DIGEST.
 TB2_SOURCES = ("btrt_sweep.cuh", "btrt_tb.cuh", "btrt_launch.cuh")
-TB2_DIGEST = "8c614ffa0c32392a"
+TB2_DIGEST = "c9b626338ac63ab1"
 TB2_DRAM_BYTES_PER_UPDATE = {("f32", "ref"): 38.6, ("f16", "local"): 20.9}
 # DRAM bytes per node of one launch of the vector-access sweep measured by ncu,
 # keyed by (storage, shift), for the sources with digest VEC_DIGEST.
 VEC_SOURCES = ("btrt_sweep.cuh", "btrt_vec.cuh", "btrt_launch.cuh")
-VEC_DIGEST = "7692bfccf9de4946"
-VEC_DRAM_BYTES_PER_UPDATE = {("f16", "local"): 41.4}
+VEC_DIGEST = "1f7f0e702b3ffe08"
+VEC_DRAM_BYTES_PER_UPDATE = {("f16", "local"): 41.4, ("f16", "local_sr"): 41.2}
 
 
 def measure_fp64_peak(iters: int = 2000):
