@@ -116,3 +116,37 @@ def test_sr_refusals():
         Lattice.from_problem(p, compute="f32", storage="f32", shift="local_sr")
     with pytest.raises(C.BtrtError):
         Lattice.from_problem(p, compute="f64", storage="f64", shift="local_sr")
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+def test_sr_unbiased_on_a_uniform_state(storage):
+    """A uniform field: every node computes the same post-collision deviations, so
+    round-to-nearest stores the same rounded value everywhere (a bias of up to half
+    a last place), while stochastic rounding stores the two neighbouring values in
+    proportions whose mean is the unrounded deviation (FP32 storage of the same
+    lattice gives that value).  Over 65536 nodes the stochastic mean is within four
+    standard errors of it and far closer than round-to-nearest."""
+    n = 256
+    p = w.random_state_problem(n, n, seed=2, nonlinear=False, source="const")
+    p = p.replace(phi0_fn=None, phi0_array=np.full((n, n), 0.7))
+    f = {}
+    for st, sh in ((storage, "local_sr"), (storage, "local"), ("f32", "local")):
+        # the initialising collision's stores (f = f_eq(phi0), the same value at every node)
+        lat = _lattice(p, st, sh).init(p.phi0(), t0=p.t0)
+        f[(st, sh)] = lat.read_f()
+    ref = f[("f32", "local")]
+    sr = f[(storage, "local_sr")] - ref
+    rn = f[(storage, "local")] - ref
+    checked = 0
+    for i in range(1, 9):
+        assert np.ptp(rn[i]) == 0.0                  # one rounded value everywhere
+        bias = abs(float(rn[i].mean()))
+        if bias == 0.0:
+            continue                                 # exactly representable: nothing to test
+        vals = np.unique(sr[i])
+        assert 1 <= len(vals) <= 2                    # the two neighbours of the exact value
+        mean, se = float(sr[i].mean()), float(sr[i].std()) / n
+        assert abs(mean) <= 4.0 * se + 1e-12, (i, mean, se, bias)
+        assert abs(mean) < 0.2 * bias, (i, mean, bias)
+        checked += 1
+    assert checked >= 4
