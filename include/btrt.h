@@ -85,7 +85,8 @@ enum { BTRT_SIDE_XMIN = 0, BTRT_SIDE_XMAX = 1, BTRT_SIDE_YMIN = 2, BTRT_SIDE_YMA
  *                    are stored scaled by 2^12 (exact), which keeps the small
  *                    deviations of fine grids out of FP16's subnormal range; their
  *                    magnitude must stay below 16.  Plain and vector kernel forms
- *                    (AUTO takes the vector form from 2^21 nodes on); not in batches.
+ *                    (AUTO takes the vector form from 2^21 nodes on); in batches
+ *                    every form but two steps per launch.
  *  BTRT_SHIFT_LOCAL_DW_SR both: double-word phi and stochastically rounded F16/BF16
  *                    deviations.  Plain kernel form only; not in batches.
  * FP64 and double-word storage are never shifted. */

@@ -154,6 +154,7 @@ __device__ __forceinline__ void stage_member(const BatchArgs<Real> &a, int membe
         sp.src_val = v[0];
         sp.wall_fac = v[1];
         sp.first = 0;
+        sp.sr_seed = sr_step_seed(M.step + k + 1);   // stochastic rounding: the seed of this step
     }
     __syncthreads();
 }
@@ -506,8 +507,8 @@ btrt_status check_members(const btrt_lattice *members, int32_t n, std::vector<bt
             return bfail(BTRT_EINVAL, "member %d: batches take FP64 or FP32 members", k);
         if (has_phi_lo(out[k]->g))
             return bfail(BTRT_EINVAL, "member %d: batches take no double-word phi planes (BTRT_SHIFT_LOCAL_DW)", k);
-        if (stochastic_store(out[k]->g))
-            return bfail(BTRT_EINVAL, "member %d: batches take no stochastically rounded storage (BTRT_SHIFT_LOCAL_SR)", k);
+        if (out[k]->g.shift == BTRT_SHIFT_LOCAL_DW_SR)
+            return bfail(BTRT_EINVAL, "member %d: batches take no double-word phi planes (BTRT_SHIFT_LOCAL_DW_SR)", k);
         if (out[k]->g.compute != out[0]->g.compute || out[k]->g.storage != out[0]->g.storage ||
             shift_of(out[k]->g) != shift_of(out[0]->g))
             return bfail(BTRT_EINVAL, "member %d: all members need the same compute and storage formats and shift", k);
@@ -645,6 +646,9 @@ void *persistent_kernel_sh(int storage) {
 template <bool LIN>
 void *persistent_kernel_for(int compute, int storage, int shift) {
     if (compute == BTRT_F64) return reinterpret_cast<void *>(&batch_kernel<double, double, kShiftNone, LIN>);
+    if (shift == kShiftLocalSR)   // 16-bit storage only
+        return storage == BTRT_F16 ? reinterpret_cast<void *>(&batch_kernel<float, __half, kShiftLocalSR, LIN>)
+                                   : reinterpret_cast<void *>(&batch_kernel<float, __nv_bfloat16, kShiftLocalSR, LIN>);
     return shift == kShiftLocal ? persistent_kernel_sh<kShiftLocal, LIN>(storage)
                                 : persistent_kernel_sh<kShiftRef, LIN>(storage);
 }
@@ -795,10 +799,12 @@ btrt_status enqueue_form(btrt_batch B, int nsteps, int want_resid) {
     if (B->shape.per_step) {
         int k = 0, flip = 0;
         if constexpr (std::is_same<Real, float>::value) {
-            if (B->shape.per_step == 2)
-                for (int j = 0; j < pairs_in_slice(B, nsteps, want_resid); ++j, k += 2, ++flip)
-                    batch_tb2_kernel<S, SH, LIN><<<(unsigned)B->ntiles2, TbGeom::THREADS, TbGeom::SMEM, B->stream>>>(
-                        a, k, flip);
+            if constexpr (!StoreSR<SH>::value) {   // the two-step form stores round-to-nearest only
+                if (B->shape.per_step == 2)
+                    for (int j = 0; j < pairs_in_slice(B, nsteps, want_resid); ++j, k += 2, ++flip)
+                        batch_tb2_kernel<S, SH, LIN><<<(unsigned)B->ntiles2, TbGeom::THREADS, TbGeom::SMEM,
+                                                       B->stream>>>(a, k, flip);
+            }
             if (B->shape.per_step == 3) {
                 // one parameter block per member range, reused by every step
                 const BatchMember<float> *hm = reinterpret_cast<const BatchMember<float> *>(B->host_members.data());
@@ -849,6 +855,9 @@ btrt_status enqueue_sh(btrt_batch B, int nsteps, int want_resid) {
 
 btrt_status enqueue(btrt_batch B, int nsteps, int want_resid) {
     if (B->compute == BTRT_F64) return enqueue_typed<double, double, kShiftNone>(B, nsteps, want_resid);
+    if (B->shift == kShiftLocalSR)   // 16-bit storage only (checked when the batch is made)
+        return B->storage == BTRT_F16 ? enqueue_typed<float, __half, kShiftLocalSR>(B, nsteps, want_resid)
+                                      : enqueue_typed<float, __nv_bfloat16, kShiftLocalSR>(B, nsteps, want_resid);
     return B->shift == kShiftLocal ? enqueue_sh<kShiftLocal>(B, nsteps, want_resid)
                                    : enqueue_sh<kShiftRef>(B, nsteps, want_resid);
 }
@@ -923,9 +932,8 @@ size_t btrt_batch_workspace_bytes_desc(const btrt_grid_desc *descs, int32_t n) {
     std::vector<MemberGeom> g;
     for (int k = 0; k < n; ++k) {
         if (btrt_workspace_bytes(&descs[k]) == 0) return 0;   // the message says why
-        if ((has_phi_lo(descs[k]) || stochastic_store(descs[k])) && descs[k].storage != BTRT_F64 &&
-            descs[k].storage != BTRT_DF64) {
-            bfail(BTRT_EINVAL, "member %d: batches take no double-word phi planes or stochastically rounded storage", k);
+        if (has_phi_lo(descs[k]) && descs[k].storage != BTRT_F64 && descs[k].storage != BTRT_DF64) {
+            bfail(BTRT_EINVAL, "member %d: batches take no double-word phi planes", k);
             return 0;
         }
         if (descs[k].compute != descs[0].compute || descs[k].compute == BTRT_DF64) {
@@ -995,6 +1003,8 @@ btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y,
         return bfail(BTRT_EINVAL, "per_step_launch must be 0, 1, 2 or 3");
     if (per_step_launch >= 2 && B->compute != BTRT_F32)
         return bfail(BTRT_EINVAL, "the two-step and vector forms serve FP32-compute batches");
+    if (per_step_launch == 2 && B->shift == kShiftLocalSR)
+        return bfail(BTRT_EINVAL, "the two-step form stores round-to-nearest values only (no BTRT_SHIFT_LOCAL_SR)");
     B->shape = Shape{block_x, block_y, rows, per_step_launch};
     return build_tiles(B);
 }
@@ -1175,6 +1185,7 @@ btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *
         BCUDA(cudaEventCreate(&e1));
         float best_ms = 1e30f;
         for (int mode = 0; mode < (B->compute == BTRT_F32 ? kForms : 2); ++mode) {
+            if (mode == 2 && B->shift == kShiftLocalSR) continue;   // no two-step form for stochastic rounding
             for (const Shape &s : kShapes) {
                 btrt_status st = btrt_batch_set_tiles(B, s.bx, s.by, s.rows, mode);
                 if (st != BTRT_OK) return st;

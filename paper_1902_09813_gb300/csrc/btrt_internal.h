@@ -38,9 +38,12 @@ inline bool has_phi_lo(const btrt_grid_desc &g) {
 inline bool stochastic_store(const btrt_grid_desc &g) {
     return g.shift == BTRT_SHIFT_LOCAL_SR || g.shift == BTRT_SHIFT_LOCAL_DW_SR;
 }
+
 // Stochastic-rounding seed of the step that produces step index n: the SplitMix64
-// output function (Steele, Lea and Flood, 2014) of the step index.
-inline unsigned int sr_step_seed(int64_t n) {
+// output function (Steele, Lea and Flood, 2014) of the step index.  Host and
+// device (the batch kernels derive each step's seed from the member's step count)
+// compute the same value.
+__host__ __device__ inline unsigned int sr_step_seed(long long n) {
     unsigned long long z = (unsigned long long)n * 0x9e3779b97f4a7c15ull + 0x632be59bd9b4e019ull;
     z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
     z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;

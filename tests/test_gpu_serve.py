@@ -17,25 +17,26 @@ def _problems(count=9, seed=21):
     return probs
 
 
-def _alone(p, steps, compute="f32", storage="f16"):
+def _alone(p, steps, compute="f32", storage="f16", shift="auto"):
     from paper_1902_09813_gb300 import Lattice
-    lat = Lattice.from_problem(p, compute=compute, storage=storage)
+    lat = Lattice.from_problem(p, compute=compute, storage=storage, shift=shift)
     lat.init(p.phi0(), t0=p.t0).step(steps)
     return lat.phi_host()
 
 
-def test_serve_results_equal_alone():
+@pytest.mark.parametrize("shift", ["auto", "local_sr"])
+def test_serve_results_equal_alone(shift):
     from paper_1902_09813_gb300.serve import Server, poisson_trace
     probs = _problems()
     trace = poisson_trace(probs, rate=400.0, seed=1)
-    srv = Server(slice_steps=20, max_steps=120, tol=1e-30)
+    srv = Server(slice_steps=20, max_steps=120, tol=1e-30, shift=shift)
     res = srv.run(trace)
     assert len(res) == len(probs)
     assert srv.stats["peak_active"] >= 2          # work overlapped on the device
     for r, p in zip(res, probs):
         assert r.steps == 120
         assert r.finished >= r.arrival
-        assert np.array_equal(r.phi, _alone(p, r.steps))
+        assert np.array_equal(r.phi, _alone(p, r.steps, shift=shift))
 
 
 def test_serve_convergence_stop_and_sequential_baseline():

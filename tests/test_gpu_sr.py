@@ -7,7 +7,8 @@ but no repeated bias); the plain and vector forms store the same values bitwise,
 since the random bits depend only on the node, the step index and the population;
 the stored values are not those of round-to-nearest; the steps are reproducible
 (same steps, same values) and survive checkpoint/resume bitwise; the kernel forms,
-storage formats and batches that do not take it refuse it."""
+storage formats and batch forms that do not take it refuse it; in the batch forms
+that take it every member stores what it stores alone."""
 import numpy as np
 import pytest
 
@@ -109,9 +110,12 @@ def test_sr_refusals():
     dw = _lattice(p, "f16", "local_dw_sr").init(p.phi0())
     with pytest.raises(C.BtrtError):
         dw.set_sweep_variant("vec")
-    for bad in (lat, dw):
-        with pytest.raises(C.BtrtError):
-            Batch([bad])
+    with pytest.raises(C.BtrtError):
+        Batch([dw])
+    b = Batch([lat])                     # stochastic rounding in batches: not in the two-step form
+    with pytest.raises(C.BtrtError):
+        b.set_tiles(32, 8, 2, 2)
+    b.close()
     with pytest.raises(C.BtrtError):
         Lattice.from_problem(p, compute="f32", storage="f32", shift="local_sr")
     with pytest.raises(C.BtrtError):
@@ -150,3 +154,24 @@ def test_sr_unbiased_on_a_uniform_state(storage):
         assert abs(mean) < 0.2 * bias, (i, mean, bias)
         checked += 1
     assert checked >= 4
+
+
+@pytest.mark.parametrize("storage", ["f16", "bf16"])
+@pytest.mark.parametrize("form", [0, 1, 3])
+def test_sr_batch_members_equal_alone(storage, form):
+    """The random bits depend on the member's own node, step and population, so a
+    member stores in a batch exactly what it stores alone (persistent, one step per
+    launch and vector batch forms; autotuning skips the two-step form)."""
+    from paper_1902_09813_gb300 import Batch
+    probs = w.batched_instances(count=6, seed=7, nmin=20, nmax=140, nsteps=0)
+    probs.append(w.random_state_problem(45, 31, seed=8, bc=(1, 1, 0, 0), nonlinear=True))
+    alone = [_lattice(p, storage, "local_sr").init(p.phi0(), t0=p.t0).step(9) for p in probs]
+    mixed = [_lattice(p, storage, "local_sr").init(p.phi0(), t0=p.t0) for p in probs]
+    b = Batch(mixed).set_tiles(32, 4, 2, form)
+    b.step(4).step(5, residual=True)
+    for a, m in zip(alone, mixed):
+        assert np.array_equal(a.phi_host(), m.phi_host())
+        assert np.array_equal(a.read_f(), m.read_f())
+    shape = b.autotune(steps_per_trial=1)
+    assert shape[3] != 2
+    b.close()
