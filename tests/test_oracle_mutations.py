@@ -19,6 +19,9 @@ MUTATIONS = {
     "drop_source_derivative": ("+ 0.5 * dt * dt * DSi", "+ 0.0 * dt * dt * DSi"),
     "K1_transposed": ("QM1[a] += (K1[2 * a + b]", "QM1[a] += (K1[2 * b + a]"),
     "dtB_sign": ("dtB[a] = (Bn[a] - Bp[a]) / dt", "dtB[a] = (Bp[a] - Bn[a]) / dt"),
+    "dtB_dropped": ("dtB[a] = (Bn[a] - Bp[a]) / dt", "dtB[a] = 0.0 * (Bn[a] - Bp[a]) / dt"),
+    "dtB_K1_factor": ("Gv[a] += (((a == b) ? 1.0 : 0.0) - 0.5 * K1[2 * a + b]) * dtB[b];",
+                      "Gv[a] += (((a == b) ? 1.0 : 0.0) - 1.0 * K1[2 * a + b]) * dtB[b];"),
     "k2_relation": ("return 8.0 * (k1 - 2.0) / (3.0 * (k1 - 4.0));",
                     "return 8.0 * (k1 - 2.0) / (3.0 * (k1 - 3.0));"),
     "second_order_trace_sign": ("second += (ci[a] * ci[b] - ((a == b) ? cs2 : 0.0)) * HM2[a][b];",
