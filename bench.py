@@ -33,6 +33,14 @@ N_MAIN = 8192
 BYTES_PER_UPDATE = {"f64": 160, "df64": 160, "f32": 80, "f16": 44, "bf16": 44}
 
 
+def state_bytes(storage: str, shift: str = "auto") -> int:
+    """Algorithmic bytes per update: one read and one write of the state (the 9
+    populations and phi; a double-word phi adds its FP32 low words, the
+    first-moment form its two 16-bit planes)."""
+    extra = 8 if shift in ("local_dw", "local_dw_sr", "moment_sr") else 0
+    return BYTES_PER_UPDATE[storage] + extra
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -81,17 +89,17 @@ FP64_NOMINAL_TOPS = 0.625
 # to them both are re-taken and the digest updated (a CPU test checks it), and
 # until then the traffic is reported as null.
 FP64_SWEEP_SOURCES = ("btrt_sweep.cuh", "btrt_dw.cuh")   # the FP64 sweep's device code
-FP64_SWEEP_DIGEST = "868baab5f6c8f892"
+FP64_SWEEP_DIGEST = "c9504380f2ab2e26"
 FP64_TRAFFIC_PER_NODE = 149.3
 # DRAM bytes per node and step of the two-step FP32-compute kernel measured by ncu,
 # keyed by (storage, shift), for the sources with digest TB2_DIGEST.
 TB2_SOURCES = ("btrt_sweep.cuh", "btrt_tb.cuh", "btrt_launch.cuh")
-TB2_DIGEST = "c9b626338ac63ab1"
+TB2_DIGEST = "9fa1844c8a23b463"
 TB2_DRAM_BYTES_PER_UPDATE = {("f32", "ref"): 38.6, ("f16", "local"): 20.9}
 # DRAM bytes per node of one launch of the vector-access sweep measured by ncu,
 # keyed by (storage, shift), for the sources with digest VEC_DIGEST.
 VEC_SOURCES = ("btrt_sweep.cuh", "btrt_vec.cuh", "btrt_launch.cuh")
-VEC_DIGEST = "1f7f0e702b3ffe08"
+VEC_DIGEST = "152e3b50034d2e84"
 VEC_DRAM_BYTES_PER_UPDATE = {("f16", "local"): 41.4, ("f16", "local_sr"): 41.2}
 
 
@@ -130,7 +138,7 @@ def kernel_form(args) -> str:
     FP32 compute (the vector form for FP16/BF16 storage on lattices of 2^21 nodes
     or more, two steps per launch otherwise), the form asked for, or the plain
     sweep."""
-    if args.compute != "f32" or args.shift in ("local_dw", "local_dw_sr"):
+    if args.compute != "f32" or args.shift in ("local_dw", "local_dw_sr", "moment_sr"):
         return "plain"
     if args.sweep != "auto":
         return args.sweep
@@ -150,7 +158,7 @@ def roofline(args, nodes, t_launch, achieved_gbs, peak_hbm, peak_kind, fp64_peak
     hbm = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": peak_hbm, "unit": "GB/s",
            "frac": round(achieved_gbs / peak_hbm, 4), "peak_kind": peak_kind,
            "frac_of_nominal_8tbs": round(achieved_gbs / 8000.0, 4),
-           "bytes_per_update": BYTES_PER_UPDATE[args.storage]}
+           "bytes_per_update": state_bytes(args.storage, args.shift)}
     if two_step_form(args):
         # algorithmic bytes count one read and one write of the state per step; the
         # two-step kernel moves about half of that through DRAM, so this fraction
@@ -329,7 +337,7 @@ def run_gpu(args):
     # dominant kernel: the sweep, one launch per step on `stream`
     t_launch = ms / args.steps * 1e-3
     peak_hbm, peak_kind = _peaks()
-    alg_bytes = BYTES_PER_UPDATE[args.storage] * nodes
+    alg_bytes = state_bytes(args.storage, args.shift) * nodes
     achieved_gbs = alg_bytes / t_launch / 1e9
 
     # end to end through the public API with host buffers: H2D of phi0 from pinned
@@ -414,7 +422,7 @@ def _time_single(p, phi0, compute, storage, steps, warmup, variant="plain", shif
     nodes = p.nx * p.ny
     mlups = nodes * steps / (ms * 1e-3) / 1e6
     peak, _ = _peaks()
-    gbs = BYTES_PER_UPDATE[storage] * mlups * 1e6 / 1e9
+    gbs = state_bytes(storage, shift) * mlups * 1e6 / 1e9
     del lat
     torch.cuda.empty_cache()
     return {"mlups": round(mlups, 1), "ms_per_step": round(ms / steps, 4),
@@ -455,6 +463,8 @@ def run_variants(args, steps=200, warmup=5):
                                                                     variant="vec", shift="local_sr")
                 out[f"{name}_f32_{st}_local_dw_sr"] = _time_single(prob, a, "f32", st, steps, warmup,
                                                                    shift="local_dw_sr")
+                out[f"{name}_f32_{st}_moment_sr"] = _time_single(prob, a, "f32", st, steps, warmup,
+                                                                 shift="moment_sr")
     out["nonlinear_f64"] = _time_single(q, q_phi0, "f64", "f64", 50, 3)
     out.update(run_d3q19(args))
     out.update(run_extended(args))
@@ -550,7 +560,7 @@ REDUCED = [("df64", "df64", "ref"), ("f32", "f32", "ref"), ("f32", "f32", "local
            ("f32", "f16", "local"), ("f32", "bf16", "ref"), ("f32", "bf16", "local"),
            ("f32", "f32", "local_dw"), ("f32", "f16", "local_dw"), ("f32", "bf16", "local_dw"),
            ("f32", "f16", "local_sr"), ("f32", "bf16", "local_sr"), ("f32", "f16", "local_dw_sr"),
-           ("f32", "bf16", "local_dw_sr")]
+           ("f32", "bf16", "local_dw_sr"), ("f32", "f16", "moment_sr"), ("f32", "bf16", "moment_sr")]
 
 
 def _fmt_key(c, s, sh):
@@ -877,7 +887,8 @@ def main():
     ap.add_argument("--n", type=int, default=N_MAIN)
     ap.add_argument("--compute", default="f64", choices=["f64", "df64", "f32"])
     ap.add_argument("--storage", default=None, choices=["f64", "df64", "f32", "f16", "bf16"])
-    ap.add_argument("--shift", default="auto", choices=["auto", "ref", "local", "local_dw", "local_sr", "local_dw_sr"],
+    ap.add_argument("--shift", default="auto",
+                    choices=["auto", "ref", "local", "local_dw", "local_sr", "local_dw_sr", "moment_sr"],
                     help="stored form of F32/F16/BF16 populations")
     ap.add_argument("--sweep", default="auto", choices=["auto", "plain", "tma", "tb2", "vec", "tb2v"],
                     help="kernel form of FP32-compute sweeps")

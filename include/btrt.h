@@ -89,9 +89,18 @@ enum { BTRT_SIDE_XMIN = 0, BTRT_SIDE_XMAX = 1, BTRT_SIDE_YMIN = 2, BTRT_SIDE_YMA
  *                    every form but two steps per launch.
  *  BTRT_SHIFT_LOCAL_DW_SR both: double-word phi and stochastically rounded F16/BF16
  *                    deviations.  Plain kernel form only; not in batches.
+ *  BTRT_SHIFT_MOMENT_SR F16/BF16: f_i^+(x) - w_i (phi(x) + 3 e_i . j(x)), j the
+ *                    writer's post-collision first moment, kept in two more planes
+ *                    of the storage format (8 more bytes per update), the value
+ *                    rounded stochastically.  What is stored is then about 1/dx
+ *                    smaller than with the local shift (the first-moment part of
+ *                    the non-equilibrium populations is taken out); the new phi is
+ *                    rounded to its FP32 plane stochastically as well (its exact
+ *                    value is phi + the TwoSum error of the collision's sum).
+ *                    Plain kernel form only; not in batches.
  * FP64 and double-word storage are never shifted. */
 enum { BTRT_SHIFT_REF = 0, BTRT_SHIFT_LOCAL = 1, BTRT_SHIFT_LOCAL_DW = 2, BTRT_SHIFT_LOCAL_SR = 3,
-       BTRT_SHIFT_LOCAL_DW_SR = 4 };
+       BTRT_SHIFT_LOCAL_DW_SR = 4, BTRT_SHIFT_MOMENT_SR = 5 };
 
 typedef struct btrt_lattice_s *btrt_lattice;
 

@@ -16,9 +16,9 @@ FIELD_SOURCE, FIELD_DIFFUSION = 1, 2
 SWEEP_AUTO, SWEEP_PLAIN, SWEEP_TMA, SWEEP_TB2, SWEEP_VEC, SWEEP_TB2V = 0, 1, 2, 3, 4, 5
 SHIFT_REF, SHIFT_LOCAL = 0, 1
 PROBE_FMA, PROBE_ADD, PROBE_MUL = 0, 1, 2
-SHIFT_LOCAL_DW, SHIFT_LOCAL_SR, SHIFT_LOCAL_DW_SR = 2, 3, 4
+SHIFT_LOCAL_DW, SHIFT_LOCAL_SR, SHIFT_LOCAL_DW_SR, SHIFT_MOMENT_SR = 2, 3, 4, 5
 SHIFTS = {"ref": SHIFT_REF, "local": SHIFT_LOCAL, "local_dw": SHIFT_LOCAL_DW, "local_sr": SHIFT_LOCAL_SR,
-          "local_dw_sr": SHIFT_LOCAL_DW_SR}
+          "local_dw_sr": SHIFT_LOCAL_DW_SR, "moment_sr": SHIFT_MOMENT_SR}
 
 FORMATS = {"f64": F64, "f32": F32, "f16": F16, "bf16": BF16, "df64": DF64}
 

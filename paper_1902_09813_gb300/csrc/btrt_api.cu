@@ -111,12 +111,13 @@ btrt_status check_desc(const btrt_grid_desc *g) {
         return fail(BTRT_EINVAL, "phi_ref, x0, y0 must be finite");
     if (g->fields & ~(BTRT_FIELD_SOURCE | BTRT_FIELD_DIFFUSION))
         return fail(BTRT_EINVAL, "unknown field bits 0x%x", g->fields);
-    if (g->shift < BTRT_SHIFT_REF || g->shift > BTRT_SHIFT_LOCAL_DW_SR)
+    if (g->shift < BTRT_SHIFT_REF || g->shift > BTRT_SHIFT_MOMENT_SR)
         return fail(BTRT_EINVAL, "unknown storage shift %d", g->shift);
     if (has_phi_lo(*g) && g->compute != BTRT_F32)
         return fail(BTRT_EINVAL, "the double-word phi planes of BTRT_SHIFT_LOCAL_DW(_SR) serve FP32 compute");
     if (stochastic_store(*g) && (g->compute != BTRT_F32 || (g->storage != BTRT_F16 && g->storage != BTRT_BF16)))
-        return fail(BTRT_EINVAL, "stochastic rounding (BTRT_SHIFT_LOCAL_SR, _DW_SR) serves F16/BF16 storage with FP32 compute");
+        return fail(BTRT_EINVAL, "stochastic rounding (BTRT_SHIFT_LOCAL_SR, _DW_SR, _MOMENT_SR) serves F16/BF16 storage "
+                    "with FP32 compute");
     const long long pitch = (long long)((g->nx + 63) / 64) * 64;
     if (9 * pitch * (long long)g->ny >= (1LL << 31))
         return fail(BTRT_EINVAL, "grid %d x %d: the nine padded planes must hold fewer than 2^31 values "
@@ -139,9 +140,12 @@ Layout make_layout(const btrt_grid_desc *g) {
     off += L.fbuf_bytes;
     // a double-word phi (BTRT_SHIFT_LOCAL_DW, _DW_SR) keeps its low words in a second plane
     const size_t phi_planes = has_phi_lo(*g) ? 2 : 1;
+    // BTRT_SHIFT_MOMENT_SR keeps the writers' first moments in two planes of the
+    // storage format after the phi plane
+    const size_t j_bytes = has_j(*g) ? 2 * (size_t)L.plane * sf : 0;
     for (int k = 0; k < 2; ++k) {
         L.off_phi[k] = off;
-        off += align_up(phi_planes * (size_t)L.plane * sr, kAlign);
+        off += align_up(phi_planes * (size_t)L.plane * sr + j_bytes, kAlign);
     }
     L.off_tab = off;
     off += align_up(2 * ((size_t)g->nx + (size_t)g->ny) * sr, kAlign);
@@ -276,6 +280,8 @@ void btrt::fill_params(btrt_lattice L, SweepParams<Real> &p, int64_t n, bool fir
     if constexpr (std::is_same<Real, float>::value) {
         p.phi_in_lo = L->phi_lo(L->cur);
         p.phi_out_lo = L->phi_lo(first ? L->cur : 1 - L->cur);
+        p.j_in = L->jplanes(L->cur);
+        p.j_out = L->jplanes(first ? L->cur : 1 - L->cur);
     }
     p.nx = g.nx;
     p.ny = g.ny;
@@ -394,7 +400,7 @@ int btrt::sweep_mode(btrt_lattice L) {
 // form from kVecAutoNodes on, the plain one below.
 constexpr long long kVecAutoNodes = 1LL << 21;
 int btrt::effective_sweep_variant(btrt_lattice L) {
-    if (L->g.compute != BTRT_F32 || has_phi_lo(L->g)) return BTRT_SWEEP_PLAIN;
+    if (L->g.compute != BTRT_F32 || has_phi_lo(L->g) || has_j(L->g)) return BTRT_SWEEP_PLAIN;
     if (L->sweep_variant != BTRT_SWEEP_AUTO) return L->sweep_variant;
     const bool s16 = L->g.storage == BTRT_F16 || L->g.storage == BTRT_BF16;
     const bool large = (long long)L->g.nx * L->g.ny >= kVecAutoNodes;
@@ -853,8 +859,24 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
     const bool sr_f16 = stochastic_store(g) && g.storage == BTRT_F16;
     // the local forms: stored relative to the node's phi (both words of a double-word phi)
     const int sh0 = shift_of(g);
-    const int sh = sh0 == kShiftLocalSR ? kShiftLocal : (sh0 == kShiftLocalDWSR ? kShiftLocalDW : sh0);
+    const int sh = (sh0 == kShiftLocalSR || sh0 == kShiftMomentSR) ? kShiftLocal
+                   : (sh0 == kShiftLocalDWSR ? kShiftLocalDW : sh0);
     std::vector<float> phiw, phiw_lo;   // the nodes' phi, for the local shifts (FP32 compute)
+    std::vector<double> jxw, jyw;       // the nodes' stored first moments (BTRT_SHIFT_MOMENT_SR)
+    if (has_j(g)) {
+        std::vector<unsigned char> jr((size_t)w * h * sf);
+        for (int c = 0; c < 2; ++c) {
+            const unsigned char *src = static_cast<unsigned char *>(L->jplanes(L->cur)) +
+                                       ((size_t)c * L->lay.plane + (size_t)y0 * L->lay.pitch + x0) * sf;
+            CUDA_TRY(cudaMemcpy2DAsync(jr.data(), w * sf, src, L->lay.pitch * sf, w * sf, h, cudaMemcpyDeviceToHost,
+                                       L->stream));
+            CUDA_TRY(cudaStreamSynchronize(L->stream));
+            std::vector<double> &dj = c == 0 ? jxw : jyw;
+            dj.resize((size_t)w * h);
+            for (size_t k = 0; k < dj.size(); ++k)
+                dj[k] = half_bits_to_double(g.storage, &jr[k * 2]) * (sr_f16 ? 1.0 / 4096.0 : 1.0);
+        }
+    }
     if (sh == kShiftLocal || sh == kShiftLocalDW) {
         phiw.resize((size_t)w * h);
         CUDA_TRY(cudaMemcpy2DAsync(phiw.data(), w * sizeof(float), L->phi<float>() + (size_t)y0 * L->lay.pitch + x0,
@@ -889,9 +911,10 @@ btrt_status btrt_read_f(btrt_lattice L, double *dst, int32_t x0, int32_t y0, int
             }
             else if (g.storage == BTRT_F32) { float fv; std::memcpy(&fv, &raw[k * 4], 4); v = fv; }
             else v = half_bits_to_double(g.storage, &raw[k * 2]) * (sr_f16 ? 1.0 / 4096.0 : 1.0);
-            const double loc = sh == kShiftLocal     ? wts[i] * (double)phiw[k]
-                               : sh == kShiftLocalDW ? wts[i] * ((double)phiw[k] + (double)phiw_lo[k])
-                                                     : 0.0;
+            double loc = sh == kShiftLocal     ? wts[i] * (double)phiw[k]
+                         : sh == kShiftLocalDW ? wts[i] * ((double)phiw[k] + (double)phiw_lo[k])
+                                               : 0.0;
+            if (has_j(g)) loc += 3.0 * wts[i] * (ex_of(i) * jxw[k] + ey_of(i) * jyw[k]);
             dst[(size_t)i * w * h + k] = v + shift + loc;
         }
     }
@@ -925,8 +948,9 @@ btrt_status btrt_set_sweep_variant(btrt_lattice L, int32_t variant) {
         return fail(BTRT_EINVAL, "the two-step sweeps serve FP32-compute lattices");
     if (variant == BTRT_SWEEP_VEC && L->g.compute != BTRT_F32)
         return fail(BTRT_EINVAL, "the vector-access sweep serves FP32-compute lattices");
-    if (has_phi_lo(L->g) && variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN)
-        return fail(BTRT_EINVAL, "lattices with double-word phi planes (BTRT_SHIFT_LOCAL_DW, _DW_SR) take the plain form");
+    if ((has_phi_lo(L->g) || has_j(L->g)) && variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN)
+        return fail(BTRT_EINVAL, "lattices with double-word phi planes (BTRT_SHIFT_LOCAL_DW, _DW_SR) or first-moment "
+                    "planes (BTRT_SHIFT_MOMENT_SR) take the plain form");
     if (stochastic_store(L->g) && variant != BTRT_SWEEP_AUTO && variant != BTRT_SWEEP_PLAIN &&
         variant != BTRT_SWEEP_VEC)
         return fail(BTRT_EINVAL, "stochastically rounded storage (BTRT_SHIFT_LOCAL_SR) takes the plain or vector form");
@@ -943,9 +967,10 @@ btrt_status btrt_get_time(btrt_lattice L, int64_t *step, double *t) {
     return BTRT_OK;
 }
 
-// Bytes of one phi buffer (both words of a double-word phi).
+// Bytes of one phi buffer (both words of a double-word phi; the first-moment planes).
 static size_t phi_state_bytes(btrt_lattice L) {
-    return (has_phi_lo(L->g) ? 2 : 1) * (size_t)L->lay.plane * elem_size(L->g.compute);
+    return (has_phi_lo(L->g) ? 2 : 1) * (size_t)L->lay.plane * elem_size(L->g.compute) +
+           (has_j(L->g) ? 2 * (size_t)L->lay.plane * elem_size(L->g.storage) : 0);
 }
 
 size_t btrt_state_bytes(btrt_lattice L) {

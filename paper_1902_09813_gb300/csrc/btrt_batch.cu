@@ -507,8 +507,8 @@ btrt_status check_members(const btrt_lattice *members, int32_t n, std::vector<bt
             return bfail(BTRT_EINVAL, "member %d: batches take FP64 or FP32 members", k);
         if (has_phi_lo(out[k]->g))
             return bfail(BTRT_EINVAL, "member %d: batches take no double-word phi planes (BTRT_SHIFT_LOCAL_DW)", k);
-        if (out[k]->g.shift == BTRT_SHIFT_LOCAL_DW_SR)
-            return bfail(BTRT_EINVAL, "member %d: batches take no double-word phi planes (BTRT_SHIFT_LOCAL_DW_SR)", k);
+        if (out[k]->g.shift == BTRT_SHIFT_LOCAL_DW_SR || has_j(out[k]->g))
+            return bfail(BTRT_EINVAL, "member %d: batches take no double-word phi or first-moment planes", k);
         if (out[k]->g.compute != out[0]->g.compute || out[k]->g.storage != out[0]->g.storage ||
             shift_of(out[k]->g) != shift_of(out[0]->g))
             return bfail(BTRT_EINVAL, "member %d: all members need the same compute and storage formats and shift", k);
@@ -932,8 +932,8 @@ size_t btrt_batch_workspace_bytes_desc(const btrt_grid_desc *descs, int32_t n) {
     std::vector<MemberGeom> g;
     for (int k = 0; k < n; ++k) {
         if (btrt_workspace_bytes(&descs[k]) == 0) return 0;   // the message says why
-        if (has_phi_lo(descs[k]) && descs[k].storage != BTRT_F64 && descs[k].storage != BTRT_DF64) {
-            bfail(BTRT_EINVAL, "member %d: batches take no double-word phi planes", k);
+        if ((has_phi_lo(descs[k]) || has_j(descs[k])) && descs[k].storage != BTRT_F64 && descs[k].storage != BTRT_DF64) {
+            bfail(BTRT_EINVAL, "member %d: batches take no double-word phi or first-moment planes", k);
             return 0;
         }
         if (descs[k].compute != descs[0].compute || descs[k].compute == BTRT_DF64) {

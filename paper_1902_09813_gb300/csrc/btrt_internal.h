@@ -36,8 +36,11 @@ inline bool has_phi_lo(const btrt_grid_desc &g) {
 }
 // Lattices whose 16-bit stored deviations are rounded stochastically.
 inline bool stochastic_store(const btrt_grid_desc &g) {
-    return g.shift == BTRT_SHIFT_LOCAL_SR || g.shift == BTRT_SHIFT_LOCAL_DW_SR;
+    return g.shift == BTRT_SHIFT_LOCAL_SR || g.shift == BTRT_SHIFT_LOCAL_DW_SR || g.shift == BTRT_SHIFT_MOMENT_SR;
 }
+// Lattices that keep the writers' first moments (two planes of the storage format
+// after the phi plane of each buffer).
+inline bool has_j(const btrt_grid_desc &g) { return g.shift == BTRT_SHIFT_MOMENT_SR; }
 
 // Stochastic-rounding seed of the step that produces step index n: the SplitMix64
 // output function (Steele, Lea and Flood, 2014) of the step index.  Host and
@@ -85,6 +88,10 @@ struct btrt_lattice_s {
         return btrt::has_phi_lo(g) ? reinterpret_cast<float *>(ws + lay.off_phi[k]) + lay.plane : nullptr;
     }
     void *fbuf(int k) { return ws + lay.off_f[k]; }
+    // first-moment planes x, y of buffer k (BTRT_SHIFT_MOMENT_SR; after the phi plane)
+    void *jplanes(int k) {
+        return btrt::has_j(g) ? ws + lay.off_phi[k] + (size_t)lay.plane * sizeof(float) : nullptr;
+    }
     template <typename Real> Real *tab() { return reinterpret_cast<Real *>(ws + lay.off_tab); }
     template <typename Real> Real *wall(int side) {
         return reinterpret_cast<Real *>(ws + lay.off_wall) + (size_t)side * lay.maxside;
@@ -140,6 +147,7 @@ inline int shift_of(const btrt_grid_desc &g) {
     case BTRT_SHIFT_LOCAL_DW: return kShiftLocalDW;
     case BTRT_SHIFT_LOCAL_SR: return kShiftLocalSR;
     case BTRT_SHIFT_LOCAL_DW_SR: return kShiftLocalDWSR;
+    case BTRT_SHIFT_MOMENT_SR: return kShiftMomentSR;
     default: return kShiftRef;
     }
 }

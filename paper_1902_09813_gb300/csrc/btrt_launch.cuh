@@ -42,11 +42,14 @@ cudaError_t launch_f32_storage(const SweepParams<float> &p, int shift, int mode,
     } else if (shift == kShiftLocalDW) {
         if (lin) launch_src<float, S, kShiftLocalDW, kLinear>(p, g, b, s);
         else launch_src<float, S, kShiftLocalDW, kGeneral>(p, g, b, s);
-    } else if (shift == kShiftLocalSR || shift == kShiftLocalDWSR) {
+    } else if (shift == kShiftLocalSR || shift == kShiftLocalDWSR || shift == kShiftMomentSR) {
         if constexpr (S16) {
             if (shift == kShiftLocalSR) {
                 if (lin) launch_src<float, S, kShiftLocalSR, kLinear>(p, g, b, s);
                 else launch_src<float, S, kShiftLocalSR, kGeneral>(p, g, b, s);
+            } else if (shift == kShiftMomentSR) {
+                if (lin) launch_src<float, S, kShiftMomentSR, kLinear>(p, g, b, s);
+                else launch_src<float, S, kShiftMomentSR, kGeneral>(p, g, b, s);
             } else {
                 if (lin) launch_src<float, S, kShiftLocalDWSR, kLinear>(p, g, b, s);
                 else launch_src<float, S, kShiftLocalDWSR, kGeneral>(p, g, b, s);

@@ -104,6 +104,8 @@ struct SweepParams {
     Real *phi_out;         // phi^n (equal to phi_in for the initialising collision)
     const Real *phi_in_lo; // kShiftLocalDW: low words of phi_in and phi_out (null otherwise)
     Real *phi_out_lo;
+    const void *j_in;      // kShiftMomentSR: first moments of the writers (planes x, y; storage format)
+    void *j_out;
     int nx, ny;
     int pitch;             // elements between rows
     int plane;             // elements between population planes; 9 * plane < 2^31
@@ -185,18 +187,25 @@ __device__ __forceinline__ dw quot(dw a, dw b) { return a / b; }
 enum { kGeneral = 0, kLinear = 1, kLinearK0One = 2 };
 // Stored form of the populations (see the top of this file).
 // kShiftLocalSR and kShiftLocalDWSR are kShiftLocal and kShiftLocalDW with the
-// stored 16-bit deviations rounded stochastically (see pack_sr).
-enum { kShiftNone = 0, kShiftRef = 1, kShiftLocal = 2, kShiftLocalDW = 3, kShiftLocalSR = 4, kShiftLocalDWSR = 5 };
+// stored 16-bit deviations rounded stochastically (see pack_sr).  kShiftMomentSR
+// also subtracts the writer's first-moment term: it stores f_i^+ - w_i (phi +
+// 3 e_i . j), j the writer's post-collision first moment kept in two planes of the
+// storage format, stochastically rounded.
+enum { kShiftNone = 0, kShiftRef = 1, kShiftLocal = 2, kShiftLocalDW = 3, kShiftLocalSR = 4, kShiftLocalDWSR = 5,
+       kShiftMomentSR = 6 };
 // The collision and the stored deviations of the local variants are those of kShiftLocal.
 template <int SH> struct CollShift {
-    static constexpr int value = (SH == kShiftLocalDW || SH == kShiftLocalSR || SH == kShiftLocalDWSR) ? kShiftLocal : SH;
+    static constexpr int value =
+        (SH == kShiftLocalDW || SH == kShiftLocalSR || SH == kShiftLocalDWSR || SH == kShiftMomentSR) ? kShiftLocal : SH;
 };
-// The pull (neighbour phi, low words) of each stored form.
+// The pull (neighbour phi, low words, first moments) of each stored form.
 template <int SH> struct PullShift {
     static constexpr int value = SH == kShiftLocalSR ? kShiftLocal : (SH == kShiftLocalDWSR ? kShiftLocalDW : SH);
 };
 // Stochastic rounding of the stored values.
-template <int SH> struct StoreSR { static constexpr bool value = SH == kShiftLocalSR || SH == kShiftLocalDWSR; };
+template <int SH> struct StoreSR {
+    static constexpr bool value = SH == kShiftLocalSR || SH == kShiftLocalDWSR || SH == kShiftMomentSR;
+};
 // Source kinds (compile-time SRC); kSrcRuntime decides per lattice at run time,
 // kSrcRuntimeNR the same among the kinds other than the reaction term (whose
 // power-law code then stays out of the kernel).
@@ -527,6 +536,23 @@ template <> __device__ __forceinline__ __nv_bfloat16 pack_sr<__nv_bfloat16>(floa
 template <> __device__ __forceinline__ __half pack_sr<__half>(float v, unsigned int r) {
     return __float2half_rz(__uint_as_float(__float_as_uint(v * kSrScaleF16) + (r >> 19)));
 }
+// The new phi of the first-moment form, rounded stochastically to FP32 as well:
+// phi = fl(phid + rs) and the TwoSum error e (phid + rs = phi + e exactly) move it
+// one FP32 place towards e with probability |e| / place.  Under diffusive scaling
+// a step changes phi by a few FP32 places, and round-to-nearest would repeat nearly
+// the same error step after step; with the local shift the stochastically rounded
+// 16-bit deviations dither that rounding, the first-moment form's far smaller ones
+// do not.  r: random bits (the node's population-9 bits).
+__device__ __forceinline__ float phi_sr(float phi, float phid, float rs, unsigned int r) {
+    const float bb = phi - rs;
+    const float e = (rs - (phi - bb)) + (phid - bb);
+    // the neighbouring FP32 value on e's side (for phi = 0, e is 0 and phi stays;
+    // a non-finite phi makes e NaN and stays too)
+    const float nb = __int_as_float(__float_as_int(phi) + (((e > 0.f) == (phi > 0.f)) ? 1 : -1));
+    const float u = __uint_as_float(0x3f800000u | (r >> 9)) - 1.f;   // uniform in [0, 1)
+    return fabsf(e) > u * fabsf(nb - phi) ? nb : phi;
+}
+
 // The stored deviation back in the compute type: FP16 values of the stochastically
 // rounded forms carry the 2^12 scale.
 template <typename S, int SH> struct DevScaled {
@@ -535,6 +561,23 @@ template <typename S, int SH> struct DevScaled {
 template <typename Real, typename S, int SH> __device__ __forceinline__ Real dev_load(S v) {
     if constexpr (DevScaled<S, SH>::value) return Storage<S>::load(v) * (1.f / kSrScaleF16);
     else return Storage<S>::load(v);
+}
+// kShiftMomentSR: the writer's first moment j in the storage format (with the
+// deviations' scale), rounded to nearest; reader and writer both use the stored
+// value, so its rounding changes only what is subtracted, not the result.
+template <typename S, int SH> __device__ __forceinline__ S j_pack(float v) {
+    if constexpr (DevScaled<S, SH>::value) return Storage<S>::pack(v * kSrScaleF16);
+    else return Storage<S>::pack(v);
+}
+// e_i . j for the compile-time direction i, and 3 w_i (1/3 on the axes, 1/12 on the diagonals)
+template <typename Real> __device__ __forceinline__ Real e_dot(int i, Real jx, Real jy) {
+    const int ex = ex_of(i), ey = ey_of(i);
+    if (ey == 0) return ex > 0 ? jx : -jx;
+    if (ex == 0) return ey > 0 ? jy : -jy;
+    return (ex > 0 ? jx : -jx) + (ey > 0 ? jy : -jy);
+}
+template <typename Real> __device__ __forceinline__ Real w3(int i) {
+    return i <= 4 ? cst<Real>(1, 3) : cst<Real>(1, 12);
 }
 
 // FP64 and double-word storage are never shifted; the other formats take the
@@ -644,8 +687,15 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
         if (wx < 0 && wy < 0) {
             const int src = sy * p.pitch + sx;
             d[i] = dev_load<Real, S, SH>(ldg<L2ONLY>(fin + BTRT_IX(p.flags, i * p.plane + src, 9 * p.plane)));
-            if constexpr (PS == kShiftLocal)
+            if constexpr (PS == kShiftLocal || PS == kShiftMomentSR)
                 if (i != 0) d[i] = fma(wgt<Real>(i), ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, src, p.plane)) - phi_prev, d[i]);
+            if constexpr (PS == kShiftMomentSR)
+                if (i != 0) {
+                    const S *jin = static_cast<const S *>(p.j_in);
+                    const Real jx = dev_load<Real, S, SH>(ldg<L2ONLY>(jin + BTRT_IX(p.flags, src, 2 * p.plane)));
+                    const Real jy = dev_load<Real, S, SH>(ldg<L2ONLY>(jin + BTRT_IX(p.flags, p.plane + src, 2 * p.plane)));
+                    d[i] = fma(w3<Real>(i), e_dot<Real>(i, jx, jy), d[i]);
+                }
             if constexpr (PS == kShiftLocalDW)
                 if (i != 0)
                     d[i] = fma(wgt<Real>(i),
@@ -666,9 +716,18 @@ __device__ __forceinline__ void pull_boundary(const SweepParams<Real> &p, const 
             // (for the local shift f_o^+ was stored relative to this node's own phi^{n-1} = rs)
             Real wt = wall_term(p, o, phi_w);
             if constexpr (PS == kShiftRef) wt = wt - Real(2) * p.wref[i];
-            if constexpr (PS == kShiftLocal || PS == kShiftLocalDW) wt = fma(Real(-2) * wgt<Real>(i), phi_prev, wt);
+            if constexpr (PS == kShiftLocal || PS == kShiftLocalDW || PS == kShiftMomentSR)
+                wt = fma(Real(-2) * wgt<Real>(i), phi_prev, wt);
             if constexpr (PS == kShiftLocalDW) wt = fma(Real(-2) * wgt<Real>(i), phi_lo, wt);
             d[i] = wt - dout;
+            if constexpr (PS == kShiftMomentSR) {
+                // f_o^+ was stored relative to this node's own first-moment term: with
+                // e_o = -e_i it returns as + 3 w_i e_i . j
+                const S *jin = static_cast<const S *>(p.j_in);
+                const Real jx = dev_load<Real, S, SH>(ldg<L2ONLY>(jin + BTRT_IX(p.flags, node, 2 * p.plane)));
+                const Real jy = dev_load<Real, S, SH>(ldg<L2ONLY>(jin + BTRT_IX(p.flags, p.plane + node, 2 * p.plane)));
+                d[i] = fma(w3<Real>(i), e_dot<Real>(i, jx, jy), d[i]);
+            }
         }
     }
 }
@@ -708,13 +767,23 @@ __device__ __forceinline__ void pull_node(const SweepParams<Real> &p, int x, int
         for (int i = 0; i < 9; ++i)
             f[i] = dev_load<Real, S, SH>(
                 ldg<L2ONLY>(fin + BTRT_IX(p.flags, i * p.plane + node - ey_of(i) * p.pitch - ex_of(i), 9 * p.plane)));
-        if constexpr (PS == kShiftLocal) {
+        if constexpr (PS == kShiftLocal || PS == kShiftMomentSR) {
 #pragma unroll
             for (int i = 1; i < 9; ++i)
                 f[i] = fma(wgt<Real>(i),
                            ldg<L2ONLY>(p.phi_in + BTRT_IX(p.flags, node - ey_of(i) * p.pitch - ex_of(i), p.plane)) -
                                phi_prev,
                            f[i]);
+        }
+        if constexpr (PS == kShiftMomentSR) {
+            const S *jin = static_cast<const S *>(p.j_in);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const int nb = node - ey_of(i) * p.pitch - ex_of(i);
+                const Real jx = dev_load<Real, S, SH>(ldg<L2ONLY>(jin + BTRT_IX(p.flags, nb, 2 * p.plane)));
+                const Real jy = dev_load<Real, S, SH>(ldg<L2ONLY>(jin + BTRT_IX(p.flags, p.plane + nb, 2 * p.plane)));
+                f[i] = fma(w3<Real>(i), e_dot<Real>(i, jx, jy), f[i]);
+            }
         }
         if constexpr (PS == kShiftLocalDW) {
 #pragma unroll
@@ -751,7 +820,24 @@ __device__ __forceinline__ double finish_node(const SweepParams<Real> &p, int x,
     const Real rs = SC == kShiftLocal ? phi_prev : p.phi_ref;
     Real phid;
     const Real phi = collide_fold<Real, MODE, SRC, SC>(p, f, rs, phi_prev, src, p.first != 0, node, phid, Lc);
-    if constexpr (StoreSR<SH>::value) {
+    if constexpr (PullShift<SH>::value == kShiftMomentSR) {
+        // the writer's first moment sum_i e_i d_i^+ (the w_i rs terms cancel), stored
+        // rounded; the deviations are taken from w_i (phi + 3 e_i . j) with the stored j
+        const Real jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
+        const Real jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
+        S *jout = static_cast<S *>(p.j_out);
+        const S jxs = j_pack<S, SH>(jx), jys = j_pack<S, SH>(jy);
+        jout[BTRT_IX(p.flags, node, 2 * p.plane)] = jxs;
+        jout[BTRT_IX(p.flags, p.plane + node, 2 * p.plane)] = jys;
+        const Real jxv = dev_load<Real, S, SH>(jxs), jyv = dev_load<Real, S, SH>(jys);
+        const unsigned int h = sr_node_bits(p.sr_seed, node);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const Real v = i == 0 ? fma(-wgt<Real>(i), phid, f[i])
+                                  : fma(-w3<Real>(i), e_dot<Real>(i, jxv, jyv), fma(-wgt<Real>(i), phid, f[i]));
+            fout[BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)] = pack_sr<S>(v, sr_bits(h, i));
+        }
+    } else if constexpr (StoreSR<SH>::value) {
         const unsigned int h = sr_node_bits(p.sr_seed, node);
 #pragma unroll
         for (int i = 0; i < 9; ++i)
@@ -779,10 +865,12 @@ __device__ __forceinline__ double finish_node(const SweepParams<Real> &p, int x,
         }
         return 0.0;
     } else {
-        p.phi_out[BTRT_IX(p.flags, node, p.plane)] = phi;
-        bad |= not_finite(phi);
+        Real phis = phi;
+        if constexpr (SH == kShiftMomentSR) phis = phi_sr(phi, phid, rs, sr_bits(sr_node_bits(p.sr_seed, node), 9));
+        p.phi_out[BTRT_IX(p.flags, node, p.plane)] = phis;
+        bad |= not_finite(phis);
         if (RESID) {
-            const double dd = static_cast<double>(phi) - static_cast<double>(phi_prev);
+            const double dd = static_cast<double>(phis) - static_cast<double>(phi_prev);
             return dd * dd;
         }
         return 0.0;

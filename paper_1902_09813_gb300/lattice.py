@@ -104,7 +104,9 @@ class Lattice:
         "local" (f^+ - w_i phi of the writing node), "local_dw" (local, with phi kept
         as a double-word pair so that it is never rounded to FP32; plain kernel form),
         "local_sr" (local, F16/BF16 storage rounded stochastically; plain and vector
-        forms), "local_dw_sr" (both; plain form) or "auto" (local for the 16-bit
+        forms), "local_dw_sr" (both; plain form), "moment_sr" (F16/BF16: the writer's
+        first-moment term subtracted as well, j kept in two more planes, stochastic
+        rounding; plain form) or "auto" (local for the 16-bit
         formats, whose rounding it keeps well below the discretisation error; ref for
         FP32 storage)."""
         storage = storage or compute

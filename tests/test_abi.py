@@ -81,11 +81,11 @@ def test_invalid_descriptions_rejected(lib, kw):
 
 def test_unknown_storage_shift_rejected(lib):
     d = _desc(compute="f32", storage="f16")
-    for bad in (5, -1):
+    for bad in (6, -1):
         d.shift = bad
         assert lib.btrt_workspace_bytes(ctypes.byref(d)) == 0
         assert b"shift" in lib.btrt_last_error()
-    for good in (0, 1, 2, 3, 4):
+    for good in (0, 1, 2, 3, 4, 5):
         d.shift = good
         assert lib.btrt_workspace_bytes(ctypes.byref(d)) > 0
 
@@ -96,7 +96,7 @@ def test_stochastic_rounding_needs_16bit_storage(lib):
     from paper_1902_09813_gb300.lattice import workspace_bytes
     from paper_1902_09813_gb300 import _capi as C
     for comp, st in (("f32", "f32"), ("f64", "f64"), ("df64", "df64")):
-        for sh in ("local_sr", "local_dw_sr"):
+        for sh in ("local_sr", "local_dw_sr", "moment_sr"):
             with pytest.raises(C.BtrtError):
                 workspace_bytes(_desc(compute=comp, storage=st, shift=sh))
     for st in ("f16", "bf16"):
@@ -104,6 +104,8 @@ def test_stochastic_rounding_needs_16bit_storage(lib):
         assert workspace_bytes(_desc(compute="f32", storage=st, shift="local_sr")) == loc
         assert workspace_bytes(_desc(compute="f32", storage=st, shift="local_dw_sr")) == \
             workspace_bytes(_desc(compute="f32", storage=st, shift="local_dw"))
+        # the first-moment form: two more planes of the storage format per buffer
+        assert workspace_bytes(_desc(compute="f32", storage=st, shift="moment_sr")) >= loc + 2 * 2 * 64 * 48 * 2
 
 
 def test_create_rejects_null_workspace(lib):

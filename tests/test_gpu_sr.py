@@ -33,23 +33,33 @@ CASES = [(37, 29, (0, 0, 0, 0), True, "trig"), (37, 29, (1, 1, 1, 1), True, "tri
          (3, 3, (1, 1, 1, 1), True, "const"), (5, 97, (1, 1, 0, 0), True, "reaction")]
 
 
-@pytest.mark.parametrize("shift", ["local_sr", "local_dw_sr"])
+RN_OF = {"local_sr": "local", "local_dw_sr": "local_dw", "moment_sr": "local"}
+
+
+@pytest.mark.parametrize("shift", ["local_sr", "local_dw_sr", "moment_sr"])
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: f"{c[0]}x{c[1]}-bc{''.join(map(str, c[2]))}-{c[4]}")
 def test_sr_matches_oracle_like_round_to_nearest(case, storage, shift):
+    """phi after 10 steps, and the post-collision populations as read back (the
+    first-moment form adds its stored j), against the FP64 oracle: at most twice
+    the error of round-to-nearest storage with the local shift."""
     nx, ny, bc, nonlin, src = case
     p = w.random_state_problem(nx, ny, seed=17 * nx + ny, bc=bc, nonlinear=nonlin, source=src,
                                flux_q=2.5 if src == "reaction" else 2.0)
     steps = 10
-    ref = oracle.OracleLattice(p, nthreads=cpu_threads()).init().step(steps).phi()
-    got = {}
-    for sh in (shift, shift.replace("_sr", "")):
+    o = oracle.OracleLattice(p, nthreads=cpu_threads()).init().step(steps)
+    ref = o.phi()
+    o.step(1)
+    got, gotf = {}, {}
+    for sh in (shift, RN_OF[shift]):
         lat = _lattice(p, storage, sh)
         lat.init(p.phi0(), t0=p.t0).step(steps)
         assert lat.check() == 0
         got[sh] = _rel(lat.phi_host(), ref)
-    rn = got[shift.replace("_sr", "")]
+        gotf[sh] = _rel(lat.read_f(), o.fpost)
+    rn = got[RN_OF[shift]]
     assert got[shift] <= 2.0 * rn + 1e-6, got
+    assert gotf[shift] <= 2.0 * gotf[RN_OF[shift]] + 1e-6, gotf
 
 
 @pytest.mark.parametrize("storage", ["f16", "bf16"])
@@ -84,7 +94,7 @@ def test_sr_differs_from_round_to_nearest_and_repeats(storage):
     assert _rel(runs[0], runs[2]) < 1e-2
 
 
-@pytest.mark.parametrize("shift", ["local_sr", "local_dw_sr"])
+@pytest.mark.parametrize("shift", ["local_sr", "local_dw_sr", "moment_sr"])
 def test_sr_checkpoint_resume_bitwise(shift):
     p = w.random_state_problem(45, 33, seed=4, bc=(1, 1, 0, 0), nonlinear=True)
     a = _lattice(p, "bf16", shift)
@@ -112,6 +122,12 @@ def test_sr_refusals():
         dw.set_sweep_variant("vec")
     with pytest.raises(C.BtrtError):
         Batch([dw])
+    mo = _lattice(p, "bf16", "moment_sr").init(p.phi0())
+    for form in ("vec", "tb2", "tb2v", "tma"):
+        with pytest.raises(C.BtrtError):
+            mo.set_sweep_variant(form)
+    with pytest.raises(C.BtrtError):
+        Batch([mo])
     b = Batch([lat])                     # stochastic rounding in batches: not in the two-step form
     with pytest.raises(C.BtrtError):
         b.set_tiles(32, 8, 2, 2)
@@ -133,11 +149,14 @@ def test_sr_unbiased_on_a_uniform_state(storage):
     n = 256
     p = w.random_state_problem(n, n, seed=2, nonlinear=False, source="const")
     p = p.replace(phi0_fn=None, phi0_array=np.full((n, n), 0.7))
+    wts = np.array([4, 1, 1, 1, 1, 0.25, 0.25, 0.25, 0.25]) / 9.0
     f = {}
     for st, sh in ((storage, "local_sr"), (storage, "local"), ("f32", "local")):
-        # the initialising collision's stores (f = f_eq(phi0), the same value at every node)
+        # the initialising collision's stores (f = f_eq(phi0), the same deviation at every
+        # node), as stored: the populations read back less w_i phi of the node (the
+        # stochastically rounded phi plane may differ from node to node by one place)
         lat = _lattice(p, st, sh).init(p.phi0(), t0=p.t0)
-        f[(st, sh)] = lat.read_f()
+        f[(st, sh)] = lat.read_f() - wts[:, None, None] * lat.phi_host()[None]
     ref = f[("f32", "local")]
     sr = f[(storage, "local_sr")] - ref
     rn = f[(storage, "local")] - ref
