@@ -89,17 +89,17 @@ FP64_NOMINAL_TOPS = 0.625
 # to them both are re-taken and the digest updated (a CPU test checks it), and
 # until then the traffic is reported as null.
 FP64_SWEEP_SOURCES = ("btrt_sweep.cuh", "btrt_dw.cuh")   # the FP64 sweep's device code
-FP64_SWEEP_DIGEST = "c9504380f2ab2e26"
+FP64_SWEEP_DIGEST = "84f1a8f8aaf78b87"
 FP64_TRAFFIC_PER_NODE = 149.3
 # DRAM bytes per node and step of the two-step FP32-compute kernel measured by ncu,
 # keyed by (storage, shift), for the sources with digest TB2_DIGEST.
 TB2_SOURCES = ("btrt_sweep.cuh", "btrt_tb.cuh", "btrt_launch.cuh")
-TB2_DIGEST = "9fa1844c8a23b463"
+TB2_DIGEST = "69edb03459b7a95e"
 TB2_DRAM_BYTES_PER_UPDATE = {("f32", "ref"): 38.6, ("f16", "local"): 20.9}
 # DRAM bytes per node of one launch of the vector-access sweep measured by ncu,
 # keyed by (storage, shift), for the sources with digest VEC_DIGEST.
 VEC_SOURCES = ("btrt_sweep.cuh", "btrt_vec.cuh", "btrt_launch.cuh")
-VEC_DIGEST = "152e3b50034d2e84"
+VEC_DIGEST = "595aba24043b714f"
 VEC_DRAM_BYTES_PER_UPDATE = {("f16", "local"): 41.4, ("f16", "local_sr"): 41.2}
 
 

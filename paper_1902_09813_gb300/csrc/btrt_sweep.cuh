@@ -536,6 +536,18 @@ template <> __device__ __forceinline__ __nv_bfloat16 pack_sr<__nv_bfloat16>(floa
 template <> __device__ __forceinline__ __half pack_sr<__half>(float v, unsigned int r) {
     return __float2half_rz(__uint_as_float(__float_as_uint(v * kSrScaleF16) + (r >> 19)));
 }
+// The same with FP16's subnormal range rounded stochastically too: the random bits
+// cover all the FP32 mantissa bits below FP16's last place there (13 in the normal
+// range, up to 23 below it; scaled values under 2^-24 are cut toward zero).  The
+// first-moment form needs it: its stored values are O(dx^2) and, even scaled,
+// reach FP16's subnormal range on fine grids.
+template <typename S> __device__ __forceinline__ S pack_sr_sub(float v, unsigned int r) { return pack_sr<S>(v, r); }
+template <> __device__ __forceinline__ __half pack_sr_sub<__half>(float v, unsigned int r) {
+    const unsigned int u = __float_as_uint(v * kSrScaleF16);
+    const int e = (int)((u >> 23) & 0xffu);
+    const int k = e >= 113 ? 13 : min(23, 126 - e);
+    return __float2half_rz(__uint_as_float(u + ((r >> 9) & ((1u << k) - 1u))));
+}
 // The new phi of the first-moment form, rounded stochastically to FP32 as well:
 // phi = fl(phid + rs) and the TwoSum error e (phid + rs = phi + e exactly) move it
 // one FP32 place towards e with probability |e| / place.  Under diffusive scaling
@@ -835,7 +847,7 @@ __device__ __forceinline__ double finish_node(const SweepParams<Real> &p, int x,
         for (int i = 0; i < 9; ++i) {
             const Real v = i == 0 ? fma(-wgt<Real>(i), phid, f[i])
                                   : fma(-w3<Real>(i), e_dot<Real>(i, jxv, jyv), fma(-wgt<Real>(i), phid, f[i]));
-            fout[BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)] = pack_sr<S>(v, sr_bits(h, i));
+            fout[BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)] = pack_sr_sub<S>(v, sr_bits(h, i));
         }
     } else if constexpr (StoreSR<SH>::value) {
         const unsigned int h = sr_node_bits(p.sr_seed, node);
