@@ -270,7 +270,11 @@ size_t btrt_batch_workspace_bytes_desc(const btrt_grid_desc *descs, int32_t n);
 
 /* Create a batch over n members in a caller-owned, 256-byte aligned device
  * workspace.  Synchronises the members' streams; the batch's own work goes to
- * cuda_stream.  Requires cooperative-launch support. */
+ * cuda_stream (it may be the legacy default stream: slice graphs are captured on
+ * a private stream and replayed on this one).  Members take FP64 or FP32 compute
+ * of one format and one storage shift; no double-word phi or first-moment planes
+ * (BTRT_SHIFT_LOCAL_DW, _DW_SR, _MOMENT_SR: BTRT_EINVAL).  Requires
+ * cooperative-launch support. */
 btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_workspace, size_t bytes,
                               void *cuda_stream, btrt_batch *out);
 
@@ -282,14 +286,18 @@ btrt_status btrt_batch_create(const btrt_lattice *members, int32_t n, void *dev_
  * residual step of btrt_batch_step in the form of 1 with the given shape;
  * 3 (FP32-compute batches only): one launch per step in the vector form of
  * BTRT_SWEEP_VEC on tiles of (4 block_x) x (block_y rows) nodes, the residual
- * step in the form of 1.  Results are bitwise the same in every form and shape. */
+ * step in the form of 1.  Stochastically rounded members (BTRT_SHIFT_LOCAL_SR)
+ * take forms 0, 1 and 3 (2: BTRT_EINVAL).  Results are bitwise the same in every
+ * form and shape, and equal to the members' results stepped alone. */
 btrt_status btrt_batch_set_tiles(btrt_batch B, int32_t block_x, int32_t block_y, int32_t rows,
                                  int32_t per_step_launch);
 
 /* Pick the fastest candidate (10 tile shapes x 2 launch forms, x 4 for FP32
- * compute with the two-step and vector forms) by timing steps_per_trial steps of
- * each after one warm-up step.  These are real steps: on a first tuning every
- * member advances by 20 (FP32: 40) x (steps_per_trial + 1) steps.
+ * compute with the two-step and vector forms, x 3 for stochastically rounded
+ * members) by timing steps_per_trial steps of each after one warm-up step (its
+ * graph captured before the timing).  These are real steps: on a first tuning every
+ * member advances by 20 (FP32: 40; stochastically rounded members: 30) x
+ * (steps_per_trial + 1) steps.
  * The choice is cached per (members, total nodes, formats) in the process and
  * reused without timing.  Writes the choice (any pointer may be NULL). */
 btrt_status btrt_batch_autotune(btrt_batch B, int32_t steps_per_trial, int32_t *block_x, int32_t *block_y,

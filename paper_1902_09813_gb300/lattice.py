@@ -305,8 +305,10 @@ class Lattice:
 
 
 class Batch:
-    """Independent lattices advanced together by one persistent launch per call
-    (see btrt_batch_* in include/btrt.h)."""
+    """Independent lattices advanced together: one batched launch form over all
+    members (persistent, one launch per step, two steps per launch or the vector
+    form; set_tiles / autotune pick it), each call's launches replayed from a CUDA
+    graph (see btrt_batch_* in include/btrt.h)."""
 
     def __init__(self, lattices, stream=None, device=None):
         self.lib = C.load()
