@@ -138,12 +138,14 @@ def kernel_form(args) -> str:
     FP32 compute (the vector form for FP16/BF16 storage on lattices of 2^21 nodes
     or more, two steps per launch otherwise), the form asked for, or the plain
     sweep."""
-    if args.compute != "f32" or args.shift in ("local_dw", "local_dw_sr", "moment_sr"):
+    if args.compute != "f32" or args.shift in ("local_dw", "local_dw_sr"):
         return "plain"
     if args.sweep != "auto":
         return args.sweep
     large = args.n * args.n >= 1 << 21
-    if args.shift == "local_sr":
+    if args.shift == "moment_sr" and args.storage == "f16":
+        return "plain"
+    if args.shift in ("local_sr", "moment_sr"):
         return "vec" if large else "plain"
     return "vec" if args.storage in ("f16", "bf16") and large else "tb2"
 
@@ -465,6 +467,8 @@ def run_variants(args, steps=200, warmup=5):
                                                                    shift="local_dw_sr")
                 out[f"{name}_f32_{st}_moment_sr"] = _time_single(prob, a, "f32", st, steps, warmup,
                                                                  shift="moment_sr")
+                out[f"{name}_f32_{st}_moment_sr_vec"] = _time_single(prob, a, "f32", st, steps, warmup,
+                                                                     variant="vec", shift="moment_sr")
     out["nonlinear_f64"] = _time_single(q, q_phi0, "f64", "f64", 50, 3)
     out.update(run_d3q19(args))
     out.update(run_extended(args))

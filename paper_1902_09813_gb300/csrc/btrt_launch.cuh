@@ -210,10 +210,15 @@ cudaError_t launch_vec_storage(const SweepParams<float> &p, int shift, int mode,
     if (shift == kShiftLocal) {
         if (lin) launch_vec_src<S, kShiftLocal, kLinear>(p, s);
         else launch_vec_src<S, kShiftLocal, kGeneral>(p, s);
-    } else if (shift == kShiftLocalSR) {
+    } else if (shift == kShiftLocalSR || shift == kShiftMomentSR) {
         if constexpr (!std::is_same<S, float>::value) {
-            if (lin) launch_vec_src<S, kShiftLocalSR, kLinear>(p, s);
-            else launch_vec_src<S, kShiftLocalSR, kGeneral>(p, s);
+            if (shift == kShiftLocalSR) {
+                if (lin) launch_vec_src<S, kShiftLocalSR, kLinear>(p, s);
+                else launch_vec_src<S, kShiftLocalSR, kGeneral>(p, s);
+            } else {
+                if (lin) launch_vec_src<S, kShiftMomentSR, kLinear>(p, s);
+                else launch_vec_src<S, kShiftMomentSR, kGeneral>(p, s);
+            }
         } else {
             return cudaErrorInvalidValue;
         }

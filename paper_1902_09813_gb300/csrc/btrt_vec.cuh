@@ -45,14 +45,23 @@ template <> struct Vec4<__half> {
         w.y = *reinterpret_cast<const unsigned int *>(&hi);
         return w;
     }
-    // stochastic rounding (pack_sr) with the random bits of each value
+    // stochastic rounding (pack_sr; pack_sr_sub with SUB) with the random bits of each value
+    template <bool SUB = false>
     static __device__ __forceinline__ W put_sr(const float (&v)[kVec], unsigned int ra, unsigned int rb,
                                                unsigned int rc, unsigned int rd) {
+        auto pk = [](float x, unsigned int r) {
+            return (unsigned int)__half_as_ushort(SUB ? pack_sr_sub<__half>(x, r) : pack_sr<__half>(x, r));
+        };
         W w;
-        w.x = (unsigned int)__half_as_ushort(pack_sr<__half>(v[0], ra)) |
-              ((unsigned int)__half_as_ushort(pack_sr<__half>(v[1], rb)) << 16);
-        w.y = (unsigned int)__half_as_ushort(pack_sr<__half>(v[2], rc)) |
-              ((unsigned int)__half_as_ushort(pack_sr<__half>(v[3], rd)) << 16);
+        w.x = pk(v[0], ra) | (pk(v[1], rb) << 16);
+        w.y = pk(v[2], rc) | (pk(v[3], rd) << 16);
+        return w;
+    }
+    // four stored values, unchanged
+    static __device__ __forceinline__ W pack_raw(const __half (&s)[kVec]) {
+        W w;
+        w.x = (unsigned int)__half_as_ushort(s[0]) | ((unsigned int)__half_as_ushort(s[1]) << 16);
+        w.y = (unsigned int)__half_as_ushort(s[2]) | ((unsigned int)__half_as_ushort(s[3]) << 16);
         return w;
     }
 };
@@ -69,6 +78,7 @@ template <> struct Vec4<__nv_bfloat16> {
         w.y = *reinterpret_cast<const unsigned int *>(&hi);
         return w;
     }
+    template <bool SUB = false>   // BF16 has no subnormal issue: SUB changes nothing
     static __device__ __forceinline__ W put_sr(const float (&v)[kVec], unsigned int ra, unsigned int rb,
                                                unsigned int rc, unsigned int rd) {
         W w;
@@ -76,6 +86,12 @@ template <> struct Vec4<__nv_bfloat16> {
               ((unsigned int)__bfloat16_as_ushort(pack_sr<__nv_bfloat16>(v[1], rb)) << 16);
         w.y = (unsigned int)__bfloat16_as_ushort(pack_sr<__nv_bfloat16>(v[2], rc)) |
               ((unsigned int)__bfloat16_as_ushort(pack_sr<__nv_bfloat16>(v[3], rd)) << 16);
+        return w;
+    }
+    static __device__ __forceinline__ W pack_raw(const __nv_bfloat16 (&s)[kVec]) {
+        W w;
+        w.x = (unsigned int)__bfloat16_as_ushort(s[0]) | ((unsigned int)__bfloat16_as_ushort(s[1]) << 16);
+        w.y = (unsigned int)__bfloat16_as_ushort(s[2]) | ((unsigned int)__bfloat16_as_ushort(s[3]) << 16);
         return w;
     }
 };
@@ -151,9 +167,11 @@ __device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0
         }
     }
 
+    constexpr bool MOMENT = PullShift<SH>::value == kShiftMomentSR;
     bool bad = false;
     float outv[9][kVec];
     float phi_o[kVec];
+    S jxo[kVec], jyo[kVec];   // the first moments stored by the first-moment form
 #pragma unroll
     for (int v = 0; v < kVec; ++v) {
         const int x = x0 + v;
@@ -169,6 +187,17 @@ __device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0
 #pragma unroll
             for (int i = 1; i < 9; ++i) f[i] = fma(wgt<float>(i), ph[1 - ey_of(i)][v - ex_of(i) + 1] - phi_prev, f[i]);
         }
+        if constexpr (MOMENT) {
+            // the writers' first-moment terms, as pull_node adds them (scalar loads: L1 hits)
+            const S *jin = static_cast<const S *>(p.j_in);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) {
+                const int nb = node + v - ey_of(i) * p.pitch - ex_of(i);
+                const float jx = dev_load<float, S, SH>(ldg<L2ONLY>(jin + BTRT_IX(p.flags, nb, 2 * p.plane)));
+                const float jy = dev_load<float, S, SH>(ldg<L2ONLY>(jin + BTRT_IX(p.flags, p.plane + nb, 2 * p.plane)));
+                f[i] = fma(w3<float>(i), e_dot<float>(i, jx, jy), f[i]);
+            }
+        }
         float xs = 0.f, xc = 0.f;
         if (SRC == kSrcTrig || (TRIG && SRC != kSrcTrig && p.src_kind == kSrcTrig)) {
             xs = p.Xs[BTRT_IX(p.flags, x, p.nx)];
@@ -178,11 +207,31 @@ __device__ __forceinline__ bool vec_interior(const SweepParams<float> &p, int x0
         const float rs = SC == kShiftLocal ? phi_prev : p.phi_ref;
         float phid;
         const float phi = collide_fold<float, MODE, SRC, SC>(p, f, rs, phi_prev, src, false, node + v, phid, Lc);
+        if constexpr (MOMENT) {
+            // as finish_node: the first moment stored rounded, the deviations taken from
+            // w_i (phi + 3 e_i . j) with the stored j, phi rounded stochastically
+            const float jx = ((f[1] - f[3]) + (f[5] - f[7])) + (f[8] - f[6]);
+            const float jy = ((f[2] - f[4]) + (f[5] - f[7])) + (f[6] - f[8]);
+            jxo[v] = j_pack<S, SH>(jx);
+            jyo[v] = j_pack<S, SH>(jy);
+            const float jxv = dev_load<float, S, SH>(jxo[v]), jyv = dev_load<float, S, SH>(jyo[v]);
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            outv[i][v] = SC == kShiftLocal ? fma(-wgt<float>(i), phid, f[i]) : f[i];
-        phi_o[v] = phi;
-        bad |= not_finite(phi);
+            for (int i = 0; i < 9; ++i)
+                outv[i][v] = i == 0 ? fma(-wgt<float>(i), phid, f[i])
+                                    : fma(-w3<float>(i), e_dot<float>(i, jxv, jyv), fma(-wgt<float>(i), phid, f[i]));
+            phi_o[v] = phi_sr(phi, phid, rs, sr_bits(sr_node_bits(p.sr_seed, node + v), 9));
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                outv[i][v] = SC == kShiftLocal ? fma(-wgt<float>(i), phid, f[i]) : f[i];
+            phi_o[v] = phi;
+        }
+        bad |= not_finite(phi_o[v]);
+    }
+    if constexpr (MOMENT) {
+        S *jout = static_cast<S *>(p.j_out);
+        *reinterpret_cast<W *>(jout + BTRT_IX(p.flags, node, 2 * p.plane)) = Vec4<S>::pack_raw(jxo);
+        *reinterpret_cast<W *>(jout + BTRT_IX(p.flags, p.plane + node, 2 * p.plane)) = Vec4<S>::pack_raw(jyo);
     }
     put(outv, phi_o);
     return bad;
@@ -225,7 +274,8 @@ __device__ __forceinline__ bool vec_group(const SweepParams<float> &p, int x0, i
 #pragma unroll
             for (int i = 0; i < 9; ++i)
                 *reinterpret_cast<W *>(fout + BTRT_IX(p.flags, i * p.plane + node, 9 * p.plane)) =
-                    V::put_sr(outv[i], sr_bits(h[0], i), sr_bits(h[1], i), sr_bits(h[2], i), sr_bits(h[3], i));
+                    V::template put_sr<PullShift<SH>::value == kShiftMomentSR>(
+                        outv[i], sr_bits(h[0], i), sr_bits(h[1], i), sr_bits(h[2], i), sr_bits(h[3], i));
         } else {
 #pragma unroll
             for (int i = 0; i < 9; ++i)
@@ -313,7 +363,9 @@ __device__ __forceinline__ bool vec_tile_edges(const SweepParams<float> &p, int 
 // x0 = 4 (32 bx + tx) .. x0 + 3 of row y = 8 by + ty.  Never the initialising
 // collision and never a residual step (the host runs those in the plain form).
 template <typename S, int SH, int MODE, int SRC>
-__global__ void __launch_bounds__(256, VecMinBlocks<S>::value) sweep_vec_kernel(const __grid_constant__ SweepParams<float> p) {
+// The first-moment form (more live values) is compiled for two blocks per SM.
+__global__ void __launch_bounds__(256, SH == kShiftMomentSR ? 2 : VecMinBlocks<S>::value)
+    sweep_vec_kernel(const __grid_constant__ SweepParams<float> p) {
     const int x0 = (blockIdx.x * blockDim.x + threadIdx.x) * kVec;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     bool bad = false;

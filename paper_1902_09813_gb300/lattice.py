@@ -106,7 +106,7 @@ class Lattice:
         "local_sr" (local, F16/BF16 storage rounded stochastically; plain and vector
         forms), "local_dw_sr" (both; plain form), "moment_sr" (F16/BF16: the writer's
         first-moment term subtracted as well, j kept in two more planes, stochastic
-        rounding; plain form) or "auto" (local for the 16-bit
+        rounding; plain and vector forms) or "auto" (local for the 16-bit
         formats, whose rounding it keeps well below the discretisation error; ref for
         FP32 storage)."""
         storage = storage or compute

@@ -20,7 +20,7 @@ FORMS_2D = [("f64", "f64", "ref", "plain"), ("df64", "df64", "ref", "plain"), ("
             ("f32", "f32", "local_dw", "plain"), ("f32", "f16", "local_dw", "plain"),
             ("f32", "f16", "local_sr", "plain"), ("f32", "bf16", "local_sr", "vec"),
             ("f32", "bf16", "local_dw_sr", "plain"), ("f32", "bf16", "moment_sr", "plain"),
-            ("f32", "f16", "moment_sr", "plain")]
+            ("f32", "f16", "moment_sr", "plain"), ("f32", "f16", "moment_sr", "vec")]
 GRIDS_3D = [(3, 3, 3, (0,) * 6), (4, 5, 6, (1,) * 6), (5, 3, 4, (1, 1, 0, 0, 1, 1))]
 FORMS_3D = [("f64", "f64", "ref"), ("f32", "f32", "ref"), ("f32", "f16", "local")]
 
