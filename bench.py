@@ -99,7 +99,7 @@ TB2_DRAM_BYTES_PER_UPDATE = {("f32", "ref"): 38.6, ("f16", "local"): 20.9}
 # DRAM bytes per node of one launch of the vector-access sweep measured by ncu,
 # keyed by (storage, shift), for the sources with digest VEC_DIGEST.
 VEC_SOURCES = ("btrt_sweep.cuh", "btrt_vec.cuh", "btrt_launch.cuh")
-VEC_DIGEST = "595aba24043b714f"
+VEC_DIGEST = "253f0579e2e2edee"
 VEC_DRAM_BYTES_PER_UPDATE = {("f16", "local"): 41.4, ("f16", "local_sr"): 41.2}
 
 
@@ -143,8 +143,6 @@ def kernel_form(args) -> str:
     if args.sweep != "auto":
         return args.sweep
     large = args.n * args.n >= 1 << 21
-    if args.shift == "moment_sr" and args.storage == "f16":
-        return "plain"
     if args.shift in ("local_sr", "moment_sr"):
         return "vec" if large else "plain"
     return "vec" if args.storage in ("f16", "bf16") and large else "tb2"

@@ -98,8 +98,7 @@ enum { BTRT_SIDE_XMIN = 0, BTRT_SIDE_XMAX = 1, BTRT_SIDE_YMIN = 2, BTRT_SIDE_YMA
  *                    rounded to its FP32 plane stochastically as well (its exact
  *                    value is phi + the TwoSum error of the collision's sum).
  *                    Plain and vector kernel forms (AUTO: the vector form from
- *                    2^21 nodes on for BF16, the plain form for FP16); not in
- *                    batches.
+ *                    2^21 nodes on); not in batches.
  * FP64 and double-word storage are never shifted. */
 enum { BTRT_SHIFT_REF = 0, BTRT_SHIFT_LOCAL = 1, BTRT_SHIFT_LOCAL_DW = 2, BTRT_SHIFT_LOCAL_SR = 3,
        BTRT_SHIFT_LOCAL_DW_SR = 4, BTRT_SHIFT_MOMENT_SR = 5 };

@@ -404,9 +404,6 @@ int btrt::effective_sweep_variant(btrt_lattice L) {
     if (L->sweep_variant != BTRT_SWEEP_AUTO) return L->sweep_variant;
     const bool s16 = L->g.storage == BTRT_F16 || L->g.storage == BTRT_BF16;
     const bool large = (long long)L->g.nx * L->g.ny >= kVecAutoNodes;
-    // the first-moment form with FP16 storage: the vector form measured no faster
-    // (68.5 / 57.9 against 68.9 / 67.3 GLUPS at 8192^2; BF16: 88.5 / 80.0 against 69.3 / 69.8)
-    if (has_j(L->g) && L->g.storage == BTRT_F16) return BTRT_SWEEP_PLAIN;
     if (stochastic_store(L->g)) return large ? BTRT_SWEEP_VEC : BTRT_SWEEP_PLAIN;
     return s16 && large ? BTRT_SWEEP_VEC : BTRT_SWEEP_TB2;
 }
