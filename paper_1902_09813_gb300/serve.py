@@ -93,7 +93,8 @@ class Server:
 
     def __init__(self, budget_bytes: float = 150e9, slice_steps: int = 100, max_steps: int = 20000,
                  tol: float = 1e-8, compute: str = "f32", storage: str = "f16",
-                 max_active: int = 4096, stream=None, tiles=None, shift: str = "auto", depth: int = 2):
+                 max_active: int = 4096, stream=None, tiles=None, shift: str = "auto", depth: int = 2,
+                 first_burst: int = 16):
         self.budget = float(budget_bytes)
         self.slice_steps = int(slice_steps)
         self.max_steps = int(max_steps)
@@ -101,6 +102,7 @@ class Server:
         self.compute, self.storage, self.shift = compute, storage, shift
         self.max_active = max_active
         self.depth_limit = max(1, int(depth))   # slices queued at once
+        self.first_burst = max(1, int(first_burst))   # admissions before the first slice of a busy period
         self.cuda = torch.cuda.is_available()
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         # admissions and retirement copies run here, beside the slices
@@ -139,7 +141,9 @@ class Server:
         st = self.stats
         while (self._pending or self._waiting or self._active or self._staged or inflight
                or self._draining or self._zombies):
-            self._admit()
+            # with nothing running, admit a first group only and start the device on it;
+            # the rest are admitted while its slices run
+            self._admit(None if inflight else self.first_burst)
             # keep depth_limit slices queued
             while len(inflight) < self.depth_limit:
                 if self._staged:
@@ -253,10 +257,10 @@ class Server:
                 self._active.remove(m)
                 self._retire(m, float(res[i]), status)
 
-    def _admit(self) -> bool:
-        """Moves arrived requests to the waiting queue and admits them while the
-        budget allows; their lattices are created and initialised on the side
-        stream.  Returns whether it admitted or rejected any."""
+    def _admit(self, limit: Optional[int] = None) -> bool:
+        """Moves arrived requests to the waiting queue and admits them (at most
+        `limit` of them) while the budget allows; their lattices are created and
+        initialised on the side stream.  Returns whether it admitted or rejected any."""
         now = self._now()
         while self._pending and self._pending[0][1] <= now:
             self._waiting.append(self._pending.popleft())
@@ -266,7 +270,8 @@ class Server:
         ta = time.perf_counter()
         resident = [m.p for m in self._active] + [m.p for m in self._staged]
         acted = False
-        while self._waiting and len(resident) < self.max_active:
+        admitted = 0
+        while self._waiting and len(resident) < self.max_active and (limit is None or admitted < limit):
             rid, arr, p = self._waiting[0]
             need = _bytes_needed(p, self.compute, self.storage)
             if need + _batch_bytes([p], self.compute, self.storage) > self.budget:
@@ -281,6 +286,7 @@ class Server:
             self._waiting.popleft()
             self._staged.append(_Member(rid, arr, self._now(), self._create(p), need, p))
             self._used += need
+            admitted += 1
             resident.append(p)
             st["peak_bytes"] = max(st["peak_bytes"], self._used + tables)
             acted = True

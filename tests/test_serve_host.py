@@ -212,3 +212,20 @@ def test_queued_slices_give_the_same_results(fakes, depth):
     caps = sum(1 for r in res if r.status == "done" and r.steps == 120)
     assert caps == 3 and srv.stats["cap_hits"] == caps
     assert srv.stats["tol_hits"] == 2 and srv.stats["unstable"] == 1
+
+
+def test_first_burst_starts_the_device_early(fakes):
+    """With nothing running, only `first_burst` requests are admitted before the
+    first slice is queued; the others join later slices, and every request still
+    stops where it would alone."""
+    probs = _problems([0.5, 0.9, 0.7, 0.5, 0.95, 0.6])
+    srv = serve.Server(budget_bytes=1e12, slice_steps=10, max_steps=60, tol=1e-6, stream=object(), first_burst=2)
+    res = srv.run([(0.0, p) for p in probs])
+    assert srv.depth[0][1] == 2                       # the first slice ran two members
+    assert srv.stats["peak_active"] > 2               # the rest joined while it ran
+    for r, p in zip(res, probs):
+        s = 10
+        while p.meta["rate"] ** s >= 1e-6 and s < 60:
+            s += 10
+        assert r.steps == s and np.all(r.phi == r.steps)
+    assert _FakeLattice.closed == len(probs) and _FakeBatch.open_ == 0
